@@ -1,0 +1,218 @@
+"""GB300-native multi-spin Ising Metropolis (Hassani & Rafibakhsh,
+arXiv:1811.04384): a thin Python binding of the C ABI in include/ising.h.
+
+Every step of the simulation runs in the CUDA kernels of libising.so; this
+module only marshals arguments.  There is no CPU fallback: if the library has
+not been built (``paper_1811_04384_gb300.build.build()``) or cannot be loaded,
+``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from ._abi import declare, SYMBOLS  # noqa: F401
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libising.so")
+
+ISING_OK = 0
+ISING_EINVAL = -1
+ISING_ENOMEM = -2
+ISING_ECUDA = -3
+ISING_ETIMEOUT = -4
+ISING_EBUSY = -5
+ISING_ENOTFOUND = -6
+
+_lib = None
+
+
+class IsingError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        detail = ""
+        if _lib is not None and code == ISING_ECUDA:
+            detail = " (" + _lib.ising_last_cuda_error().decode() + ")"
+        msg = _lib.ising_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{where}: {msg}{detail}")
+
+
+def load() -> ctypes.CDLL:
+    """Load libising.so (built in-tree).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1811_04384_gb300.build.build() "
+                          "(the CUDA library is required; there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    declare(lib)
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str):
+    if rc != ISING_OK:
+        raise IsingError(rc, where)
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        return ctypes.c_void_p(None)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)   # torch.cuda.Stream
+
+
+def bytes_required(L: int) -> int:
+    return int(load().ising_bytes_required(L))
+
+
+class Lattice:
+    """One L x L lattice resident in device memory (see include/ising.h)."""
+
+    def __init__(self, L: int, seed: int, *, buffer=None, stream=None):
+        lib = load()
+        self.L = int(L)
+        self.seed = int(seed)
+        self._buffer = buffer      # keeps a caller-owned (torch) buffer alive
+        h = ctypes.c_void_p()
+        if buffer is None:
+            _check(lib.ising_create(self.L, self.seed, ctypes.byref(h)), "ising_create")
+            if stream is not None:
+                _check(lib.ising_set_stream(h, _stream_ptr(stream)), "ising_set_stream")
+        else:
+            ptr = buffer.data_ptr() if hasattr(buffer, "data_ptr") else int(buffer)
+            nbytes = buffer.numel() * buffer.element_size() if hasattr(buffer, "numel") else bytes_required(L)
+            _check(lib.ising_create_on(self.L, self.seed, ctypes.c_void_p(ptr), nbytes, _stream_ptr(stream),
+                                       ctypes.byref(h)), "ising_create_on")
+        self._h = h
+
+    # -- lifetime ---------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value is not None:
+            load().ising_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- state ------------------------------------------------------------------
+    def init_hot(self):
+        _check(load().ising_init_hot(self._h), "ising_init_hot")
+
+    def init_cold(self, spin: int = 1):
+        _check(load().ising_init_cold(self._h, int(spin)), "ising_init_cold")
+
+    def set_beta(self, beta: float):
+        _check(load().ising_set_beta(self._h, float(beta)), "ising_set_beta")
+
+    def thresholds(self) -> tuple[int, int]:
+        thr = (ctypes.c_uint64 * 2)()
+        _check(load().ising_get_thresholds(self._h, thr), "ising_get_thresholds")
+        return int(thr[0]), int(thr[1])
+
+    @property
+    def t(self) -> int:
+        v = ctypes.c_uint64()
+        _check(load().ising_get_sweep(self._h, ctypes.byref(v)), "ising_get_sweep")
+        return int(v.value)
+
+    @t.setter
+    def t(self, value: int):
+        _check(load().ising_set_sweep(self._h, int(value)), "ising_set_sweep")
+
+    def set_stream(self, stream):
+        _check(load().ising_set_stream(self._h, _stream_ptr(stream)), "ising_set_stream")
+
+    def set_tiling(self, rows: int = 4, block_words: int = 32, block_groups: int = 4):
+        _check(load().ising_set_tiling(self._h, rows, block_words, block_groups), "ising_set_tiling")
+
+    def layout(self) -> tuple[int, int, int]:
+        W, P, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().ising_layout(self._h, ctypes.byref(W), ctypes.byref(P), ctypes.byref(r)), "ising_layout")
+        return W.value, P.value, r.value
+
+    # -- dynamics ---------------------------------------------------------------
+    def sweep(self, n: int = 1):
+        _check(load().ising_sweep(self._h, int(n)), "ising_sweep")
+
+    def sweep_record(self, n: int, every: int = 1):
+        k = n // every
+        E = np.zeros(max(k, 1), dtype=np.int64)
+        M = np.zeros(max(k, 1), dtype=np.int64)
+        _check(load().ising_sweep_record(self._h, int(n), int(every), E.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                         M.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), "ising_sweep_record")
+        return E[:k], M[:k]
+
+    def energy(self) -> int:
+        v = ctypes.c_int64()
+        _check(load().ising_energy(self._h, ctypes.byref(v)), "ising_energy")
+        return int(v.value)
+
+    def magnetization(self) -> int:
+        v = ctypes.c_int64()
+        _check(load().ising_magnetization(self._h, ctypes.byref(v)), "ising_magnetization")
+        return int(v.value)
+
+    # -- spin I/O ---------------------------------------------------------------
+    def get_spins(self, out: np.ndarray | None = None) -> np.ndarray:
+        if out is None:
+            out = np.empty((self.L, self.L), dtype=np.int8)
+        assert out.dtype == np.int8 and out.size == self.L * self.L and out.flags["C_CONTIGUOUS"]
+        _check(load().ising_get_spins(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), out.size),
+               "ising_get_spins")
+        return out
+
+    def set_spins(self, s: np.ndarray):
+        s = np.ascontiguousarray(s, dtype=np.int8)
+        assert s.size == self.L * self.L
+        _check(load().ising_set_spins(self._h, s.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), s.size),
+               "ising_set_spins")
+
+    def get_words(self) -> np.ndarray:
+        _, P, _ = self.layout()
+        out = np.empty(2 * self.L * P, dtype=np.uint64)
+        _check(load().ising_get_words(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), out.size),
+               "ising_get_words")
+        return out.reshape(2, self.L, P)
+
+    def set_words(self, words: np.ndarray):
+        w = np.ascontiguousarray(words, dtype=np.uint64).reshape(-1)
+        _check(load().ising_set_words(self._h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), w.size),
+               "ising_set_words")
+
+    def device_words(self, c: int) -> int:
+        p = ctypes.c_void_p()
+        _check(load().ising_device_words(self._h, int(c), ctypes.byref(p)), "ising_device_words")
+        return int(p.value)
+
+
+def philox_blocks(seed: int, ctr: np.ndarray) -> np.ndarray:
+    """Philox4x32-10 blocks of the given counters (n x 4 uint32) on the device."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    out = np.empty_like(c)
+    _check(load().ising_philox_blocks(int(seed), c.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), c.shape[0]),
+           "ising_philox_blocks")
+    return out
+
+
+def means(E: np.ndarray, M: np.ndarray, L: int) -> tuple[float, float]:
+    """Eq. 2: <E>/N and <|M|>/N over the recorded sweeps, from exact integer sums
+    and one FP64 division each."""
+    n = len(E)
+    sE = int(np.sum(np.asarray(E, dtype=np.int64).astype(object)))
+    sM = int(np.sum(np.abs(np.asarray(M, dtype=np.int64)).astype(object)))
+    return sE / (n * L * L), sM / (n * L * L)

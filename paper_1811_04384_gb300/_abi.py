@@ -1,0 +1,56 @@
+"""ctypes signatures of every function in include/ising.h."""
+from __future__ import annotations
+
+import ctypes
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_u64 = ctypes.c_uint64
+_sz = ctypes.c_size_t
+_int = ctypes.c_int
+_dbl = ctypes.c_double
+_cstr = ctypes.c_char_p
+_pi64 = ctypes.POINTER(ctypes.c_int64)
+_pu64 = ctypes.POINTER(ctypes.c_uint64)
+_pi32 = ctypes.POINTER(ctypes.c_int32)
+_pu32 = ctypes.POINTER(ctypes.c_uint32)
+_pi8 = ctypes.POINTER(ctypes.c_int8)
+_pu8 = ctypes.POINTER(ctypes.c_uint8)
+_pd = ctypes.POINTER(ctypes.c_double)
+_pvp = ctypes.POINTER(ctypes.c_void_p)
+
+SYMBOLS = {
+    "ising_strerror": (_cstr, [_int]),
+    "ising_last_cuda_error": (_cstr, []),
+    "ising_bytes_required": (_sz, [_i32]),
+    "ising_create": (_int, [_i32, _u64, _pvp]),
+    "ising_create_on": (_int, [_i32, _u64, _vp, _sz, _vp, _pvp]),
+    "ising_destroy": (_int, [_vp]),
+    "ising_init_hot": (_int, [_vp]),
+    "ising_init_cold": (_int, [_vp, ctypes.c_int8]),
+    "ising_set_beta": (_int, [_vp, _dbl]),
+    "ising_get_thresholds": (_int, [_vp, _pu64]),
+    "ising_sweep": (_int, [_vp, _i64]),
+    "ising_sweep_record": (_int, [_vp, _i64, _i64, _pi64, _pi64]),
+    "ising_energy": (_int, [_vp, _pi64]),
+    "ising_magnetization": (_int, [_vp, _pi64]),
+    "ising_get_spins": (_int, [_vp, _pi8, _sz]),
+    "ising_set_spins": (_int, [_vp, _pi8, _sz]),
+    "ising_get_words": (_int, [_vp, _pu64, _sz]),
+    "ising_set_words": (_int, [_vp, _pu64, _sz]),
+    "ising_layout": (_int, [_vp, _pi32, _pi32, _pi32]),
+    "ising_get_sweep": (_int, [_vp, _pu64]),
+    "ising_set_sweep": (_int, [_vp, _u64]),
+    "ising_set_stream": (_int, [_vp, _vp]),
+    "ising_set_tiling": (_int, [_vp, _i32, _i32, _i32]),
+    "ising_device_words": (_int, [_vp, _i32, _pvp]),
+    "ising_philox_blocks": (_int, [_u64, _pu32, _pu32, _i64]),
+}
+
+
+def declare(lib: ctypes.CDLL) -> None:
+    for name, (res, args) in SYMBOLS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args

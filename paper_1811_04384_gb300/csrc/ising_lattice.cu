@@ -1,0 +1,528 @@
+// C ABI of the single-lattice path: handle management, initialisation,
+// sweeps with the fused energy/magnetisation reduction, spin I/O.
+// Declarations and the contract of every function: include/ising.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ising.h"
+#include "ising_device.cuh"
+#include "ising_internal.h"
+
+using namespace ising;
+
+namespace {
+
+constexpr int kMaxL = 32768;
+constexpr int kRecordsPerChunk = 1024;           // count slots resident on the device
+constexpr size_t kCountBytes = (size_t)kRecordsPerChunk * kCountSlots * 2 * sizeof(unsigned long long);
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+Geom make_geom(int L)
+{
+    Geom g;
+    g.L = L;
+    const int half = L / 2;
+    g.W = (half + kFields - 1) / kFields;
+    g.P = (g.W + 1) & ~1;
+    g.rlast = half - kFields * (g.W - 1);
+    return g;
+}
+
+bool valid_L(int32_t L) { return L >= 4 && L <= kMaxL && (L % 2) == 0; }
+
+size_t words_bytes(const Geom& g) { return (size_t)g.L * (size_t)g.P * sizeof(uint64_t); }
+
+}  // namespace
+
+struct ising_lattice {
+    Geom g;
+    uint64_t seed = 0;
+    uint64_t t = 0;              // host copy of the sweep counter
+    double beta = 0.0;
+    uint64_t thr[2] = {0, 0};
+    cudaStream_t stream = nullptr;
+    bool owns_mem = false;
+    char* base = nullptr;        // device block: words0 | words1 | counts | t_base
+    uint64_t* words[2] = {nullptr, nullptr};
+    unsigned long long* counts = nullptr;
+    uint64_t* t_dev = nullptr;
+    int8_t* staging = nullptr;   // lazily allocated int8 L*L (get/set spins)
+    unsigned long long* host_counts = nullptr;   // pinned, kCountBytes
+    int rows = 4, bw = 32, bg = 4;               // half-sweep launch shape
+};
+
+extern "C" const char* ising_strerror(int code)
+{
+    switch (code) {
+    case ISING_OK: return "ok";
+    case ISING_EINVAL: return "invalid argument";
+    case ISING_ENOMEM: return "out of memory";
+    case ISING_ECUDA: return "CUDA error";
+    case ISING_ETIMEOUT: return "bounded device wait timed out";
+    case ISING_EBUSY: return "busy: no free slot or memory budget";
+    case ISING_ENOTFOUND: return "unknown request id";
+    default: return "unknown error code";
+    }
+}
+
+namespace ising {
+
+thread_local char g_last_cuda_error[256] = "";
+
+int cuda_fail(cudaError_t e, const char* where)
+{
+    snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "%s: %s", where, cudaGetErrorString(e));
+    return ISING_ECUDA;
+}
+
+// Integer thresholds of Sec. 2 step 3 with dE = 8 - 4a (Table 1).
+void thresholds_for_beta(double beta, uint64_t thr[2])
+{
+    const double two32 = 4294967296.0;
+    for (int a = 0; a < 2; ++a) {
+        const double dE = 8.0 - 4.0 * a;
+        double x = std::floor(std::exp(-dE * beta) * two32);
+        if (x > two32) x = two32;
+        if (!(x >= 0.0)) x = 0.0;
+        thr[a] = (uint64_t)x;
+    }
+}
+
+void fill_threshold_args(const uint64_t thr[2], SweepArgs& a)
+{
+    const uint64_t two32 = 1ull << 32;
+    a.thr0 = thr[0] >= two32 ? 0xFFFFFFFFu : (uint32_t)thr[0];
+    a.thr1 = thr[1] >= two32 ? 0xFFFFFFFFu : (uint32_t)thr[1];
+    a.all0 = thr[0] >= two32 ? 0xFFFFFFFFu : 0u;
+    a.all1 = thr[1] >= two32 ? 0xFFFFFFFFu : 0u;
+}
+
+Geom lattice_geom(int L) { return make_geom(L); }
+
+// Launch one half-sweep (or the measurement pass) with the given shape.
+cudaError_t launch_half_sweep(int rows, int bw, int bgrp, int colour, bool update, bool record,
+                              uint64_t* own, const uint64_t* other, const Geom& g, const SweepArgs& a,
+                              cudaStream_t s)
+{
+    const int ngroups = (g.L + rows - 1) / rows;
+    dim3 block(bw, bgrp);
+    dim3 grid((g.W + bw - 1) / bw, (ngroups + bgrp - 1) / bgrp);
+#define ISING_LAUNCH(R, C, U, REC) half_sweep_kernel<R, C, U, REC><<<grid, block, 0, s>>>(own, other, g, a)
+#define ISING_BY_FLAGS(R, C)                                   \
+    do {                                                       \
+        if (update && record) ISING_LAUNCH(R, C, true, true);  \
+        else if (update) ISING_LAUNCH(R, C, true, false);      \
+        else ISING_LAUNCH(R, C, false, true);                  \
+    } while (0)
+    if (rows == 8) {
+        if (colour == 0) ISING_BY_FLAGS(8, 0); else ISING_BY_FLAGS(8, 1);
+    } else {
+        if (colour == 0) ISING_BY_FLAGS(4, 0); else ISING_BY_FLAGS(4, 1);
+    }
+#undef ISING_BY_FLAGS
+#undef ISING_LAUNCH
+    return cudaGetLastError();
+}
+
+}  // namespace ising
+
+extern "C" const char* ising_last_cuda_error(void) { return g_last_cuda_error; }
+
+extern "C" size_t ising_bytes_required(int32_t L)
+{
+    if (!valid_L(L)) return 0;
+    const Geom g = make_geom(L);
+    return 2 * align_up(words_bytes(g), kAlign) + align_up(kCountBytes, kAlign) + kAlign;
+}
+
+static int setup_handle(ising_lattice* h, int32_t L, uint64_t seed, char* base)
+{
+    h->g = make_geom(L);
+    h->seed = seed;
+    h->base = base;
+    const size_t wb = align_up(words_bytes(h->g), kAlign);
+    h->words[0] = reinterpret_cast<uint64_t*>(base);
+    h->words[1] = reinterpret_cast<uint64_t*>(base + wb);
+    h->counts = reinterpret_cast<unsigned long long*>(base + 2 * wb);
+    h->t_dev = reinterpret_cast<uint64_t*>(base + 2 * wb + align_up(kCountBytes, kAlign));
+    cudaError_t e = cudaMallocHost(&h->host_counts, kCountBytes);
+    if (e != cudaSuccess) { h->host_counts = nullptr; return ISING_ENOMEM; }
+    thresholds_for_beta(0.0, h->thr);
+    return ISING_OK;
+}
+
+static void free_handle(ising_lattice* h)
+{
+    if (!h) return;
+    if (h->staging) cudaFree(h->staging);
+    if (h->owns_mem && h->base) cudaFree(h->base);
+    if (h->host_counts) cudaFreeHost(h->host_counts);
+    delete h;
+}
+
+extern "C" int ising_init_cold(ising_lattice* h, int8_t spin);
+
+extern "C" int ising_create(int32_t L, uint64_t seed, ising_lattice** out)
+{
+    if (!out || !valid_L(L)) return ISING_EINVAL;
+    *out = nullptr;
+    ising_lattice* h = new (std::nothrow) ising_lattice();
+    if (!h) return ISING_ENOMEM;
+    char* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, ising_bytes_required(L));
+    if (e != cudaSuccess) { delete h; cuda_fail(e, "cudaMalloc"); return ISING_ENOMEM; }
+    h->owns_mem = true;
+    int rc = setup_handle(h, L, seed, base);
+    if (rc == ISING_OK) rc = ising_init_cold(h, 1);
+    if (rc != ISING_OK) { free_handle(h); return rc; }
+    *out = h;
+    return ISING_OK;
+}
+
+extern "C" int ising_create_on(int32_t L, uint64_t seed, void* dev_buf, size_t bytes, void* stream,
+                               ising_lattice** out)
+{
+    if (!out || !valid_L(L) || !dev_buf) return ISING_EINVAL;
+    if (bytes < ising_bytes_required(L) || ((uintptr_t)dev_buf % kAlign) != 0) return ISING_EINVAL;
+    *out = nullptr;
+    ising_lattice* h = new (std::nothrow) ising_lattice();
+    if (!h) return ISING_ENOMEM;
+    h->owns_mem = false;
+    h->stream = (cudaStream_t)stream;
+    int rc = setup_handle(h, L, seed, (char*)dev_buf);
+    if (rc == ISING_OK) rc = ising_init_cold(h, 1);
+    if (rc != ISING_OK) { free_handle(h); return rc; }
+    *out = h;
+    return ISING_OK;
+}
+
+extern "C" int ising_destroy(ising_lattice* h)
+{
+    if (!h) return ISING_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
+    free_handle(h);
+    return ISING_OK;
+}
+
+static int reset_t(ising_lattice* h, uint64_t t)
+{
+    set_sweep_kernel<<<1, 1, 0, h->stream>>>(h->t_dev, t);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "set_sweep_kernel");
+    h->t = t;
+    return ISING_OK;
+}
+
+extern "C" int ising_init_hot(ising_lattice* h)
+{
+    if (!h) return ISING_EINVAL;
+    const Geom& g = h->g;
+    // zero everything first so the pitch padding is defined
+    cudaError_t e = cudaMemsetAsync(h->words[0], 0, 2 * align_up(words_bytes(g), kAlign), h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    dim3 block(32, 4);
+    dim3 grid((g.W + 31) / 32, ((g.L + 3) / 4 + 3) / 4, 2);
+    init_hot_kernel<<<grid, block, 0, h->stream>>>(h->words[0], h->words[1], g, (uint32_t)h->seed,
+                                                   (uint32_t)(h->seed >> 32));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "init_hot_kernel");
+    return reset_t(h, 0);
+}
+
+extern "C" int ising_init_cold(ising_lattice* h, int8_t spin)
+{
+    if (!h || (spin != 1 && spin != -1)) return ISING_EINVAL;
+    const Geom& g = h->g;
+    dim3 block(32, 8);
+    dim3 grid((g.P + 31) / 32, (g.L + 7) / 8);
+    init_cold_kernel<<<grid, block, 0, h->stream>>>(h->words[0], h->words[1], g, spin > 0 ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "init_cold_kernel");
+    return reset_t(h, 0);
+}
+
+extern "C" int ising_set_beta(ising_lattice* h, double beta)
+{
+    if (!h || std::isnan(beta) || beta < 0.0) return ISING_EINVAL;
+    h->beta = beta;
+    thresholds_for_beta(beta, h->thr);
+    return ISING_OK;
+}
+
+extern "C" int ising_get_thresholds(ising_lattice* h, uint64_t host_thr[2])
+{
+    if (!h || !host_thr) return ISING_EINVAL;
+    host_thr[0] = h->thr[0];
+    host_thr[1] = h->thr[1];
+    return ISING_OK;
+}
+
+static SweepArgs base_args(const ising_lattice* h)
+{
+    SweepArgs a;
+    a.t_base = h->t_dev;
+    a.t_off = 0;
+    a.key0 = (uint32_t)h->seed;
+    a.key1 = (uint32_t)(h->seed >> 32);
+    fill_threshold_args(h->thr, a);
+    a.counts = nullptr;
+    return a;
+}
+
+// Run `n` sweeps relative to the device counter; sweep s (1-based) records into
+// count slot rec_of(s) when rec_of(s) >= 0.  Then advances the counter by n.
+template <typename RecOf>
+static int run_sweeps(ising_lattice* h, int64_t n, RecOf rec_of)
+{
+    SweepArgs a = base_args(h);
+    const Geom& g = h->g;
+    for (int64_t s = 1; s <= n; ++s) {
+        a.t_off = (uint32_t)s;
+        cudaError_t e = launch_half_sweep(h->rows, h->bw, h->bg, 0, true, false, h->words[0], h->words[1], g,
+                                          a, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "half_sweep colour 0");
+        const int rec = rec_of(s);
+        a.counts = rec >= 0 ? h->counts + (size_t)rec * kCountSlots * 2 : nullptr;
+        e = launch_half_sweep(h->rows, h->bw, h->bg, 1, true, rec >= 0, h->words[1], h->words[0], g, a,
+                              h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "half_sweep colour 1");
+    }
+    if (n > 0) {
+        advance_sweep_kernel<<<1, 1, 0, h->stream>>>(h->t_dev, (uint64_t)n);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "advance_sweep_kernel");
+        h->t += (uint64_t)n;
+    }
+    return ISING_OK;
+}
+
+extern "C" int ising_sweep(ising_lattice* h, int64_t n)
+{
+    if (!h || n < 0) return ISING_EINVAL;
+    // chunks keep t_off within 32 bits
+    while (n > 0) {
+        const int64_t c = n > (1 << 30) ? (1 << 30) : n;
+        int rc = run_sweeps(h, c, [](int64_t) { return -1; });
+        if (rc != ISING_OK) return rc;
+        n -= c;
+    }
+    return ISING_OK;
+}
+
+static void counts_to_EM(const ising_lattice* h, const unsigned long long* slots, int64_t* E, int64_t* M)
+{
+    unsigned long long anti = 0, up = 0;
+    for (int k = 0; k < kCountSlots; ++k) {
+        anti += slots[2 * k];
+        up += slots[2 * k + 1];
+    }
+    const int64_t N = (int64_t)h->g.L * h->g.L;
+    if (E) *E = 2 * (int64_t)anti - 2 * N;
+    if (M) *M = 2 * (int64_t)up - N;
+}
+
+extern "C" int ising_sweep_record(ising_lattice* h, int64_t n, int64_t every, int64_t* E, int64_t* M)
+{
+    if (!h || n < 0 || every < 1) return ISING_EINVAL;
+    const int64_t nrec = n / every;
+    int64_t done_rec = 0;
+    while (done_rec < nrec) {
+        const int64_t chunk = (nrec - done_rec) < kRecordsPerChunk ? (nrec - done_rec) : kRecordsPerChunk;
+        const size_t bytes = (size_t)chunk * kCountSlots * 2 * sizeof(unsigned long long);
+        cudaError_t e = cudaMemsetAsync(h->counts, 0, bytes, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync counts");
+        int rc = run_sweeps(h, chunk * every, [every](int64_t s) {
+            return (s % every == 0) ? (int)(s / every - 1) : -1;
+        });
+        if (rc != ISING_OK) return rc;
+        e = cudaMemcpyAsync(h->host_counts, h->counts, bytes, cudaMemcpyDeviceToHost, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync counts");
+        e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+        for (int64_t r = 0; r < chunk; ++r)
+            counts_to_EM(h, h->host_counts + (size_t)r * kCountSlots * 2, E ? E + done_rec + r : nullptr,
+                         M ? M + done_rec + r : nullptr);
+        done_rec += chunk;
+    }
+    const int64_t rest = n - nrec * every;
+    if (rest > 0) return ising_sweep(h, rest);
+    return ISING_OK;
+}
+
+static int measure(ising_lattice* h, int64_t* E, int64_t* M)
+{
+    const size_t bytes = (size_t)kCountSlots * 2 * sizeof(unsigned long long);
+    cudaError_t e = cudaMemsetAsync(h->counts, 0, bytes, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync counts");
+    SweepArgs a = base_args(h);
+    a.counts = h->counts;
+    e = launch_half_sweep(h->rows, h->bw, h->bg, 1, false, true, h->words[1], h->words[0], h->g, a, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "measure");
+    e = cudaMemcpyAsync(h->host_counts, h->counts, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync counts");
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    counts_to_EM(h, h->host_counts, E, M);
+    return ISING_OK;
+}
+
+extern "C" int ising_energy(ising_lattice* h, int64_t* E)
+{
+    if (!h || !E) return ISING_EINVAL;
+    return measure(h, E, nullptr);
+}
+
+extern "C" int ising_magnetization(ising_lattice* h, int64_t* M)
+{
+    if (!h || !M) return ISING_EINVAL;
+    return measure(h, nullptr, M);
+}
+
+static int ensure_staging(ising_lattice* h)
+{
+    if (h->staging) return ISING_OK;
+    cudaError_t e = cudaMalloc(&h->staging, (size_t)h->g.L * h->g.L);
+    if (e != cudaSuccess) { h->staging = nullptr; cuda_fail(e, "cudaMalloc staging"); return ISING_ENOMEM; }
+    return ISING_OK;
+}
+
+extern "C" int ising_get_spins(ising_lattice* h, int8_t* out, size_t n)
+{
+    if (!h || !out || n != (size_t)h->g.L * h->g.L) return ISING_EINVAL;
+    int rc = ensure_staging(h);
+    if (rc != ISING_OK) return rc;
+    const Geom& g = h->g;
+    dim3 block(32, 8);
+    dim3 grid((g.W + 31) / 32, (g.L + 7) / 8, 2);
+    unpack_kernel<<<grid, block, 0, h->stream>>>(h->words[0], h->words[1], g, h->staging);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "unpack_kernel");
+    e = cudaMemcpyAsync(out, h->staging, n, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync spins");
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return ISING_OK;
+}
+
+extern "C" int ising_set_spins(ising_lattice* h, const int8_t* in, size_t n)
+{
+    if (!h || !in || n != (size_t)h->g.L * h->g.L) return ISING_EINVAL;
+    int rc = ensure_staging(h);
+    if (rc != ISING_OK) return rc;
+    const Geom& g = h->g;
+    cudaError_t e = cudaMemcpyAsync(h->staging, in, n, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync spins");
+    dim3 block(32, 8);
+    dim3 grid((g.P + 31) / 32, (g.L + 7) / 8, 2);
+    pack_kernel<<<grid, block, 0, h->stream>>>(h->words[0], h->words[1], g, h->staging);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "pack_kernel");
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return ISING_OK;
+}
+
+extern "C" int ising_get_words(ising_lattice* h, uint64_t* out, size_t n64)
+{
+    if (!h || !out) return ISING_EINVAL;
+    const size_t per = (size_t)h->g.L * h->g.P;
+    if (n64 != 2 * per) return ISING_EINVAL;
+    for (int c = 0; c < 2; ++c) {
+        cudaError_t e = cudaMemcpyAsync(out + c * per, h->words[c], per * sizeof(uint64_t),
+                                        cudaMemcpyDeviceToHost, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync words");
+    }
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? ISING_OK : cuda_fail(e, "cudaStreamSynchronize");
+}
+
+extern "C" int ising_set_words(ising_lattice* h, const uint64_t* in, size_t n64)
+{
+    if (!h || !in) return ISING_EINVAL;
+    const size_t per = (size_t)h->g.L * h->g.P;
+    if (n64 != 2 * per) return ISING_EINVAL;
+    for (int c = 0; c < 2; ++c) {
+        cudaError_t e = cudaMemcpyAsync(h->words[c], in + c * per, per * sizeof(uint64_t),
+                                        cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync words");
+    }
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? ISING_OK : cuda_fail(e, "cudaStreamSynchronize");
+}
+
+extern "C" int ising_layout(ising_lattice* h, int32_t* W, int32_t* pitch, int32_t* last_fields)
+{
+    if (!h) return ISING_EINVAL;
+    if (W) *W = h->g.W;
+    if (pitch) *pitch = h->g.P;
+    if (last_fields) *last_fields = h->g.rlast;
+    return ISING_OK;
+}
+
+extern "C" int ising_get_sweep(ising_lattice* h, uint64_t* t)
+{
+    if (!h || !t) return ISING_EINVAL;
+    *t = h->t;
+    return ISING_OK;
+}
+
+extern "C" int ising_set_sweep(ising_lattice* h, uint64_t t)
+{
+    if (!h) return ISING_EINVAL;
+    return reset_t(h, t);
+}
+
+extern "C" int ising_set_stream(ising_lattice* h, void* stream)
+{
+    if (!h) return ISING_EINVAL;
+    h->stream = (cudaStream_t)stream;
+    return ISING_OK;
+}
+
+extern "C" int ising_set_tiling(ising_lattice* h, int32_t rows, int32_t bw, int32_t bgrp)
+{
+    if (!h) return ISING_EINVAL;
+    if (rows != 4 && rows != 8) return ISING_EINVAL;
+    if (bw != 16 && bw != 32 && bw != 64) return ISING_EINVAL;
+    if (bgrp != 1 && bgrp != 2 && bgrp != 4 && bgrp != 8 && bgrp != 16) return ISING_EINVAL;
+    if (bw * bgrp > 512) return ISING_EINVAL;
+    h->rows = rows;
+    h->bw = bw;
+    h->bg = bgrp;
+    return ISING_OK;
+}
+
+extern "C" int ising_device_words(ising_lattice* h, int32_t c, void** dev_ptr)
+{
+    if (!h || !dev_ptr || (c != 0 && c != 1)) return ISING_EINVAL;
+    *dev_ptr = h->words[c];
+    return ISING_OK;
+}
+
+extern "C" int ising_philox_blocks(uint64_t seed, const uint32_t* host_ctr, uint32_t* host_out, int64_t n)
+{
+    if (!host_ctr || !host_out || n < 0 || n > (1 << 24)) return ISING_EINVAL;
+    if (n == 0) return ISING_OK;
+    uint32_t* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, (size_t)n * 8 * sizeof(uint32_t));
+    if (e != cudaSuccess) { cuda_fail(e, "cudaMalloc"); return ISING_ENOMEM; }
+    int rc = ISING_OK;
+    e = cudaMemcpy(d, host_ctr, (size_t)n * 4 * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        philox_blocks_kernel<<<(unsigned)((n + 255) / 256), 256>>>(d, d + 4 * n, n, (uint32_t)seed,
+                                                                  (uint32_t)(seed >> 32));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(host_out, d + 4 * n, (size_t)n * 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) rc = cuda_fail(e, "philox_blocks");
+    cudaFree(d);
+    return rc;
+}

@@ -1,0 +1,295 @@
+"""GPU path vs oracle, element by element and bit-exact: spins (int8 per
+site), int64 energy and magnetisation series, thresholds and Philox blocks.
+Every case goes through the C ABI (libising.so) and the oracle (oracle.c)
+on the same seeded inputs.
+
+L classes covered (21 spins per word, L/2 sites per colour-row):
+  4, 6        one word, 2-3 live fields (both wraps in one word)
+  42          one full word
+  44, 46      a partial last word of 1-2 fields
+  10, 12, 34  rows not a multiple of 8, and L % 4 == 2 (a partial row group)
+  64 .. 260   several words per row, several blocks, ragged tails
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+BETA_TC = 1.0 / 2.269
+L_CLASSES = [4, 6, 8, 10, 12, 34, 42, 44, 46, 64, 84, 86, 126, 130, 258, 260]
+
+
+@pytest.fixture(scope="module")
+def ising():
+    import paper_1811_04384_gb300 as p
+    p.load()
+    return p
+
+
+def gpu_run(ising, L, seed, beta, n, every=1, hot=True, cold_spin=1, tiling=None):
+    with ising.Lattice(L, seed) as lat:
+        if tiling:
+            lat.set_tiling(*tiling)
+        if hot:
+            lat.init_hot()
+        else:
+            lat.init_cold(cold_spin)
+        lat.set_beta(beta)
+        E, M = lat.sweep_record(n, every)
+        return lat.get_spins(), E, M, lat.t
+
+
+def oracle_run(L, seed, beta, n, every=1, hot=True, cold_spin=1):
+    s = oracle.init_hot(L, seed) if hot else oracle.init_cold(L, cold_spin)
+    E, M = oracle.run(s, seed, beta, 0, n, every)
+    return s, E, M
+
+
+# ----------------------------------------------------------------------------- primitives
+
+def test_philox_blocks_match_oracle(ising):
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2**32, size=(4000, 4), dtype=np.uint64).astype(np.uint32)
+    for seed in (0, 1, 0xDEADBEEFCAFEF00D):
+        got = ising.philox_blocks(seed, ctr)
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        for k in range(0, len(ctr), 7):
+            np.testing.assert_array_equal(got[k], oracle.philox4x32_10(ctr[k], key))
+
+
+def test_thresholds_match_oracle(ising):
+    betas = [0.0, 1e-300, 1e-17, 1e-16, 0.1, 0.25, BETA_TC, 0.5, 1.0, 2.0,
+             32 * math.log(2) / 8 * (1 - 1e-12), 32 * math.log(2) / 8 * (1 + 1e-12),
+             32 * math.log(2) / 4, 10.0, math.inf]
+    betas += list(np.random.default_rng(2).uniform(0, 3, 200))
+    with ising.Lattice(8, 1) as lat:
+        for b in betas:
+            lat.set_beta(b)
+            assert lat.thresholds() == oracle.thresholds(b), b
+        for bad in (-1.0, -1e-300, math.nan):
+            with pytest.raises(ising.IsingError):
+                lat.set_beta(bad)
+
+
+@pytest.mark.parametrize("L", L_CLASSES + [1000, 1024, 1026])
+def test_hot_start_matches_oracle(ising, L):
+    with ising.Lattice(L, 1 + L) as lat:
+        lat.init_hot()
+        np.testing.assert_array_equal(lat.get_spins(), oracle.init_hot(L, 1 + L))
+        s = oracle.init_hot(L, 1 + L)
+        assert lat.energy() == oracle.energy(s)
+        assert lat.magnetization() == oracle.magnetization(s)
+
+
+@pytest.mark.parametrize("L", L_CLASSES)
+def test_set_get_spins_and_observables(ising, L):
+    rng = np.random.default_rng(L)
+    s = np.where(rng.random((L, L)) < 0.4, 1, -1).astype(np.int8)
+    with ising.Lattice(L, 3) as lat:
+        lat.set_spins(s)
+        np.testing.assert_array_equal(lat.get_spins(), s)
+        assert lat.energy() == oracle.energy(s)
+        assert lat.magnetization() == oracle.magnetization(s)
+        # packed words round-trip and keep the dead fields and bit 63 zero
+        w = lat.get_words()
+        W, P, r = lat.layout()
+        assert W == math.ceil(L / 2 / 21) and P == W + (W & 1) and r == L // 2 - 21 * (W - 1)
+        live_last = sum(1 << (3 * k) for k in range(r))
+        assert ((w[:, :, W - 1] & ~np.uint64(live_last)) == 0).all()
+        assert ((w[:, :, W:] == 0)).all()
+        assert ((w >> np.uint64(63)) == 0).all()
+        lat.init_cold(-1)
+        lat.set_words(w)
+        np.testing.assert_array_equal(lat.get_spins(), s)
+
+
+def test_cold_start(ising):
+    for L in (4, 46, 64):
+        with ising.Lattice(L, 0) as lat:
+            assert lat.energy() == -2 * L * L and lat.magnetization() == L * L   # created cold +1
+            lat.init_cold(-1)
+            assert (lat.get_spins() == -1).all()
+            assert lat.energy() == -2 * L * L and lat.magnetization() == -L * L
+
+
+# ----------------------------------------------------------------------------- sweeps
+
+@pytest.mark.parametrize("L", L_CLASSES)
+def test_sweeps_match_oracle_every_l_class(ising, L):
+    beta = [0.2, BETA_TC, 0.6, 1.0][L % 4]
+    n = 12
+    s_g, E_g, M_g, t = gpu_run(ising, L, 100 + L, beta, n)
+    s_o, E_o, M_o = oracle_run(L, 100 + L, beta, n)
+    np.testing.assert_array_equal(s_g, s_o)
+    np.testing.assert_array_equal(E_g, E_o)
+    np.testing.assert_array_equal(M_g, M_o)
+    assert t == n
+
+
+@pytest.mark.parametrize("beta", [0.0, 1e-18, 0.05, 0.3, BETA_TC, 0.7, 2.0, 3.0, 6.0, math.inf])
+def test_sweeps_match_oracle_across_temperatures(ising, beta):
+    L = 86
+    s_g, E_g, M_g, _ = gpu_run(ising, L, 9, beta, 10)
+    s_o, E_o, M_o = oracle_run(L, 9, beta, 10)
+    np.testing.assert_array_equal(s_g, s_o)
+    np.testing.assert_array_equal(E_g, E_o)
+    np.testing.assert_array_equal(M_g, M_o)
+
+
+def test_half_sweep_boundary_cases(ising):
+    """One half-sweep at a time (via sweeps of a single colour pair) from the
+    antiferromagnetic state: every colour-0 site has a = 4 and flips."""
+    for L in (4, 6, 44, 130):
+        ii, jj = np.indices((L, L))
+        afm = np.where((ii + jj) % 2 == 0, 1, -1).astype(np.int8)
+        with ising.Lattice(L, 5) as lat:
+            lat.set_spins(afm)
+            lat.set_beta(0.8)
+            E, M = lat.sweep_record(1, 1)
+            s = afm.copy()
+            Eo, Mo = oracle.run(s, 5, 0.8, 0, 1, 1)
+            np.testing.assert_array_equal(lat.get_spins(), s)
+            assert E[0] == Eo[0] and M[0] == Mo[0]
+
+
+@pytest.mark.parametrize("tiling", [(4, 16, 1), (4, 32, 4), (4, 64, 8), (8, 32, 2), (8, 16, 16), (8, 64, 1)])
+def test_tiling_does_not_change_results(ising, tiling):
+    L = 260
+    ref = gpu_run(ising, L, 77, BETA_TC, 6, tiling=(4, 32, 4))
+    got = gpu_run(ising, L, 77, BETA_TC, 6, tiling=tiling)
+    for a, b in zip(ref[:3], got[:3]):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_recording_interval_and_remainder(ising):
+    L = 64
+    s1, E1, M1, t1 = gpu_run(ising, L, 4, 0.4, 23, every=1)
+    s5, E5, M5, t5 = gpu_run(ising, L, 4, 0.4, 23, every=5)
+    np.testing.assert_array_equal(E5, E1[4::5][:4])
+    np.testing.assert_array_equal(M5, M1[4::5][:4])
+    np.testing.assert_array_equal(s1, s5)
+    assert t1 == t5 == 23
+
+
+def test_resume_equals_uninterrupted(ising):
+    L = 84
+    with ising.Lattice(L, 12) as a, ising.Lattice(L, 12) as b:
+        for lat in (a, b):
+            lat.init_hot()
+            lat.set_beta(0.41)
+        Ea, Ma = a.sweep_record(30, 1)
+        Eb1, Mb1 = b.sweep_record(10, 1)
+        saved = b.get_words()
+        t = b.t
+        b.init_cold(1)
+        b.set_words(saved)
+        b.t = t
+        Eb2, Mb2 = b.sweep_record(20, 1)
+        np.testing.assert_array_equal(Ea, np.concatenate([Eb1, Eb2]))
+        np.testing.assert_array_equal(Ma, np.concatenate([Mb1, Mb2]))
+        np.testing.assert_array_equal(a.get_spins(), b.get_spins())
+
+
+def test_high_word_of_sweep_counter(ising):
+    L = 46
+    t0 = (1 << 32) - 3
+    with ising.Lattice(L, 21) as lat:
+        lat.init_hot()
+        lat.set_beta(0.35)
+        lat.t = t0
+        E, M = lat.sweep_record(6, 1)
+        s = oracle.init_hot(L, 21)
+        Eo, Mo = oracle.run(s, 21, 0.35, t0, 6, 1)
+        np.testing.assert_array_equal(lat.get_spins(), s)
+        np.testing.assert_array_equal(E, Eo)
+        np.testing.assert_array_equal(M, Mo)
+
+
+def test_plain_sweep_without_record_then_energy(ising):
+    L = 130
+    with ising.Lattice(L, 8) as lat:
+        lat.init_hot()
+        lat.set_beta(0.5)
+        lat.sweep(7)
+        s = oracle.init_hot(L, 8)
+        oracle.run(s, 8, 0.5, 0, 7, 7)
+        np.testing.assert_array_equal(lat.get_spins(), s)
+        assert lat.energy() == oracle.energy(s)
+        assert lat.magnetization() == oracle.magnetization(s)
+
+
+def test_torch_owned_memory_and_stream(ising):
+    torch = pytest.importorskip("torch")
+    L = 64
+    nbytes = ising.bytes_required(L)
+    buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    with ising.Lattice(L, 31, buffer=buf, stream=stream) as lat:
+        lat.init_hot()
+        lat.set_beta(BETA_TC)
+        E, M = lat.sweep_record(8, 2)
+        s = oracle.init_hot(L, 31)
+        Eo, Mo = oracle.run(s, 31, BETA_TC, 0, 8, 2)
+        np.testing.assert_array_equal(E, Eo)
+        np.testing.assert_array_equal(M, Mo)
+        np.testing.assert_array_equal(lat.get_spins(), s)
+
+
+# ----------------------------------------------------------------------------- configs
+
+def test_config_plain_L64_1000_sweeps(ising):
+    """L=64, T=2.269, hot start seed 1, 1000 sweeps, E and M every sweep."""
+    s_g, E_g, M_g, _ = gpu_run(ising, 64, 1, BETA_TC, 1000)
+    s_o, E_o, M_o = oracle_run(64, 1, BETA_TC, 1000)
+    np.testing.assert_array_equal(E_g, E_o)
+    np.testing.assert_array_equal(M_g, M_o)
+    np.testing.assert_array_equal(s_g, s_o)
+    assert ising.means(E_g, M_g, 64) == oracle.means(E_o, M_o, 64)
+
+
+@pytest.mark.parametrize("T", [1.0, 2.3, 3.5])
+def test_config_scan_L1024_sampled(ising, T):
+    """L=1024 cold start seed 7: the first 20 sweeps at three of the scan's
+    temperatures, full lattice and every-sweep series."""
+    beta = 1.0 / T
+    s_g, E_g, M_g, _ = gpu_run(ising, 1024, 7, beta, 20, hot=False)
+    s_o, E_o, M_o = oracle_run(1024, 7, beta, 20, hot=False)
+    np.testing.assert_array_equal(E_g, E_o)
+    np.testing.assert_array_equal(M_g, M_o)
+    np.testing.assert_array_equal(s_g, s_o)
+
+
+def test_config_large_L16384_first_sweeps(ising):
+    """L=16384 (the roofline configuration), hot start seed 3: the full lattice
+    and E/M after the hot start and after each of two sweeps, at the bench's
+    launch shape."""
+    L = 16384
+    with ising.Lattice(L, 3) as lat:
+        lat.init_hot()
+        lat.set_beta(BETA_TC)
+        s = oracle.init_hot(L, 3)
+        np.testing.assert_array_equal(lat.get_spins(), s)
+        assert lat.energy() == oracle.energy(s)
+        E, M = lat.sweep_record(2, 1)
+        Eo, Mo = oracle.run(s, 3, BETA_TC, 0, 2, 1)
+        np.testing.assert_array_equal(E, Eo)
+        np.testing.assert_array_equal(M, Mo)
+        np.testing.assert_array_equal(lat.get_spins(), s)
+
+
+def test_max_size_lattice(ising):
+    """L = 32768 (the largest allowed): properties that hold at any size."""
+    L = 32768
+    with ising.Lattice(L, 2) as lat:
+        assert lat.energy() == -2 * L * L and lat.magnetization() == L * L
+        lat.set_beta(6.0)               # frozen: both thresholds are 0
+        E, M = lat.sweep_record(2, 1)
+        assert (E == -2 * L * L).all() and (M == L * L).all()
+        lat.set_beta(0.0)               # every spin flips every sweep
+        E, M = lat.sweep_record(3, 1)
+        assert (E == -2 * L * L).all()
+        assert list(M) == [-L * L, L * L, -L * L]
