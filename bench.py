@@ -51,12 +51,13 @@ MUL_RESULTS_PER_SITE = 10       # Philox4x32-10: 20 32x32->64 products per 4 sit
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tiling", default=None, help="rows,block_words,block_groups")
+    ap.add_argument("--L", type=int, default=L_LARGE, help="lattice side (profiling of a smaller case)")
     return ap.parse_args()
 
 
@@ -85,7 +86,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
         time.sleep(0.3)
@@ -182,7 +183,7 @@ def main():
     lib_build.build()
     import paper_1811_04384_gb300 as ising
 
-    L = L_LARGE
+    L = args.L
     seed = SEED_LARGE + 1000003 * rank        # replicas: independent seeds
     stream = torch.cuda.Stream()
     lat = ising.Lattice(L, seed, stream=stream)
@@ -277,8 +278,8 @@ def main():
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_s * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "large: L=16384 periodic Ising (J=1, h=0), T=2.269, hot start seed 3, "
-                                   "E/M every 10 sweeps; step = 10 sweeps + E/M record",
+            "config": {"workload": (f"large: L={L} periodic Ising (J=1, h=0), T=2.269, hot start seed 3, "
+                                    "E/M every 10 sweeps; step = 10 sweeps + E/M record"),
                        "L": L, "sweeps_per_step": SWEEPS_PER_STEP, "parallelism": f"replicas x{world}",
                        "l2": "flushed between steps (256 MB write; lattice 103 MB < L2)",
                        "tiling": args.tiling or "default 4,32,4"},
