@@ -192,101 +192,4 @@ half_sweep_kernel(uint64_t* __restrict__ own, const uint64_t* __restrict__ other
         block_add_counts(a.counts, anti, up);
 }
 
-// Hot start: s = +1 iff the site's Philox draw at t = 0 is below 2^31.
-// Thread = (4-row group, word, colour).
-__global__ void init_hot_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom g,
-                                uint32_t key0, uint32_t key1)
-{
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    const int grp = blockIdx.y * blockDim.y + threadIdx.y;
-    const int c = blockIdx.z;
-    if (w >= g.W || grp * 4 >= g.L) return;
-    const uint64_t live = live_mask(g, w);
-    uint64_t word[4] = {0, 0, 0, 0};
-    for (int k = 0; k < kFields; ++k) {
-        uint32_t x[4] = {(uint32_t)grp, (uint32_t)(w * kFields + k), 0u, (uint32_t)c};
-        philox10(x, key0, key1);
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-            word[e] |= (uint64_t)((x[e] >> 31) ^ 1u) << (3 * k);
-    }
-    uint64_t* arr = c ? w1 : w0;
-    for (int e = 0; e < 4; ++e) {
-        const int i = grp * 4 + e;
-        if (i < g.L) arr[(size_t)i * g.P + w] = word[e] & live;
-    }
-}
-
-// Cold start (all up or all down); also zeroes the pitch padding.
-__global__ void init_cold_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom g, int up)
-{
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y * blockDim.y + threadIdx.y;
-    if (w >= g.P || i >= g.L) return;
-    const uint64_t v = (w < g.W && up) ? live_mask(g, w) : 0ull;
-    w0[(size_t)i * g.P + w] = v;
-    w1[(size_t)i * g.P + w] = v;
-}
-
-// int8 spins (row-major L x L, > 0 is up) -> packed colour words.
-__global__ void pack_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom g,
-                            const int8_t* __restrict__ s)
-{
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y * blockDim.y + threadIdx.y;
-    const int c = blockIdx.z;
-    if (w >= g.P || i >= g.L) return;
-    uint64_t word = 0;
-    if (w < g.W) {
-        const int nf = (w == g.W - 1) ? g.rlast : kFields;
-        const int par = (i + c) & 1;
-        const int8_t* row = s + (size_t)i * g.L;
-        for (int k = 0; k < nf; ++k) {
-            const int j = 2 * (w * kFields + k) + par;
-            word |= (uint64_t)(row[j] > 0) << (3 * k);
-        }
-    }
-    (c ? w1 : w0)[(size_t)i * g.P + w] = word;
-}
-
-// Packed colour words -> int8 spins (+1 / -1).
-__global__ void unpack_kernel(const uint64_t* __restrict__ w0, const uint64_t* __restrict__ w1, Geom g,
-                              int8_t* __restrict__ s)
-{
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y * blockDim.y + threadIdx.y;
-    const int c = blockIdx.z;
-    if (w >= g.W || i >= g.L) return;
-    const uint64_t word = (c ? w1 : w0)[(size_t)i * g.P + w];
-    const int nf = (w == g.W - 1) ? g.rlast : kFields;
-    const int par = (i + c) & 1;
-    int8_t* row = s + (size_t)i * g.L;
-    for (int k = 0; k < nf; ++k) {
-        const int j = 2 * (w * kFields + k) + par;
-        row[j] = ((word >> (3 * k)) & 1ull) ? (int8_t)1 : (int8_t)-1;
-    }
-}
-
-// t_base += n (end of a chunk of sweeps).
-__global__ void advance_sweep_kernel(uint64_t* t_base, uint64_t n)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) *t_base += n;
-}
-
-__global__ void set_sweep_kernel(uint64_t* t_base, uint64_t t)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) *t_base = t;
-}
-
-// Test hook: Philox4x32-10 blocks of arbitrary counters.
-__global__ void philox_blocks_kernel(const uint32_t* __restrict__ ctr, uint32_t* __restrict__ out,
-                                     int64_t n, uint32_t key0, uint32_t key1)
-{
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n) return;
-    uint32_t x[4] = {ctr[4 * b], ctr[4 * b + 1], ctr[4 * b + 2], ctr[4 * b + 3]};
-    philox10(x, key0, key1);
-    for (int e = 0; e < 4; ++e) out[4 * b + e] = x[e];
-}
-
 }  // namespace ising
