@@ -163,6 +163,45 @@ int ising_device_words(ising_lattice *h, int32_t c, void **dev_ptr);
 int ising_philox_blocks(uint64_t seed, const uint32_t *host_ctr, uint32_t *host_out,
                         int64_t n);
 
+
+/* ---- Allocation-free record path ----------------------------------------
+ * The paper has no counterpart to this entry point.  It is for callers that
+ * cannot call cudaMalloc: for example a plug-in running inside a host program
+ * that owns all device memory through its own pool, or a latency-critical
+ * loop in which an allocation (which may synchronise the device) is not
+ * acceptable.  It runs the same sweeps and fused energy/magnetisation
+ * reduction as ising_sweep_record, but on a packed lattice the caller owns,
+ * and it allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *
+ * dev_words0 / dev_words1: caller-owned device arrays of colour 0 and 1 in
+ * the library's packed layout (L rows x pitch words each, as ising_layout()
+ * and ising_device_words() describe), updated in place.  Sweeps t0+1 ..
+ * t0+n run with key `seed` at inverse temperature `beta`; host_E and host_M
+ * (caller-owned host arrays, either may be NULL) receive the n / every
+ * records taken after sweeps t0+every, t0+2*every, ...  No handle and no
+ * sweep counter is involved: the caller tracks t.  Work is ordered on
+ * cudaStream_t `stream` (NULL = legacy default stream); the call
+ * synchronises it before returning.
+ *
+ * Scratch: the count slots, per-record results and sweep counter live in one
+ * fixed file-scope device array of about 528 KB, which every GPU that loads
+ * the library holds until the process exits.  It holds at most
+ * ISING_NOALLOC_MAX_RECORDS records per call; n / every above that returns
+ * ISING_EINVAL before any device work.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call
+ * shares the array, which keeps the previous call's contents (each call
+ * clears the slots it uses first): calls that overlap on the GPU, on any
+ * streams, race and give wrong results.
+ * Errors: EINVAL (NULL words, bad L, n < 0, every < 1, beta < 0 or NaN, too
+ * many records), ECUDA. */
+#define ISING_NOALLOC_MAX_RECORDS 1024
+int ising_sweep_record_noalloc(uint64_t *dev_words0, uint64_t *dev_words1, int32_t L,
+                               uint64_t seed, double beta, uint64_t t0, int64_t n,
+                               int64_t every, int64_t *host_E, int64_t *host_M,
+                               void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,6 +25,7 @@ ISING_ECUDA = -3
 ISING_ETIMEOUT = -4
 ISING_EBUSY = -5
 ISING_ENOTFOUND = -6
+ISING_NOALLOC_MAX_RECORDS = 1024   # records one ising_sweep_record_noalloc call can hold
 
 _lib = None
 

@@ -46,6 +46,7 @@ SYMBOLS = {
     "ising_set_tiling": (_int, [_vp, _i32, _i32, _i32]),
     "ising_device_words": (_int, [_vp, _i32, _pvp]),
     "ising_philox_blocks": (_int, [_u64, _pu32, _pu32, _i64]),
+    "ising_sweep_record_noalloc": (_int, [_vp, _vp, _i32, _u64, _dbl, _u64, _i64, _i64, _pi64, _pi64, _vp]),
 }
 
 
