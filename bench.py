@@ -44,8 +44,9 @@ SWEEPS_PER_STEP = 10
 METRIC = "spin-updates/ns"
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
-IMAD_PER_SM_CLK = 64            # 32-bit integer multiply results per SM per clock
-MUL_RESULTS_PER_SITE = 10       # Philox4x32-10: 20 32x32->64 products per 4 sites
+MULWIDE_PER_SM_CLK = 32         # 32x32->64 integer multiplies (IMAD.WIDE) per SM per clock
+MULWIDE_PER_SITE = 4            # Philox4x32-10 with the counter-independent rounds hoisted:
+                                # 16 multiplies per call, one call per 4 sites
 
 
 def parse():
@@ -58,6 +59,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tiling", default=None, help="rows,block_words,block_groups")
     ap.add_argument("--L", type=int, default=L_LARGE, help="lattice side (profiling of a smaller case)")
+    ap.add_argument("--workload", default="large", choices=["large", "plain", "scan", "batched", "serving"],
+                    help="large (default): L=16384 roofline config; plain: L=64 x 1000 sweeps; "
+                         "scan: L=1024 x 26 temperatures; batched: 512 uneven replicas vs per-instance launches")
+    ap.add_argument("--sweeps", type=int, default=None, help="override the workload's sweep count")
+    ap.add_argument("--instances", type=int, default=None,
+                    help="batched: compare with per-instance launches on the first N replicas only")
     return ap.parse_args()
 
 
@@ -165,11 +172,185 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def splitmix64(x: int) -> int:
+    """SplitMix64 output for state x (Steele, Lea, Flood 2014): per-replica seeds."""
+    z = (x + 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & 0xFFFFFFFFFFFFFFFF
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & 0xFFFFFFFFFFFFFFFF
+    return z ^ (z >> 31)
+
+
+def batched_replicas(n=512, seed=11):
+    """The batched configuration: L uniform on {32..2048} (powers of two), T
+    uniform on [1.5, 3.5] (numpy default_rng(seed)), hot starts with seed
+    SplitMix64(seed * 2^32 + r)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    Ls = rng.choice([32, 64, 128, 256, 512, 1024, 2048], size=n).astype(np.int32)
+    Ts = rng.uniform(1.5, 3.5, size=n)
+    seeds = np.array([splitmix64((seed << 32) + r) for r in range(n)], dtype=np.uint64)
+    return Ls, 1.0 / Ts, seeds
+
+
+def emit(line):
+    print(json.dumps(line), flush=True)
+
+
+def run_batched(args, ising, local):
+    import numpy as np
+    import torch
+    Ls, betas, seeds = batched_replicas()
+    n = len(Ls)
+    sweeps = args.sweeps or 5000
+    with ising.Batch([32], [0.4], [1], [1]) as warm:      # loads the kernels, captures a graph once
+        warm.sweep([10], every=1)
+    b = ising.Batch(Ls, betas, seeds, np.ones(n, dtype=np.uint8))
+    updates = float(np.sum(Ls.astype(np.float64) ** 2)) * sweeps
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        E, M = b.sweep(sweeps, every=1)
+        torch.cuda.synchronize()
+        dt_b = time.perf_counter() - t0
+    k = args.instances or n
+    t0 = time.perf_counter()
+    exact = True
+    upd_k = 0.0
+    for r in range(k):
+        with ising.Lattice(int(Ls[r]), int(seeds[r])) as lat:
+            lat.init_hot()
+            lat.set_beta(float(betas[r]))
+            Ep, Mp = lat.sweep_record(sweeps, 1)
+        exact &= bool(np.array_equal(Ep, E[r]) and np.array_equal(Mp, M[r]))
+        upd_k += float(Ls[r]) ** 2 * sweeps
+    dt_p = time.perf_counter() - t0
+    b.close()
+    emit({"metric": METRIC, "value": updates / (dt_b * 1e9), "unit": METRIC, "n_gpus": 1, "steps": 1,
+          "warmup": 1, "ms_per_step": dt_b * 1e3, "higher_is_better": True, "scaling": "weak",
+          "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+          "config": {"workload": f"batched: {n} replicas, L uniform on {{32..2048}}, T uniform [1.5,3.5] "
+                                 f"(seed 11), hot starts, {sweeps} sweeps, E/M every sweep",
+                     "replica_updates": updates},
+          "per_instance": {"value": upd_k / (dt_p * 1e9), "unit": METRIC, "replicas": k,
+                           "path": "one ising_lattice per replica, ising_sweep_record(sweeps, 1)",
+                           "bit_exact_vs_batched": exact},
+          "batched_over_per_instance": (updates / dt_b) / (upd_k / dt_p),
+          "clocks": clocks.summary(), "gpu_launches": 2 * sweeps + (sweeps + 49) // 50})
+
+
+def run_scan(args, ising, local):
+    import numpy as np
+    import torch
+    from math import pi  # noqa: F401
+    Ts = np.array([(10 + k) / 10.0 for k in range(26)])
+    L = 1024
+    n = len(Ts)
+    therm = 2000
+    meas = args.sweeps or 10000
+    b = ising.Batch([L] * n, 1.0 / Ts, [7] * n, np.zeros(n, dtype=np.uint8))
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.sweep(therm, every=therm)
+        E, M = b.sweep(meas, every=1)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    b.close()
+    per_T = []
+    for r in range(n):
+        e, m = ising.means(E[r], M[r], L)
+        per_T.append({"T": float(Ts[r]), "E_per_spin": e, "absM_per_spin": m})
+    emit({"metric": METRIC, "value": n * L * L * (therm + meas) / (dt * 1e9), "unit": METRIC, "n_gpus": 1,
+          "steps": 1, "warmup": 0, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+          "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+          "config": {"workload": f"scan: L={L}, T=1.0..3.5 step 0.1 ({n} replicas in one batch), cold start, "
+                                 f"seed 7, {therm}+{meas} sweeps, E/M every measured sweep"},
+          "per_T": per_T, "clocks": clocks.summary()})
+
+
+def run_serving(args, ising, local):
+    import numpy as np
+    from paper_1811_04384_gb300 import serving
+    n = args.instances or 400
+    stream = serving.poisson_stream(n, rate=200.0, seed=13)
+    budget = 4 << 30
+    with ClockSampler(local) as clocks:
+        reqs, stats = serving.serve_stream(stream, budget, max_jobs=256, epoch_sweeps=50, every=1)
+    lat = np.array([r.result.done_s - r.result.submit_s for r in reqs])
+    wait = np.array([r.result.start_s - r.result.submit_s for r in reqs])
+    ok = all(r.result.status == 0 for r in reqs)
+    updates = float(sum(r.L * r.L * r.sweeps for r in reqs))
+    # bit-exact: every 10th job again, alone, through the single-lattice path
+    exact = True
+    checked = 0
+    for r in reqs[::10]:
+        with ising.Lattice(r.L, r.seed) as lat1:
+            lat1.init_hot()
+            lat1.set_beta(r.beta)
+            E, M = lat1.sweep_record(r.sweeps, 1)
+        exact &= bool(np.array_equal(E, r.E) and np.array_equal(M, r.M))
+        checked += 1
+    span = max(r.result.done_s for r in reqs) - min(r.result.submit_s for r in reqs)
+    emit({"metric": METRIC, "value": updates / (span * 1e9), "unit": METRIC, "n_gpus": 1, "steps": 1,
+          "warmup": 0, "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak",
+          "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+          "config": {"workload": f"serving: {n} Poisson arrivals (200 req/s, seed 13), L in {{64..4096}}, "
+                                 "T in [1.5,3.5], sweeps log-uniform 100..10000, hot starts, E/M every sweep",
+                     "hbm_budget_bytes": budget, "max_jobs": 256, "epoch_sweeps": 50},
+          "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                        "mean": float(lat.mean()), "queue_wait_p50": float(np.percentile(wait, 50))},
+          "offered_updates_per_ns": updates / (stream[-1][0] * 1e9),
+          "device_busy_updates_per_ns": stats["spin_updates"] / (stats["busy_s"] * 1e9),
+          "epochs": stats["epochs"], "all_ok": ok,
+          "alone_vs_mix": {"jobs_checked": checked, "bit_exact": exact},
+          "clocks": clocks.summary()})
+
+
+def run_plain(args, ising, local):
+    import numpy as np
+    import torch
+    L, n = 64, args.sweeps or 1000
+    with ising.Lattice(L, 1) as lat:          # warm-up
+        lat.init_hot()
+        lat.set_beta(BETA)
+        lat.sweep_record(20, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with ising.Lattice(L, 1) as lat:
+        lat.init_hot()
+        lat.set_beta(BETA)
+        E, M = lat.sweep_record(n, 1)
+    dt_plain = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    with ising.Batch([L], [BETA], [1], [1]) as b:
+        Eb, Mb = b.sweep([n], every=1)
+    dt_graph = time.perf_counter() - t0
+    exact = bool(np.array_equal(E, Eb[0]) and np.array_equal(M, Mb[0]))
+    emit({"metric": METRIC, "value": L * L * n / (dt_plain * 1e9), "unit": METRIC, "n_gpus": 1, "steps": 1,
+          "warmup": 1, "ms_per_step": dt_plain * 1e3, "higher_is_better": True, "scaling": "weak",
+          "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+          "config": {"workload": f"plain: L={L}, T=2.269, hot start seed 1, {n} sweeps, E/M every sweep "
+                                 "(launch-bound; wall clock incl. create/init)"},
+          "graph_captured": {"value": L * L * n / (dt_graph * 1e9), "unit": METRIC,
+                             "path": "ising_batch with one replica (CUDA graph of 50 sweeps)",
+                             "bit_exact_vs_plain": exact}})
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload != "large":
+        import torch
+        torch.cuda.set_device(local)
+        from paper_1811_04384_gb300 import build as lib_build
+        lib_build.build()
+        import paper_1811_04384_gb300 as ising
+        if rank == 0:
+            {"batched": run_batched, "scan": run_scan, "plain": run_plain,
+             "serving": run_serving}[args.workload](args, ising, local)
         return
 
     import numpy as np
@@ -232,10 +413,10 @@ def main():
     launches_per_step = 2 * SWEEPS_PER_STEP + 1     # half-sweeps + counter advance
     half_sweep_s = dev_s / (args.steps * 2 * SWEEPS_PER_STEP)
 
-    # roofline of the half-sweep kernel: integer multiplies of Philox4x32-10
+    # roofline of the half-sweep kernel: the 32x32->64 multiplies of Philox4x32-10
     sites_per_launch = L * L // 2
-    achieved_imad = sites_per_launch * MUL_RESULTS_PER_SITE / half_sweep_s / 1e12
-    peak_imad = SM_COUNT * IMAD_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    achieved_mul = sites_per_launch * MULWIDE_PER_SITE / half_sweep_s / 1e12
+    peak_mul = SM_COUNT * MULWIDE_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
     W = (L // 2 + 20) // 21
     P = W + (W & 1)
     hbm_bytes_per_launch = 3 * L * P * 8          # read own + write own + read other colour
@@ -284,12 +465,13 @@ def main():
                        "l2": "flushed between steps (256 MB write; lattice 103 MB < L2)",
                        "tiling": args.tiling or "default 4,32,4"},
             "wall_s": wall,
-            "roofline": {"bound": "alu", "achieved": achieved_imad, "peak": peak_imad,
-                         "unit": "T int32-mul/s", "frac": achieved_imad / peak_imad, "traffic": None,
+            "roofline": {"bound": "alu", "achieved": achieved_mul, "peak": peak_mul,
+                         "unit": "T mul.wide.u32/s", "frac": achieved_mul / peak_mul, "traffic": None,
                          "kernel": "half_sweep_kernel",
                          "achieved_spin_updates_per_ns": sites_per_launch / half_sweep_s / 1e9,
-                         "peak_spin_updates_per_ns": peak_imad * 1e12 / MUL_RESULTS_PER_SITE / 1e9,
-                         "peak_basis": "152 SMs x 64 int32 multiply results/clk x 2070 MHz; 10 per site",
+                         "peak_spin_updates_per_ns": peak_mul * 1e12 / MULWIDE_PER_SITE / 1e9,
+                         "peak_basis": ("152 SMs x 32 IMAD.WIDE/clk/SM x 2070 MHz (of nominal clock); "
+                                        "4 per site (16 per Philox4x32-10 call, 4 sites per call)"),
                          "hbm_achieved_gbs": hbm_bytes_per_launch / half_sweep_s / 1e9,
                          "hbm_peak_gbs": hbm_peak,
                          "hbm_frac": hbm_bytes_per_launch / half_sweep_s / 1e9 / hbm_peak},

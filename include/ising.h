@@ -145,12 +145,26 @@ int ising_set_sweep(ising_lattice *h, uint64_t t);
 /* Use cudaStream_t `stream` (NULL = legacy default stream) from now on. */
 int ising_set_stream(ising_lattice *h, void *stream);
 
-/* Launch shape of the half-sweep kernels: rows_per_thread in {4, 8},
- * block_words (threads along a row) in {16, 32, 64}, block_groups (threads
- * along the columns) in {1, 2, 4, 8, 16}; block_words * block_groups <= 512.
- * Results do not depend on the shape (the draws are keyed by site). */
+/* Launch shape of the half-sweep kernels: rows_per_thread must be 4 (one
+ * Philox call serves four rows); block_words (threads along a row) in
+ * {16, 32, 64}; block_groups (threads down the columns) in {1, 2, 4, 8, 16};
+ * 32 <= block_words * block_groups <= 256.  Default 4, 32, 4.  Results do
+ * not depend on the shape (the draws are keyed by site). */
 int ising_set_tiling(ising_lattice *h, int32_t rows_per_thread,
                      int32_t block_words, int32_t block_groups);
+
+/* Execution path of ising_sweep / ising_sweep_record.  ISING_PATH_LAUNCHES:
+ * two kernel launches per sweep, all SMs.  ISING_PATH_RESIDENT: temporal
+ * blocking with the whole lattice on chip -- one block copies both colour
+ * arrays into shared memory and runs all requested sweeps there in one
+ * launch (lattices with 2 L pitch 8 bytes <= 220 KB, i.e. L up to about
+ * 740; larger -> EINVAL); it removes the per-sweep launch latency that
+ * bounds small lattices.  ISING_PATH_AUTO (default): resident for L <= 128.
+ * Results are identical on every path. */
+#define ISING_PATH_AUTO 0
+#define ISING_PATH_LAUNCHES 1
+#define ISING_PATH_RESIDENT 2
+int ising_set_path(ising_lattice *h, int32_t path);
 
 /* Device pointer to the colour-c array (c = 0 or 1), for zero-copy use by
  * other device code on the same stream.  Returned in *dev_ptr. */
@@ -163,6 +177,120 @@ int ising_device_words(ising_lattice *h, int32_t c, void **dev_ptr);
 int ising_philox_blocks(uint64_t seed, const uint32_t *host_ctr, uint32_t *host_out,
                         int64_t n);
 
+
+/* ---- Batches of independent replicas --------------------------------------
+ * Many lattices of uneven size, each at its own temperature and seed, swept
+ * together: every half-sweep of every replica runs in ONE kernel launch whose
+ * blocks are tiles of the replicas (a tile table built at creation), and a
+ * chunk of sweeps is captured once into a CUDA graph and replayed.  This
+ * covers the paper's energy-versus-temperature scan (Sec. 5, one replica per
+ * temperature).  Each replica's results are bit-identical to a single
+ * ising_lattice with the same L, seed, beta and start: the draws are keyed by
+ * (seed, sweep, colour, site) and do not depend on the tiling. */
+typedef struct ising_batch ising_batch;   /* opaque, library-owned */
+
+/* Create n >= 1 replicas.  Replica r: side L[r] (as ising_create), inverse
+ * temperature beta[r] (as ising_set_beta), seed seed[r], hot start if
+ * hot[r] != 0 (as ising_init_hot) else all +1, and t = 0.  All arrays are
+ * caller-owned host arrays of n entries; hot may be NULL (all cold).  One
+ * device allocation holds every replica.  The batch owns a non-blocking CUDA
+ * stream (graph capture needs one).  Errors: EINVAL, ENOMEM, ECUDA. */
+int ising_batch_create(int32_t n, const int32_t *L, const double *beta,
+                       const uint64_t *seed, const uint8_t *hot, ising_batch **out);
+
+int ising_batch_destroy(ising_batch *b);
+
+/* Replica r runs sweeps[r] >= 0 sweeps (t_r+1 .. t_r+sweeps[r]); all
+ * replicas advance in lockstep and a replica whose sweeps are done drops
+ * out.  E and M are recorded after every `every`-th sweep of each replica:
+ * host_E[r] / host_M[r] (caller-owned host arrays of sweeps[r] / every
+ * entries; any of them, or host_E / host_M themselves, may be NULL).
+ * Synchronises the batch's stream. */
+int ising_batch_sweep(ising_batch *b, const int64_t *sweeps, int64_t every,
+                      int64_t **host_E, int64_t **host_M);
+
+/* Spins of replica r (as ising_get_spins, n = L[r]^2).  Synchronises. */
+int ising_batch_get_spins(ising_batch *b, int32_t r, int8_t *host_out, size_t n);
+
+/* Sweep counter of replica r. */
+int ising_batch_get_sweep(ising_batch *b, int32_t r, uint64_t *t);
+
+/* Threads per tile (64, 128 or 256; default 128) and sweeps per captured
+ * graph (1 .. 1024; default 50).  Rebuilds the tile table.  Results do not
+ * depend on either. */
+int ising_batch_set_tiling(ising_batch *b, int32_t threads_per_tile, int32_t graph_chunk);
+
+/* One call (the batch entry of the C ABI): create, sweep, copy each
+ * replica's final spins to final_spins[r] (host arrays of L[r]^2 int8; the
+ * array or any entry may be NULL), destroy. */
+int ising_batch_run(int32_t n, const int32_t *L, const double *beta, const uint64_t *seed,
+                    const uint8_t *hot, const int64_t *sweeps, int64_t every,
+                    int64_t **host_E, int64_t **host_M, int8_t **final_spins);
+
+/* ---- Serving: continuous batching of simulation jobs -----------------------
+ * A server owns a fixed device arena (its HBM budget) and a worker thread.
+ * Jobs (L, beta, seed, start, sweeps) are admitted in arrival order while a
+ * slot and arena space are free; every admitted job advances in epochs of
+ * the batched half-sweep together with all other running jobs, so jobs that
+ * arrive while others run join at the next epoch boundary.  A job's results
+ * are bit-identical to running it alone (ising_lattice with the same
+ * arguments): its draws depend only on its own seed and sweep numbers. */
+typedef struct ising_server ising_server;   /* opaque, library-owned */
+
+typedef struct ising_job {
+    int32_t L;            /* lattice side, as ising_create */
+    double beta;          /* inverse temperature, >= 0 */
+    uint64_t seed;        /* Philox seed */
+    int32_t hot;          /* != 0: hot start, else all +1 */
+    int64_t sweeps;       /* >= 1 */
+    int64_t every;        /* record E/M after sweeps every, 2*every, ... (>= 1) */
+    int64_t *host_E;      /* caller-owned, sweeps / every entries, or NULL */
+    int64_t *host_M;      /* caller-owned, sweeps / every entries, or NULL */
+    int8_t *host_spins;   /* caller-owned, L*L final spins, or NULL */
+} ising_job;               /* the host arrays must stay valid until the job is done */
+
+typedef struct ising_result {
+    int32_t status;       /* ISING_OK done; ISING_EBUSY queued or running; < 0 failed */
+    int32_t state;        /* 0 queued, 1 running, 2 done, 3 failed, 4 cancelled */
+    double submit_s;      /* seconds since server creation (steady clock) */
+    double start_s;       /* admission time, or -1 */
+    double done_s;        /* completion time, or -1 */
+    int64_t sweeps_done;
+} ising_result;
+
+/* Create a server on the current device with an arena of hbm_budget_bytes
+ * (allocated once), at most max_jobs concurrently running jobs (1..4096) and
+ * epochs of epoch_sweeps sweeps (1..100000), max_jobs * epoch_sweeps <= 2^22.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int ising_server_create(size_t hbm_budget_bytes, int32_t max_jobs, int32_t epoch_sweeps,
+                        ising_server **out);
+
+/* Queue a job (copied); *id receives its id.  Thread-safe.  Errors: EINVAL
+ * (bad job), ENOMEM (the job alone exceeds the whole arena). */
+int ising_server_submit(ising_server *srv, const ising_job *job, uint64_t *id);
+
+/* Non-blocking status of job `id`.  Thread-safe.  ENOTFOUND for an unknown
+ * (or already released) id. */
+int ising_server_poll(ising_server *srv, uint64_t id, ising_result *out);
+
+/* Wait up to timeout_ms (< 0: forever) for job `id` to finish; *out as poll.
+ * Returns ISING_ETIMEOUT if it is still queued or running. */
+int ising_server_wait(ising_server *srv, uint64_t id, int64_t timeout_ms, ising_result *out);
+
+/* Cancel a job that is still queued (running jobs finish). */
+int ising_server_cancel(ising_server *srv, uint64_t id);
+
+/* Forget a finished job's record (its id becomes unknown). */
+int ising_server_release(ising_server *srv, uint64_t id);
+
+/* Totals since creation: jobs done, spin updates done, epochs run, seconds
+ * the worker spent with at least one job on the device; any may be NULL. */
+int ising_server_stats(ising_server *srv, int64_t *jobs_done, double *spin_updates, int64_t *epochs,
+                       double *busy_s);
+
+/* Stop the worker after the running jobs' current epoch, fail the queued
+ * ones (state cancelled), free the arena.  Jobs still running are failed. */
+int ising_server_destroy(ising_server *srv);
 
 /* ---- Allocation-free record path ----------------------------------------
  * The paper has no counterpart to this entry point.  It is for callers that

@@ -25,6 +25,9 @@ ISING_ECUDA = -3
 ISING_ETIMEOUT = -4
 ISING_EBUSY = -5
 ISING_ENOTFOUND = -6
+ISING_PATH_AUTO = 0
+ISING_PATH_LAUNCHES = 1
+ISING_PATH_RESIDENT = 2
 ISING_NOALLOC_MAX_RECORDS = 1024   # records one ising_sweep_record_noalloc call can hold
 
 _lib = None
@@ -140,6 +143,10 @@ class Lattice:
     def set_tiling(self, rows: int = 4, block_words: int = 32, block_groups: int = 4):
         _check(load().ising_set_tiling(self._h, rows, block_words, block_groups), "ising_set_tiling")
 
+    def set_path(self, path: int):
+        """ISING_PATH_AUTO, ISING_PATH_LAUNCHES or ISING_PATH_RESIDENT."""
+        _check(load().ising_set_path(self._h, int(path)), "ising_set_path")
+
     def layout(self) -> tuple[int, int, int]:
         W, P, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         _check(load().ising_layout(self._h, ctypes.byref(W), ctypes.byref(P), ctypes.byref(r)), "ising_layout")
@@ -198,6 +205,101 @@ class Lattice:
         p = ctypes.c_void_p()
         _check(load().ising_device_words(self._h, int(c), ctypes.byref(p)), "ising_device_words")
         return int(p.value)
+
+
+def _ptr_array(arrays, ctype):
+    """A C array of pointers to the given numpy arrays (None -> NULL)."""
+    arr = (ctypes.c_void_p * len(arrays))()
+    for k, a in enumerate(arrays):
+        arr[k] = None if a is None else a.ctypes.data_as(ctypes.c_void_p).value
+    return arr
+
+
+class Batch:
+    """Independent replicas of uneven L, each with its own beta, seed and
+    start, swept together (see ising_batch_* in include/ising.h)."""
+
+    def __init__(self, L, beta, seed, hot=None):
+        lib = load()
+        self.L = np.ascontiguousarray(L, dtype=np.int32)
+        self.n = len(self.L)
+        self.beta = np.ascontiguousarray(beta, dtype=np.float64)
+        self.seed = np.ascontiguousarray(seed, dtype=np.uint64)
+        hot_arr = None if hot is None else np.ascontiguousarray(hot, dtype=np.uint8)
+        assert len(self.beta) == self.n and len(self.seed) == self.n
+        h = ctypes.c_void_p()
+        _check(lib.ising_batch_create(self.n, self.L.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      self.beta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      self.seed.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                      None if hot_arr is None else hot_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                      ctypes.byref(h)), "ising_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value is not None:
+            load().ising_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_tiling(self, threads_per_tile: int = 128, graph_chunk: int = 50):
+        _check(load().ising_batch_set_tiling(self._h, threads_per_tile, graph_chunk), "ising_batch_set_tiling")
+
+    def sweep(self, sweeps, every: int = 1, record: bool = True):
+        """Replica r runs sweeps[r] sweeps; returns lists of int64 E and M arrays
+        (sweeps[r] // every entries each), or None if record is False."""
+        sw = np.ascontiguousarray(np.broadcast_to(np.asarray(sweeps, dtype=np.int64), (self.n,)))
+        E = [np.zeros(max(int(s), 0) // max(every, 1), dtype=np.int64) for s in sw] if record else None
+        M = [np.zeros(max(int(s), 0) // max(every, 1), dtype=np.int64) for s in sw] if record else None
+        pe = _ptr_array(E, ctypes.c_int64) if record else None
+        pm = _ptr_array(M, ctypes.c_int64) if record else None
+        _check(load().ising_batch_sweep(self._h, sw.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(every),
+                                        pe, pm), "ising_batch_sweep")
+        return (E, M) if record else None
+
+    def get_spins(self, r: int) -> np.ndarray:
+        L = int(self.L[r])
+        out = np.empty((L, L), dtype=np.int8)
+        _check(load().ising_batch_get_spins(self._h, int(r), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                                            out.size), "ising_batch_get_spins")
+        return out
+
+    def t(self, r: int) -> int:
+        v = ctypes.c_uint64()
+        _check(load().ising_batch_get_sweep(self._h, int(r), ctypes.byref(v)), "ising_batch_get_sweep")
+        return int(v.value)
+
+
+def batch_run(L, beta, seed, hot, sweeps, every: int = 1, final_spins: bool = False):
+    """The one-call batch entry (ising_batch_run): returns (E, M, spins)."""
+    lib = load()
+    L = np.ascontiguousarray(L, dtype=np.int32)
+    n = len(L)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    seed = np.ascontiguousarray(seed, dtype=np.uint64)
+    hot = np.ascontiguousarray(hot, dtype=np.uint8)
+    sw = np.ascontiguousarray(np.broadcast_to(np.asarray(sweeps, dtype=np.int64), (n,)))
+    E = [np.zeros(int(s) // every, dtype=np.int64) for s in sw]
+    M = [np.zeros(int(s) // every, dtype=np.int64) for s in sw]
+    S = [np.empty((int(l), int(l)), dtype=np.int8) for l in L] if final_spins else None
+    _check(lib.ising_batch_run(n, L.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                               beta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                               seed.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                               hot.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                               sw.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(every),
+                               _ptr_array(E, ctypes.c_int64), _ptr_array(M, ctypes.c_int64),
+                               _ptr_array(S, ctypes.c_int8) if S is not None else None), "ising_batch_run")
+    return E, M, S
 
 
 def philox_blocks(seed: int, ctr: np.ndarray) -> np.ndarray:

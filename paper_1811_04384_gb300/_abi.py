@@ -3,6 +3,20 @@ from __future__ import annotations
 
 import ctypes
 
+
+class IsingJob(ctypes.Structure):
+    """struct ising_job (include/ising.h)."""
+    _fields_ = [("L", ctypes.c_int32), ("beta", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("hot", ctypes.c_int32), ("sweeps", ctypes.c_int64), ("every", ctypes.c_int64),
+                ("host_E", ctypes.POINTER(ctypes.c_int64)), ("host_M", ctypes.POINTER(ctypes.c_int64)),
+                ("host_spins", ctypes.POINTER(ctypes.c_int8))]
+
+
+class IsingResult(ctypes.Structure):
+    """struct ising_result (include/ising.h)."""
+    _fields_ = [("status", ctypes.c_int32), ("state", ctypes.c_int32), ("submit_s", ctypes.c_double),
+                ("start_s", ctypes.c_double), ("done_s", ctypes.c_double), ("sweeps_done", ctypes.c_int64)]
+
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
 _i64 = ctypes.c_int64
@@ -45,7 +59,23 @@ SYMBOLS = {
     "ising_set_stream": (_int, [_vp, _vp]),
     "ising_set_tiling": (_int, [_vp, _i32, _i32, _i32]),
     "ising_device_words": (_int, [_vp, _i32, _pvp]),
+    "ising_set_path": (_int, [_vp, _i32]),
     "ising_philox_blocks": (_int, [_u64, _pu32, _pu32, _i64]),
+    "ising_batch_create": (_int, [_i32, _pi32, _pd, _pu64, _pu8, _pvp]),
+    "ising_batch_destroy": (_int, [_vp]),
+    "ising_batch_sweep": (_int, [_vp, _pi64, _i64, _vp, _vp]),
+    "ising_batch_get_spins": (_int, [_vp, _i32, _pi8, _sz]),
+    "ising_batch_get_sweep": (_int, [_vp, _i32, _pu64]),
+    "ising_batch_set_tiling": (_int, [_vp, _i32, _i32]),
+    "ising_batch_run": (_int, [_i32, _pi32, _pd, _pu64, _pu8, _pi64, _i64, _vp, _vp, _vp]),
+    "ising_server_create": (_int, [_sz, _i32, _i32, _pvp]),
+    "ising_server_submit": (_int, [_vp, ctypes.POINTER(IsingJob), _pu64]),
+    "ising_server_poll": (_int, [_vp, _u64, ctypes.POINTER(IsingResult)]),
+    "ising_server_wait": (_int, [_vp, _u64, _i64, ctypes.POINTER(IsingResult)]),
+    "ising_server_cancel": (_int, [_vp, _u64]),
+    "ising_server_release": (_int, [_vp, _u64]),
+    "ising_server_stats": (_int, [_vp, _pi64, _pd, _pi64, _pd]),
+    "ising_server_destroy": (_int, [_vp]),
     "ising_sweep_record_noalloc": (_int, [_vp, _vp, _i32, _u64, _dbl, _u64, _i64, _i64, _pi64, _pi64, _vp]),
 }
 

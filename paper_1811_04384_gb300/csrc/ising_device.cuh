@@ -33,9 +33,10 @@ struct Geom {
 struct SweepArgs {
     const uint64_t* t_base;    // device: sweep counter before this chunk
     uint32_t t_off;            // this half-sweep belongs to sweep *t_base + t_off
-    uint32_t key0, key1;       // Philox key = (lo32(seed), hi32(seed))
     uint32_t thr0, thr1;       // integer thresholds clamped to 2^32 - 1 ...
     uint32_t all0, all1;       // ... and ~0u where the threshold is 2^32
+    uint32_t one;              // the value 1, as a launch operand (see accept_insert)
+    PhiloxKeys rk;             // round keys of the key (lo32(seed), hi32(seed))
     unsigned long long* counts;  // E/M count slots of this record (RECORD only)
 };
 
@@ -50,24 +51,8 @@ __device__ __forceinline__ uint64_t live_mask(const Geom& g, int w)
                           : kSpinBits;
 }
 
-// Other-colour word aligned so that field k holds the horizontal neighbour
-// at m - 1 (dir = 0) or m + 1 (dir = 1) of field k of word w.
-__device__ __forceinline__ uint64_t side_word(const uint64_t* __restrict__ orow, const Geom& g,
-                                             int w, uint64_t center, int dir)
-{
-    if (dir == 0) {
-        const int wp = (w > 0) ? w - 1 : g.W - 1;
-        const int sh = (w > 0) ? 60 : 3 * (g.rlast - 1);
-        return (center << 3) | (__ldg(orow + wp) >> sh);
-    } else {
-        const int wn = (w < g.W - 1) ? w + 1 : 0;
-        const int sh = (w < g.W - 1) ? 60 : 3 * (g.rlast - 1);
-        return (center >> 3) | (__ldg(orow + wn) << sh);
-    }
-}
-
-// Block-wide sum of two counters into slot (blockIdx % kCountSlots) of `counts`.
-__device__ __forceinline__ void block_add_counts(unsigned long long* counts, uint32_t anti, uint32_t up)
+// Block-wide sum of two counters, added with one atomic each to target[0..1].
+__device__ __forceinline__ void block_add_counts(unsigned long long* target, uint32_t anti, uint32_t up)
 {
     __shared__ unsigned int s_anti[32], s_up[32];
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
@@ -84,17 +69,30 @@ __device__ __forceinline__ void block_add_counts(unsigned long long* counts, uin
         a = __reduce_add_sync(0xffffffffu, a);
         u = __reduce_add_sync(0xffffffffu, u);
         if (lane == 0) {
-            const int slot = (blockIdx.x + gridDim.x * blockIdx.y) % kCountSlots;
-            atomicAdd(counts + 2 * slot + 0, (unsigned long long)a);
-            atomicAdd(counts + 2 * slot + 1, (unsigned long long)u);
+            atomicAdd(target + 0, (unsigned long long)a);
+            atomicAdd(target + 1, (unsigned long long)u);
         }
     }
 }
 
-// One Metropolis half-sweep of colour C (Sec. 2 steps 1-3 for every site of
-// the colour at once; same-colour sites are never neighbours).  A thread owns
-// ROWS consecutive rows (a multiple of 4: one Philox call covers the four
-// rows 4g..4g+3 of one field) of one word column.
+// Set the bit of field k in the accept masks A0 (r < thr0) and A1 (r < thr1).
+// The two inserts are written as predicated PTX so that the compare result
+// never becomes a 0/1 value: the first is a multiply-add (K * one + A0, which
+// runs on the FMA pipe), the second an OR on the ALU, balancing the two pipes
+// against the Philox multiplies (FMA) and XORs (ALU).
+__device__ __forceinline__ void accept_insert(uint32_t& A0, uint32_t& A1, uint32_t r, uint32_t thr0,
+                                              uint32_t thr1, uint32_t K, uint32_t one)
+{
+    asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p mad.lo.u32 %0, %3, %4, %0;\n\t}"
+        : "+r"(A0) : "r"(r), "r"(thr0), "r"(K), "r"(one));
+    asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+        : "+r"(A1) : "r"(r), "r"(thr1), "r"(K));
+}
+
+// The work of one thread: rows row0 .. row0+3 (those below L) of word column
+// w of colour C, at sweep t (Sec. 2 steps 1-3 for every site of the colour at
+// once; same-colour sites are never neighbours).  One Philox call covers the
+// four rows of one field.
 //
 // Per row, with s the own word and u, d, h0, h1 the four aligned neighbour
 // words, x_n = s ^ n has the spin bit of field k set iff neighbour n is
@@ -102,94 +100,121 @@ __device__ __forceinline__ void block_add_counts(unsigned long long* counts, uin
 //   any = x1|x2|x3|x4                     (a >= 1)
 //   ge2 = x1&x2 | x3&x4 | (x1^x2)&(x3^x4) (a >= 2: dE <= 0, Table 1)
 //   accept = ge2 | any & (r < thr1) | ~any & (r < thr0)
+// GLOBAL selects read-only-cache loads (lattice in global memory) or plain
+// loads (lattice in shared memory).
 // UPDATE = false skips the flip (measurement only).  RECORD adds the
 // anti-aligned bond count of the (updated) colour-1 words and the up-spin
-// count of both colours to the count slots: E = 2 anti - 2 L^2, M = 2 up - L^2.
-template <int ROWS, int C, bool UPDATE, bool RECORD>
-__global__ void __launch_bounds__(512)
-half_sweep_kernel(uint64_t* __restrict__ own, const uint64_t* __restrict__ other, Geom g, SweepArgs a)
+// count of both colours to anti / up: E = 2 anti - 2 L^2, M = 2 up - L^2.
+template <int C, bool UPDATE, bool RECORD, bool GLOBAL = true>
+__device__ __forceinline__ void sweep_rows(uint64_t* __restrict__ own, const uint64_t* __restrict__ other,
+                                           const Geom& g, int row0, int w, uint64_t t, const PhiloxKeys& rk,
+                                           uint32_t thr0, uint32_t thr1, uint32_t all0w, uint32_t all1w,
+                                           uint32_t one, uint32_t& anti, uint32_t& up)
 {
-    static_assert(ROWS % 4 == 0, "ROWS must be a multiple of 4");
-    constexpr int NG = ROWS / 4;
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    const int row0 = (blockIdx.y * blockDim.y + threadIdx.y) * ROWS;
-    const bool active = (w < g.W) && (row0 < g.L);
-    uint32_t anti = 0, up = 0;
+    constexpr int ROWS = 4;
+    const int nrows = min(ROWS, g.L - row0);
+    const uint64_t live = live_mask(g, w);
 
-    if (active) {
-        const int nrows = min(ROWS, g.L - row0);
-        const uint64_t live = live_mask(g, w);
-
-        uint64_t acc0[ROWS], acc1[ROWS];
-        if (UPDATE) {
-            const uint64_t t = *a.t_base + a.t_off;
-            const uint32_t tl = (uint32_t)t;
-            const uint32_t th = ((uint32_t)(t >> 32) << 1) | (uint32_t)C;
-            PhiloxRowKey pk[NG];
+    // All loads first: their latency overlaps the Philox work below.
+    uint64_t oc[ROWS + 2], sw[ROWS], side[ROWS];
 #pragma unroll
-            for (int q = 0; q < NG; ++q)
-                pk[q] = philox_row_key((uint32_t)(row0 / 4 + q), tl, th, a.key0, a.key1);
-#pragma unroll
-            for (int r = 0; r < ROWS; ++r) { acc0[r] = 0; acc1[r] = 0; }
-            const uint32_t m0 = (uint32_t)w * kFields;
-#pragma unroll
-            for (int k = 0; k < kFields; ++k) {
-#pragma unroll
-                for (int q = 0; q < NG; ++q) {
-                    uint32_t rnd[4];
-                    philox_row(pk[q], m0 + (uint32_t)k, rnd);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        acc0[4 * q + e] |= (uint64_t)(rnd[e] < a.thr0) << (3 * k);
-                        acc1[4 * q + e] |= (uint64_t)(rnd[e] < a.thr1) << (3 * k);
-                    }
-                }
-            }
+    for (int r = 0; r < ROWS + 2; ++r) {
+        if (r <= nrows + 1) {
+            const int i = wrap_row(row0 - 1 + r, g.L);
+            oc[r] = GLOBAL ? __ldg(other + (size_t)i * g.P + w) : other[(size_t)i * g.P + w];
+        } else {
+            oc[r] = 0;
         }
-
-        // Other-colour rows row0-1 .. row0+nrows (center column w).
-        uint64_t oc[ROWS + 2];
+    }
 #pragma unroll
-        for (int r = 0; r < ROWS + 2; ++r) {
-            if (r <= nrows + 1) {
-                const int i = wrap_row(row0 - 1 + r, g.L);
-                oc[r] = __ldg(other + (size_t)i * g.P + w);
-            } else {
-                oc[r] = 0;
-            }
+    for (int r = 0; r < ROWS; ++r) {
+        if (r < nrows) {
+            const int i = row0 + r;
+            sw[r] = own[(size_t)i * g.P + w];
+            const int dir = (r + C) & 1;     // row0 is a multiple of 4
+            const int wn = dir == 0 ? ((w > 0) ? w - 1 : g.W - 1) : ((w < g.W - 1) ? w + 1 : 0);
+            side[r] = GLOBAL ? __ldg(other + (size_t)i * g.P + wn) : other[(size_t)i * g.P + wn];
+        } else {
+            sw[r] = 0;
+            side[r] = 0;
         }
-        const uint64_t all0 = ((uint64_t)a.all0 << 32 | a.all0) & live;
-        const uint64_t all1 = ((uint64_t)a.all1 << 32 | a.all1) & live;
+    }
+
+    uint32_t lo0[ROWS] = {0, 0, 0, 0}, hi0[ROWS] = {0, 0, 0, 0};
+    uint32_t lo1[ROWS] = {0, 0, 0, 0}, hi1[ROWS] = {0, 0, 0, 0};
+    if (UPDATE) {
+        const uint32_t tl = (uint32_t)t;
+        const uint32_t th = ((uint32_t)(t >> 32) << 1) | (uint32_t)C;
+        const PhiloxRowKey pk = philox_row_key((uint32_t)(row0 >> 2), tl, th, rk);
+        const uint32_t m0 = (uint32_t)w * kFields;
 #pragma unroll
-        for (int r = 0; r < ROWS; ++r) {
-            if (r < nrows) {
-                const int i = row0 + r;
-                uint64_t* srow = own + (size_t)i * g.P;
-                const uint64_t s = srow[w];
-                const uint64_t u = oc[r], d = oc[r + 2], h0 = oc[r + 1];
-                const int dir = (r + C) & 1;   // row0 is a multiple of 4
-                const uint64_t h1 = side_word(other + (size_t)i * g.P, g, w, h0, dir);
-                const uint64_t x1 = s ^ u, x2 = s ^ d, x3 = s ^ h0, x4 = s ^ h1;
-                uint64_t s_new = s;
-                if (UPDATE) {
-                    const uint64_t any = x1 | x2 | x3 | x4;
-                    const uint64_t ge2 = (x1 & x2) | (x3 & x4) | ((x1 ^ x2) & (x3 ^ x4));
-                    const uint64_t c0 = acc0[r] | all0;
-                    const uint64_t c1 = acc1[r] | all1;
-                    const uint64_t accept = ge2 | (any & c1) | (~any & c0);
-                    s_new = s ^ (accept & live);
-                    srow[w] = s_new;
-                }
-                if (RECORD) {
-                    anti += __popcll((s_new ^ u) & live) + __popcll((s_new ^ d) & live)
-                          + __popcll((s_new ^ h0) & live) + __popcll((s_new ^ h1) & live);
-                    up += __popcll(s_new & live) + __popcll(h0 & live);
-                }
+        for (int k = 0; k < kFields; ++k) {
+            uint32_t rnd[4];
+            philox_row(pk, rk, m0 + (uint32_t)k, rnd);
+            // field k: bit 3k of the word; fields 0..10 in the low half, 11..20 in the high half
+            const uint32_t K = (k <= 10) ? (1u << (3 * k)) : (1u << (3 * k - 32));
+#pragma unroll
+            for (int e = 0; e < ROWS; ++e) {
+                if (k <= 10) accept_insert(lo0[e], lo1[e], rnd[e], thr0, thr1, K, one);
+                else accept_insert(hi0[e], hi1[e], rnd[e], thr0, thr1, K, one);
             }
         }
     }
-    if (RECORD)
-        block_add_counts(a.counts, anti, up);
+    const uint64_t all0 = ((uint64_t)all0w << 32 | all0w) & live;
+    const uint64_t all1 = ((uint64_t)all1w << 32 | all1w) & live;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        if (r < nrows) {
+            const int i = row0 + r;
+            const uint64_t s = sw[r];
+            const uint64_t u = oc[r], d = oc[r + 2], h0 = oc[r + 1];
+            // the other-colour word shifted by one field (horizontal neighbour at m -/+ 1)
+            uint64_t h1;
+            if (((r + C) & 1) == 0) {
+                const int sh = (w > 0) ? 60 : 3 * (g.rlast - 1);
+                h1 = (h0 << 3) | (side[r] >> sh);
+            } else {
+                const int sh = (w < g.W - 1) ? 60 : 3 * (g.rlast - 1);
+                h1 = (h0 >> 3) | (side[r] << sh);
+            }
+            const uint64_t x1 = s ^ u, x2 = s ^ d, x3 = s ^ h0, x4 = s ^ h1;
+            uint64_t s_new = s;
+            if (UPDATE) {
+                const uint64_t any = x1 | x2 | x3 | x4;
+                const uint64_t ge2 = (x1 & x2) | (x3 & x4) | ((x1 ^ x2) & (x3 ^ x4));
+                const uint64_t c0 = ((uint64_t)hi0[r] << 32 | lo0[r]) | all0;
+                const uint64_t c1 = ((uint64_t)hi1[r] << 32 | lo1[r]) | all1;
+                const uint64_t accept = ge2 | (any & c1) | (~any & c0);
+                s_new = s ^ (accept & live);
+                own[(size_t)i * g.P + w] = s_new;
+            }
+            if (RECORD) {
+                anti += __popcll((s_new ^ u) & live) + __popcll((s_new ^ d) & live)
+                      + __popcll((s_new ^ h0) & live) + __popcll((s_new ^ h1) & live);
+                up += __popcll(s_new & live) + __popcll(h0 & live);
+            }
+        }
+    }
+}
+
+// One half-sweep of colour C over one lattice: thread (x, y) of the grid owns
+// word column x and rows 4y .. 4y+3.  At most 256 threads per block.
+template <int C, bool UPDATE, bool RECORD>
+__global__ void __launch_bounds__(256, 3)
+half_sweep_kernel(uint64_t* __restrict__ own, const uint64_t* __restrict__ other, Geom g, SweepArgs a)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    const int row0 = (blockIdx.y * blockDim.y + threadIdx.y) * 4;
+    uint32_t anti = 0, up = 0;
+    if (w < g.W && row0 < g.L) {
+        const uint64_t t = UPDATE ? *a.t_base + a.t_off : 0;
+        sweep_rows<C, UPDATE, RECORD>(own, other, g, row0, w, t, a.rk, a.thr0, a.thr1, a.all0, a.all1,
+                                      a.one, anti, up);
+    }
+    if (RECORD) {
+        const int slot = (blockIdx.x + gridDim.x * blockIdx.y) % kCountSlots;
+        block_add_counts(a.counts + 2 * slot, anti, up);
+    }
 }
 
 }  // namespace ising

@@ -19,9 +19,23 @@ void thresholds_for_beta(double beta, uint64_t thr[2]);
 // "always accept" masks for a threshold of 2^32.
 void fill_threshold_args(const uint64_t thr[2], SweepArgs& a);
 
+// Launch arguments for key `seed`, thresholds `thr`, device sweep counter
+// t_base (t_off and counts left 0).
+SweepArgs make_sweep_args(uint64_t seed, const uint64_t thr[2], const uint64_t* t_base);
+
 Geom lattice_geom(int L);
 
-cudaError_t launch_half_sweep(int rows, int bw, int bgrp, int colour, bool update, bool record,
+// Stand-alone kernels of ising_lattice.cu, for other translation units.
+cudaError_t launch_init_hot(uint64_t* w0, uint64_t* w1, const Geom& g, uint64_t seed, cudaStream_t s);
+cudaError_t launch_init_cold(uint64_t* w0, uint64_t* w1, const Geom& g, int up, cudaStream_t s);
+cudaError_t launch_unpack(const uint64_t* w0, const uint64_t* w1, const Geom& g, int8_t* out, cudaStream_t s);
+
+// Geometry checks shared by the entry points.
+bool valid_side(int32_t L);
+
+// One half-sweep of one lattice (update and/or record), or the measurement
+// pass (update = false, record = true, colour 1); block = bw x bgrp threads.
+cudaError_t launch_half_sweep(int bw, int bgrp, int colour, bool update, bool record,
                               uint64_t* own, const uint64_t* other, const Geom& g, const SweepArgs& a,
                               cudaStream_t s);
 

@@ -3,6 +3,7 @@
 // Declarations and the contract of every function: include/ising.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -104,6 +105,68 @@ __global__ void set_sweep_kernel(uint64_t* t_base, uint64_t t)
     if (threadIdx.x == 0 && blockIdx.x == 0) *t_base = t;
 }
 
+// Temporal blocking with the whole lattice on chip: one block copies both
+// colour arrays into shared memory, runs sweeps t0+1 .. t0+n there (a block
+// barrier between half-sweeps), records E and M after every `every`-th sweep
+// with an on-chip reduction (records[2k] = E, records[2k+1] = M), and copies
+// the lattice back.  For lattices whose 2 L P words fit in shared memory.
+__global__ void __launch_bounds__(256, 1)
+resident_sweeps_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom g, SweepArgs a, uint64_t t0,
+                       int n, int every, long long* __restrict__ records)
+{
+    extern __shared__ __align__(16) uint64_t lattice[];
+    __shared__ unsigned int red_anti[8], red_up[8];
+    const size_t words = (size_t)g.L * g.P;
+    uint64_t* s0 = lattice;
+    uint64_t* s1 = lattice + words;
+    for (size_t k = threadIdx.x; k < words; k += blockDim.x) {
+        s0[k] = w0[k];
+        s1[k] = w1[k];
+    }
+    __syncthreads();
+    const int items = ((g.L + 3) / 4) * g.W;
+    const long long N = (long long)g.L * g.L;
+    for (int s = 1; s <= n; ++s) {
+        const uint64_t t = t0 + (uint64_t)s;
+        uint32_t dummy0 = 0, dummy1 = 0;
+        for (int it = threadIdx.x; it < items; it += blockDim.x) {
+            const int grp = it / g.W, w = it - grp * g.W;
+            sweep_rows<0, true, false, false>(s0, s1, g, grp * 4, w, t, a.rk, a.thr0, a.thr1, a.all0, a.all1,
+                                              a.one, dummy0, dummy1);
+        }
+        __syncthreads();
+        const bool record = (s % every) == 0;
+        uint32_t anti = 0, up = 0;
+        for (int it = threadIdx.x; it < items; it += blockDim.x) {
+            const int grp = it / g.W, w = it - grp * g.W;
+            if (record)
+                sweep_rows<1, true, true, false>(s1, s0, g, grp * 4, w, t, a.rk, a.thr0, a.thr1, a.all0, a.all1,
+                                                 a.one, anti, up);
+            else
+                sweep_rows<1, true, false, false>(s1, s0, g, grp * 4, w, t, a.rk, a.thr0, a.thr1, a.all0, a.all1,
+                                                  a.one, anti, up);
+        }
+        if (record) {
+            anti = __reduce_add_sync(0xffffffffu, anti);
+            up = __reduce_add_sync(0xffffffffu, up);
+            if ((threadIdx.x & 31) == 0) { red_anti[threadIdx.x >> 5] = anti; red_up[threadIdx.x >> 5] = up; }
+        }
+        __syncthreads();
+        if (record && threadIdx.x == 0) {
+            unsigned long long sa = 0, su = 0;
+            for (int k = 0; k < (int)(blockDim.x + 31) / 32; ++k) { sa += red_anti[k]; su += red_up[k]; }
+            const int rec = s / every - 1;
+            records[2 * rec] = 2 * (long long)sa - 2 * N;
+            records[2 * rec + 1] = 2 * (long long)su - N;
+        }
+    }
+    __syncthreads();
+    for (size_t k = threadIdx.x; k < words; k += blockDim.x) {
+        w0[k] = s0[k];
+        w1[k] = s1[k];
+    }
+}
+
 // Test hook: Philox4x32-10 blocks of arbitrary counters.
 __global__ void philox_blocks_kernel(const uint32_t* __restrict__ ctr, uint32_t* __restrict__ out,
                                      int64_t n, uint32_t key0, uint32_t key1)
@@ -123,6 +186,8 @@ constexpr int kMaxL = 32768;
 constexpr int kRecordsPerChunk = 1024;           // count slots resident on the device
 constexpr size_t kCountBytes = (size_t)kRecordsPerChunk * kCountSlots * 2 * sizeof(unsigned long long);
 constexpr size_t kAlign = 256;
+constexpr size_t kResidentMaxBytes = 220 * 1024;   // shared memory for the on-chip path
+constexpr int kResidentAutoMaxL = 0;                // auto: on-chip up to this side
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -157,7 +222,9 @@ struct ising_lattice {
     uint64_t* t_dev = nullptr;
     int8_t* staging = nullptr;   // lazily allocated int8 L*L (get/set spins)
     unsigned long long* host_counts = nullptr;   // pinned, kCountBytes
-    int rows = 4, bw = 32, bg = 4;               // half-sweep launch shape
+    int bw = 32, bg = 4;                         // half-sweep block shape
+    int path = ISING_PATH_AUTO;                  // multi-block launches or on-chip resident sweeps
+    bool resident_attr = false;                  // dynamic shared memory attribute set
 };
 
 extern "C" const char* ising_strerror(int code)
@@ -208,28 +275,60 @@ void fill_threshold_args(const uint64_t thr[2], SweepArgs& a)
 
 Geom lattice_geom(int L) { return make_geom(L); }
 
-// Launch one half-sweep (or the measurement pass) with the given shape.
-cudaError_t launch_half_sweep(int rows, int bw, int bgrp, int colour, bool update, bool record,
+bool valid_side(int32_t L) { return valid_L(L); }
+
+cudaError_t launch_init_hot(uint64_t* w0, uint64_t* w1, const Geom& g, uint64_t seed, cudaStream_t s)
+{
+    dim3 block(32, 4);
+    dim3 grid((g.W + 31) / 32, ((g.L + 3) / 4 + 3) / 4, 2);
+    init_hot_kernel<<<grid, block, 0, s>>>(w0, w1, g, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_cold(uint64_t* w0, uint64_t* w1, const Geom& g, int up, cudaStream_t s)
+{
+    dim3 block(32, 8);
+    dim3 grid((g.P + 31) / 32, (g.L + 7) / 8);
+    init_cold_kernel<<<grid, block, 0, s>>>(w0, w1, g, up);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const uint64_t* w0, const uint64_t* w1, const Geom& g, int8_t* out, cudaStream_t s)
+{
+    dim3 block(32, 8);
+    dim3 grid((g.W + 31) / 32, (g.L + 7) / 8, 2);
+    unpack_kernel<<<grid, block, 0, s>>>(w0, w1, g, out);
+    return cudaGetLastError();
+}
+
+SweepArgs make_sweep_args(uint64_t seed, const uint64_t thr[2], const uint64_t* t_base)
+{
+    SweepArgs a;
+    a.t_base = t_base;
+    a.t_off = 0;
+    fill_threshold_args(thr, a);
+    a.one = 1;
+    a.rk = philox_keys((uint32_t)seed, (uint32_t)(seed >> 32));
+    a.counts = nullptr;
+    return a;
+}
+
+cudaError_t launch_half_sweep(int bw, int bgrp, int colour, bool update, bool record,
                               uint64_t* own, const uint64_t* other, const Geom& g, const SweepArgs& a,
                               cudaStream_t s)
 {
-    const int ngroups = (g.L + rows - 1) / rows;
+    const int ngroups = (g.L + 3) / 4;
     dim3 block(bw, bgrp);
     dim3 grid((g.W + bw - 1) / bw, (ngroups + bgrp - 1) / bgrp);
-#define ISING_LAUNCH(R, C, U, REC) half_sweep_kernel<R, C, U, REC><<<grid, block, 0, s>>>(own, other, g, a)
-#define ISING_BY_FLAGS(R, C)                                   \
-    do {                                                       \
-        if (update && record) ISING_LAUNCH(R, C, true, true);  \
-        else if (update) ISING_LAUNCH(R, C, true, false);      \
-        else ISING_LAUNCH(R, C, false, true);                  \
-    } while (0)
-    if (rows == 8) {
-        if (colour == 0) ISING_BY_FLAGS(8, 0); else ISING_BY_FLAGS(8, 1);
+    if (colour == 0) {
+        if (record) half_sweep_kernel<0, true, true><<<grid, block, 0, s>>>(own, other, g, a);
+        else half_sweep_kernel<0, true, false><<<grid, block, 0, s>>>(own, other, g, a);
+    } else if (!update) {
+        half_sweep_kernel<1, false, true><<<grid, block, 0, s>>>(own, other, g, a);
     } else {
-        if (colour == 0) ISING_BY_FLAGS(4, 0); else ISING_BY_FLAGS(4, 1);
+        if (record) half_sweep_kernel<1, true, true><<<grid, block, 0, s>>>(own, other, g, a);
+        else half_sweep_kernel<1, true, false><<<grid, block, 0, s>>>(own, other, g, a);
     }
-#undef ISING_BY_FLAGS
-#undef ISING_LAUNCH
     return cudaGetLastError();
 }
 
@@ -368,14 +467,7 @@ extern "C" int ising_get_thresholds(ising_lattice* h, uint64_t host_thr[2])
 
 static SweepArgs base_args(const ising_lattice* h)
 {
-    SweepArgs a;
-    a.t_base = h->t_dev;
-    a.t_off = 0;
-    a.key0 = (uint32_t)h->seed;
-    a.key1 = (uint32_t)(h->seed >> 32);
-    fill_threshold_args(h->thr, a);
-    a.counts = nullptr;
-    return a;
+    return make_sweep_args(h->seed, h->thr, h->t_dev);
 }
 
 // Run `n` sweeps relative to the device counter; sweep s (1-based) records into
@@ -387,12 +479,12 @@ static int run_sweeps(ising_lattice* h, int64_t n, RecOf rec_of)
     const Geom& g = h->g;
     for (int64_t s = 1; s <= n; ++s) {
         a.t_off = (uint32_t)s;
-        cudaError_t e = launch_half_sweep(h->rows, h->bw, h->bg, 0, true, false, h->words[0], h->words[1], g,
+        cudaError_t e = launch_half_sweep(h->bw, h->bg, 0, true, false, h->words[0], h->words[1], g,
                                           a, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "half_sweep colour 0");
         const int rec = rec_of(s);
         a.counts = rec >= 0 ? h->counts + (size_t)rec * kCountSlots * 2 : nullptr;
-        e = launch_half_sweep(h->rows, h->bw, h->bg, 1, true, rec >= 0, h->words[1], h->words[0], g, a,
+        e = launch_half_sweep(h->bw, h->bg, 1, true, rec >= 0, h->words[1], h->words[0], g, a,
                               h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "half_sweep colour 1");
     }
@@ -405,9 +497,62 @@ static int run_sweeps(ising_lattice* h, int64_t n, RecOf rec_of)
     return ISING_OK;
 }
 
+static size_t resident_bytes(const Geom& g) { return 2 * (size_t)g.L * g.P * sizeof(uint64_t); }
+
+static bool use_resident(const ising_lattice* h)
+{
+    if (h->path == ISING_PATH_LAUNCHES) return false;
+    if (resident_bytes(h->g) > kResidentMaxBytes) return false;
+    return h->path == ISING_PATH_RESIDENT || h->g.L <= kResidentAutoMaxL;
+}
+
+// n sweeps with the lattice resident in shared memory, E/M records (if any)
+// written as (E, M) pairs into the count buffer.
+static int run_resident(ising_lattice* h, int n, int every)
+{
+    const Geom& g = h->g;
+    const size_t bytes = resident_bytes(g);
+    if (!h->resident_attr) {
+        cudaError_t e = cudaFuncSetAttribute(resident_sweeps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kResidentMaxBytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+        h->resident_attr = true;
+    }
+    const int items = ((g.L + 3) / 4) * g.W;
+    const int threads = std::min(256, std::max(32, (items + 31) / 32 * 32));
+    SweepArgs a = base_args(h);
+    resident_sweeps_kernel<<<1, threads, bytes, h->stream>>>(h->words[0], h->words[1], g, a, h->t, n, every,
+                                                             reinterpret_cast<long long*>(h->counts));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "resident_sweeps_kernel");
+    advance_sweep_kernel<<<1, 1, 0, h->stream>>>(h->t_dev, (uint64_t)n);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "advance_sweep_kernel");
+    h->t += (uint64_t)n;
+    return ISING_OK;
+}
+
+extern "C" int ising_set_path(ising_lattice* h, int32_t path)
+{
+    if (!h) return ISING_EINVAL;
+    if (path != ISING_PATH_AUTO && path != ISING_PATH_LAUNCHES && path != ISING_PATH_RESIDENT) return ISING_EINVAL;
+    if (path == ISING_PATH_RESIDENT && resident_bytes(h->g) > kResidentMaxBytes) return ISING_EINVAL;
+    h->path = path;
+    return ISING_OK;
+}
+
 extern "C" int ising_sweep(ising_lattice* h, int64_t n)
 {
     if (!h || n < 0) return ISING_EINVAL;
+    if (use_resident(h)) {
+        while (n > 0) {
+            const int c = (int)std::min<int64_t>(n, 1 << 30);
+            int rc = run_resident(h, c, 0x7fffffff);
+            if (rc != ISING_OK) return rc;
+            n -= c;
+        }
+        return ISING_OK;
+    }
     // chunks keep t_off within 32 bits
     while (n > 0) {
         const int64_t c = n > (1 << 30) ? (1 << 30) : n;
@@ -435,6 +580,26 @@ extern "C" int ising_sweep_record(ising_lattice* h, int64_t n, int64_t every, in
     if (!h || n < 0 || every < 1) return ISING_EINVAL;
     const int64_t nrec = n / every;
     int64_t done_rec = 0;
+    if (use_resident(h) && every <= (1 << 20)) {
+        while (done_rec < nrec) {
+            const int64_t chunk = std::min<int64_t>(nrec - done_rec, kRecordsPerChunk);
+            int rc = run_resident(h, (int)(chunk * every), (int)every);
+            if (rc != ISING_OK) return rc;
+            const size_t bytes = (size_t)chunk * 2 * sizeof(long long);
+            cudaError_t e = cudaMemcpyAsync(h->host_counts, h->counts, bytes, cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "resident records");
+            const long long* rec = reinterpret_cast<const long long*>(h->host_counts);
+            for (int64_t r = 0; r < chunk; ++r) {
+                if (E) E[done_rec + r] = rec[2 * r];
+                if (M) M[done_rec + r] = rec[2 * r + 1];
+            }
+            done_rec += chunk;
+        }
+        const int64_t rest = n - nrec * every;
+        if (rest > 0) return ising_sweep(h, rest);
+        return ISING_OK;
+    }
     while (done_rec < nrec) {
         const int64_t chunk = (nrec - done_rec) < kRecordsPerChunk ? (nrec - done_rec) : kRecordsPerChunk;
         const size_t bytes = (size_t)chunk * kCountSlots * 2 * sizeof(unsigned long long);
@@ -465,7 +630,7 @@ static int measure(ising_lattice* h, int64_t* E, int64_t* M)
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync counts");
     SweepArgs a = base_args(h);
     a.counts = h->counts;
-    e = launch_half_sweep(h->rows, h->bw, h->bg, 1, false, true, h->words[1], h->words[0], h->g, a, h->stream);
+    e = launch_half_sweep(h->bw, h->bg, 1, false, true, h->words[1], h->words[0], h->g, a, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "measure");
     e = cudaMemcpyAsync(h->host_counts, h->counts, bytes, cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync counts");
@@ -591,11 +756,10 @@ extern "C" int ising_set_stream(ising_lattice* h, void* stream)
 extern "C" int ising_set_tiling(ising_lattice* h, int32_t rows, int32_t bw, int32_t bgrp)
 {
     if (!h) return ISING_EINVAL;
-    if (rows != 4 && rows != 8) return ISING_EINVAL;
+    if (rows != 4) return ISING_EINVAL;
     if (bw != 16 && bw != 32 && bw != 64) return ISING_EINVAL;
     if (bgrp != 1 && bgrp != 2 && bgrp != 4 && bgrp != 8 && bgrp != 16) return ISING_EINVAL;
-    if (bw * bgrp > 512) return ISING_EINVAL;
-    h->rows = rows;
+    if (bw * bgrp > 256 || bw * bgrp < 32) return ISING_EINVAL;
     h->bw = bw;
     h->bg = bgrp;
     return ISING_OK;

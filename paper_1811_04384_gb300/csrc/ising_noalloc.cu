@@ -108,19 +108,15 @@ extern "C" int ising_sweep_record_noalloc(uint64_t* dev_words0, uint64_t* dev_wo
     const ising::Geom g = ising::lattice_geom(L);
     uint64_t thr[2];
     ising::thresholds_for_beta(beta, thr);
-    ising::SweepArgs a;
-    a.t_base = reinterpret_cast<const uint64_t*>(scratch + kTOffset);
-    a.key0 = (uint32_t)seed;
-    a.key1 = (uint32_t)(seed >> 32);
-    ising::fill_threshold_args(thr, a);
+    ising::SweepArgs a = ising::make_sweep_args(seed, thr, reinterpret_cast<const uint64_t*>(scratch + kTOffset));
     for (int64_t step = 1; step <= n; ++step) {
         a.t_off = (uint32_t)step;
         a.counts = nullptr;
-        e = ising::launch_half_sweep(4, 32, 4, 0, true, false, dev_words0, dev_words1, g, a, s);
+        e = ising::launch_half_sweep(32, 4, 0, true, false, dev_words0, dev_words1, g, a, s);
         if (e != cudaSuccess) return ising::cuda_fail(e, "half_sweep colour 0");
         const bool rec = (step % every) == 0;
         if (rec) a.counts = scratch + (size_t)(step / every - 1) * kSlots * 2;
-        e = ising::launch_half_sweep(4, 32, 4, 1, true, rec, dev_words1, dev_words0, g, a, s);
+        e = ising::launch_half_sweep(32, 4, 1, true, rec, dev_words1, dev_words0, g, a, s);
         if (e != cudaSuccess) return ising::cuda_fail(e, "half_sweep colour 1");
     }
     if (nrec > 0) {

@@ -51,50 +51,61 @@ ISING_HD void philox10(uint32_t x[4], uint32_t k0, uint32_t k1)
                      k1 + (uint32_t)r * kPhiloxW1);
 }
 
+// Round keys (k0 + r W0, k1 + r W1), r = 0..9, built once on the host so that
+// the rounds read them as launch constants.
+struct PhiloxKeys {
+    uint32_t k0[10];
+    uint32_t k1[10];
+};
+
+ISING_HD PhiloxKeys philox_keys(uint32_t k0, uint32_t k1)
+{
+    PhiloxKeys rk;
+    for (int r = 0; r < 10; ++r) {
+        rk.k0[r] = k0 + (uint32_t)r * kPhiloxW0;
+        rk.k1[r] = k1 + (uint32_t)r * kPhiloxW1;
+    }
+    return rk;
+}
+
 // Philox4x32-10 for counters (g, m, tl, th) where g, tl, th are fixed for the
 // thread and m varies.  Every product and XOR of the first three rounds that
-// does not depend on m is computed once here.
+// does not depend on m is computed once here, leaving 16 multiplies per call.
 struct PhiloxRowKey {
     uint32_t a;      // round 0: y0 = a ^ m
     uint32_t y3k;    // round 1: z2 = hi(M0 y0) ^ y3k
     uint32_t z1k;    // round 2: v0 = hi(M1 z2) ^ z1k
     uint32_t hiC;    // round 2: v2 = hiC ^ lo(M0 y0)
     uint32_t v3;     // round 2: v3 (independent of m)
-    uint32_t k0, k1; // key
 };
 
-ISING_HD PhiloxRowKey philox_row_key(uint32_t g, uint32_t tl, uint32_t th,
-                                                       uint32_t k0, uint32_t k1)
+ISING_HD PhiloxRowKey philox_row_key(uint32_t g, uint32_t tl, uint32_t th, const PhiloxKeys& rk)
 {
     PhiloxRowKey p;
     uint32_t h0, l0, h1, l1;
     // round 0 on (g, m, tl, th)
     mul_hilo(kPhiloxM0, g, h0, l0);
     mul_hilo(kPhiloxM1, tl, h1, l1);
-    p.a = h1 ^ k0;                          // y0 = h1 ^ m ^ k0
+    p.a = h1 ^ rk.k0[0];                    // y0 = h1 ^ m ^ k0
     const uint32_t y1 = l1;
-    const uint32_t y2 = h0 ^ th ^ k1;
+    const uint32_t y2 = h0 ^ th ^ rk.k1[0];
     const uint32_t y3 = l0;
     // round 1: the x2 product is fixed
-    const uint32_t r1k0 = k0 + kPhiloxW0, r1k1 = k1 + kPhiloxW1;
     uint32_t h1b, l1b;
     mul_hilo(kPhiloxM1, y2, h1b, l1b);
-    const uint32_t z0 = h1b ^ y1 ^ r1k0;
+    const uint32_t z0 = h1b ^ y1 ^ rk.k0[1];
     const uint32_t z1 = l1b;
-    p.y3k = y3 ^ r1k1;                      // z2 = hi(M0 y0) ^ y3 ^ r1k1
+    p.y3k = y3 ^ rk.k1[1];                  // z2 = hi(M0 y0) ^ y3 ^ k1
     // round 2: the x0 product is fixed
-    const uint32_t r2k0 = k0 + 2u * kPhiloxW0, r2k1 = k1 + 2u * kPhiloxW1;
     uint32_t h0c, l0c;
     mul_hilo(kPhiloxM0, z0, h0c, l0c);
-    p.z1k = z1 ^ r2k0;                      // v0 = hi(M1 z2) ^ z1 ^ r2k0
-    p.hiC = h0c ^ r2k1;                     // v2 = h0c ^ z3 ^ r2k1
+    p.z1k = z1 ^ rk.k0[2];                  // v0 = hi(M1 z2) ^ z1 ^ k0
+    p.hiC = h0c ^ rk.k1[2];                 // v2 = h0c ^ z3 ^ k1
     p.v3 = l0c;
-    p.k0 = k0;
-    p.k1 = k1;
     return p;
 }
 
-ISING_HD void philox_row(const PhiloxRowKey& p, uint32_t m, uint32_t out[4])
+ISING_HD void philox_row(const PhiloxRowKey& p, const PhiloxKeys& rk, uint32_t m, uint32_t out[4])
 {
     uint32_t h, l;
     const uint32_t y0 = p.a ^ m;
@@ -108,8 +119,7 @@ ISING_HD void philox_row(const PhiloxRowKey& p, uint32_t m, uint32_t out[4])
     uint32_t x3 = p.v3;
 #pragma unroll
     for (int r = 3; r < 10; ++r)
-        philox_round(x0, x1, x2, x3, p.k0 + (uint32_t)r * kPhiloxW0,
-                     p.k1 + (uint32_t)r * kPhiloxW1);
+        philox_round(x0, x1, x2, x3, rk.k0[r], rk.k1[r]);
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
