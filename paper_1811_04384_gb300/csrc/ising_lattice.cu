@@ -187,7 +187,7 @@ constexpr int kRecordsPerChunk = 1024;           // count slots resident on the 
 constexpr size_t kCountBytes = (size_t)kRecordsPerChunk * kCountSlots * 2 * sizeof(unsigned long long);
 constexpr size_t kAlign = 256;
 constexpr size_t kResidentMaxBytes = 220 * 1024;   // shared memory for the on-chip path
-constexpr int kResidentAutoMaxL = 0;                // auto: on-chip up to this side
+constexpr int kResidentAutoMaxL = 128;              // auto: on-chip up to this side
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

@@ -1,0 +1,66 @@
+"""The on-chip (temporal-blocked) path: the whole lattice in one block's
+shared memory for all requested sweeps.  Bit-exact with the launch path and
+the oracle; covers the L classes that fit (up to 2 L pitch 8 B <= 220 KB)."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ising():
+    import paper_1811_04384_gb300 as p
+    p.load()
+    return p
+
+
+def run(ising, L, seed, beta, n, every, path, hot=True):
+    with ising.Lattice(L, seed) as lat:
+        lat.set_path(path)
+        if hot:
+            lat.init_hot()
+        lat.set_beta(beta)
+        E, M = lat.sweep_record(n, every)
+        lat.sweep(3)
+        return E, M, lat.get_spins(), lat.t, lat.energy()
+
+
+@pytest.mark.parametrize("L", [4, 6, 10, 42, 44, 64, 86, 128, 130, 256, 512, 700])
+def test_resident_equals_launches(ising, L):
+    beta = 0.3 + (L % 7) * 0.05
+    a = run(ising, L, 40 + L, beta, 25, 3, ising.ISING_PATH_RESIDENT)
+    b = run(ising, L, 40 + L, beta, 25, 3, ising.ISING_PATH_LAUNCHES)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+    assert a[3] == 28
+
+
+def test_resident_matches_oracle_plain_config(ising):
+    E, M, S, _, _ = run(ising, 64, 1, 1.0 / 2.269, 1000, 1, ising.ISING_PATH_RESIDENT)
+    s = oracle.init_hot(64, 1)
+    Eo, Mo = oracle.run(s, 1, 1.0 / 2.269, 0, 1000, 1)
+    oracle.run(s, 1, 1.0 / 2.269, 1000, 3, 3)
+    np.testing.assert_array_equal(E, Eo)
+    np.testing.assert_array_equal(M, Mo)
+    np.testing.assert_array_equal(S, s)
+
+
+def test_resident_many_records_and_chunks(ising):
+    # more records than one device chunk holds (1024), and a remainder
+    a = run(ising, 32, 5, 0.44, 2600, 2, ising.ISING_PATH_RESIDENT)
+    b = run(ising, 32, 5, 0.44, 2600, 2, ising.ISING_PATH_LAUNCHES)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_resident_rejects_lattices_that_do_not_fit(ising):
+    with ising.Lattice(1024, 1) as lat:
+        with pytest.raises(ising.IsingError):
+            lat.set_path(ising.ISING_PATH_RESIDENT)
+        lat.set_path(ising.ISING_PATH_AUTO)     # auto falls back to launches
+        lat.sweep(1)
+    with ising.Lattice(64, 1) as lat:
+        with pytest.raises(ising.IsingError):
+            lat.set_path(7)
