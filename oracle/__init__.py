@@ -54,6 +54,10 @@ def _load():
         sig = {
             "ora_philox4x32_10": (None, [u32p, u32p, u32p]),
             "ora_philox4x64_10": (None, [u64p, u64p, u64p]),
+            "ora_philox4x32_r": (None, [u32p, u32p, ctypes.c_int, u32p]),
+            "ora_set_sweep_rounds": (None, [ctypes.c_int]),
+            "ora_site_draw_r": (ctypes.c_uint32, [ctypes.c_uint64, ctypes.c_uint64,
+                                                  ctypes.c_int, ctypes.c_int, ctypes.c_int]),
             "ora_site_draw": (ctypes.c_uint32, [ctypes.c_uint64, ctypes.c_uint64,
                                                 ctypes.c_int, ctypes.c_int]),
             "ora_thresholds": (None, [ctypes.c_double, u64p]),
@@ -92,6 +96,30 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     _load().ora_philox4x32_10(_ptr(c, ctypes.c_uint32), _ptr(k, ctypes.c_uint32),
                               _ptr(out, ctypes.c_uint32))
     return out
+
+
+def philox4x32_r(ctr, key, rounds: int) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _load().ora_philox4x32_r(_ptr(c, ctypes.c_uint32), _ptr(k, ctypes.c_uint32), int(rounds),
+                             _ptr(out, ctypes.c_uint32))
+    return out
+
+
+class sweep_rounds:
+    """Context manager: the oracle's sweeps use `rounds` Philox rounds (10 is
+    the default scheme, 7 the opt-in cheaper one); the hot start keeps 10."""
+
+    def __init__(self, rounds: int):
+        self.rounds = int(rounds)
+
+    def __enter__(self):
+        _load().ora_set_sweep_rounds(self.rounds)
+        return self
+
+    def __exit__(self, *exc):
+        _load().ora_set_sweep_rounds(10)
 
 
 def philox4x64_10(ctr, key) -> np.ndarray:

@@ -43,13 +43,16 @@
  * structure, so that the 64-bit member can be checked against an independent
  * published implementation. */
 
-void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+/* Philox4x32 with `rounds` rounds (SC'11 defines the family; 10 is its
+ * recommended member, 7 the fewest rounds at which its authors found it to
+ * pass their statistical test batteries). */
+void ora_philox4x32_r(const uint32_t ctr[4], const uint32_t key[2], int rounds, uint32_t out[4])
 {
     const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
     const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
     uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
     uint32_t k0 = key[0], k1 = key[1];
-    for (int round = 0; round < 10; ++round) {
+    for (int round = 0; round < rounds; ++round) {
         uint64_t p0 = (uint64_t)M0 * (uint64_t)x0;
         uint64_t p1 = (uint64_t)M1 * (uint64_t)x2;
         uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
@@ -62,6 +65,11 @@ void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
         k0 += W0; k1 += W1;
     }
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    ora_philox4x32_r(ctr, key, 10, out);
 }
 
 void ora_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
@@ -85,16 +93,28 @@ void ora_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t ou
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-/* The uint32 draw of site (i, j) at sweep t (t = 0: initialisation). */
-uint32_t ora_site_draw(uint64_t seed, uint64_t t, int i, int j)
+/* Number of Philox rounds the sweeps use: 10 (default) or 7 (an opt-in
+ * cheaper scheme).  The hot start always uses 10. */
+static int g_sweep_rounds = 10;
+
+void ora_set_sweep_rounds(int rounds) { g_sweep_rounds = rounds; }
+
+/* The uint32 draw of site (i, j) at sweep t with `rounds` Philox rounds. */
+uint32_t ora_site_draw_r(uint64_t seed, uint64_t t, int i, int j, int rounds)
 {
     int c = (i + j) & 1;
     uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
     uint32_t ctr[4] = { (uint32_t)(i >> 2), (uint32_t)(j >> 1),
                         (uint32_t)t, ((uint32_t)(t >> 32) << 1) | (uint32_t)c };
     uint32_t out[4];
-    ora_philox4x32_10(ctr, key, out);
+    ora_philox4x32_r(ctr, key, rounds, out);
     return out[i & 3];
+}
+
+/* The uint32 draw of site (i, j) at sweep t (t = 0: initialisation). */
+uint32_t ora_site_draw(uint64_t seed, uint64_t t, int i, int j)
+{
+    return ora_site_draw_r(seed, t, i, j, 10);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -205,7 +225,7 @@ void ora_half_sweep(int L, int8_t *s, uint64_t seed, uint64_t t, int c,
             if (a >= 2) {
                 flip = 1;                               /* dE <= 0 */
             } else {
-                uint32_t r = ora_site_draw(seed, t, i, j);
+                uint32_t r = ora_site_draw_r(seed, t, i, j, g_sweep_rounds);
                 flip = ((uint64_t)r < thr[a]);          /* strict < */
             }
             if (stats) {

@@ -422,3 +422,54 @@ def test_onsager_and_yang(T, golden_dir):
     if T < 2.2:
         m, dm = exact.binned_error(np.abs(M) / (L * L), 40)
         assert abs(m - m_y) < 4.5 * dm + 2e-3, (m, m_y, dm)
+
+
+# ----------------------------------------------------------------------------- Philox rounds (opt-in scheme)
+
+def test_philox_round_count_family():
+    """The R-round member is the same iteration stopped after R rounds: R = 10
+    equals the pinned Philox4x32-10, and rounds compose (one round applied to
+    the R-round output with the round-R key equals R + 1 rounds)."""
+    rng = np.random.default_rng(21)
+    W0, W1 = 0x9E3779B9, 0xBB67AE85
+    M0, M1 = 0xD2511F53, 0xCD9E8D57
+    for _ in range(200):
+        ctr = rng.integers(0, 2**32, size=4, dtype=np.uint64).astype(np.uint32)
+        key = rng.integers(0, 2**32, size=2, dtype=np.uint64).astype(np.uint32)
+        np.testing.assert_array_equal(oracle.philox4x32_r(ctr, key, 10), oracle.philox4x32_10(ctr, key))
+        x = [int(v) for v in oracle.philox4x32_r(ctr, key, 7)]
+        k0 = (int(key[0]) + 7 * W0) % 2**32
+        k1 = (int(key[1]) + 7 * W1) % 2**32
+        p0, p1 = M0 * x[0], M1 * x[2]
+        step = [(p1 >> 32) ^ x[1] ^ k0, p1 & 0xFFFFFFFF, (p0 >> 32) ^ x[3] ^ k1, p0 & 0xFFFFFFFF]
+        np.testing.assert_array_equal(oracle.philox4x32_r(ctr, key, 8), np.array(step, dtype=np.uint32))
+    assert not np.array_equal(oracle.philox4x32_r([1, 2, 3, 4], [5, 6], 7), oracle.philox4x32_10([1, 2, 3, 4], [5, 6]))
+
+
+def test_seven_round_chain_keeps_the_boltzmann_law(golden_dir):
+    """The opt-in 7-round scheme drives the same Metropolis rule: the 4x4 chain
+    still matches exact enumeration, and its flips use the 7-round draws."""
+    vals = load_exact(golden_dir)
+    beta = BETA_TC
+    e_ex = vals[("enum_e_per_spin", "4", beta)]
+    m_ex = vals[("enum_absm_per_spin", "4", beta)]
+    with oracle.sweep_rounds(7):
+        s = oracle.init_hot(4, 3)
+        oracle.run(s, 3, beta, 0, 1000)
+        E, M = oracle.run(s, 3, beta, 1000, 200000)
+        # the flip set of one half-sweep uses the 7-round draw of each site
+        L = 8
+        c = oracle.init_cold(L, 1)
+        oracle.half_sweep_thr(c, 9, 4, 0, 2**31, 2**31)
+        for i in range(L):
+            for j in range(L):
+                want = ((i + j) & 1) == 0 and oracle._load().ora_site_draw_r(9, 4, i, j, 7) < 2**31
+                assert (c[i, j] == -1) == want
+    e, de = exact.binned_error(E / 16.0, 50)
+    m, dm = exact.binned_error(np.abs(M) / 16.0, 50)
+    assert abs(e - e_ex) < 4.5 * de
+    assert abs(m - m_ex) < 4.5 * dm
+    # outside the context the default (10 rounds) is back
+    s10 = oracle.init_cold(8, 1)
+    oracle.half_sweep_thr(s10, 9, 4, 0, 2**31, 2**31)
+    assert not np.array_equal(s10, c)
