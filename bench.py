@@ -46,7 +46,8 @@ SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 MULWIDE_PER_SM_CLK = 32         # 32x32->64 integer multiplies (IMAD.WIDE) per SM per clock
 MULWIDE_PER_SITE = 4            # Philox4x32-10 with the counter-independent rounds hoisted:
-                                # 16 multiplies per call, one call per 4 sites
+                                # 16 multiplies per call, one call per 4 sites (10 per call,
+                                # 2.5 per site, for the opt-in 7-round scheme)
 
 
 def parse():
@@ -63,6 +64,8 @@ def parse():
                     help="large (default): L=16384 roofline config; plain: L=64 x 1000 sweeps; "
                          "scan: L=1024 x 26 temperatures; batched: 512 uneven replicas vs per-instance launches")
     ap.add_argument("--sweeps", type=int, default=None, help="override the workload's sweep count")
+    ap.add_argument("--rng", type=int, default=10, choices=[10, 7],
+                    help="Philox rounds of the sweep draws: 10 (default scheme) or the opt-in 7")
     ap.add_argument("--instances", type=int, default=None,
                     help="batched: compare with per-instance launches on the first N replicas only")
     return ap.parse_args()
@@ -190,6 +193,24 @@ def batched_replicas(n=512, seed=11):
     Ts = rng.uniform(1.5, 3.5, size=n)
     seeds = np.array([splitmix64((seed << 32) + r) for r in range(n)], dtype=np.uint64)
     return Ls, 1.0 / Ts, seeds
+
+
+def max_over_ranks(values, world, device="cuda"):
+    """Element-wise maximum of per-rank timings (seconds) over all ranks; the
+    whole-job time of a weak-scaling run is the slowest rank's."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units per nanosecond of the whole job: every rank did units_per_rank in
+    at most `seconds`."""
+    return world * units_per_rank / (seconds * 1e9)
 
 
 def emit(line):
@@ -370,6 +391,8 @@ def main():
     lat = ising.Lattice(L, seed, stream=stream)
     if args.tiling:
         lat.set_tiling(*[int(x) for x in args.tiling.split(",")])
+    if args.rng == 7:
+        lat.set_rng(ising.ISING_RNG_PHILOX4X32_7)
     lat.init_hot()
     lat.set_beta(BETA)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -403,19 +426,17 @@ def main():
         wall = time.perf_counter() - w0
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     dev_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([dev_s, wall], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dev_s, wall = float(t[0]), float(t[1])
+    dev_s, wall = max_over_ranks([dev_s, wall], world)
 
     updates_per_rank = args.steps * SWEEPS_PER_STEP * L * L
-    value = world * updates_per_rank / (dev_s * 1e9)
+    value = whole_job_rate(updates_per_rank, world, dev_s)
     launches_per_step = 2 * SWEEPS_PER_STEP + 1     # half-sweeps + counter advance
     half_sweep_s = dev_s / (args.steps * 2 * SWEEPS_PER_STEP)
 
     # roofline of the half-sweep kernel: the 32x32->64 multiplies of Philox4x32-10
     sites_per_launch = L * L // 2
-    achieved_mul = sites_per_launch * MULWIDE_PER_SITE / half_sweep_s / 1e12
+    mul_per_site = MULWIDE_PER_SITE if args.rng == 10 else 2.5
+    achieved_mul = sites_per_launch * mul_per_site / half_sweep_s / 1e12
     peak_mul = SM_COUNT * MULWIDE_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
     W = (L // 2 + 20) // 21
     P = W + (W & 1)
@@ -439,11 +460,8 @@ def main():
             lat.sweep_record(SWEEPS_PER_STEP, SWEEPS_PER_STEP)
         barrier()
         e_dt = time.perf_counter() - e0
-        if world > 1:
-            t = torch.tensor([e_dt], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e_dt = float(t[0])
-        e2e = {"value": world * n_e2e * SWEEPS_PER_STEP * L * L / (e_dt * 1e9), "unit": METRIC,
+        e_dt = max_over_ranks([e_dt], world)[0]
+        e2e = {"value": whole_job_rate(n_e2e * SWEEPS_PER_STEP * L * L, world, e_dt), "unit": METRIC,
                "h2d_bytes_per_step": L * L, "d2h_bytes_per_step": 32 * 16, "steps": n_e2e,
                "path": "ising_set_spins (pinned int8 L*L) + ising_sweep_record(10, 10) per step"}
 
@@ -463,13 +481,14 @@ def main():
                                     "E/M every 10 sweeps; step = 10 sweeps + E/M record"),
                        "L": L, "sweeps_per_step": SWEEPS_PER_STEP, "parallelism": f"replicas x{world}",
                        "l2": "flushed between steps (256 MB write; lattice 103 MB < L2)",
-                       "tiling": args.tiling or "default 4,32,4"},
+                       "tiling": args.tiling or "default 4,32,4",
+                       "rng": f"Philox4x32-{args.rng}"},
             "wall_s": wall,
             "roofline": {"bound": "alu", "achieved": achieved_mul, "peak": peak_mul,
                          "unit": "T mul.wide.u32/s", "frac": achieved_mul / peak_mul, "traffic": None,
                          "kernel": "half_sweep_kernel",
                          "achieved_spin_updates_per_ns": sites_per_launch / half_sweep_s / 1e9,
-                         "peak_spin_updates_per_ns": peak_mul * 1e12 / MULWIDE_PER_SITE / 1e9,
+                         "peak_spin_updates_per_ns": peak_mul * 1e12 / mul_per_site / 1e9,
                          "peak_basis": ("152 SMs x 32 IMAD.WIDE/clk/SM x 2070 MHz (of nominal clock); "
                                         "4 per site (16 per Philox4x32-10 call, 4 sites per call)"),
                          "hbm_achieved_gbs": hbm_bytes_per_launch / half_sweep_s / 1e9,

@@ -166,6 +166,17 @@ int ising_set_tiling(ising_lattice *h, int32_t rows_per_thread,
 #define ISING_PATH_RESIDENT 2
 int ising_set_path(ising_lattice *h, int32_t path);
 
+/* Random-number scheme of the sweeps.  ISING_RNG_PHILOX4X32_10 (default) is
+ * the generator of the conventions above.  ISING_RNG_PHILOX4X32_7 is an
+ * opt-in cheaper member of the same family: the same keying and counters,
+ * the iteration stopped after 7 rounds (Salmon et al. report 7 as the fewest
+ * rounds at which Philox4x32 passed their test batteries; 10 keeps a safety
+ * margin).  It gives a different, equally reproducible trajectory with the
+ * same stationary distribution; the hot start always uses 10 rounds. */
+#define ISING_RNG_PHILOX4X32_10 0
+#define ISING_RNG_PHILOX4X32_7 1
+int ising_set_rng(ising_lattice *h, int32_t scheme);
+
 /* Device pointer to the colour-c array (c = 0 or 1), for zero-copy use by
  * other device code on the same stream.  Returned in *dev_ptr. */
 int ising_device_words(ising_lattice *h, int32_t c, void **dev_ptr);
@@ -291,6 +302,26 @@ int ising_server_stats(ising_server *srv, int64_t *jobs_done, double *spin_updat
 /* Stop the worker after the running jobs' current epoch, fail the queued
  * ones (state cancelled), free the arena.  Jobs still running are failed. */
 int ising_server_destroy(ising_server *srv);
+
+/* ---- Autotuning ---------------------------------------------------------
+ * Time the candidate launch shapes on the current device and return the
+ * fastest.  Every candidate must leave a bit-identical lattice (the draws are
+ * keyed by site, not by thread); a difference returns ISING_ECUDA.  The
+ * caller applies the choice (ising_set_tiling / ising_set_path,
+ * ising_batch_set_tiling); the Python binding keeps the choices in a JSON
+ * table. */
+
+/* Single lattice of side L: tilings (block_words x block_groups) on the launch
+ * path and, if the lattice fits, the on-chip path; `sweeps` timed sweeps
+ * each (1..100000) from a hot start at T = 2.269.  Outputs may be NULL. */
+int ising_autotune(int32_t L, int32_t sweeps, int32_t *best_block_words, int32_t *best_block_groups,
+                   int32_t *best_path, double *ns_per_update);
+
+/* Batch (arguments as ising_batch_create): threads per tile {64, 128, 256}
+ * x graph chunk {10, 50, 200}, `sweeps` timed sweeps per replica. */
+int ising_batch_autotune(int32_t n, const int32_t *L, const double *beta, const uint64_t *seed,
+                         const uint8_t *hot, int64_t sweeps, int32_t *best_threads, int32_t *best_chunk,
+                         double *ns_per_update);
 
 /* ---- Allocation-free record path ----------------------------------------
  * The paper has no counterpart to this entry point.  It is for callers that

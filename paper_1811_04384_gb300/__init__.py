@@ -25,6 +25,8 @@ ISING_ECUDA = -3
 ISING_ETIMEOUT = -4
 ISING_EBUSY = -5
 ISING_ENOTFOUND = -6
+ISING_RNG_PHILOX4X32_10 = 0
+ISING_RNG_PHILOX4X32_7 = 1
 ISING_PATH_AUTO = 0
 ISING_PATH_LAUNCHES = 1
 ISING_PATH_RESIDENT = 2
@@ -142,6 +144,10 @@ class Lattice:
 
     def set_tiling(self, rows: int = 4, block_words: int = 32, block_groups: int = 4):
         _check(load().ising_set_tiling(self._h, rows, block_words, block_groups), "ising_set_tiling")
+
+    def set_rng(self, scheme: int):
+        """ISING_RNG_PHILOX4X32_10 (default) or the opt-in ISING_RNG_PHILOX4X32_7."""
+        _check(load().ising_set_rng(self._h, int(scheme)), "ising_set_rng")
 
     def set_path(self, path: int):
         """ISING_PATH_AUTO, ISING_PATH_LAUNCHES or ISING_PATH_RESIDENT."""

@@ -208,6 +208,7 @@ extern "C" int ising_batch_set_tiling(ising_batch* b, int32_t threads, int32_t c
 extern "C" int ising_batch_sweep(ising_batch* b, const int64_t* sweeps, int64_t every, int64_t** host_E,
                                  int64_t** host_M)
 {
+    TraceRange trace("ising_batch_sweep");
     if (!b || !sweeps || every < 1 || every > 0x7fffffff) return ISING_EINVAL;
     int64_t max_s = 0;
     size_t words = 0;

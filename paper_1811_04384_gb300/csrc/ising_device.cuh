@@ -16,6 +16,10 @@
 #include <cstdint>
 #include "philox.cuh"
 
+#ifndef ISING_INSERTS_ON_ALU
+#define ISING_INSERTS_ON_ALU 0
+#endif
+
 namespace ising {
 
 constexpr int kFields = 21;
@@ -36,6 +40,7 @@ struct SweepArgs {
     uint32_t thr0, thr1;       // integer thresholds clamped to 2^32 - 1 ...
     uint32_t all0, all1;       // ... and ~0u where the threshold is 2^32
     uint32_t one;              // the value 1, as a launch operand (see accept_insert)
+    uint32_t rounds;           // Philox rounds of the sweep draws: 10 (default) or 7 (opt-in)
     PhiloxKeys rk;             // round keys of the key (lo32(seed), hi32(seed))
     unsigned long long* counts;  // E/M count slots of this record (RECORD only)
 };
@@ -75,19 +80,56 @@ __device__ __forceinline__ void block_add_counts(unsigned long long* target, uin
     }
 }
 
-// Set the bit of field k in the accept masks A0 (r < thr0) and A1 (r < thr1).
-// The two inserts are written as predicated PTX so that the compare result
-// never becomes a 0/1 value: the first is a multiply-add (K * one + A0, which
-// runs on the FMA pipe), the second an OR on the ALU, balancing the two pipes
-// against the Philox multiplies (FMA) and XORs (ALU).
-__device__ __forceinline__ void accept_insert(uint32_t& A0, uint32_t& A1, uint32_t r, uint32_t thr0,
-                                              uint32_t thr1, uint32_t K, uint32_t one)
+// Accept bits of one field for one row.  A1 collects r < thr1 at bit K2 (the
+// spin bit of the field within its 32-bit half), A0 collects r < thr0 at bit
+// K2 + 1.  The inserts are predicated PTX, so a compare result never becomes
+// a 0/1 value and the bit is an immediate: the r < thr1 insert is an OR on the
+// ALU, the r < thr0 insert a multiply-add (K * one + A0) on the FMA pipe, which
+// balances the two pipes against the Philox XORs (ALU) and multiplies (FMA).
+template <int K2>
+__device__ __forceinline__ void accept_insert(uint32_t& A1, uint32_t& A0, uint32_t r, uint32_t thr0,
+                                              uint32_t thr1, uint32_t one)
 {
-    asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p mad.lo.u32 %0, %3, %4, %0;\n\t}"
-        : "+r"(A0) : "r"(r), "r"(thr0), "r"(K), "r"(one));
     asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
-        : "+r"(A1) : "r"(r), "r"(thr1), "r"(K));
+        : "+r"(A1) : "r"(r), "r"(thr1), "n"(1u << K2));
+#if ISING_INSERTS_ON_ALU
+    asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p or.b32 %0, %0, %3;\n\t}"
+        : "+r"(A0) : "r"(r), "r"(thr0), "n"(2u << K2));
+#else
+    asm("{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, %2;\n\t@p mad.lo.u32 %0, %4, %3, %0;\n\t}"
+        : "+r"(A0) : "r"(r), "r"(thr0), "n"(2u << K2), "r"(one));
+#endif
 }
+
+// Accumulators of one row: [0] r < thr1 bits of fields 0..10, [1] r < thr0
+// (shifted up one bit) of fields 0..10, [2], [3] the same for fields 11..20.
+struct AcceptBits {
+    uint32_t a[4][4];   // [row][word]
+};
+
+// Fields k .. 20 of one Philox row group (compile-time k: immediate bit masks).
+template <int k, int ROUNDS>
+struct FieldLoop {
+    __device__ __forceinline__ static void run(const PhiloxRowKey& pk, const PhiloxKeys& rk, uint32_t m0,
+                                               AcceptBits& acc, uint32_t thr0, uint32_t thr1, uint32_t one)
+    {
+        uint32_t rnd[4];
+        philox_row<ROUNDS>(pk, rk, m0 + (uint32_t)k, rnd);
+        constexpr int half = k <= 10 ? 0 : 2;
+        constexpr int K2 = k <= 10 ? 3 * k : 3 * k - 32;
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            accept_insert<K2>(acc.a[e][half], acc.a[e][half + 1], rnd[e], thr0, thr1, one);
+        FieldLoop<k + 1, ROUNDS>::run(pk, rk, m0, acc, thr0, thr1, one);
+    }
+};
+template <int ROUNDS>
+struct FieldLoop<kFields, ROUNDS> {
+    __device__ __forceinline__ static void run(const PhiloxRowKey&, const PhiloxKeys&, uint32_t, AcceptBits&,
+                                               uint32_t, uint32_t, uint32_t)
+    {
+    }
+};
 
 // The work of one thread: rows row0 .. row0+3 (those below L) of word column
 // w of colour C, at sweep t (Sec. 2 steps 1-3 for every site of the colour at
@@ -101,11 +143,11 @@ __device__ __forceinline__ void accept_insert(uint32_t& A0, uint32_t& A1, uint32
 //   ge2 = x1&x2 | x3&x4 | (x1^x2)&(x3^x4) (a >= 2: dE <= 0, Table 1)
 //   accept = ge2 | any & (r < thr1) | ~any & (r < thr0)
 // GLOBAL selects read-only-cache loads (lattice in global memory) or plain
-// loads (lattice in shared memory).
+// loads (lattice in shared memory).  Offsets are 32-bit (L * pitch < 2^32).
 // UPDATE = false skips the flip (measurement only).  RECORD adds the
 // anti-aligned bond count of the (updated) colour-1 words and the up-spin
 // count of both colours to anti / up: E = 2 anti - 2 L^2, M = 2 up - L^2.
-template <int C, bool UPDATE, bool RECORD, bool GLOBAL = true>
+template <int C, bool UPDATE, bool RECORD, bool GLOBAL = true, int ROUNDS = 10>
 __device__ __forceinline__ void sweep_rows(uint64_t* __restrict__ own, const uint64_t* __restrict__ other,
                                            const Geom& g, int row0, int w, uint64_t t, const PhiloxKeys& rk,
                                            uint32_t thr0, uint32_t thr1, uint32_t all0w, uint32_t all1w,
@@ -114,58 +156,55 @@ __device__ __forceinline__ void sweep_rows(uint64_t* __restrict__ own, const uin
     constexpr int ROWS = 4;
     const int nrows = min(ROWS, g.L - row0);
     const uint64_t live = live_mask(g, w);
+    const uint32_t P = (uint32_t)g.P;
+    const uint32_t base = (uint32_t)row0 * P + (uint32_t)w;
+    const uint32_t up_off = row0 == 0 ? (uint32_t)(g.L - 1) * P + (uint32_t)w : base - P;
+    const uint32_t dn_off = row0 + nrows >= g.L ? (uint32_t)w : base + (uint32_t)nrows * P;
+    const uint32_t wl = (uint32_t)((w > 0) ? w - 1 : g.W - 1);
+    const uint32_t wr = (uint32_t)((w < g.W - 1) ? w + 1 : 0);
 
     // All loads first: their latency overlaps the Philox work below.
+    // oc[r] = other-colour row row0 - 1 + r (periodic), column w.
     uint64_t oc[ROWS + 2], sw[ROWS], side[ROWS];
-#pragma unroll
-    for (int r = 0; r < ROWS + 2; ++r) {
-        if (r <= nrows + 1) {
-            const int i = wrap_row(row0 - 1 + r, g.L);
-            oc[r] = GLOBAL ? __ldg(other + (size_t)i * g.P + w) : other[(size_t)i * g.P + w];
-        } else {
-            oc[r] = 0;
-        }
-    }
+    oc[0] = GLOBAL ? __ldg(other + up_off) : other[up_off];
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
         if (r < nrows) {
-            const int i = row0 + r;
-            sw[r] = own[(size_t)i * g.P + w];
-            const int dir = (r + C) & 1;     // row0 is a multiple of 4
-            const int wn = dir == 0 ? ((w > 0) ? w - 1 : g.W - 1) : ((w < g.W - 1) ? w + 1 : 0);
-            side[r] = GLOBAL ? __ldg(other + (size_t)i * g.P + wn) : other[(size_t)i * g.P + wn];
+            const uint32_t o = base + (uint32_t)r * P;
+            oc[r + 1] = GLOBAL ? __ldg(other + o) : other[o];
+            sw[r] = own[o];
+            const uint32_t os = o - (uint32_t)w + ((((r + C) & 1) == 0) ? wl : wr);   // row0 is a multiple of 4
+            side[r] = GLOBAL ? __ldg(other + os) : other[os];
         } else {
+            oc[r + 1] = 0;
             sw[r] = 0;
             side[r] = 0;
         }
     }
+    {
+        const uint64_t dn = GLOBAL ? __ldg(other + dn_off) : other[dn_off];   // row below the last present row
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r)
+            if (r + 1 == nrows) oc[r + 2] = dn;
+        if (nrows == ROWS) oc[ROWS + 1] = dn;
+    }
 
-    uint32_t lo0[ROWS] = {0, 0, 0, 0}, hi0[ROWS] = {0, 0, 0, 0};
-    uint32_t lo1[ROWS] = {0, 0, 0, 0}, hi1[ROWS] = {0, 0, 0, 0};
+    AcceptBits acc;
+#pragma unroll
+    for (int e = 0; e < ROWS; ++e)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc.a[e][q] = 0;
     if (UPDATE) {
         const uint32_t tl = (uint32_t)t;
         const uint32_t th = ((uint32_t)(t >> 32) << 1) | (uint32_t)C;
         const PhiloxRowKey pk = philox_row_key((uint32_t)(row0 >> 2), tl, th, rk);
-        const uint32_t m0 = (uint32_t)w * kFields;
-#pragma unroll
-        for (int k = 0; k < kFields; ++k) {
-            uint32_t rnd[4];
-            philox_row(pk, rk, m0 + (uint32_t)k, rnd);
-            // field k: bit 3k of the word; fields 0..10 in the low half, 11..20 in the high half
-            const uint32_t K = (k <= 10) ? (1u << (3 * k)) : (1u << (3 * k - 32));
-#pragma unroll
-            for (int e = 0; e < ROWS; ++e) {
-                if (k <= 10) accept_insert(lo0[e], lo1[e], rnd[e], thr0, thr1, K, one);
-                else accept_insert(hi0[e], hi1[e], rnd[e], thr0, thr1, K, one);
-            }
-        }
+        FieldLoop<0, ROUNDS>::run(pk, rk, (uint32_t)w * kFields, acc, thr0, thr1, one);
     }
     const uint64_t all0 = ((uint64_t)all0w << 32 | all0w) & live;
     const uint64_t all1 = ((uint64_t)all1w << 32 | all1w) & live;
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
         if (r < nrows) {
-            const int i = row0 + r;
             const uint64_t s = sw[r];
             const uint64_t u = oc[r], d = oc[r + 2], h0 = oc[r + 1];
             // the other-colour word shifted by one field (horizontal neighbour at m -/+ 1)
@@ -182,11 +221,11 @@ __device__ __forceinline__ void sweep_rows(uint64_t* __restrict__ own, const uin
             if (UPDATE) {
                 const uint64_t any = x1 | x2 | x3 | x4;
                 const uint64_t ge2 = (x1 & x2) | (x3 & x4) | ((x1 ^ x2) & (x3 ^ x4));
-                const uint64_t c0 = ((uint64_t)hi0[r] << 32 | lo0[r]) | all0;
-                const uint64_t c1 = ((uint64_t)hi1[r] << 32 | lo1[r]) | all1;
+                const uint64_t c1 = ((uint64_t)acc.a[r][2] << 32 | acc.a[r][0]) | all1;
+                const uint64_t c0 = (((uint64_t)acc.a[r][3] << 32 | acc.a[r][1]) >> 1) | all0;
                 const uint64_t accept = ge2 | (any & c1) | (~any & c0);
                 s_new = s ^ (accept & live);
-                own[(size_t)i * g.P + w] = s_new;
+                own[base + (uint32_t)r * P] = s_new;
             }
             if (RECORD) {
                 anti += __popcll((s_new ^ u) & live) + __popcll((s_new ^ d) & live)
@@ -198,8 +237,9 @@ __device__ __forceinline__ void sweep_rows(uint64_t* __restrict__ own, const uin
 }
 
 // One half-sweep of colour C over one lattice: thread (x, y) of the grid owns
-// word column x and rows 4y .. 4y+3.  At most 256 threads per block.
-template <int C, bool UPDATE, bool RECORD>
+// word column x and rows 4y .. 4y+3.  At most 256 threads per block.  ROUNDS:
+// Philox rounds of the draws (10, or the opt-in 7).
+template <int C, bool UPDATE, bool RECORD, int ROUNDS = 10>
 __global__ void __launch_bounds__(256, 3)
 half_sweep_kernel(uint64_t* __restrict__ own, const uint64_t* __restrict__ other, Geom g, SweepArgs a)
 {
@@ -208,8 +248,8 @@ half_sweep_kernel(uint64_t* __restrict__ own, const uint64_t* __restrict__ other
     uint32_t anti = 0, up = 0;
     if (w < g.W && row0 < g.L) {
         const uint64_t t = UPDATE ? *a.t_base + a.t_off : 0;
-        sweep_rows<C, UPDATE, RECORD>(own, other, g, row0, w, t, a.rk, a.thr0, a.thr1, a.all0, a.all1,
-                                      a.one, anti, up);
+        sweep_rows<C, UPDATE, RECORD, true, ROUNDS>(own, other, g, row0, w, t, a.rk, a.thr0, a.thr1, a.all0,
+                                                    a.all1, a.one, anti, up);
     }
     if (RECORD) {
         const int slot = (blockIdx.x + gridDim.x * blockIdx.y) % kCountSlots;

@@ -2,11 +2,21 @@
 // the C ABI).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <cstdint>
 
 #include "ising_device.cuh"
 
 namespace ising {
+
+// NVTX range for the duration of a scope (visible in Nsight timelines; a
+// no-op unless a tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Record `e` with its call site for ising_last_cuda_error(); returns ISING_ECUDA.
 int cuda_fail(cudaError_t e, const char* where);

@@ -110,6 +110,7 @@ __global__ void set_sweep_kernel(uint64_t* t_base, uint64_t t)
 // barrier between half-sweeps), records E and M after every `every`-th sweep
 // with an on-chip reduction (records[2k] = E, records[2k+1] = M), and copies
 // the lattice back.  For lattices whose 2 L P words fit in shared memory.
+template <int ROUNDS>
 __global__ void __launch_bounds__(256, 1)
 resident_sweeps_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom g, SweepArgs a, uint64_t t0,
                        int n, int every, long long* __restrict__ records)
@@ -131,8 +132,8 @@ resident_sweeps_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geo
         uint32_t dummy0 = 0, dummy1 = 0;
         for (int it = threadIdx.x; it < items; it += blockDim.x) {
             const int grp = it / g.W, w = it - grp * g.W;
-            sweep_rows<0, true, false, false>(s0, s1, g, grp * 4, w, t, a.rk, a.thr0, a.thr1, a.all0, a.all1,
-                                              a.one, dummy0, dummy1);
+            sweep_rows<0, true, false, false, ROUNDS>(s0, s1, g, grp * 4, w, t, a.rk, a.thr0, a.thr1, a.all0,
+                                                      a.all1, a.one, dummy0, dummy1);
         }
         __syncthreads();
         const bool record = (s % every) == 0;
@@ -140,11 +141,11 @@ resident_sweeps_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geo
         for (int it = threadIdx.x; it < items; it += blockDim.x) {
             const int grp = it / g.W, w = it - grp * g.W;
             if (record)
-                sweep_rows<1, true, true, false>(s1, s0, g, grp * 4, w, t, a.rk, a.thr0, a.thr1, a.all0, a.all1,
-                                                 a.one, anti, up);
+                sweep_rows<1, true, true, false, ROUNDS>(s1, s0, g, grp * 4, w, t, a.rk, a.thr0, a.thr1, a.all0,
+                                                         a.all1, a.one, anti, up);
             else
-                sweep_rows<1, true, false, false>(s1, s0, g, grp * 4, w, t, a.rk, a.thr0, a.thr1, a.all0, a.all1,
-                                                  a.one, anti, up);
+                sweep_rows<1, true, false, false, ROUNDS>(s1, s0, g, grp * 4, w, t, a.rk, a.thr0, a.thr1, a.all0,
+                                                          a.all1, a.one, anti, up);
         }
         if (record) {
             anti = __reduce_add_sync(0xffffffffu, anti);
@@ -224,6 +225,7 @@ struct ising_lattice {
     unsigned long long* host_counts = nullptr;   // pinned, kCountBytes
     int bw = 32, bg = 4;                         // half-sweep block shape
     int path = ISING_PATH_AUTO;                  // multi-block launches or on-chip resident sweeps
+    int rounds = 10;                             // Philox rounds of the sweep draws
     bool resident_attr = false;                  // dynamic shared memory attribute set
 };
 
@@ -308,9 +310,25 @@ SweepArgs make_sweep_args(uint64_t seed, const uint64_t thr[2], const uint64_t* 
     a.t_off = 0;
     fill_threshold_args(thr, a);
     a.one = 1;
+    a.rounds = 10;
     a.rk = philox_keys((uint32_t)seed, (uint32_t)(seed >> 32));
     a.counts = nullptr;
     return a;
+}
+
+template <int ROUNDS>
+static void launch_half_sweep_r(dim3 grid, dim3 block, int colour, bool update, bool record, uint64_t* own,
+                                const uint64_t* other, const Geom& g, const SweepArgs& a, cudaStream_t s)
+{
+    if (colour == 0) {
+        if (record) half_sweep_kernel<0, true, true, ROUNDS><<<grid, block, 0, s>>>(own, other, g, a);
+        else half_sweep_kernel<0, true, false, ROUNDS><<<grid, block, 0, s>>>(own, other, g, a);
+    } else if (!update) {
+        half_sweep_kernel<1, false, true><<<grid, block, 0, s>>>(own, other, g, a);
+    } else {
+        if (record) half_sweep_kernel<1, true, true, ROUNDS><<<grid, block, 0, s>>>(own, other, g, a);
+        else half_sweep_kernel<1, true, false, ROUNDS><<<grid, block, 0, s>>>(own, other, g, a);
+    }
 }
 
 cudaError_t launch_half_sweep(int bw, int bgrp, int colour, bool update, bool record,
@@ -320,15 +338,8 @@ cudaError_t launch_half_sweep(int bw, int bgrp, int colour, bool update, bool re
     const int ngroups = (g.L + 3) / 4;
     dim3 block(bw, bgrp);
     dim3 grid((g.W + bw - 1) / bw, (ngroups + bgrp - 1) / bgrp);
-    if (colour == 0) {
-        if (record) half_sweep_kernel<0, true, true><<<grid, block, 0, s>>>(own, other, g, a);
-        else half_sweep_kernel<0, true, false><<<grid, block, 0, s>>>(own, other, g, a);
-    } else if (!update) {
-        half_sweep_kernel<1, false, true><<<grid, block, 0, s>>>(own, other, g, a);
-    } else {
-        if (record) half_sweep_kernel<1, true, true><<<grid, block, 0, s>>>(own, other, g, a);
-        else half_sweep_kernel<1, true, false><<<grid, block, 0, s>>>(own, other, g, a);
-    }
+    if (a.rounds == 7) launch_half_sweep_r<7>(grid, block, colour, update, record, own, other, g, a, s);
+    else launch_half_sweep_r<10>(grid, block, colour, update, record, own, other, g, a, s);
     return cudaGetLastError();
 }
 
@@ -423,6 +434,7 @@ static int reset_t(ising_lattice* h, uint64_t t)
 
 extern "C" int ising_init_hot(ising_lattice* h)
 {
+    TraceRange trace("ising_init_hot");
     if (!h) return ISING_EINVAL;
     const Geom& g = h->g;
     // zero everything first so the pitch padding is defined
@@ -467,7 +479,9 @@ extern "C" int ising_get_thresholds(ising_lattice* h, uint64_t host_thr[2])
 
 static SweepArgs base_args(const ising_lattice* h)
 {
-    return make_sweep_args(h->seed, h->thr, h->t_dev);
+    SweepArgs a = make_sweep_args(h->seed, h->thr, h->t_dev);
+    a.rounds = (uint32_t)h->rounds;
+    return a;
 }
 
 // Run `n` sweeps relative to the device counter; sweep s (1-based) records into
@@ -513,22 +527,38 @@ static int run_resident(ising_lattice* h, int n, int every)
     const Geom& g = h->g;
     const size_t bytes = resident_bytes(g);
     if (!h->resident_attr) {
-        cudaError_t e = cudaFuncSetAttribute(resident_sweeps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(resident_sweeps_kernel<10>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kResidentMaxBytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(resident_sweeps_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kResidentMaxBytes);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
         h->resident_attr = true;
     }
     const int items = ((g.L + 3) / 4) * g.W;
     const int threads = std::min(256, std::max(32, (items + 31) / 32 * 32));
     SweepArgs a = base_args(h);
-    resident_sweeps_kernel<<<1, threads, bytes, h->stream>>>(h->words[0], h->words[1], g, a, h->t, n, every,
-                                                             reinterpret_cast<long long*>(h->counts));
+    if (a.rounds == 7)
+        resident_sweeps_kernel<7><<<1, threads, bytes, h->stream>>>(h->words[0], h->words[1], g, a, h->t, n, every,
+                                                                    reinterpret_cast<long long*>(h->counts));
+    else
+        resident_sweeps_kernel<10><<<1, threads, bytes, h->stream>>>(h->words[0], h->words[1], g, a, h->t, n, every,
+                                                                     reinterpret_cast<long long*>(h->counts));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "resident_sweeps_kernel");
     advance_sweep_kernel<<<1, 1, 0, h->stream>>>(h->t_dev, (uint64_t)n);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "advance_sweep_kernel");
     h->t += (uint64_t)n;
+    return ISING_OK;
+}
+
+extern "C" int ising_set_rng(ising_lattice* h, int32_t scheme)
+{
+    if (!h) return ISING_EINVAL;
+    if (scheme == ISING_RNG_PHILOX4X32_10) h->rounds = 10;
+    else if (scheme == ISING_RNG_PHILOX4X32_7) h->rounds = 7;
+    else return ISING_EINVAL;
     return ISING_OK;
 }
 
@@ -543,6 +573,7 @@ extern "C" int ising_set_path(ising_lattice* h, int32_t path)
 
 extern "C" int ising_sweep(ising_lattice* h, int64_t n)
 {
+    TraceRange trace("ising_sweep");
     if (!h || n < 0) return ISING_EINVAL;
     if (use_resident(h)) {
         while (n > 0) {
@@ -577,6 +608,7 @@ static void counts_to_EM(const ising_lattice* h, const unsigned long long* slots
 
 extern "C" int ising_sweep_record(ising_lattice* h, int64_t n, int64_t every, int64_t* E, int64_t* M)
 {
+    TraceRange trace("ising_sweep_record");
     if (!h || n < 0 || every < 1) return ISING_EINVAL;
     const int64_t nrec = n / every;
     int64_t done_rec = 0;
@@ -662,6 +694,7 @@ static int ensure_staging(ising_lattice* h)
 
 extern "C" int ising_get_spins(ising_lattice* h, int8_t* out, size_t n)
 {
+    TraceRange trace("ising_get_spins");
     if (!h || !out || n != (size_t)h->g.L * h->g.L) return ISING_EINVAL;
     int rc = ensure_staging(h);
     if (rc != ISING_OK) return rc;
@@ -680,6 +713,7 @@ extern "C" int ising_get_spins(ising_lattice* h, int8_t* out, size_t n)
 
 extern "C" int ising_set_spins(ising_lattice* h, const int8_t* in, size_t n)
 {
+    TraceRange trace("ising_set_spins");
     if (!h || !in || n != (size_t)h->g.L * h->g.L) return ISING_EINVAL;
     int rc = ensure_staging(h);
     if (rc != ISING_OK) return rc;

@@ -191,6 +191,7 @@ int ensure_tiles(ising_server* s, size_t n)
 // running set and the jobs it names are only changed by the worker).
 int run_epoch(ising_server* s, const std::vector<uint64_t>& run, std::vector<Job*>& jp)
 {
+    TraceRange trace("ising_server_epoch");
     const int threads = 128;
     std::vector<BatchReplica> reps(run.size());
     std::vector<BatchTile> tiles;

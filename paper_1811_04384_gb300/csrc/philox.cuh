@@ -105,8 +105,12 @@ ISING_HD PhiloxRowKey philox_row_key(uint32_t g, uint32_t tl, uint32_t th, const
     return p;
 }
 
+// ROUNDS = 10 is Philox4x32-10; ROUNDS = 7 the opt-in cheaper member of the
+// same family (the same iteration stopped after 7 rounds).
+template <int ROUNDS = 10>
 ISING_HD void philox_row(const PhiloxRowKey& p, const PhiloxKeys& rk, uint32_t m, uint32_t out[4])
 {
+    static_assert(ROUNDS >= 3 && ROUNDS <= 10, "3..10 rounds");
     uint32_t h, l;
     const uint32_t y0 = p.a ^ m;
     mul_hilo(kPhiloxM0, y0, h, l);
@@ -118,7 +122,7 @@ ISING_HD void philox_row(const PhiloxRowKey& p, const PhiloxKeys& rk, uint32_t m
     uint32_t x2 = p.hiC ^ z3;
     uint32_t x3 = p.v3;
 #pragma unroll
-    for (int r = 3; r < 10; ++r)
+    for (int r = 3; r < ROUNDS; ++r)
         philox_round(x0, x1, x2, x3, rk.k0[r], rk.k1[r]);
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }

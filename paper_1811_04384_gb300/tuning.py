@@ -1,0 +1,83 @@
+"""Autotuned launch shapes (ising_autotune / ising_batch_autotune in
+include/ising.h), kept in a JSON table next to this file:
+
+    {"device": "...", "lattice": {"<L>": {"block_words": .., "block_groups": ..,
+     "path": .., "ns_per_update": ..}}, "batch": {...}}
+
+`apply(lattice)` sets the tuned shape for the lattice's side when the table
+holds one for the current device.  Choosing a shape never changes results.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+
+import numpy as np
+
+from . import _check, load
+
+TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
+
+
+def _device_name() -> str:
+    try:
+        import torch
+        return torch.cuda.get_device_name(0)
+    except Exception:
+        return "unknown"
+
+
+def tune_lattice(L: int, sweeps: int = 20) -> dict:
+    bw, bg, path = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    ns = ctypes.c_double()
+    _check(load().ising_autotune(int(L), int(sweeps), ctypes.byref(bw), ctypes.byref(bg), ctypes.byref(path),
+                                 ctypes.byref(ns)), "ising_autotune")
+    return {"block_words": bw.value, "block_groups": bg.value, "path": path.value, "ns_per_update": ns.value}
+
+
+def tune_batch(L, beta, seed, hot, sweeps: int = 50) -> dict:
+    L = np.ascontiguousarray(L, dtype=np.int32)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    seed = np.ascontiguousarray(seed, dtype=np.uint64)
+    hot = np.ascontiguousarray(hot, dtype=np.uint8)
+    th, ch = ctypes.c_int32(), ctypes.c_int32()
+    ns = ctypes.c_double()
+    _check(load().ising_batch_autotune(len(L), L.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                       beta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       seed.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                       hot.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), int(sweeps),
+                                       ctypes.byref(th), ctypes.byref(ch), ctypes.byref(ns)), "ising_batch_autotune")
+    return {"threads_per_tile": th.value, "graph_chunk": ch.value, "ns_per_update": ns.value}
+
+
+def load_table(path: str = TABLE) -> dict:
+    if not os.path.exists(path):
+        return {}
+    with open(path) as f:
+        return json.load(f)
+
+
+def save_table(table: dict, path: str = TABLE):
+    with open(path, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+
+
+def tune_all(Ls, sweeps: int = 20, path: str = TABLE) -> dict:
+    table = {"device": _device_name(), "lattice": {}}
+    for L in Ls:
+        table["lattice"][str(int(L))] = tune_lattice(int(L), sweeps)
+    save_table(table, path)
+    return table
+
+
+def apply(lattice, table: dict | None = None) -> bool:
+    """Set the tuned tiling/path of lattice.L if the table has one for this device."""
+    table = load_table() if table is None else table
+    entry = table.get("lattice", {}).get(str(lattice.L))
+    if not entry or table.get("device") != _device_name():
+        return False
+    lattice.set_path(entry["path"])
+    if entry["path"] == 1:
+        lattice.set_tiling(4, entry["block_words"], entry["block_groups"])
+    return True

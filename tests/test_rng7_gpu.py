@@ -1,0 +1,45 @@
+"""The opt-in 7-round Philox scheme: bit-exact with the oracle run with the
+same scheme, on the launch and on-chip paths; it differs from the default."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ising():
+    import paper_1811_04384_gb300 as p
+    p.load()
+    return p
+
+
+@pytest.mark.parametrize("L", [6, 44, 64, 130, 258])
+@pytest.mark.parametrize("path", [1, 2])
+def test_seven_rounds_match_oracle(ising, L, path):
+    beta = 0.42
+    with ising.Lattice(L, 99) as lat:
+        lat.set_rng(ising.ISING_RNG_PHILOX4X32_7)
+        if path == 2 and L > 700:
+            pytest.skip("does not fit on chip")
+        lat.set_path(path)
+        lat.init_hot()
+        lat.set_beta(beta)
+        E, M = lat.sweep_record(9, 3)
+        spins = lat.get_spins()
+    with oracle.sweep_rounds(7):
+        s = oracle.init_hot(L, 99)
+        Eo, Mo = oracle.run(s, 99, beta, 0, 9, 3)
+    np.testing.assert_array_equal(E, Eo)
+    np.testing.assert_array_equal(M, Mo)
+    np.testing.assert_array_equal(spins, s)
+    s10 = oracle.init_hot(L, 99)
+    oracle.run(s10, 99, beta, 0, 9, 3)
+    assert not np.array_equal(spins, s10)
+
+
+def test_rng_scheme_rejects_unknown(ising):
+    with ising.Lattice(64, 1) as lat:
+        with pytest.raises(ising.IsingError):
+            lat.set_rng(5)
