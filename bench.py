@@ -45,6 +45,10 @@ METRIC = "spin-updates/ns"
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 MULWIDE_PER_SM_CLK = 32         # 32x32->64 integer multiplies (IMAD.WIDE) per SM per clock
+# DRAM bytes (read + write) per half-sweep launch of the current kernel at
+# L = 16384, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum;
+# profiles/launches_large_L16384.md); None for other sizes and the 7-round scheme.
+MEASURED_TRAFFIC = {16384: 1.128e8}
 MULWIDE_PER_SITE = 4            # Philox4x32-10 with the counter-independent rounds hoisted:
                                 # 16 multiplies per call, one call per 4 sites (10 per call,
                                 # 2.5 per site, for the opt-in 7-round scheme)
@@ -485,7 +489,8 @@ def main():
                        "rng": f"Philox4x32-{args.rng}"},
             "wall_s": wall,
             "roofline": {"bound": "alu", "achieved": achieved_mul, "peak": peak_mul,
-                         "unit": "T mul.wide.u32/s", "frac": achieved_mul / peak_mul, "traffic": None,
+                         "unit": "T mul.wide.u32/s", "frac": achieved_mul / peak_mul,
+                         "traffic": MEASURED_TRAFFIC.get(L) if args.rng == 10 else None,
                          "kernel": "half_sweep_kernel",
                          "achieved_spin_updates_per_ns": sites_per_launch / half_sweep_s / 1e9,
                          "peak_spin_updates_per_ns": peak_mul * 1e12 / mul_per_site / 1e9,

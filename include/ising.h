@@ -86,6 +86,21 @@ int ising_create(int32_t L, uint64_t seed, ising_lattice **out);
 int ising_create_on(int32_t L, uint64_t seed, void *dev_buf, size_t bytes,
                     void *stream, ising_lattice **out);
 
+/* The paper's own word layout (Sec. 3, Fig. 1-2) as an alternative:
+ * ISING_LAYOUT_COLUMN_INTERLEAVED stores the lattice as N x L words,
+ * N = L / 21, word S(I, J) holding s(I + kN, J) in field k, with the
+ * one-field rotation of the neighbour word across the top and bottom word
+ * rows, and updates it with the arithmetic form of Eq. 3.  Needs L % 84 == 0
+ * (the paper's L = 21N with N divisible by 4, e.g. 1008 and 2016).  The
+ * chain, E and M are identical to the default row-packed layout
+ * (ISING_LAYOUT_ROW_PACKED), which works for any even L.  Calls that expose
+ * the row-packed words (ising_get_words, ising_set_words, ising_layout,
+ * ising_device_words, ising_set_tiling, the on-chip path) return EINVAL on
+ * an interleaved lattice. */
+#define ISING_LAYOUT_ROW_PACKED 0
+#define ISING_LAYOUT_COLUMN_INTERLEAVED 1
+int ising_create_layout(int32_t L, uint64_t seed, int32_t layout, ising_lattice **out);
+
 /* Release the handle and every device buffer the library allocated for it
  * (not a caller-owned dev_buf).  NULL is accepted. */
 int ising_destroy(ising_lattice *h);
@@ -226,6 +241,9 @@ int ising_batch_get_spins(ising_batch *b, int32_t r, int8_t *host_out, size_t n)
 /* Sweep counter of replica r. */
 int ising_batch_get_sweep(ising_batch *b, int32_t r, uint64_t *t);
 
+/* Random-number scheme of every replica (as ising_set_rng). */
+int ising_batch_set_rng(ising_batch *b, int32_t scheme);
+
 /* Threads per tile (64, 128 or 256; default 128) and sweeps per captured
  * graph (1 .. 1024; default 50).  Rebuilds the tile table.  Results do not
  * depend on either. */
@@ -258,6 +276,7 @@ typedef struct ising_job {
     int64_t *host_E;      /* caller-owned, sweeps / every entries, or NULL */
     int64_t *host_M;      /* caller-owned, sweeps / every entries, or NULL */
     int8_t *host_spins;   /* caller-owned, L*L final spins, or NULL */
+    int32_t rng;          /* ISING_RNG_PHILOX4X32_10 (0) or ISING_RNG_PHILOX4X32_7 (1) */
 } ising_job;               /* the host arrays must stay valid until the job is done */
 
 typedef struct ising_result {

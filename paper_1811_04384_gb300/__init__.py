@@ -25,6 +25,8 @@ ISING_ECUDA = -3
 ISING_ETIMEOUT = -4
 ISING_EBUSY = -5
 ISING_ENOTFOUND = -6
+ISING_LAYOUT_ROW_PACKED = 0
+ISING_LAYOUT_COLUMN_INTERLEAVED = 1
 ISING_RNG_PHILOX4X32_10 = 0
 ISING_RNG_PHILOX4X32_7 = 1
 ISING_PATH_AUTO = 0
@@ -79,13 +81,17 @@ def bytes_required(L: int) -> int:
 class Lattice:
     """One L x L lattice resident in device memory (see include/ising.h)."""
 
-    def __init__(self, L: int, seed: int, *, buffer=None, stream=None):
+    def __init__(self, L: int, seed: int, *, buffer=None, stream=None, layout: int = 0):
         lib = load()
         self.L = int(L)
         self.seed = int(seed)
         self._buffer = buffer      # keeps a caller-owned (torch) buffer alive
         h = ctypes.c_void_p()
-        if buffer is None:
+        if layout != ISING_LAYOUT_ROW_PACKED:
+            _check(lib.ising_create_layout(self.L, self.seed, int(layout), ctypes.byref(h)), "ising_create_layout")
+            if stream is not None:
+                _check(lib.ising_set_stream(h, _stream_ptr(stream)), "ising_set_stream")
+        elif buffer is None:
             _check(lib.ising_create(self.L, self.seed, ctypes.byref(h)), "ising_create")
             if stream is not None:
                 _check(lib.ising_set_stream(h, _stream_ptr(stream)), "ising_set_stream")
@@ -257,6 +263,9 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+    def set_rng(self, scheme: int):
+        _check(load().ising_batch_set_rng(self._h, int(scheme)), "ising_batch_set_rng")
 
     def set_tiling(self, threads_per_tile: int = 128, graph_chunk: int = 50):
         _check(load().ising_batch_set_tiling(self._h, threads_per_tile, graph_chunk), "ising_batch_set_tiling")

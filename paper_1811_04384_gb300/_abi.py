@@ -9,7 +9,7 @@ class IsingJob(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("beta", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("hot", ctypes.c_int32), ("sweeps", ctypes.c_int64), ("every", ctypes.c_int64),
                 ("host_E", ctypes.POINTER(ctypes.c_int64)), ("host_M", ctypes.POINTER(ctypes.c_int64)),
-                ("host_spins", ctypes.POINTER(ctypes.c_int8))]
+                ("host_spins", ctypes.POINTER(ctypes.c_int8)), ("rng", ctypes.c_int32)]
 
 
 class IsingResult(ctypes.Structure):
@@ -40,6 +40,7 @@ SYMBOLS = {
     "ising_bytes_required": (_sz, [_i32]),
     "ising_create": (_int, [_i32, _u64, _pvp]),
     "ising_create_on": (_int, [_i32, _u64, _vp, _sz, _vp, _pvp]),
+    "ising_create_layout": (_int, [_i32, _u64, _i32, _pvp]),
     "ising_destroy": (_int, [_vp]),
     "ising_init_hot": (_int, [_vp]),
     "ising_init_cold": (_int, [_vp, ctypes.c_int8]),
@@ -68,6 +69,7 @@ SYMBOLS = {
     "ising_batch_get_spins": (_int, [_vp, _i32, _pi8, _sz]),
     "ising_batch_get_sweep": (_int, [_vp, _i32, _pu64]),
     "ising_batch_set_tiling": (_int, [_vp, _i32, _i32]),
+    "ising_batch_set_rng": (_int, [_vp, _i32]),
     "ising_batch_run": (_int, [_i32, _pi32, _pd, _pu64, _pu8, _pi64, _i64, _vp, _vp, _vp]),
     "ising_server_create": (_int, [_sz, _i32, _i32, _pvp]),
     "ising_server_submit": (_int, [_vp, ctypes.POINTER(IsingJob), _pu64]),

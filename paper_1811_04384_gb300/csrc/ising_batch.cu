@@ -171,6 +171,7 @@ extern "C" int ising_batch_create(int32_t n, const int32_t* L, const double* bet
         R.rk = a.rk;
         R.thr0 = a.thr0; R.thr1 = a.thr1; R.all0 = a.all0; R.all1 = a.all1;
         R.every = 1;
+        R.rounds = 10;
         R.items = (uint32_t)((g.L + 3) / 4) * (uint32_t)g.W;
         b->h_reps.push_back(R);
     }
@@ -186,6 +187,17 @@ extern "C" int ising_batch_create(int32_t n, const int32_t* L, const double* bet
 extern "C" int ising_batch_destroy(ising_batch* b)
 {
     free_batch(b);
+    return ISING_OK;
+}
+
+extern "C" int ising_batch_set_rng(ising_batch* b, int32_t scheme)
+{
+    if (!b) return ISING_EINVAL;
+    uint32_t rounds;
+    if (scheme == ISING_RNG_PHILOX4X32_10) rounds = 10;
+    else if (scheme == ISING_RNG_PHILOX4X32_7) rounds = 7;
+    else return ISING_EINVAL;
+    for (BatchReplica& R : b->h_reps) R.rounds = rounds;
     return ISING_OK;
 }
 

@@ -20,6 +20,7 @@ struct BatchReplica {
     uint32_t phase;                 // records after sweeps s with (phase + s) % every == 0
     unsigned long long* counts;     // record k -> counts[2k], counts[2k+1] (anti, up)
     uint32_t items;                 // ceil(L/4) * W thread items
+    uint32_t rounds;                // Philox rounds of the sweep draws (10 or the opt-in 7)
 };
 
 struct BatchTile {
@@ -51,12 +52,21 @@ batch_half_sweep_kernel(const BatchReplica* __restrict__ reps, const BatchTile* 
         uint64_t* own = C == 0 ? R->w0 : R->w1;
         const uint64_t* other = C == 0 ? R->w1 : R->w0;
         const PhiloxKeys rk = R->rk;
-        if (record)
-            sweep_rows<C, true, true>(own, other, g, grp * 4, w, t, rk, R->thr0, R->thr1, R->all0, R->all1,
-                                      one, anti, up);
-        else
-            sweep_rows<C, true, false>(own, other, g, grp * 4, w, t, rk, R->thr0, R->thr1, R->all0, R->all1,
-                                       one, anti, up);
+        if (R->rounds == 7) {
+            if (record)
+                sweep_rows<C, true, true, true, 7>(own, other, g, grp * 4, w, t, rk, R->thr0, R->thr1, R->all0,
+                                                   R->all1, one, anti, up);
+            else
+                sweep_rows<C, true, false, true, 7>(own, other, g, grp * 4, w, t, rk, R->thr0, R->thr1, R->all0,
+                                                    R->all1, one, anti, up);
+        } else {
+            if (record)
+                sweep_rows<C, true, true>(own, other, g, grp * 4, w, t, rk, R->thr0, R->thr1, R->all0, R->all1,
+                                          one, anti, up);
+            else
+                sweep_rows<C, true, false>(own, other, g, grp * 4, w, t, rk, R->thr0, R->thr1, R->all0, R->all1,
+                                           one, anti, up);
+        }
     }
     if (record)
         block_add_counts(R->counts + 2 * (size_t)(ps / R->every - 1), anti, up);

@@ -14,6 +14,7 @@
 #include "../../include/ising.h"
 #include "ising_device.cuh"
 #include "ising_internal.h"
+#include "ising_interleaved.h"
 
 using namespace ising;
 
@@ -226,6 +227,7 @@ struct ising_lattice {
     int bw = 32, bg = 4;                         // half-sweep block shape
     int path = ISING_PATH_AUTO;                  // multi-block launches or on-chip resident sweeps
     int rounds = 10;                             // Philox rounds of the sweep draws
+    int layout = ISING_LAYOUT_ROW_PACKED;        // or the paper's column-interleaved words
     bool resident_attr = false;                  // dynamic shared memory attribute set
 };
 
@@ -398,6 +400,36 @@ extern "C" int ising_create(int32_t L, uint64_t seed, ising_lattice** out)
     return ISING_OK;
 }
 
+extern "C" int ising_create_layout(int32_t L, uint64_t seed, int32_t layout, ising_lattice** out)
+{
+    if (layout == ISING_LAYOUT_ROW_PACKED) return ising_create(L, seed, out);
+    if (layout != ISING_LAYOUT_COLUMN_INTERLEAVED || !out || !ci_valid_side(L)) return ISING_EINVAL;
+    *out = nullptr;
+    ising_lattice* h = new (std::nothrow) ising_lattice();
+    if (!h) return ISING_ENOMEM;
+    // one N x L array of words, then the count slots and the sweep counter
+    const size_t sb = align_up((size_t)(L / 21) * L * sizeof(uint64_t), kAlign);
+    char* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, sb + align_up(kCountBytes, kAlign) + kAlign);
+    if (e != cudaSuccess) { delete h; cuda_fail(e, "cudaMalloc"); return ISING_ENOMEM; }
+    h->owns_mem = true;
+    h->layout = layout;
+    h->g = make_geom(L);
+    h->seed = seed;
+    h->base = base;
+    h->words[0] = reinterpret_cast<uint64_t*>(base);
+    h->words[1] = nullptr;
+    h->counts = reinterpret_cast<unsigned long long*>(base + sb);
+    h->t_dev = reinterpret_cast<uint64_t*>(base + sb + align_up(kCountBytes, kAlign));
+    e = cudaMallocHost(&h->host_counts, kCountBytes);
+    if (e != cudaSuccess) { h->host_counts = nullptr; free_handle(h); return ISING_ENOMEM; }
+    thresholds_for_beta(0.0, h->thr);
+    int rc = ising_init_cold(h, 1);
+    if (rc != ISING_OK) { free_handle(h); return rc; }
+    *out = h;
+    return ISING_OK;
+}
+
 extern "C" int ising_create_on(int32_t L, uint64_t seed, void* dev_buf, size_t bytes, void* stream,
                                ising_lattice** out)
 {
@@ -436,6 +468,11 @@ extern "C" int ising_init_hot(ising_lattice* h)
 {
     TraceRange trace("ising_init_hot");
     if (!h) return ISING_EINVAL;
+    if (h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED) {
+        cudaError_t e = ci_init_hot(h->words[0], h->g.L, h->seed, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "ci_init_hot");
+        return reset_t(h, 0);
+    }
     const Geom& g = h->g;
     // zero everything first so the pitch padding is defined
     cudaError_t e = cudaMemsetAsync(h->words[0], 0, 2 * align_up(words_bytes(g), kAlign), h->stream);
@@ -452,6 +489,11 @@ extern "C" int ising_init_hot(ising_lattice* h)
 extern "C" int ising_init_cold(ising_lattice* h, int8_t spin)
 {
     if (!h || (spin != 1 && spin != -1)) return ISING_EINVAL;
+    if (h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED) {
+        cudaError_t e = ci_init_cold(h->words[0], h->g.L, spin > 0 ? 1 : 0, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "ci_init_cold");
+        return reset_t(h, 0);
+    }
     const Geom& g = h->g;
     dim3 block(32, 8);
     dim3 grid((g.P + 31) / 32, (g.L + 7) / 8);
@@ -484,6 +526,15 @@ static SweepArgs base_args(const ising_lattice* h)
     return a;
 }
 
+// One half-sweep of the handle's lattice in its layout.
+static cudaError_t launch_hs(const ising_lattice* h, int colour, bool update, bool record, const SweepArgs& a)
+{
+    if (h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED)
+        return ci_half_sweep(colour, update, record, h->words[0], h->g.L, a, h->stream);
+    return launch_half_sweep(h->bw, h->bg, colour, update, record, h->words[colour], h->words[1 - colour], h->g, a,
+                             h->stream);
+}
+
 // Run `n` sweeps relative to the device counter; sweep s (1-based) records into
 // count slot rec_of(s) when rec_of(s) >= 0.  Then advances the counter by n.
 template <typename RecOf>
@@ -493,13 +544,11 @@ static int run_sweeps(ising_lattice* h, int64_t n, RecOf rec_of)
     const Geom& g = h->g;
     for (int64_t s = 1; s <= n; ++s) {
         a.t_off = (uint32_t)s;
-        cudaError_t e = launch_half_sweep(h->bw, h->bg, 0, true, false, h->words[0], h->words[1], g,
-                                          a, h->stream);
+        cudaError_t e = launch_hs(h, 0, true, false, a);
         if (e != cudaSuccess) return cuda_fail(e, "half_sweep colour 0");
         const int rec = rec_of(s);
         a.counts = rec >= 0 ? h->counts + (size_t)rec * kCountSlots * 2 : nullptr;
-        e = launch_half_sweep(h->bw, h->bg, 1, true, rec >= 0, h->words[1], h->words[0], g, a,
-                              h->stream);
+        e = launch_hs(h, 1, true, rec >= 0, a);
         if (e != cudaSuccess) return cuda_fail(e, "half_sweep colour 1");
     }
     if (n > 0) {
@@ -515,7 +564,7 @@ static size_t resident_bytes(const Geom& g) { return 2 * (size_t)g.L * g.P * siz
 
 static bool use_resident(const ising_lattice* h)
 {
-    if (h->path == ISING_PATH_LAUNCHES) return false;
+    if (h->layout != ISING_LAYOUT_ROW_PACKED || h->path == ISING_PATH_LAUNCHES) return false;
     if (resident_bytes(h->g) > kResidentMaxBytes) return false;
     return h->path == ISING_PATH_RESIDENT || h->g.L <= kResidentAutoMaxL;
 }
@@ -566,7 +615,8 @@ extern "C" int ising_set_path(ising_lattice* h, int32_t path)
 {
     if (!h) return ISING_EINVAL;
     if (path != ISING_PATH_AUTO && path != ISING_PATH_LAUNCHES && path != ISING_PATH_RESIDENT) return ISING_EINVAL;
-    if (path == ISING_PATH_RESIDENT && resident_bytes(h->g) > kResidentMaxBytes) return ISING_EINVAL;
+    if (path == ISING_PATH_RESIDENT && (h->layout != ISING_LAYOUT_ROW_PACKED || resident_bytes(h->g) > kResidentMaxBytes))
+        return ISING_EINVAL;
     h->path = path;
     return ISING_OK;
 }
@@ -662,7 +712,7 @@ static int measure(ising_lattice* h, int64_t* E, int64_t* M)
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync counts");
     SweepArgs a = base_args(h);
     a.counts = h->counts;
-    e = launch_half_sweep(h->bw, h->bg, 1, false, true, h->words[1], h->words[0], h->g, a, h->stream);
+    e = launch_hs(h, 1, false, true, a);
     if (e != cudaSuccess) return cuda_fail(e, "measure");
     e = cudaMemcpyAsync(h->host_counts, h->counts, bytes, cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync counts");
@@ -699,10 +749,15 @@ extern "C" int ising_get_spins(ising_lattice* h, int8_t* out, size_t n)
     int rc = ensure_staging(h);
     if (rc != ISING_OK) return rc;
     const Geom& g = h->g;
-    dim3 block(32, 8);
-    dim3 grid((g.W + 31) / 32, (g.L + 7) / 8, 2);
-    unpack_kernel<<<grid, block, 0, h->stream>>>(h->words[0], h->words[1], g, h->staging);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e;
+    if (h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED) {
+        e = ci_unpack(h->words[0], g.L, h->staging, h->stream);
+    } else {
+        dim3 block(32, 8);
+        dim3 grid((g.W + 31) / 32, (g.L + 7) / 8, 2);
+        unpack_kernel<<<grid, block, 0, h->stream>>>(h->words[0], h->words[1], g, h->staging);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return cuda_fail(e, "unpack_kernel");
     e = cudaMemcpyAsync(out, h->staging, n, cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync spins");
@@ -720,10 +775,14 @@ extern "C" int ising_set_spins(ising_lattice* h, const int8_t* in, size_t n)
     const Geom& g = h->g;
     cudaError_t e = cudaMemcpyAsync(h->staging, in, n, cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync spins");
-    dim3 block(32, 8);
-    dim3 grid((g.P + 31) / 32, (g.L + 7) / 8, 2);
-    pack_kernel<<<grid, block, 0, h->stream>>>(h->words[0], h->words[1], g, h->staging);
-    e = cudaGetLastError();
+    if (h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED) {
+        e = ci_pack(h->words[0], g.L, h->staging, h->stream);
+    } else {
+        dim3 block(32, 8);
+        dim3 grid((g.P + 31) / 32, (g.L + 7) / 8, 2);
+        pack_kernel<<<grid, block, 0, h->stream>>>(h->words[0], h->words[1], g, h->staging);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return cuda_fail(e, "pack_kernel");
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
@@ -733,6 +792,7 @@ extern "C" int ising_set_spins(ising_lattice* h, const int8_t* in, size_t n)
 extern "C" int ising_get_words(ising_lattice* h, uint64_t* out, size_t n64)
 {
     if (!h || !out) return ISING_EINVAL;
+    if (h->layout != ISING_LAYOUT_ROW_PACKED) return ISING_EINVAL;   // row-packed words only
     const size_t per = (size_t)h->g.L * h->g.P;
     if (n64 != 2 * per) return ISING_EINVAL;
     for (int c = 0; c < 2; ++c) {
@@ -747,6 +807,7 @@ extern "C" int ising_get_words(ising_lattice* h, uint64_t* out, size_t n64)
 extern "C" int ising_set_words(ising_lattice* h, const uint64_t* in, size_t n64)
 {
     if (!h || !in) return ISING_EINVAL;
+    if (h->layout != ISING_LAYOUT_ROW_PACKED) return ISING_EINVAL;   // row-packed words only
     const size_t per = (size_t)h->g.L * h->g.P;
     if (n64 != 2 * per) return ISING_EINVAL;
     for (int c = 0; c < 2; ++c) {
@@ -761,6 +822,7 @@ extern "C" int ising_set_words(ising_lattice* h, const uint64_t* in, size_t n64)
 extern "C" int ising_layout(ising_lattice* h, int32_t* W, int32_t* pitch, int32_t* last_fields)
 {
     if (!h) return ISING_EINVAL;
+    if (h->layout != ISING_LAYOUT_ROW_PACKED) return ISING_EINVAL;   // row-packed words only
     if (W) *W = h->g.W;
     if (pitch) *pitch = h->g.P;
     if (last_fields) *last_fields = h->g.rlast;
@@ -790,6 +852,7 @@ extern "C" int ising_set_stream(ising_lattice* h, void* stream)
 extern "C" int ising_set_tiling(ising_lattice* h, int32_t rows, int32_t bw, int32_t bgrp)
 {
     if (!h) return ISING_EINVAL;
+    if (h->layout != ISING_LAYOUT_ROW_PACKED) return ISING_EINVAL;   // row-packed words only
     if (rows != 4) return ISING_EINVAL;
     if (bw != 16 && bw != 32 && bw != 64) return ISING_EINVAL;
     if (bgrp != 1 && bgrp != 2 && bgrp != 4 && bgrp != 8 && bgrp != 16) return ISING_EINVAL;
@@ -802,6 +865,7 @@ extern "C" int ising_set_tiling(ising_lattice* h, int32_t rows, int32_t bw, int3
 extern "C" int ising_device_words(ising_lattice* h, int32_t c, void** dev_ptr)
 {
     if (!h || !dev_ptr || (c != 0 && c != 1)) return ISING_EINVAL;
+    if (h->layout != ISING_LAYOUT_ROW_PACKED) return ISING_EINVAL;   // row-packed words only
     *dev_ptr = h->words[c];
     return ISING_OK;
 }

@@ -137,6 +137,7 @@ int valid_job(const ising_job* j)
     if (!j || !valid_side(j->L)) return 0;
     if (std::isnan(j->beta) || j->beta < 0.0) return 0;
     if (j->sweeps < 1 || j->sweeps > 0x7fffffff || j->every < 1 || j->every > 0x7fffffff) return 0;
+    if (j->rng != ISING_RNG_PHILOX4X32_10 && j->rng != ISING_RNG_PHILOX4X32_7) return 0;
     return 1;
 }
 
@@ -430,6 +431,7 @@ extern "C" int ising_server_submit(ising_server* s, const ising_job* job, uint64
     j.rep.rk = a.rk;
     j.rep.thr0 = a.thr0; j.rep.thr1 = a.thr1; j.rep.all0 = a.all0; j.rep.all1 = a.all1;
     j.rep.items = (uint32_t)((j.g.L + 3) / 4) * (uint32_t)j.g.W;
+    j.rep.rounds = job->rng == ISING_RNG_PHILOX4X32_7 ? 7 : 10;
     {
         std::lock_guard<std::mutex> lock(s->mu);
         if (s->stop) return ISING_EBUSY;

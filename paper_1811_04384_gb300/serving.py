@@ -20,8 +20,9 @@ STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "cancelled"}
 class Request:
     """One job and its caller-owned result arrays (kept alive until done)."""
 
-    def __init__(self, L, beta, seed, sweeps, every=1, hot=True, want_spins=False):
+    def __init__(self, L, beta, seed, sweeps, every=1, hot=True, want_spins=False, rng=0):
         self.L, self.beta, self.seed = int(L), float(beta), int(seed)
+        self.rng = int(rng)
         self.sweeps, self.every, self.hot = int(sweeps), int(every), bool(hot)
         self.E = np.zeros(self.sweeps // self.every, dtype=np.int64)
         self.M = np.zeros(self.sweeps // self.every, dtype=np.int64)
@@ -33,7 +34,8 @@ class Request:
         return IsingJob(self.L, self.beta, self.seed, 1 if self.hot else 0, self.sweeps, self.every,
                         self.E.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                         self.M.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                        self.spins.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)) if self.spins is not None else None)
+                        self.spins.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)) if self.spins is not None else None,
+                        self.rng)
 
 
 class Server:

@@ -43,3 +43,27 @@ def test_rng_scheme_rejects_unknown(ising):
     with ising.Lattice(64, 1) as lat:
         with pytest.raises(ising.IsingError):
             lat.set_rng(5)
+
+
+def test_seven_rounds_in_batches_and_served_jobs(ising):
+    from paper_1811_04384_gb300 import serving
+    Ls, betas, seeds = [32, 64, 130], [0.3, 0.44, 0.6], [4, 5, 6]
+    with ising.Batch(Ls, betas, seeds, [1, 1, 1]) as b:
+        b.set_rng(ising.ISING_RNG_PHILOX4X32_7)
+        E, M = b.sweep(11, every=1)
+        spins = [b.get_spins(r) for r in range(3)]
+    reqs = [serving.Request(L, be, s, 11, 1, rng=ising.ISING_RNG_PHILOX4X32_7, want_spins=True)
+            for L, be, s in zip(Ls, betas, seeds)]
+    with serving.Server(64 << 20, max_jobs=4, epoch_sweeps=4) as srv:
+        for r in reqs:
+            srv.submit(r)
+        for r in reqs:
+            assert srv.wait(r.id).status == 0
+    for r, (L, be, s) in enumerate(zip(Ls, betas, seeds)):
+        with oracle.sweep_rounds(7):
+            so = oracle.init_hot(L, s)
+            Eo, Mo = oracle.run(so, s, be, 0, 11, 1)
+        np.testing.assert_array_equal(E[r], Eo)
+        np.testing.assert_array_equal(spins[r], so)
+        np.testing.assert_array_equal(reqs[r].E, Eo)
+        np.testing.assert_array_equal(reqs[r].spins, so)
