@@ -485,7 +485,7 @@ def main():
                                     "E/M every 10 sweeps; step = 10 sweeps + E/M record"),
                        "L": L, "sweeps_per_step": SWEEPS_PER_STEP, "parallelism": f"replicas x{world}",
                        "l2": "flushed between steps (256 MB write; lattice 103 MB < L2)",
-                       "tiling": args.tiling or "default 4,32,4",
+                       "tiling": args.tiling or "default 4,16,8",
                        "rng": f"Philox4x32-{args.rng}"},
             "wall_s": wall,
             "roofline": {"bound": "alu", "achieved": achieved_mul, "peak": peak_mul,

@@ -163,7 +163,7 @@ int ising_set_stream(ising_lattice *h, void *stream);
 /* Launch shape of the half-sweep kernels: rows_per_thread must be 4 (one
  * Philox call serves four rows); block_words (threads along a row) in
  * {16, 32, 64}; block_groups (threads down the columns) in {1, 2, 4, 8, 16};
- * 32 <= block_words * block_groups <= 256.  Default 4, 32, 4.  Results do
+ * 32 <= block_words * block_groups <= 256.  Default 4, 16, 8.  Results do
  * not depend on the shape (the draws are keyed by site). */
 int ising_set_tiling(ising_lattice *h, int32_t rows_per_thread,
                      int32_t block_words, int32_t block_groups);

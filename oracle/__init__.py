@@ -56,6 +56,9 @@ def _load():
             "ora_philox4x64_10": (None, [u64p, u64p, u64p]),
             "ora_philox4x32_r": (None, [u32p, u32p, ctypes.c_int, u32p]),
             "ora_set_sweep_rounds": (None, [ctypes.c_int]),
+            "ora_half_sweep_rows": (None, [ctypes.c_int, i8p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                           u64p, ctypes.c_int, ctypes.c_int]),
+            "ora_philox4x32_10_many": (None, [ctypes.c_int64, u32p, u32p, u32p]),
             "ora_site_draw_r": (ctypes.c_uint32, [ctypes.c_uint64, ctypes.c_uint64,
                                                   ctypes.c_int, ctypes.c_int, ctypes.c_int]),
             "ora_site_draw": (ctypes.c_uint32, [ctypes.c_uint64, ctypes.c_uint64,
@@ -96,6 +99,25 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     _load().ora_philox4x32_10(_ptr(c, ctypes.c_uint32), _ptr(k, ctypes.c_uint32),
                               _ptr(out, ctypes.c_uint32))
     return out
+
+
+def philox4x32_10_many(ctr, key) -> np.ndarray:
+    """Philox4x32-10 blocks of n counters (n x 4 uint32)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros_like(c)
+    _load().ora_philox4x32_10_many(c.shape[0], _ptr(c, ctypes.c_uint32), _ptr(k, ctypes.c_uint32),
+                                   _ptr(out, ctypes.c_uint32))
+    return out
+
+
+def half_sweep_rows(s: np.ndarray, seed: int, t: int, c: int, beta: float, i0: int, i1: int) -> None:
+    """Update colour c at sweep t in rows i0..i1-1 only (rows i0-1 and i1 are
+    read as halos): one strip of a row-strip partition (Sec. 4)."""
+    L = s.shape[0]
+    _check(L, s)
+    thr = np.array(thresholds(beta), dtype=np.uint64)
+    _load().ora_half_sweep_rows(L, _ptr(s, ctypes.c_int8), seed, t, c, _ptr(thr, ctypes.c_uint64), i0, i1)
 
 
 def philox4x32_r(ctr, key, rounds: int) -> np.ndarray:

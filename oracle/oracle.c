@@ -237,6 +237,33 @@ void ora_half_sweep(int L, int8_t *s, uint64_t seed, uint64_t t, int c,
         }
 }
 
+/* The same update restricted to rows i0 .. i1-1 (a strip of a row-strip
+ * partition, Sec. 4): it reads rows i0-1 and i1 as halo rows. */
+void ora_half_sweep_rows(int L, int8_t *s, uint64_t seed, uint64_t t, int c,
+                         const uint64_t thr[2], int i0, int i1)
+{
+    for (int i = i0; i < i1; ++i)
+        for (int j = 0; j < L; ++j) {
+            if (((i + j) & 1) != c)
+                continue;
+            int a = ora_group_value(L, s, i, j);
+            int flip = 1;
+            if (a < 2) {
+                uint32_t r = ora_site_draw_r(seed, t, i, j, g_sweep_rounds);
+                flip = ((uint64_t)r < thr[a]);
+            }
+            if (flip)
+                s[i * L + j] = (int8_t)(-s[i * L + j]);
+        }
+}
+
+/* Many Philox4x32-10 blocks: out[4k..4k+3] = Philox(ctr[4k..4k+3], key). */
+void ora_philox4x32_10_many(int64_t n, const uint32_t *ctr, const uint32_t key[2], uint32_t *out)
+{
+    for (int64_t k = 0; k < n; ++k)
+        ora_philox4x32_10(ctr + 4 * k, key, out + 4 * k);
+}
+
 void ora_sweep(int L, int8_t *s, uint64_t seed, uint64_t t, double beta, int64_t *stats)
 {
     uint64_t thr[2];

@@ -224,7 +224,7 @@ struct ising_lattice {
     uint64_t* t_dev = nullptr;
     int8_t* staging = nullptr;   // lazily allocated int8 L*L (get/set spins)
     unsigned long long* host_counts = nullptr;   // pinned, kCountBytes
-    int bw = 32, bg = 4;                         // half-sweep block shape
+    int bw = 16, bg = 8;                         // half-sweep block shape (autotuned at L = 16384)
     int path = ISING_PATH_AUTO;                  // multi-block launches or on-chip resident sweeps
     int rounds = 10;                             // Philox rounds of the sweep draws
     int layout = ISING_LAYOUT_ROW_PACKED;        // or the paper's column-interleaved words

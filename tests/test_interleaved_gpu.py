@@ -1,0 +1,95 @@
+"""The paper's column-interleaved word layout (Sec. 3): N x L words, word
+S(I, J) holding s(I + kN, J), one-field rotation across the top and bottom
+word rows, Eq. 3 in arithmetic form.  Same chain as the row-packed layout, so
+spins and E/M are bit-exact with the oracle and with the default layout."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ising():
+    import paper_1811_04384_gb300 as p
+    p.load()
+    return p
+
+
+def interleaved(ising, L, seed):
+    return ising.Lattice(L, seed, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED)
+
+
+@pytest.mark.parametrize("L", [84, 168, 252])
+def test_interleaved_matches_oracle(ising, L):
+    beta = 0.41
+    with interleaved(ising, L, 5 + L) as lat:
+        lat.init_hot()
+        np.testing.assert_array_equal(lat.get_spins(), oracle.init_hot(L, 5 + L))
+        lat.set_beta(beta)
+        E, M = lat.sweep_record(12, 2)
+        spins = lat.get_spins()
+        e_now, m_now = lat.energy(), lat.magnetization()
+    s = oracle.init_hot(L, 5 + L)
+    Eo, Mo = oracle.run(s, 5 + L, beta, 0, 12, 2)
+    np.testing.assert_array_equal(E, Eo)
+    np.testing.assert_array_equal(M, Mo)
+    np.testing.assert_array_equal(spins, s)
+    assert e_now == oracle.energy(s) and m_now == oracle.magnetization(s)
+
+
+@pytest.mark.parametrize("L", [1008, 2016])
+def test_paper_sizes_equal_row_packed(ising, L):
+    """The paper's lattice sizes (N = 48 and 96 word rows)."""
+    with interleaved(ising, L, 11) as a, ising.Lattice(L, 11) as b:
+        for lat in (a, b):
+            lat.init_hot()
+            lat.set_beta(1.0 / 2.269)
+        Ea, Ma = a.sweep_record(20, 1)
+        Eb, Mb = b.sweep_record(20, 1)
+        np.testing.assert_array_equal(Ea, Eb)
+        np.testing.assert_array_equal(Ma, Mb)
+        np.testing.assert_array_equal(a.get_spins(), b.get_spins())
+    if L == 1008:
+        s = oracle.init_hot(L, 11)
+        Eo, _ = oracle.run(s, 11, 1.0 / 2.269, 0, 20, 1)
+        np.testing.assert_array_equal(Ea, Eo)
+
+
+def test_interleaved_spin_io_cold_start_and_seven_rounds(ising):
+    L = 168
+    rng = np.random.default_rng(2)
+    s = np.where(rng.random((L, L)) < 0.3, 1, -1).astype(np.int8)
+    with interleaved(ising, L, 3) as lat:
+        assert lat.energy() == -2 * L * L and lat.magnetization() == L * L   # created cold +1
+        lat.set_spins(s)
+        np.testing.assert_array_equal(lat.get_spins(), s)
+        assert lat.energy() == oracle.energy(s)
+        lat.init_cold(-1)
+        assert lat.magnetization() == -L * L
+        lat.init_hot()
+        lat.set_rng(ising.ISING_RNG_PHILOX4X32_7)
+        lat.set_beta(0.5)
+        E, M = lat.sweep_record(6, 3)
+        got = lat.get_spins()
+    with oracle.sweep_rounds(7):
+        so = oracle.init_hot(L, 3)
+        Eo, Mo = oracle.run(so, 3, 0.5, 0, 6, 3)
+    np.testing.assert_array_equal(E, Eo)
+    np.testing.assert_array_equal(got, so)
+
+
+def test_interleaved_rejects_sizes_and_row_packed_calls(ising):
+    for bad in (42, 126, 170, 0):
+        with pytest.raises(ising.IsingError):
+            interleaved(ising, bad, 1)
+    with interleaved(ising, 84, 1) as lat:
+        with pytest.raises(ising.IsingError):
+            lat.get_words()
+        with pytest.raises(ising.IsingError):
+            lat.layout()
+        with pytest.raises(ising.IsingError):
+            lat.set_path(ising.ISING_PATH_RESIDENT)
+        with pytest.raises(ising.IsingError):
+            lat.set_tiling(4, 32, 4)

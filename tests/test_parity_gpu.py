@@ -61,6 +61,17 @@ def test_philox_blocks_match_oracle(ising):
             np.testing.assert_array_equal(got[k], oracle.philox4x32_10(ctr[k], key))
 
 
+def test_philox_million_counters(ising):
+    """10^6 counters with all four words varying, including the carry edges."""
+    rng = np.random.default_rng(11)
+    ctr = rng.integers(0, 2**32, size=(1_000_000, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:4] = [[0xFFFFFFFF] * 4, [0, 0, 0, 0], [0xFFFFFFFF, 0, 0xFFFFFFFF, 0], [1, 1, 1, 1]]
+    for seed in (3, 0xFFFFFFFFFFFFFFFF):
+        got = ising.philox_blocks(seed, ctr)
+        ref = oracle.philox4x32_10_many(ctr, [seed & 0xFFFFFFFF, seed >> 32])
+        np.testing.assert_array_equal(got, ref)
+
+
 def test_thresholds_match_oracle(ising):
     betas = [0.0, 1e-300, 1e-17, 1e-16, 0.1, 0.25, BETA_TC, 0.5, 1.0, 2.0,
              32 * math.log(2) / 8 * (1 - 1e-12), 32 * math.log(2) / 8 * (1 + 1e-12),
