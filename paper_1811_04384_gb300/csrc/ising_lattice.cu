@@ -581,12 +581,13 @@ static int run_resident(ising_lattice* h, int n, int every)
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(resident_sweeps_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kResidentMaxBytes);
+
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
         h->resident_attr = true;
     }
     const int items = ((g.L + 3) / 4) * g.W;
-    const int threads = std::min(256, std::max(32, (items + 31) / 32 * 32));
     SweepArgs a = base_args(h);
+    const int threads = std::min(256, std::max(32, (items + 31) / 32 * 32));
     if (a.rounds == 7)
         resident_sweeps_kernel<7><<<1, threads, bytes, h->stream>>>(h->words[0], h->words[1], g, a, h->t, n, every,
                                                                     reinterpret_cast<long long*>(h->counts));
