@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the plain-vs-batched comparison")
     ap.add_argument("--tiling", default=None, help="rows,block_words,block_groups")
     ap.add_argument("--L", type=int, default=L_LARGE, help="lattice side (profiling of a smaller case)")
     ap.add_argument("--workload", default="large", choices=["large", "plain", "scan", "batched", "serving"],
@@ -220,6 +221,40 @@ def whole_job_rate(units_per_rank, world, seconds):
 
 def emit(line):
     print(json.dumps(line), flush=True)
+
+
+def batched_summary(ising, sweeps=5000, instances=32):
+    """The batched configuration in one batch, and the same replicas (first
+    `instances`) as per-instance ising_sweep_record calls, bit-compared."""
+    import numpy as np
+    import torch
+    Ls, betas, seeds = batched_replicas()
+    n = len(Ls)
+    with ising.Batch([32], [0.4], [1], [1]) as warm:
+        warm.sweep([10], every=1)
+    b = ising.Batch(Ls, betas, seeds, np.ones(n, dtype=np.uint8))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E, M = b.sweep(sweeps, every=1)
+    dt_b = time.perf_counter() - t0
+    b.close()
+    exact = True
+    upd_k = 0.0
+    t0 = time.perf_counter()
+    for r in range(instances):
+        with ising.Lattice(int(Ls[r]), int(seeds[r])) as lat:
+            lat.init_hot()
+            lat.set_beta(float(betas[r]))
+            Ep, Mp = lat.sweep_record(sweeps, 1)
+        exact &= bool(np.array_equal(Ep, E[r]) and np.array_equal(Mp, M[r]))
+        upd_k += float(Ls[r]) ** 2 * sweeps
+    dt_p = time.perf_counter() - t0
+    v_b = float(np.sum(Ls.astype(np.float64) ** 2)) * sweeps / (dt_b * 1e9)
+    v_p = upd_k / (dt_p * 1e9)
+    return {"value": v_b, "unit": METRIC, "replicas": n, "sweeps": sweeps,
+            "per_instance_value": v_p, "per_instance_replicas": instances,
+            "batched_over_per_instance": v_b / v_p, "bit_exact": exact,
+            "timing": "wall clock around ising_batch_sweep / each ising_sweep_record (both synchronise)"}
 
 
 def run_batched(args, ising, local):
@@ -482,6 +517,12 @@ def main():
                "h2d_bytes_per_step": L * L, "d2h_bytes_per_step": 32 * 16, "steps": n_e2e,
                "path": "ising_set_spins (pinned int8 L*L) + ising_sweep_record(10, 10) per step"}
 
+    # plain vs batched: the batched configuration (512 uneven replicas, one
+    # launch per colour, CUDA graph) against per-instance calls on a sample
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batched:
+        batched = batched_summary(ising, sweeps=5000, instances=32)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt = oracle_sample(L, 1, BETA, SEED_LARGE)
@@ -514,6 +555,7 @@ def main():
                          "hbm_frac": hbm_bytes_per_launch / half_sweep_s / 1e9 / hbm_peak},
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "batched": batched,
             "clocks": cs,
             "gpu_launches": args.steps * launches_per_step,
             "E_last": E_series[-1], "M_last": M_series[-1],

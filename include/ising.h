@@ -106,10 +106,12 @@ int ising_create_layout(int32_t L, uint64_t seed, int32_t layout, ising_lattice 
 int ising_destroy(ising_lattice *h);
 
 /* Hot start (Sec. 5.1: every spin up or down at random): s(i,j) = +1 iff the
- * site's Philox draw at t = 0 is below 2^31.  Resets t to 0. */
+ * site's Philox draw at t = 0 is below 2^31.  Resets t to 0.  Asynchronous on
+ * the stream.  Errors: EINVAL (NULL), ECUDA. */
 int ising_init_hot(ising_lattice *h);
 
-/* Cold start: every spin = `spin` (+1 or -1, else EINVAL).  Resets t to 0. */
+/* Cold start: every spin = `spin` (+1 or -1, else EINVAL).  Resets t to 0.
+ * Asynchronous on the stream.  Errors: EINVAL, ECUDA. */
 int ising_init_cold(ising_lattice *h, int8_t spin);
 
 /* Set the inverse temperature (Sec. 2 step 3: acceptance exp(-beta dE)).
@@ -121,23 +123,29 @@ int ising_set_beta(ising_lattice *h, double beta);
  * host_thr[1] = thr for a = 1 (dE = 4); each in [0, 2^32]. */
 int ising_get_thresholds(ising_lattice *h, uint64_t host_thr[2]);
 
-/* Run n >= 0 full sweeps t+1 .. t+n (t += n).  Asynchronous on the stream. */
+/* Run n >= 0 full sweeps t+1 .. t+n (t += n).  A sweep is the paper's Monte
+ * Carlo iteration (Sec. 2: every spin proposed once), in checkerboard order:
+ * all colour-0 sites, then all colour-1 sites.  Asynchronous on the stream.
+ * Errors: EINVAL (NULL, n < 0), ECUDA. */
 int ising_sweep(ising_lattice *h, int64_t n);
 
 /* Run n sweeps and record E and M after sweeps t+every, t+2*every, ...:
  * host_E and host_M (caller-owned host arrays) receive n / every entries
- * each; either may be NULL.  n >= 0, every >= 1.  Synchronises the stream.
+ * each; either may be NULL.  n >= 0, 1 <= every <= 2^22.  Synchronises the stream.
  * The counts come from the reduction fused into the colour-1 half-sweep. */
 int ising_sweep_record(ising_lattice *h, int64_t n, int64_t every,
                        int64_t *host_E, int64_t *host_M);
 
-/* Current energy (Eq. 1, Sec. 5.3) / magnetisation, exact.  Synchronises. */
+/* Current energy (Eq. 1, Sec. 5.3) / magnetisation, exact.  Synchronises.
+ * Errors: EINVAL (NULL), ECUDA. */
 int ising_energy(ising_lattice *h, int64_t *host_E);
 int ising_magnetization(ising_lattice *h, int64_t *host_M);
 
 /* Copy the spins to / from a caller-owned host array of n = L*L int8 values,
  * row-major s[i*L + j], each +1 or -1 (set: any value > 0 counts as +1).
- * Packing and unpacking run on the device.  n != L*L -> EINVAL.
+ * Packing and unpacking run on the device through an int8 L*L staging
+ * buffer that the library allocates on first use (also for ising_create_on
+ * lattices) and frees in ising_destroy.  n != L*L -> EINVAL.
  * Synchronises.  Neither changes t. */
 int ising_get_spins(ising_lattice *h, int8_t *host_out, size_t n);
 int ising_set_spins(ising_lattice *h, const int8_t *host_in, size_t n);
@@ -257,7 +265,7 @@ int ising_batch_run(int32_t n, const int32_t *L, const double *beta, const uint6
                     int64_t **host_E, int64_t **host_M, int8_t **final_spins);
 
 /* ---- Serving: continuous batching of simulation jobs -----------------------
- * A server owns a fixed device arena (its HBM budget) and a worker thread.
+ * The paper has no counterpart: it runs one lattice per MPI job.  A server owns a fixed device arena (its HBM budget) and a worker thread.
  * Jobs (L, beta, seed, start, sweeps) are admitted in arrival order while a
  * slot and arena space are free; every admitted job advances in epochs of
  * the batched half-sweep together with all other running jobs, so jobs that
@@ -323,7 +331,7 @@ int ising_server_stats(ising_server *srv, int64_t *jobs_done, double *spin_updat
 int ising_server_destroy(ising_server *srv);
 
 /* ---- Autotuning ---------------------------------------------------------
- * Time the candidate launch shapes on the current device and return the
+ * No counterpart in the paper.  Time the candidate launch shapes on the current device and return the
  * fastest.  Every candidate must leave a bit-identical lattice (the draws are
  * keyed by site, not by thread); a difference returns ISING_ECUDA.  The
  * caller applies the choice (ising_set_tiling / ising_set_path,

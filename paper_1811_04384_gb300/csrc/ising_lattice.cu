@@ -660,10 +660,10 @@ static void counts_to_EM(const ising_lattice* h, const unsigned long long* slots
 extern "C" int ising_sweep_record(ising_lattice* h, int64_t n, int64_t every, int64_t* E, int64_t* M)
 {
     TraceRange trace("ising_sweep_record");
-    if (!h || n < 0 || every < 1) return ISING_EINVAL;
+    if (!h || n < 0 || every < 1 || every > (1 << 22)) return ISING_EINVAL;   // a chunk's offsets fit 32 bits
     const int64_t nrec = n / every;
     int64_t done_rec = 0;
-    if (use_resident(h) && every <= (1 << 20)) {
+    if (use_resident(h)) {
         while (done_rec < nrec) {
             const int64_t chunk = std::min<int64_t>(nrec - done_rec, kRecordsPerChunk);
             int rc = run_resident(h, (int)(chunk * every), (int)every);

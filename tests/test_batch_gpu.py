@@ -92,3 +92,29 @@ def test_batch_rejects_bad_arguments(ising):
             b.set_tiling(96, 10)
         with pytest.raises(ising.IsingError):
             b.sweep([-1])
+
+
+def test_batched_configuration_at_full_size(ising):
+    """All 512 replicas of the batched configuration (L on {32..2048}, T on
+    [1.5, 3.5], seed 11), 8 sweeps with E/M every sweep: every replica equals
+    its single-lattice run; replicas up to L = 128 also equal the oracle."""
+    import bench
+    Ls, betas, seeds = bench.batched_replicas()
+    n = len(Ls)
+    sweeps = 8
+    with ising.Batch(Ls, betas, seeds, np.ones(n, dtype=np.uint8)) as b:
+        E, M = b.sweep(sweeps, every=1)
+        checked_oracle = 0
+        for r in range(n):
+            Ep, Mp, Sp = plain_run(ising, int(Ls[r]), float(betas[r]), int(seeds[r]), 1, sweeps, 1)
+            np.testing.assert_array_equal(E[r], Ep)
+            np.testing.assert_array_equal(M[r], Mp)
+            if r % 16 == 0:
+                np.testing.assert_array_equal(b.get_spins(r), Sp)
+            if Ls[r] <= 128 and checked_oracle < 12:
+                s = oracle.init_hot(int(Ls[r]), int(seeds[r]))
+                Eo, Mo = oracle.run(s, int(seeds[r]), float(betas[r]), 0, sweeps, 1)
+                np.testing.assert_array_equal(E[r], Eo)
+                np.testing.assert_array_equal(M[r], Mo)
+                checked_oracle += 1
+        assert checked_oracle == 12
