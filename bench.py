@@ -257,6 +257,16 @@ def batched_summary(ising, sweeps=5000, instances=32):
             "timing": "wall clock around ising_batch_sweep / each ising_sweep_record (both synchronise)"}
 
 
+BATCH_LANES = 4      # ising_batch default: independent graph branches
+
+
+def batch_launches(n_replicas: int, sweeps: int, chunk: int = 50) -> int:
+    """Kernels one ising_batch_sweep launches: two half-sweeps per sweep per
+    non-empty lane, one chunk-counter advance per replayed graph."""
+    lanes = min(BATCH_LANES, n_replicas)
+    return 2 * sweeps * lanes + (sweeps + chunk - 1) // chunk
+
+
 def run_batched(args, ising, local):
     import numpy as np
     import torch
@@ -296,7 +306,7 @@ def run_batched(args, ising, local):
                            "path": "one ising_lattice per replica, ising_sweep_record(sweeps, 1)",
                            "bit_exact_vs_batched": exact},
           "batched_over_per_instance": (updates / dt_b) / (upd_k / dt_p),
-          "clocks": clocks.summary(), "gpu_launches": 2 * sweeps + (sweeps + 49) // 50})
+          "clocks": clocks.summary(), "gpu_launches": batch_launches(n, sweeps)})
 
 
 def run_scan(args, ising, local):
@@ -326,7 +336,8 @@ def run_scan(args, ising, local):
           "vs_baseline": None, "dtype": "u64", "data": "synthetic",
           "config": {"workload": f"scan: L={L}, T=1.0..3.5 step 0.1 ({n} replicas in one batch), cold start, "
                                  f"seed 7, {therm}+{meas} sweeps, E/M every measured sweep"},
-          "per_T": per_T, "clocks": clocks.summary()})
+          "per_T": per_T, "clocks": clocks.summary(),
+          "gpu_launches": batch_launches(n, therm) + batch_launches(n, meas)})
 
 
 def run_serving(args, ising, local):

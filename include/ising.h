@@ -257,6 +257,15 @@ int ising_batch_set_rng(ising_batch *b, int32_t scheme);
  * depend on either. */
 int ising_batch_set_tiling(ising_batch *b, int32_t threads_per_tile, int32_t graph_chunk);
 
+/* Lanes (1 .. 8; default 2): the replicas are split, largest first, into
+ * `lanes` groups of about equal work (sum of L^2), and each group is an
+ * independent branch of the captured graph, so the blocks of one lane can
+ * fill SMs that another lane's last wave of blocks leaves idle.  No
+ * counterpart in the paper (it is a scheduling choice).  Synchronises the
+ * batch's stream and rebuilds the tile table.  Results do not depend on it.
+ * Errors: EINVAL (lanes out of range), ENOMEM, ECUDA. */
+int ising_batch_set_lanes(ising_batch *b, int32_t lanes);
+
 /* One call (the batch entry of the C ABI): create, sweep, copy each
  * replica's final spins to final_spins[r] (host arrays of L[r]^2 int8; the
  * array or any entry may be NULL), destroy. */
@@ -345,10 +354,11 @@ int ising_autotune(int32_t L, int32_t sweeps, int32_t *best_block_words, int32_t
                    int32_t *best_path, double *ns_per_update);
 
 /* Batch (arguments as ising_batch_create): threads per tile {64, 128, 256}
- * x graph chunk {10, 50, 200}, `sweeps` timed sweeps per replica. */
+ * x graph chunk {10, 50, 200} x lanes {1, 2, 4}, `sweeps` timed sweeps per
+ * replica.  Outputs may be NULL. */
 int ising_batch_autotune(int32_t n, const int32_t *L, const double *beta, const uint64_t *seed,
                          const uint8_t *hot, int64_t sweeps, int32_t *best_threads, int32_t *best_chunk,
-                         double *ns_per_update);
+                         int32_t *best_lanes, double *ns_per_update);
 
 /* ---- Allocation-free record path ----------------------------------------
  * The paper has no counterpart to this entry point.  It is for callers that

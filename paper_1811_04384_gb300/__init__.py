@@ -270,6 +270,10 @@ class Batch:
     def set_tiling(self, threads_per_tile: int = 128, graph_chunk: int = 50):
         _check(load().ising_batch_set_tiling(self._h, threads_per_tile, graph_chunk), "ising_batch_set_tiling")
 
+    def set_lanes(self, lanes: int = 4):
+        """Independent graph branches the replicas are split into (1..8)."""
+        _check(load().ising_batch_set_lanes(self._h, int(lanes)), "ising_batch_set_lanes")
+
     def sweep(self, sweeps, every: int = 1, record: bool = True):
         """Replica r runs sweeps[r] sweeps; returns lists of int64 E and M arrays
         (sweeps[r] // every entries each), or None if record is False."""

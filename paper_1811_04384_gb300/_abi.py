@@ -70,6 +70,7 @@ SYMBOLS = {
     "ising_batch_get_sweep": (_int, [_vp, _i32, _pu64]),
     "ising_batch_set_tiling": (_int, [_vp, _i32, _i32]),
     "ising_batch_set_rng": (_int, [_vp, _i32]),
+    "ising_batch_set_lanes": (_int, [_vp, _i32]),
     "ising_batch_run": (_int, [_i32, _pi32, _pd, _pu64, _pu8, _pi64, _i64, _vp, _vp, _vp]),
     "ising_server_create": (_int, [_sz, _i32, _i32, _pvp]),
     "ising_server_submit": (_int, [_vp, ctypes.POINTER(IsingJob), _pu64]),
@@ -80,7 +81,7 @@ SYMBOLS = {
     "ising_server_stats": (_int, [_vp, _pi64, _pd, _pi64, _pd]),
     "ising_server_destroy": (_int, [_vp]),
     "ising_autotune": (_int, [_i32, _i32, _pi32, _pi32, _pi32, _pd]),
-    "ising_batch_autotune": (_int, [_i32, _pi32, _pd, _pu64, _pu8, _i64, _pi32, _pi32, _pd]),
+    "ising_batch_autotune": (_int, [_i32, _pi32, _pd, _pu64, _pu8, _i64, _pi32, _pi32, _pi32, _pd]),
     "ising_sweep_record_noalloc": (_int, [_vp, _vp, _i32, _u64, _dbl, _u64, _i64, _i64, _pi64, _pi64, _vp]),
 }
 

@@ -1,7 +1,10 @@
 // Batches of independent replicas (uneven L, own beta and seed) swept in
-// lockstep: one kernel launch per colour covers every replica, its blocks
-// being tiles of the replicas listed in a tile table; a chunk of sweeps is
-// captured once into a CUDA graph and replayed.  Contract: include/ising.h.
+// lockstep: one kernel launch per colour covers every replica of a lane, its
+// blocks being tiles of the replicas listed in a tile table; a chunk of
+// sweeps is captured once into a CUDA graph and replayed.  The replicas are
+// split into lanes of about equal work, and each lane is an independent
+// branch of the graph, so the blocks of one lane fill the SMs that the last
+// wave of another leaves idle.  Contract: include/ising.h.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,6 +22,7 @@ using namespace ising;
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int kMaxLanes = 8;
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
@@ -37,6 +41,12 @@ struct ising_batch {
     int ntiles = 0;
     int threads = 128;
     int chunk = 50;
+    int lanes = 4;
+    int lane_tile0[kMaxLanes] = {};         // first tile of each lane in d_tiles
+    int lane_ntiles[kMaxLanes] = {};
+    cudaStream_t lane_stream[kMaxLanes] = {};   // lane 0 runs on `stream`
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[kMaxLanes] = {};
     uint32_t* d_chunk_base = nullptr;
     unsigned long long* d_counts = nullptr;
     size_t counts_cap = 0;                  // in 64-bit words
@@ -48,6 +58,7 @@ struct ising_batch {
     cudaGraphExec_t graph = nullptr;        // captured chunk of sweeps
     int graph_chunk = 0;
     int graph_threads = 0;
+    int graph_lanes = 0;
 };
 
 namespace {
@@ -64,22 +75,42 @@ void free_batch(ising_batch* b)
     cudaFree(b->d_counts);
     cudaFree(b->staging);
     if (b->h_counts) cudaFreeHost(b->h_counts);
+    for (int k = 0; k < kMaxLanes; ++k) {
+        if (b->lane_stream[k]) cudaStreamDestroy(b->lane_stream[k]);
+        if (b->join[k]) cudaEventDestroy(b->join[k]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
 
-// Tile table: every replica's items cut into blocks of `threads`, largest
-// replicas first.
+// Lanes and tile table.  Replicas, largest first, go to the lane with the
+// least work so far (L^2 each); each lane's tiles are contiguous in the
+// table, every replica's items cut into blocks of `threads`.
 int build_tiles(ising_batch* b)
 {
     std::vector<int> order(b->n);
     for (int r = 0; r < b->n; ++r) order[r] = r;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->geom[x].L > b->geom[y].L; });
-    std::vector<BatchTile> tiles;
+    std::vector<int> lane_of(b->n, 0);
+    double work[kMaxLanes] = {};
     for (int r : order) {
-        const Geom& g = b->geom[r];
-        const uint32_t items = (uint32_t)((g.L + 3) / 4) * (uint32_t)g.W;
-        for (uint32_t f = 0; f < items; f += (uint32_t)b->threads) tiles.push_back({r, (int)f});
+        int best = 0;
+        for (int k = 1; k < b->lanes; ++k)
+            if (work[k] < work[best]) best = k;
+        lane_of[r] = best;
+        work[best] += (double)b->geom[r].L * b->geom[r].L;
+    }
+    std::vector<BatchTile> tiles;
+    for (int k = 0; k < kMaxLanes; ++k) {
+        b->lane_tile0[k] = (int)tiles.size();
+        for (int r : order) {
+            if (k >= b->lanes || lane_of[r] != k) continue;
+            const Geom& g = b->geom[r];
+            const uint32_t items = (uint32_t)((g.L + 3) / 4) * (uint32_t)g.W;
+            for (uint32_t f = 0; f < items; f += (uint32_t)b->threads) tiles.push_back({r, (int)f});
+        }
+        b->lane_ntiles[k] = (int)tiles.size() - b->lane_tile0[k];
     }
     if (b->d_tiles) cudaFree(b->d_tiles);
     b->d_tiles = nullptr;
@@ -91,22 +122,53 @@ int build_tiles(ising_batch* b)
     return ISING_OK;
 }
 
+// Streams and events of lanes 1 .. lanes-1 (created once, kept).
+int ensure_lane_streams(ising_batch* b)
+{
+    cudaError_t e = cudaSuccess;
+    if (!b->fork) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int k = 1; k < b->lanes && e == cudaSuccess; ++k) {
+        if (!b->lane_stream[k]) e = cudaStreamCreateWithFlags(&b->lane_stream[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess && !b->join[k]) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
+    }
+    return e == cudaSuccess ? ISING_OK : cuda_fail(e, "lane streams");
+}
+
+// One chunk of sweeps as a graph: lane 0 on the batch's stream, lanes
+// 1.. forked from it and joined back before the chunk counter advances.
 int capture_graph(ising_batch* b)
 {
-    if (b->graph && b->graph_chunk == b->chunk && b->graph_threads == b->threads) return ISING_OK;
+    if (b->graph && b->graph_chunk == b->chunk && b->graph_threads == b->threads && b->graph_lanes == b->lanes)
+        return ISING_OK;
     if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    int rc = ensure_lane_streams(b);
+    if (rc != ISING_OK) return rc;
+    cudaStream_t st[kMaxLanes];
+    for (int k = 0; k < b->lanes; ++k) st[k] = k == 0 ? b->stream : b->lane_stream[k];
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-    cudaError_t le = cudaSuccess;
+    cudaError_t le = cudaEventRecord(b->fork, b->stream);
+    for (int k = 1; k < b->lanes && le == cudaSuccess; ++k)
+        if (b->lane_ntiles[k] > 0) le = cudaStreamWaitEvent(st[k], b->fork, 0);
     for (int s = 1; s <= b->chunk && le == cudaSuccess; ++s) {
-        batch_half_sweep_kernel<0><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_reps, b->d_tiles,
-                                                                         b->d_chunk_base, (uint32_t)s, 1u);
-        le = cudaGetLastError();
-        if (le != cudaSuccess) break;
-        batch_half_sweep_kernel<1><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_reps, b->d_tiles,
-                                                                         b->d_chunk_base, (uint32_t)s, 1u);
-        le = cudaGetLastError();
+        for (int k = 0; k < b->lanes && le == cudaSuccess; ++k) {
+            const int nt = b->lane_ntiles[k];
+            if (nt == 0) continue;
+            const BatchTile* tiles = b->d_tiles + b->lane_tile0[k];
+            batch_half_sweep_kernel<0><<<nt, b->threads, 0, st[k]>>>(b->d_reps, tiles, b->d_chunk_base,
+                                                                   (uint32_t)s, 1u);
+            le = cudaGetLastError();
+            if (le != cudaSuccess) break;
+            batch_half_sweep_kernel<1><<<nt, b->threads, 0, st[k]>>>(b->d_reps, tiles, b->d_chunk_base,
+                                                                   (uint32_t)s, 1u);
+            le = cudaGetLastError();
+        }
+    }
+    for (int k = 1; k < b->lanes && le == cudaSuccess; ++k) {
+        if (b->lane_ntiles[k] == 0) continue;
+        le = cudaEventRecord(b->join[k], st[k]);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(b->stream, b->join[k], 0);
     }
     if (le == cudaSuccess) {
         batch_advance_kernel<<<1, 1, 0, b->stream>>>(b->d_chunk_base, (uint32_t)b->chunk);
@@ -120,6 +182,7 @@ int capture_graph(ising_batch* b)
     if (e != cudaSuccess) { b->graph = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
     b->graph_chunk = b->chunk;
     b->graph_threads = b->threads;
+    b->graph_lanes = b->lanes;
     return ISING_OK;
 }
 
@@ -215,6 +278,16 @@ extern "C" int ising_batch_set_tiling(ising_batch* b, int32_t threads, int32_t c
         return build_tiles(b);
     }
     return ISING_OK;
+}
+
+extern "C" int ising_batch_set_lanes(ising_batch* b, int32_t lanes)
+{
+    if (!b || lanes < 1 || lanes > kMaxLanes) return ISING_EINVAL;
+    if (lanes == b->lanes) return ISING_OK;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    b->lanes = lanes;
+    return build_tiles(b);
 }
 
 extern "C" int ising_batch_sweep(ising_batch* b, const int64_t* sweeps, int64_t every, int64_t** host_E,

@@ -1,7 +1,9 @@
 // Serving: continuous batching of simulation jobs on one device.  A worker
 // thread admits queued jobs into a fixed device arena (first-fit), runs
-// epochs of the batched half-sweep over every running job, scatters each
-// epoch's E/M records into the jobs' host arrays, and retires finished jobs.
+// epochs of the batched half-sweep over every running job (split into lanes
+// of about equal work on separate streams, so one lane's blocks fill the SMs
+// another lane's last wave leaves idle), scatters each epoch's E/M records
+// into the jobs' host arrays, and retires finished jobs.
 // Contract: include/ising.h.
 #include <cuda_runtime.h>
 
@@ -27,6 +29,7 @@ using namespace ising;
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int kLanes = 4;   // independent streams an epoch's jobs are split over
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 enum JobState { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3, kCancelled = 4 };
@@ -121,7 +124,10 @@ struct ising_server {
     unsigned long long* h_counts = nullptr;
     int8_t* staging = nullptr;
     size_t staging_cap = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;                 // lane 0, copies
+    cudaStream_t lane_stream[kLanes] = {};         // lanes 1 .. kLanes-1
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[kLanes] = {};
     std::thread worker;
 
     double now() const
@@ -195,8 +201,8 @@ int run_epoch(ising_server* s, const std::vector<uint64_t>& run, std::vector<Job
     TraceRange trace("ising_server_epoch");
     const int threads = 128;
     std::vector<BatchReplica> reps(run.size());
-    std::vector<BatchTile> tiles;
     uint32_t max_n = 0;
+    std::vector<double> work(run.size());
     for (size_t a = 0; a < run.size(); ++a) {
         Job& j = *jp[a];
         BatchReplica& R = j.rep;
@@ -208,7 +214,30 @@ int run_epoch(ising_server* s, const std::vector<uint64_t>& run, std::vector<Job
         R.counts = s->d_counts + a * 2 * (size_t)s->epoch;
         reps[a] = R;
         max_n = std::max(max_n, R.nsweeps);
-        for (uint32_t f = 0; f < R.items; f += threads) tiles.push_back({(int)a, (int)f});
+        work[a] = (double)j.g.L * j.g.L * R.nsweeps;
+    }
+    // lanes: jobs, most work first, to the lane with the least work so far;
+    // each lane's tiles are contiguous and it runs on its own stream
+    std::vector<size_t> order(run.size());
+    for (size_t a = 0; a < order.size(); ++a) order[a] = a;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return work[x] > work[y]; });
+    std::vector<int> lane_of(run.size(), 0);
+    double lane_work[kLanes] = {};
+    for (size_t a : order) {
+        int best = 0;
+        for (int k = 1; k < kLanes; ++k)
+            if (lane_work[k] < lane_work[best]) best = k;
+        lane_of[a] = best;
+        lane_work[best] += work[a];
+    }
+    std::vector<BatchTile> tiles;
+    int lane_tile0[kLanes], lane_nt[kLanes];
+    for (int k = 0; k < kLanes; ++k) {
+        lane_tile0[k] = (int)tiles.size();
+        for (size_t a : order)
+            if (lane_of[a] == k)
+                for (uint32_t f = 0; f < reps[a].items; f += threads) tiles.push_back({(int)a, (int)f});
+        lane_nt[k] = (int)tiles.size() - lane_tile0[k];
     }
     int rc = ensure_tiles(s, tiles.size());
     if (rc != ISING_OK) return rc;
@@ -220,12 +249,26 @@ int run_epoch(ising_server* s, const std::vector<uint64_t>& run, std::vector<Job
     if (e == cudaSuccess)
         e = cudaMemsetAsync(s->d_counts, 0, run.size() * 2 * (size_t)s->epoch * sizeof(unsigned long long), s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "server epoch setup");
-    const unsigned nt = (unsigned)tiles.size();
-    for (uint32_t k = 1; k <= max_n; ++k) {
-        batch_half_sweep_kernel<0><<<nt, threads, 0, s->stream>>>(s->d_reps, s->d_tiles, s->d_zero, k, 1u);
-        batch_half_sweep_kernel<1><<<nt, threads, 0, s->stream>>>(s->d_reps, s->d_tiles, s->d_zero, k, 1u);
+    cudaStream_t st[kLanes];
+    for (int k = 0; k < kLanes; ++k) st[k] = k == 0 ? s->stream : s->lane_stream[k];
+    e = cudaEventRecord(s->fork, s->stream);
+    for (int k = 1; k < kLanes && e == cudaSuccess; ++k)
+        if (lane_nt[k] > 0) e = cudaStreamWaitEvent(st[k], s->fork, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "server epoch fork");
+    for (uint32_t n = 1; n <= max_n; ++n) {
+        for (int k = 0; k < kLanes; ++k) {
+            if (lane_nt[k] == 0) continue;
+            const BatchTile* t = s->d_tiles + lane_tile0[k];
+            batch_half_sweep_kernel<0><<<lane_nt[k], threads, 0, st[k]>>>(s->d_reps, t, s->d_zero, n, 1u);
+            batch_half_sweep_kernel<1><<<lane_nt[k], threads, 0, st[k]>>>(s->d_reps, t, s->d_zero, n, 1u);
+        }
     }
     e = cudaGetLastError();
+    for (int k = 1; k < kLanes && e == cudaSuccess; ++k) {
+        if (lane_nt[k] == 0) continue;
+        e = cudaEventRecord(s->join[k], st[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->join[k], 0);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "server epoch launch");
     e = cudaMemcpyAsync(s->h_counts, s->d_counts, run.size() * 2 * (size_t)s->epoch * sizeof(unsigned long long),
                         cudaMemcpyDeviceToHost, s->stream);
@@ -371,6 +414,11 @@ void free_server(ising_server* s)
     cudaFree(s->d_counts);
     cudaFree(s->staging);
     if (s->h_counts) cudaFreeHost(s->h_counts);
+    for (int k = 0; k < kLanes; ++k) {
+        if (s->lane_stream[k]) cudaStreamDestroy(s->lane_stream[k]);
+        if (s->join[k]) cudaEventDestroy(s->join[k]);
+    }
+    if (s->fork) cudaEventDestroy(s->fork);
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s->alloc;
     delete s;
@@ -395,6 +443,12 @@ extern "C" int ising_server_create(size_t budget, int32_t max_jobs, int32_t epoc
     const size_t counts_words = (size_t)max_jobs * 2 * epoch_sweeps;
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) { s->stream = nullptr; free_server(s); return cuda_fail(e, "cudaStreamCreate"); }
+    e = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming);
+    for (int k = 1; k < kLanes && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&s->lane_stream[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) { free_server(s); return cuda_fail(e, "server lane streams"); }
     if (!s->alloc || cudaMalloc(&s->arena, budget) != cudaSuccess ||
         cudaMalloc(&s->d_reps, (size_t)max_jobs * sizeof(BatchReplica)) != cudaSuccess ||
         cudaMalloc(&s->d_zero, sizeof(uint32_t)) != cudaSuccess ||

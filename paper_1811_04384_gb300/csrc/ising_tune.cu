@@ -1,6 +1,6 @@
 // Autotuner: times the launch shapes of the single-lattice path (and the
-// on-chip path where the lattice fits) and the tile size / graph chunk of the
-// batch path on the current device, checks that every candidate leaves a
+// on-chip path where the lattice fits) and the tile size / graph chunk /
+// lanes of the batch path on the current device, checks that every candidate leaves a
 // bit-identical lattice, and reports the fastest.  Contract: include/ising.h.
 #include <cuda_runtime.h>
 
@@ -95,24 +95,27 @@ extern "C" int ising_autotune(int32_t L, int32_t sweeps, int32_t* best_bw, int32
 
 extern "C" int ising_batch_autotune(int32_t n, const int32_t* L, const double* beta, const uint64_t* seed,
                                     const uint8_t* hot, int64_t sweeps, int32_t* best_threads, int32_t* best_chunk,
-                                    double* ns_per_update)
+                                    int32_t* best_lanes, double* ns_per_update)
 {
     if (n < 1 || !L || !beta || !seed || sweeps < 1 || sweeps > 100000) return ISING_EINVAL;
     const int threads[3] = {64, 128, 256};
     const int chunks[3] = {10, 50, 200};
+    const int lanes[3] = {1, 2, 4};
     double updates = 0.0;
     for (int r = 0; r < n; ++r) updates += (double)L[r] * L[r] * (double)sweeps;
     std::vector<int64_t> sw(n, sweeps);
     std::vector<std::vector<int8_t>> ref(n), got(n);
     double best = -1.0;
-    int bt = 128, bc = 50;
+    int bt = 128, bc = 50, bl = 4;
     bool first = true;
     for (int ti = 0; ti < 3; ++ti) {
-        for (int ci = 0; ci < 3; ++ci) {
+        for (int k = 0; k < 9; ++k) {
+            const int ci = k % 3, li = k / 3;
             ising_batch* b = nullptr;
             int rc = ising_batch_create(n, L, beta, seed, hot, &b);
             if (rc != ISING_OK) return rc;
             rc = ising_batch_set_tiling(b, threads[ti], chunks[ci]);
+            if (rc == ISING_OK) rc = ising_batch_set_lanes(b, lanes[li]);
             std::vector<int64_t> one(n, 1);
             if (rc == ISING_OK) rc = ising_batch_sweep(b, one.data(), 1, nullptr, nullptr);   // warm-up, graph capture
             // ising_batch_sweep synchronises the batch's stream, so the host clock times it
@@ -132,11 +135,13 @@ extern "C" int ising_batch_autotune(int32_t n, const int32_t* L, const double* b
                 best = ms;
                 bt = threads[ti];
                 bc = chunks[ci];
+                bl = lanes[li];
             }
         }
     }
     if (best_threads) *best_threads = bt;
     if (best_chunk) *best_chunk = bc;
+    if (best_lanes) *best_lanes = bl;
     if (ns_per_update) *ns_per_update = best * 1e6 / updates;
     return ISING_OK;
 }

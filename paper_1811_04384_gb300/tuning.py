@@ -41,14 +41,15 @@ def tune_batch(L, beta, seed, hot, sweeps: int = 50) -> dict:
     beta = np.ascontiguousarray(beta, dtype=np.float64)
     seed = np.ascontiguousarray(seed, dtype=np.uint64)
     hot = np.ascontiguousarray(hot, dtype=np.uint8)
-    th, ch = ctypes.c_int32(), ctypes.c_int32()
+    th, ch, ln = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     ns = ctypes.c_double()
     _check(load().ising_batch_autotune(len(L), L.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                        beta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                        seed.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
                                        hot.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), int(sweeps),
-                                       ctypes.byref(th), ctypes.byref(ch), ctypes.byref(ns)), "ising_batch_autotune")
-    return {"threads_per_tile": th.value, "graph_chunk": ch.value, "ns_per_update": ns.value}
+                                       ctypes.byref(th), ctypes.byref(ch), ctypes.byref(ln), ctypes.byref(ns)),
+           "ising_batch_autotune")
+    return {"threads_per_tile": th.value, "graph_chunk": ch.value, "lanes": ln.value, "ns_per_update": ns.value}
 
 
 def load_table(path: str = TABLE) -> dict:

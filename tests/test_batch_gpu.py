@@ -61,6 +61,30 @@ def test_batch_tiling_and_chunk_do_not_change_results(ising, threads, chunk):
             np.testing.assert_array_equal(ref.get_spins(r), b.get_spins(r))
 
 
+@pytest.mark.parametrize("lanes,threads", [(1, 128), (3, 64), (4, 256), (8, 128)])
+def test_batch_lanes_do_not_change_results(ising, lanes, threads):
+    """Splitting the replicas into independent graph branches (8 lanes for 5
+    replicas leaves lanes empty) gives the same series and spins as one lane."""
+    Ls = [8, 64, 100, 258, 46]
+    betas = [0.3, 0.44, 0.5, 0.6, 0.2]
+    seeds = [1, 2, 3, 4, 5]
+    with ising.Batch(Ls, betas, seeds, [1] * 5) as ref, ising.Batch(Ls, betas, seeds, [1] * 5) as b:
+        ref.set_lanes(1)
+        b.set_tiling(threads, 7)
+        b.set_lanes(lanes)
+        E0, M0 = ref.sweep([23, 23, 17, 23, 5], every=1)
+        E1, M1 = b.sweep([23, 23, 17, 23, 5], every=1)
+        b.set_lanes(2)                       # re-split between calls: the chain continues
+        E2, M2 = b.sweep([4, 4, 4, 4, 4], every=2)
+        E3, M3 = ref.sweep([4, 4, 4, 4, 4], every=2)
+        for r in range(5):
+            np.testing.assert_array_equal(E0[r], E1[r])
+            np.testing.assert_array_equal(M0[r], M1[r])
+            np.testing.assert_array_equal(E2[r], E3[r])
+            np.testing.assert_array_equal(M2[r], M3[r])
+            np.testing.assert_array_equal(ref.get_spins(r), b.get_spins(r))
+
+
 def test_batch_continues_across_calls(ising):
     Ls = [32, 64]
     with ising.Batch(Ls, [0.4, 0.45], [9, 10], [1, 1]) as b, ising.Batch(Ls, [0.4, 0.45], [9, 10], [1, 1]) as c:
@@ -90,6 +114,9 @@ def test_batch_rejects_bad_arguments(ising):
     with ising.Batch([64], [0.4], [1]) as b:
         with pytest.raises(ising.IsingError):
             b.set_tiling(96, 10)
+        for bad in (0, 9, -1):
+            with pytest.raises(ising.IsingError):
+                b.set_lanes(bad)
         with pytest.raises(ising.IsingError):
             b.sweep([-1])
 

@@ -311,3 +311,21 @@ def test_max_size_lattice(ising):
         E, M = lat.sweep_record(3, 1)
         assert (E == -2 * L * L).all()
         assert list(M) == [-L * L, L * L, -L * L]
+
+
+@pytest.mark.parametrize("L", [4, 44, 46, 86, 130, 258])
+def test_sweeps_keep_dead_fields_and_padding_zero(ising, L):
+    """Canary check: after many sweeps at beta = 0 (every live spin flips every
+    sweep) and at T_c, the dead fields of the last word, bit 63 and the pitch
+    padding are still zero in both colour arrays."""
+    with ising.Lattice(L, 8) as lat:
+        lat.init_hot()
+        W, P, r = lat.layout()
+        live_last = sum(1 << (3 * k) for k in range(r))
+        for beta in (0.0, BETA_TC):
+            lat.set_beta(beta)
+            lat.sweep(25)
+            w = lat.get_words()
+            assert ((w[:, :, W - 1] & ~np.uint64(live_last)) == 0).all()
+            assert ((w[:, :, :W - 1] & ~np.uint64(0x1249249249249249)) == 0).all()
+            assert (w[:, :, W:] == 0).all()

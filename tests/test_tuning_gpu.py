@@ -42,4 +42,5 @@ def test_autotune_batch_choice_is_valid(ising):
     best = tuning.tune_batch([32, 64, 256], [0.3, 0.44, 0.6], [1, 2, 3], [1, 1, 1], sweeps=5)
     assert best["threads_per_tile"] in (64, 128, 256)
     assert best["graph_chunk"] in (10, 50, 200)
+    assert best["lanes"] in (1, 2, 4)
     assert best["ns_per_update"] > 0
