@@ -169,9 +169,12 @@ int ising_set_sweep(ising_lattice *h, uint64_t t);
 int ising_set_stream(ising_lattice *h, void *stream);
 
 /* Launch shape of the half-sweep kernels: rows_per_thread must be 4 (one
- * Philox call serves four rows); block_words (threads along a row) in
- * {16, 32, 64}; block_groups (threads down the columns) in {1, 2, 4, 8, 16};
- * 32 <= block_words * block_groups <= 256.  Default 4, 16, 8.  Results do
+ * Philox call serves four rows).  block_words == 0 selects a 1-D grid over
+ * the thread items (item = row group * W + word, no padding columns) with
+ * block_groups threads per block, in {64, 128, 192, 256}.  Otherwise a 2-D
+ * grid: block_words (threads along a row) in {16, 32, 64}; block_groups
+ * (threads down the columns) in {1, 2, 4, 8, 16}; 32 <= block_words *
+ * block_groups <= 256.  Default 4, 0, 128 (1-D, 128 threads).  Results do
  * not depend on the shape (the draws are keyed by site). */
 int ising_set_tiling(ising_lattice *h, int32_t rows_per_thread,
                      int32_t block_words, int32_t block_groups);
@@ -347,8 +350,9 @@ int ising_server_destroy(ising_server *srv);
  * ising_batch_set_tiling); the Python binding keeps the choices in a JSON
  * table. */
 
-/* Single lattice of side L: tilings (block_words x block_groups) on the launch
- * path and, if the lattice fits, the on-chip path; `sweeps` timed sweeps
+/* Single lattice of side L: the launch shapes of ising_set_tiling (1-D with
+ * 64/128/192/256 threads, eleven 2-D block_words x block_groups) and, if the
+ * lattice fits, the on-chip path; `sweeps` timed sweeps
  * each (1..100000) from a hot start at T = 2.269.  Outputs may be NULL. */
 int ising_autotune(int32_t L, int32_t sweeps, int32_t *best_block_words, int32_t *best_block_groups,
                    int32_t *best_path, double *ns_per_update);

@@ -148,7 +148,7 @@ class Lattice:
     def set_stream(self, stream):
         _check(load().ising_set_stream(self._h, _stream_ptr(stream)), "ising_set_stream")
 
-    def set_tiling(self, rows: int = 4, block_words: int = 32, block_groups: int = 4):
+    def set_tiling(self, rows: int = 4, block_words: int = 0, block_groups: int = 128):
         _check(load().ising_set_tiling(self._h, rows, block_words, block_groups), "ising_set_tiling")
 
     def set_rng(self, scheme: int):

@@ -236,15 +236,26 @@ __device__ __forceinline__ void sweep_rows(uint64_t* __restrict__ own, const uin
     }
 }
 
-// One half-sweep of colour C over one lattice: thread (x, y) of the grid owns
-// word column x and rows 4y .. 4y+3.  At most 256 threads per block.  ROUNDS:
-// Philox rounds of the draws (10, or the opt-in 7).
-template <int C, bool UPDATE, bool RECORD, int ROUNDS = 10>
+// One half-sweep of colour C over one lattice.  LINEAR: a 1-D grid whose
+// thread k owns item k = group * W + w (word w of rows 4 group .. 4 group + 3),
+// so no thread idles on padding columns and the blocks tile the lattice
+// without a partial column of blocks.  Otherwise thread (x, y) of a 2-D grid
+// owns word column x and rows 4y .. 4y+3.  At most 256 threads per block.
+// ROUNDS: Philox rounds of the draws (10, or the opt-in 7).
+template <int C, bool UPDATE, bool RECORD, int ROUNDS = 10, bool LINEAR = true>
 __global__ void __launch_bounds__(256, 3)
 half_sweep_kernel(uint64_t* __restrict__ own, const uint64_t* __restrict__ other, Geom g, SweepArgs a)
 {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    const int row0 = (blockIdx.y * blockDim.y + threadIdx.y) * 4;
+    int w, row0;
+    if (LINEAR) {
+        const uint32_t item = blockIdx.x * blockDim.x + threadIdx.x;
+        const uint32_t grp = item / (uint32_t)g.W;
+        w = (int)(item - grp * (uint32_t)g.W);
+        row0 = (int)grp * 4;
+    } else {
+        w = blockIdx.x * blockDim.x + threadIdx.x;
+        row0 = (blockIdx.y * blockDim.y + threadIdx.y) * 4;
+    }
     uint32_t anti = 0, up = 0;
     if (w < g.W && row0 < g.L) {
         const uint64_t t = UPDATE ? *a.t_base + a.t_off : 0;

@@ -224,7 +224,7 @@ struct ising_lattice {
     uint64_t* t_dev = nullptr;
     int8_t* staging = nullptr;   // lazily allocated int8 L*L (get/set spins)
     unsigned long long* host_counts = nullptr;   // pinned, kCountBytes
-    int bw = 16, bg = 8;                         // half-sweep block shape (autotuned at L = 16384)
+    int bw = 0, bg = 128;                        // half-sweep shape: linear items, 128 threads a block
     int path = ISING_PATH_AUTO;                  // multi-block launches or on-chip resident sweeps
     int rounds = 10;                             // Philox rounds of the sweep draws
     int layout = ISING_LAYOUT_ROW_PACKED;        // or the paper's column-interleaved words
@@ -318,30 +318,38 @@ SweepArgs make_sweep_args(uint64_t seed, const uint64_t thr[2], const uint64_t* 
     return a;
 }
 
-template <int ROUNDS>
+template <int ROUNDS, bool LIN>
 static void launch_half_sweep_r(dim3 grid, dim3 block, int colour, bool update, bool record, uint64_t* own,
                                 const uint64_t* other, const Geom& g, const SweepArgs& a, cudaStream_t s)
 {
     if (colour == 0) {
-        if (record) half_sweep_kernel<0, true, true, ROUNDS><<<grid, block, 0, s>>>(own, other, g, a);
-        else half_sweep_kernel<0, true, false, ROUNDS><<<grid, block, 0, s>>>(own, other, g, a);
+        if (record) half_sweep_kernel<0, true, true, ROUNDS, LIN><<<grid, block, 0, s>>>(own, other, g, a);
+        else half_sweep_kernel<0, true, false, ROUNDS, LIN><<<grid, block, 0, s>>>(own, other, g, a);
     } else if (!update) {
-        half_sweep_kernel<1, false, true><<<grid, block, 0, s>>>(own, other, g, a);
+        half_sweep_kernel<1, false, true, 10, LIN><<<grid, block, 0, s>>>(own, other, g, a);
     } else {
-        if (record) half_sweep_kernel<1, true, true, ROUNDS><<<grid, block, 0, s>>>(own, other, g, a);
-        else half_sweep_kernel<1, true, false, ROUNDS><<<grid, block, 0, s>>>(own, other, g, a);
+        if (record) half_sweep_kernel<1, true, true, ROUNDS, LIN><<<grid, block, 0, s>>>(own, other, g, a);
+        else half_sweep_kernel<1, true, false, ROUNDS, LIN><<<grid, block, 0, s>>>(own, other, g, a);
     }
 }
 
+// bw == 0: linear items, bgrp threads per block; else bw x bgrp 2-D blocks.
 cudaError_t launch_half_sweep(int bw, int bgrp, int colour, bool update, bool record,
                               uint64_t* own, const uint64_t* other, const Geom& g, const SweepArgs& a,
                               cudaStream_t s)
 {
     const int ngroups = (g.L + 3) / 4;
+    if (bw == 0) {
+        const uint32_t items = (uint32_t)ngroups * (uint32_t)g.W;
+        dim3 block(bgrp), grid((items + bgrp - 1) / bgrp);
+        if (a.rounds == 7) launch_half_sweep_r<7, true>(grid, block, colour, update, record, own, other, g, a, s);
+        else launch_half_sweep_r<10, true>(grid, block, colour, update, record, own, other, g, a, s);
+        return cudaGetLastError();
+    }
     dim3 block(bw, bgrp);
     dim3 grid((g.W + bw - 1) / bw, (ngroups + bgrp - 1) / bgrp);
-    if (a.rounds == 7) launch_half_sweep_r<7>(grid, block, colour, update, record, own, other, g, a, s);
-    else launch_half_sweep_r<10>(grid, block, colour, update, record, own, other, g, a, s);
+    if (a.rounds == 7) launch_half_sweep_r<7, false>(grid, block, colour, update, record, own, other, g, a, s);
+    else launch_half_sweep_r<10, false>(grid, block, colour, update, record, own, other, g, a, s);
     return cudaGetLastError();
 }
 
@@ -855,6 +863,12 @@ extern "C" int ising_set_tiling(ising_lattice* h, int32_t rows, int32_t bw, int3
     if (!h) return ISING_EINVAL;
     if (h->layout != ISING_LAYOUT_ROW_PACKED) return ISING_EINVAL;   // row-packed words only
     if (rows != 4) return ISING_EINVAL;
+    if (bw == 0) {                                  // linear items, bgrp threads per block
+        if (bgrp != 64 && bgrp != 128 && bgrp != 192 && bgrp != 256) return ISING_EINVAL;
+        h->bw = 0;
+        h->bg = bgrp;
+        return ISING_OK;
+    }
     if (bw != 16 && bw != 32 && bw != 64) return ISING_EINVAL;
     if (bgrp != 1 && bgrp != 2 && bgrp != 4 && bgrp != 8 && bgrp != 16) return ISING_EINVAL;
     if (bw * bgrp > 256 || bw * bgrp < 32) return ISING_EINVAL;

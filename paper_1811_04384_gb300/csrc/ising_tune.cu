@@ -65,7 +65,9 @@ extern "C" int ising_autotune(int32_t L, int32_t sweeps, int32_t* best_bw, int32
                               double* ns_per_update)
 {
     if (!ising::valid_side(L) || sweeps < 1 || sweeps > 100000) return ISING_EINVAL;
-    std::vector<Candidate> cands = {{32, 4, ISING_PATH_LAUNCHES},  {16, 2, ISING_PATH_LAUNCHES},
+    std::vector<Candidate> cands = {{0, 128, ISING_PATH_LAUNCHES},  {0, 64, ISING_PATH_LAUNCHES},
+                                    {0, 192, ISING_PATH_LAUNCHES},  {0, 256, ISING_PATH_LAUNCHES},
+                                    {32, 4, ISING_PATH_LAUNCHES},  {16, 2, ISING_PATH_LAUNCHES},
                                     {16, 4, ISING_PATH_LAUNCHES},  {16, 8, ISING_PATH_LAUNCHES},
                                     {16, 16, ISING_PATH_LAUNCHES}, {32, 1, ISING_PATH_LAUNCHES},
                                     {32, 2, ISING_PATH_LAUNCHES},  {32, 8, ISING_PATH_LAUNCHES},

@@ -167,8 +167,11 @@ def test_half_sweep_boundary_cases(ising):
             assert E[0] == Eo[0] and M[0] == Mo[0]
 
 
-@pytest.mark.parametrize("tiling", [(4, 16, 2), (4, 32, 1), (4, 64, 4), (4, 32, 8), (4, 16, 16), (4, 64, 1)])
+@pytest.mark.parametrize("tiling", [(4, 16, 2), (4, 32, 1), (4, 64, 4), (4, 32, 8), (4, 16, 16), (4, 64, 1),
+                                    (4, 0, 64), (4, 0, 128), (4, 0, 192), (4, 0, 256)])
 def test_tiling_does_not_change_results(ising, tiling):
+    """2-D block shapes and 1-D item grids (L = 260: 65 row groups x 7 words,
+    455 items, so every 1-D block size leaves a ragged last block)."""
     L = 260
     ref = gpu_run(ising, L, 77, BETA_TC, 6, tiling=(4, 32, 4))
     got = gpu_run(ising, L, 77, BETA_TC, 6, tiling=tiling)
@@ -178,7 +181,8 @@ def test_tiling_does_not_change_results(ising, tiling):
 
 def test_rejected_tilings(ising):
     with ising.Lattice(64, 1) as lat:
-        for bad in [(8, 32, 4), (4, 48, 4), (4, 64, 8), (4, 16, 1), (4, 32, 3)]:
+        for bad in [(8, 32, 4), (4, 48, 4), (4, 64, 8), (4, 16, 1), (4, 32, 3), (4, 0, 32), (4, 0, 96),
+                    (4, 0, 512), (4, -16, 8)]:
             with pytest.raises(ising.IsingError):
                 lat.set_tiling(*bad)
 
