@@ -66,9 +66,11 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the plain-vs-batched comparison")
     ap.add_argument("--tiling", default=None, help="rows,block_words,block_groups")
     ap.add_argument("--L", type=int, default=L_LARGE, help="lattice side (profiling of a smaller case)")
-    ap.add_argument("--workload", default="large", choices=["large", "plain", "scan", "batched", "serving"],
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "plain", "scan", "batched", "serving", "paper"],
                     help="large (default): L=16384 roofline config; plain: L=64 x 1000 sweeps; "
-                         "scan: L=1024 x 26 temperatures; batched: 512 uneven replicas vs per-instance launches")
+                         "scan: L=1024 x 26 temperatures; batched: 512 uneven replicas vs per-instance launches; "
+                         "paper: the paper's three test cases (Table 2) in both word layouts")
     ap.add_argument("--sweeps", type=int, default=None, help="override the workload's sweep count")
     ap.add_argument("--rng", type=int, default=10, choices=[10, 7],
                     help="Philox rounds of the sweep draws: 10 (default scheme) or the opt-in 7")
@@ -420,6 +422,60 @@ def run_plain(args, ising, local):
           "bit_exact_across_paths": exact})
 
 
+# The paper's test cases (Table 2): lattice side and iterations; an iteration
+# is 10 update attempts per spin, i.e. 10 sweeps of the checkerboard chain.
+PAPER_CASES = [("case 1", 2016, 5000), ("case 2", 2016, 4500), ("case 3", 1008, 4500)]
+
+
+def run_paper(args, ising, local):
+    """The paper's three test cases as equal spin-update counts of the
+    checkerboard chain, in the row-packed layout and in the paper's own
+    column-interleaved layout; E/M once per iteration (every 10 sweeps)."""
+    import numpy as np
+    import torch
+    stream = torch.cuda.Stream()
+    cases = []
+    total_updates, total_s = 0.0, 0.0
+    with ClockSampler(local) as clocks:
+        for name, L, iters in PAPER_CASES:
+            sweeps = (args.sweeps or 10 * iters)
+            sweeps -= sweeps % 10
+            entry = {"case": name, "L": L, "iterations": sweeps // 10, "sweeps": sweeps}
+            series = {}
+            for lname, layout in (("row_packed", ising.ISING_LAYOUT_ROW_PACKED),
+                                  ("column_interleaved", ising.ISING_LAYOUT_COLUMN_INTERLEAVED)):
+                with ising.Lattice(L, SEED_LARGE, stream=stream, layout=layout) as lat:
+                    lat.init_hot()
+                    lat.set_beta(BETA)
+                    lat.sweep_record(10, 10)                     # warm-up (module load)
+                    lat.init_hot()
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    E, M = lat.sweep_record(sweeps, 10)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    dt = e0.elapsed_time(e1) / 1e3
+                series[lname] = (E, M)
+                entry[lname] = {"seconds": dt, "value": L * L * sweeps / (dt * 1e9)}
+                if lname == "row_packed":
+                    total_updates += L * L * sweeps
+                    total_s += dt
+            entry["bit_exact_across_layouts"] = bool(np.array_equal(series["row_packed"][0],
+                                                                    series["column_interleaved"][0]) and
+                                                     np.array_equal(series["row_packed"][1],
+                                                                    series["column_interleaved"][1]))
+            entry["E_per_spin_last"] = float(series["row_packed"][0][-1]) / (L * L)
+            cases.append(entry)
+    emit({"metric": METRIC, "value": total_updates / (total_s * 1e9), "unit": METRIC, "n_gpus": 1, "steps": 1,
+          "warmup": 1, "ms_per_step": total_s * 1e3, "higher_is_better": True, "scaling": "weak",
+          "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+          "config": {"workload": "paper: the three test cases of Table 2 (L = 2016, 2016, 1008; 5000, 4500, "
+                                 "4500 iterations of 10 sweeps), T=2.269, hot start seed 3, E/M every iteration; "
+                                 "value = row-packed layout over all three cases (CUDA events)"},
+          "cases": cases, "clocks": clocks.summary()})
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -434,7 +490,7 @@ def main():
         import paper_1811_04384_gb300 as ising
         if rank == 0:
             {"batched": run_batched, "scan": run_scan, "plain": run_plain,
-             "serving": run_serving}[args.workload](args, ising, local)
+             "serving": run_serving, "paper": run_paper}[args.workload](args, ising, local)
         return
 
     import numpy as np

@@ -185,7 +185,10 @@ int ising_set_tiling(ising_lattice *h, int32_t rows_per_thread,
  * arrays into shared memory and runs all requested sweeps there in one
  * launch (lattices with 2 L pitch 8 bytes <= 220 KB, i.e. L up to about
  * 740; larger -> EINVAL); it removes the per-sweep launch latency that
- * bounds small lattices.  ISING_PATH_AUTO (default): resident for L <= 128.
+ * bounds small lattices.  Up to L = 168 the fields of each thread item are
+ * split over 2, 4 or 32 lanes, so that a small lattice still gives all four
+ * schedulers of the SM work.  ISING_PATH_AUTO (default): resident while
+ * ceil(L/4) * ceil(L/42) <= 256 thread items (L <= 204).
  * Results are identical on every path. */
 #define ISING_PATH_AUTO 0
 #define ISING_PATH_LAUNCHES 1

@@ -169,6 +169,87 @@ resident_sweeps_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geo
     }
 }
 
+// One item's half-sweep on the on-chip path with F lanes per item: one warp
+// (F = 32, sweep_item_warp) or an aligned group of 2, 4 or 8 lanes
+// (sweep_item_lanes).
+template <int F, int C, bool RECORD, int ROUNDS>
+__device__ __forceinline__ void item_half_sweep(uint64_t* own, const uint64_t* other, const Geom& g, int item,
+                                                bool valid, int q, uint64_t t, const SweepArgs& a, uint32_t& anti,
+                                                uint32_t& up)
+{
+    if constexpr (F == 32)
+        sweep_item_warp<C, RECORD, ROUNDS>(own, other, g, item, valid, q, t, a.rk, a.thr0, a.thr1, a.all0, a.all1,
+                                           anti, up);
+    else
+        sweep_item_lanes<C, RECORD, F, ROUNDS>(own, other, g, item, valid, q, t, a.rk, a.thr0, a.thr1, a.all0,
+                                               a.all1, anti, up);
+}
+
+// The on-chip path for small lattices with F lanes per item: F times the
+// threads of resident_sweeps_kernel, each with 1/F of the Philox calls, so a
+// lattice of a few dozen items keeps all four schedulers of the SM busy
+// instead of one warp.  Groups loop over the items.  Same records and
+// results as resident_sweeps_kernel.  blockDim.x: a multiple of 32, <= 512.
+template <int F, int ROUNDS>
+__global__ void __launch_bounds__(512, 1)
+resident_group_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom g, SweepArgs a, uint64_t t0,
+                      int n, int every, long long* __restrict__ records)
+{
+    extern __shared__ __align__(16) uint64_t lattice[];
+    __shared__ unsigned int red_anti[32], red_up[32];
+    const size_t words = (size_t)g.L * g.P;
+    uint64_t* s0 = lattice;
+    uint64_t* s1 = lattice + words;
+    for (size_t k = threadIdx.x; k < words; k += blockDim.x) {
+        s0[k] = w0[k];
+        s1[k] = w1[k];
+    }
+    __syncthreads();
+    const int items = ((g.L + 3) / 4) * g.W;
+    const int per_pass = (int)blockDim.x / F;
+    const int slot = (int)threadIdx.x / F, q = (int)threadIdx.x % F;
+    const int nwarps = (int)blockDim.x / 32;
+    const int warp = (int)threadIdx.x / 32, lane = (int)threadIdx.x % 32;
+    const int passes = (items + per_pass - 1) / per_pass;
+    const long long N = (long long)g.L * g.L;
+    for (int s = 1; s <= n; ++s) {
+        const uint64_t t = t0 + (uint64_t)s;
+        uint32_t dummy0 = 0, dummy1 = 0;
+        for (int p = 0; p < passes; ++p) {
+            const int it = p * per_pass + slot;
+            item_half_sweep<F, 0, false, ROUNDS>(s0, s1, g, it, it < items, q, t, a, dummy0, dummy1);
+        }
+        __syncthreads();
+        const bool record = (s % every) == 0;
+        uint32_t anti = 0, up = 0;
+        for (int p = 0; p < passes; ++p) {
+            const int it = p * per_pass + slot;
+            if (record) item_half_sweep<F, 1, true, ROUNDS>(s1, s0, g, it, it < items, q, t, a, anti, up);
+            else item_half_sweep<F, 1, false, ROUNDS>(s1, s0, g, it, it < items, q, t, a, anti, up);
+        }
+        if (record) {
+            anti = __reduce_add_sync(0xffffffffu, anti);
+            up = __reduce_add_sync(0xffffffffu, up);
+            if (lane == 0) { red_anti[warp] = anti; red_up[warp] = up; }
+        }
+        __syncthreads();
+        if (record && warp == 0) {          // up to 32 warp sums, each below 2^31: fits 32 bits
+            const unsigned int sa = __reduce_add_sync(0xffffffffu, lane < nwarps ? red_anti[lane] : 0u);
+            const unsigned int su = __reduce_add_sync(0xffffffffu, lane < nwarps ? red_up[lane] : 0u);
+            if (lane == 0) {
+                const int rec = s / every - 1;
+                records[2 * rec] = 2 * (long long)sa - 2 * N;
+                records[2 * rec + 1] = 2 * (long long)su - N;
+            }
+        }
+    }
+    __syncthreads();
+    for (size_t k = threadIdx.x; k < words; k += blockDim.x) {
+        w0[k] = s0[k];
+        w1[k] = s1[k];
+    }
+}
+
 // Test hook: Philox4x32-10 blocks of arbitrary counters.
 __global__ void philox_blocks_kernel(const uint32_t* __restrict__ ctr, uint32_t* __restrict__ out,
                                      int64_t n, uint32_t key0, uint32_t key1)
@@ -189,7 +270,7 @@ constexpr int kRecordsPerChunk = 1024;           // count slots resident on the 
 constexpr size_t kCountBytes = (size_t)kRecordsPerChunk * kCountSlots * 2 * sizeof(unsigned long long);
 constexpr size_t kAlign = 256;
 constexpr size_t kResidentMaxBytes = 220 * 1024;   // shared memory for the on-chip path
-constexpr int kResidentAutoMaxL = 128;              // auto: on-chip up to this side
+constexpr int kResidentAutoMaxItems = 256;          // auto: on-chip while one block of 256 threads covers the items
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -574,11 +655,53 @@ static bool use_resident(const ising_lattice* h)
 {
     if (h->layout != ISING_LAYOUT_ROW_PACKED || h->path == ISING_PATH_LAUNCHES) return false;
     if (resident_bytes(h->g) > kResidentMaxBytes) return false;
-    return h->path == ISING_PATH_RESIDENT || h->g.L <= kResidentAutoMaxL;
+    return h->path == ISING_PATH_RESIDENT || ((h->g.L + 3) / 4) * h->g.W <= kResidentAutoMaxItems;
 }
 
 // n sweeps with the lattice resident in shared memory, E/M records (if any)
 // written as (E, M) pairs into the count buffer.
+// Lanes per item of the on-chip path (0: one thread per item,
+// resident_sweeps_kernel), from a GB300 sweep of 1000 recorded sweeps at
+// L = 16 .. 256 over 1, 2, 4, 8 and 32 lanes: one warp per item up to 12
+// items (L <= 42), 4 lanes up to 100 items (L <= 126), 2 lanes up to 200
+// (L <= 168); above that the extra merge work outweighs the parallelism.
+// Every choice gives the same results.  At most 416 threads (launch bound 512).
+static int resident_lanes(const Geom& g)
+{
+    const int items = ((g.L + 3) / 4) * g.W;
+    if (items <= 12) return 32;
+    if (items <= 100) return 4;
+    if (items <= 200) return 2;
+    return 0;
+}
+
+template <int F>
+static cudaError_t launch_resident_group(const ising_lattice* h, const SweepArgs& a, size_t bytes, int n, int every,
+                                         long long* rec)
+{
+    const Geom& g = h->g;
+    const int items = ((g.L + 3) / 4) * g.W;
+    const int threads = (items * F + 31) / 32 * 32;      // <= 416 by resident_lanes
+    if (a.rounds == 7)
+        resident_group_kernel<F, 7><<<1, threads, bytes, h->stream>>>(h->words[0], h->words[1], g, a, h->t, n, every,
+                                                                      rec);
+    else
+        resident_group_kernel<F, 10><<<1, threads, bytes, h->stream>>>(h->words[0], h->words[1], g, a, h->t, n,
+                                                                       every, rec);
+    return cudaGetLastError();
+}
+
+template <int F>
+static cudaError_t allow_group_smem()
+{
+    cudaError_t e = cudaFuncSetAttribute(resident_group_kernel<F, 10>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kResidentMaxBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(resident_group_kernel<F, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kResidentMaxBytes);
+    return e;
+}
+
 static int run_resident(ising_lattice* h, int n, int every)
 {
     const Geom& g = h->g;
@@ -589,21 +712,32 @@ static int run_resident(ising_lattice* h, int n, int every)
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(resident_sweeps_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kResidentMaxBytes);
-
+        if (e == cudaSuccess) e = allow_group_smem<2>();
+        if (e == cudaSuccess) e = allow_group_smem<4>();
+        if (e == cudaSuccess) e = allow_group_smem<32>();
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
         h->resident_attr = true;
     }
     const int items = ((g.L + 3) / 4) * g.W;
     SweepArgs a = base_args(h);
-    const int threads = std::min(256, std::max(32, (items + 31) / 32 * 32));
-    if (a.rounds == 7)
-        resident_sweeps_kernel<7><<<1, threads, bytes, h->stream>>>(h->words[0], h->words[1], g, a, h->t, n, every,
-                                                                    reinterpret_cast<long long*>(h->counts));
-    else
-        resident_sweeps_kernel<10><<<1, threads, bytes, h->stream>>>(h->words[0], h->words[1], g, a, h->t, n, every,
-                                                                     reinterpret_cast<long long*>(h->counts));
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "resident_sweeps_kernel");
+    long long* rec = reinterpret_cast<long long*>(h->counts);
+    cudaError_t e = cudaSuccess;
+    switch (resident_lanes(g)) {
+    case 32: e = launch_resident_group<32>(h, a, bytes, n, every, rec); break;
+    case 4: e = launch_resident_group<4>(h, a, bytes, n, every, rec); break;
+    case 2: e = launch_resident_group<2>(h, a, bytes, n, every, rec); break;
+    default: {
+        const int threads = std::min(256, std::max(32, (items + 31) / 32 * 32));
+        if (a.rounds == 7)
+            resident_sweeps_kernel<7><<<1, threads, bytes, h->stream>>>(h->words[0], h->words[1], g, a, h->t, n,
+                                                                        every, rec);
+        else
+            resident_sweeps_kernel<10><<<1, threads, bytes, h->stream>>>(h->words[0], h->words[1], g, a, h->t, n,
+                                                                         every, rec);
+        e = cudaGetLastError();
+    }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "resident sweeps kernel");
     advance_sweep_kernel<<<1, 1, 0, h->stream>>>(h->t_dev, (uint64_t)n);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "advance_sweep_kernel");

@@ -27,7 +27,11 @@ def run(ising, L, seed, beta, n, every, path, hot=True):
         return E, M, lat.get_spins(), lat.t, lat.energy()
 
 
-@pytest.mark.parametrize("L", [4, 6, 10, 42, 44, 64, 86, 128, 130, 256, 512, 700])
+# Lanes per item on the on-chip path (items = ceil(L/4) * W): a warp up to 12
+# items (L <= 42), 4 lanes up to 100 items (L = 44 .. 126), 2 lanes up to 200
+# (L = 128 .. 168), one thread per item above (L >= 170).
+@pytest.mark.parametrize("L", [4, 6, 10, 42, 44, 46, 64, 66, 84, 86, 100, 126, 128, 130, 168, 170, 200,
+                               256, 300, 512, 700])
 def test_resident_equals_launches(ising, L):
     beta = 0.3 + (L % 7) * 0.05
     a = run(ising, L, 40 + L, beta, 25, 3, ising.ISING_PATH_RESIDENT)
@@ -35,6 +39,20 @@ def test_resident_equals_launches(ising, L):
     for x, y in zip(a, b):
         np.testing.assert_array_equal(x, y)
     assert a[3] == 28
+
+
+@pytest.mark.parametrize("L", [32, 64, 66, 130, 256])
+def test_resident_seven_round_scheme_equals_launches(ising, L):
+    def go(path):
+        with ising.Lattice(L, 9) as lat:
+            lat.set_rng(ising.ISING_RNG_PHILOX4X32_7)
+            lat.set_path(path)
+            lat.init_hot()
+            lat.set_beta(0.42)
+            E, M = lat.sweep_record(12, 1)
+            return E, M, lat.get_spins()
+    for x, y in zip(go(ising.ISING_PATH_RESIDENT), go(ising.ISING_PATH_LAUNCHES)):
+        np.testing.assert_array_equal(x, y)
 
 
 def test_resident_matches_oracle_plain_config(ising):
