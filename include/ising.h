@@ -179,6 +179,17 @@ int ising_set_stream(ising_lattice *h, void *stream);
 int ising_set_tiling(ising_lattice *h, int32_t rows_per_thread,
                      int32_t block_words, int32_t block_groups);
 
+/* Lanes per thread item on the launch path: 1, 2, 4 or 8, or 0 (default)
+ * for the library's choice by lattice size (4 up to 8192 items, i.e. L up to
+ * about 1100; 1 above).  With F lanes, lane q of an item
+ * (4 rows x 1 word) draws the fields q, q + F, ... and the lanes merge their
+ * accept bits with warp shuffles: F times the threads, each with 1/F of the
+ * item's Philox calls.  This fills the GPU for lattices whose one thread
+ * per item would leave SMs idle.  No counterpart in the paper (a scheduling
+ * choice); results do not depend on it.  Row-packed layout only (EINVAL
+ * otherwise; EINVAL for other values). */
+int ising_set_item_lanes(ising_lattice *h, int32_t lanes);
+
 /* Execution path of ising_sweep / ising_sweep_record.  ISING_PATH_LAUNCHES:
  * two kernel launches per sweep, all SMs.  ISING_PATH_RESIDENT: temporal
  * blocking with the whole lattice on chip -- one block copies both colour
@@ -354,11 +365,13 @@ int ising_server_destroy(ising_server *srv);
  * table. */
 
 /* Single lattice of side L: the launch shapes of ising_set_tiling (1-D with
- * 64/128/192/256 threads, eleven 2-D block_words x block_groups) and, if the
- * lattice fits, the on-chip path; `sweeps` timed sweeps
- * each (1..100000) from a hot start at T = 2.269.  Outputs may be NULL. */
+ * 64/128/192/256 threads, eleven 2-D block_words x block_groups) with one
+ * thread per item, the 1-D shape with 2, 4 and 8 lanes per item
+ * (ising_set_item_lanes) and, if the lattice fits, the on-chip path;
+ * `sweeps` timed sweeps each (1..100000) from a hot start at T = 2.269.
+ * best_item_lanes is 0 for the on-chip path.  Outputs may be NULL. */
 int ising_autotune(int32_t L, int32_t sweeps, int32_t *best_block_words, int32_t *best_block_groups,
-                   int32_t *best_path, double *ns_per_update);
+                   int32_t *best_path, int32_t *best_item_lanes, double *ns_per_update);
 
 /* Batch (arguments as ising_batch_create): threads per tile {64, 128, 256}
  * x graph chunk {10, 50, 200} x lanes {1, 2, 4}, `sweeps` timed sweeps per

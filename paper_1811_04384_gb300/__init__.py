@@ -151,6 +151,10 @@ class Lattice:
     def set_tiling(self, rows: int = 4, block_words: int = 0, block_groups: int = 128):
         _check(load().ising_set_tiling(self._h, rows, block_words, block_groups), "ising_set_tiling")
 
+    def set_item_lanes(self, lanes: int = 0):
+        """Lanes per thread item on the launch path: 1, 2, 4, 8 or 0 (auto)."""
+        _check(load().ising_set_item_lanes(self._h, int(lanes)), "ising_set_item_lanes")
+
     def set_rng(self, scheme: int):
         """ISING_RNG_PHILOX4X32_10 (default) or the opt-in ISING_RNG_PHILOX4X32_7."""
         _check(load().ising_set_rng(self._h, int(scheme)), "ising_set_rng")

@@ -58,6 +58,7 @@ SYMBOLS = {
     "ising_get_sweep": (_int, [_vp, _pu64]),
     "ising_set_sweep": (_int, [_vp, _u64]),
     "ising_set_stream": (_int, [_vp, _vp]),
+    "ising_set_item_lanes": (_int, [_vp, _i32]),
     "ising_set_tiling": (_int, [_vp, _i32, _i32, _i32]),
     "ising_device_words": (_int, [_vp, _i32, _pvp]),
     "ising_set_path": (_int, [_vp, _i32]),
@@ -80,7 +81,7 @@ SYMBOLS = {
     "ising_server_release": (_int, [_vp, _u64]),
     "ising_server_stats": (_int, [_vp, _pi64, _pd, _pi64, _pd]),
     "ising_server_destroy": (_int, [_vp]),
-    "ising_autotune": (_int, [_i32, _i32, _pi32, _pi32, _pi32, _pd]),
+    "ising_autotune": (_int, [_i32, _i32, _pi32, _pi32, _pi32, _pi32, _pd]),
     "ising_batch_autotune": (_int, [_i32, _pi32, _pd, _pu64, _pu8, _i64, _pi32, _pi32, _pi32, _pd]),
     "ising_sweep_record_noalloc": (_int, [_vp, _vp, _i32, _u64, _dbl, _u64, _i64, _i64, _pi64, _pi64, _vp]),
 }

@@ -49,4 +49,8 @@ cudaError_t launch_half_sweep(int bw, int bgrp, int colour, bool update, bool re
                               uint64_t* own, const uint64_t* other, const Geom& g, const SweepArgs& a,
                               cudaStream_t s);
 
+// A half-sweep that updates, with F = 2, 4 or 8 lanes per thread item.
+cudaError_t launch_half_sweep_lanes(int F, int colour, bool record, uint64_t* own, const uint64_t* other,
+                                    const Geom& g, const SweepArgs& a, cudaStream_t s);
+
 }  // namespace ising

@@ -250,6 +250,52 @@ resident_group_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom
     }
 }
 
+// One half-sweep of colour C over all SMs with F lanes per thread item
+// (sweep_item_lanes on the lattice in global memory): for lattices whose one
+// thread per item would leave SMs idle and each thread with a long chain of
+// 21 Philox calls.  Thread k of the grid is lane k % F of item k / F.  Same
+// results as half_sweep_kernel.
+template <int C, bool RECORD, int F, int ROUNDS>
+__global__ void __launch_bounds__(128, 4)
+half_sweep_lanes_kernel(uint64_t* __restrict__ own, const uint64_t* __restrict__ other, Geom g, SweepArgs a)
+{
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int item = (int)(k / F), q = (int)(k % F);
+    const int items = ((g.L + 3) / 4) * g.W;
+    const uint64_t t = *a.t_base + a.t_off;
+    uint32_t anti = 0, up = 0;
+    sweep_item_lanes<C, RECORD, F, ROUNDS>(own, other, g, item, item < items, q, t, a.rk, a.thr0, a.thr1, a.all0,
+                                           a.all1, anti, up);
+    if (RECORD) block_add_counts(a.counts + 2 * (blockIdx.x % kCountSlots), anti, up);
+}
+
+template <int F, int ROUNDS>
+static void launch_lanes_r(int colour, bool record, uint64_t* own, const uint64_t* other, const Geom& g,
+                           const SweepArgs& a, cudaStream_t s)
+{
+    const uint32_t threads = (uint32_t)(((g.L + 3) / 4) * g.W) * F;
+    const dim3 block(128), grid((threads + 127) / 128);
+    if (colour == 0) half_sweep_lanes_kernel<0, false, F, ROUNDS><<<grid, block, 0, s>>>(own, other, g, a);
+    else if (record) half_sweep_lanes_kernel<1, true, F, ROUNDS><<<grid, block, 0, s>>>(own, other, g, a);
+    else half_sweep_lanes_kernel<1, false, F, ROUNDS><<<grid, block, 0, s>>>(own, other, g, a);
+}
+
+// A half-sweep that updates, with F = 2, 4 or 8 lanes per item.
+cudaError_t launch_half_sweep_lanes(int F, int colour, bool record, uint64_t* own, const uint64_t* other,
+                                    const Geom& g, const SweepArgs& a, cudaStream_t s)
+{
+    const bool r7 = a.rounds == 7;
+    switch (F) {
+    case 2: r7 ? launch_lanes_r<2, 7>(colour, record, own, other, g, a, s)
+               : launch_lanes_r<2, 10>(colour, record, own, other, g, a, s); break;
+    case 4: r7 ? launch_lanes_r<4, 7>(colour, record, own, other, g, a, s)
+               : launch_lanes_r<4, 10>(colour, record, own, other, g, a, s); break;
+    default: r7 ? launch_lanes_r<8, 7>(colour, record, own, other, g, a, s)
+                : launch_lanes_r<8, 10>(colour, record, own, other, g, a, s); break;
+    }
+    return cudaGetLastError();
+}
+
 // Test hook: Philox4x32-10 blocks of arbitrary counters.
 __global__ void philox_blocks_kernel(const uint32_t* __restrict__ ctr, uint32_t* __restrict__ out,
                                      int64_t n, uint32_t key0, uint32_t key1)
@@ -309,6 +355,7 @@ struct ising_lattice {
     int path = ISING_PATH_AUTO;                  // multi-block launches or on-chip resident sweeps
     int rounds = 10;                             // Philox rounds of the sweep draws
     int layout = ISING_LAYOUT_ROW_PACKED;        // or the paper's column-interleaved words
+    int item_lanes = 0;                          // lanes per thread item on the launch path (0: auto)
     bool resident_attr = false;                  // dynamic shared memory attribute set
 };
 
@@ -615,11 +662,28 @@ static SweepArgs base_args(const ising_lattice* h)
     return a;
 }
 
+// Lanes per thread item on the launch path: the handle's choice, else 4 up
+// to 8192 items (L <= about 1100) and 1 above.  Measured on GB300 (sweeps
+// without records, spin-updates/ns, F = 1 / 2 / 4 / 8 lanes): L = 512:
+// 21 / 27 / 32 / 32; L = 1024: 85 / 102 / 128 / 128; L = 2048: 340 / 340 /
+// 340 / 256; L = 4096: 815 / 680 / 584 / 454.  Below L = 2048 each launch is
+// short and the lanes shorten it further; above, one thread per item fills
+// the GPU and the merge is pure overhead.
+static int item_lanes(const ising_lattice* h)
+{
+    if (h->item_lanes > 0) return h->item_lanes;
+    const int items = ((h->g.L + 3) / 4) * h->g.W;
+    return items <= 8192 ? 4 : 1;
+}
+
 // One half-sweep of the handle's lattice in its layout.
 static cudaError_t launch_hs(const ising_lattice* h, int colour, bool update, bool record, const SweepArgs& a)
 {
     if (h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED)
         return ci_half_sweep(colour, update, record, h->words[0], h->g.L, a, h->stream);
+    const int F = item_lanes(h);
+    if (update && F > 1)
+        return launch_half_sweep_lanes(F, colour, record, h->words[colour], h->words[1 - colour], h->g, a, h->stream);
     return launch_half_sweep(h->bw, h->bg, colour, update, record, h->words[colour], h->words[1 - colour], h->g, a,
                              h->stream);
 }
@@ -1008,6 +1072,15 @@ extern "C" int ising_set_tiling(ising_lattice* h, int32_t rows, int32_t bw, int3
     if (bw * bgrp > 256 || bw * bgrp < 32) return ISING_EINVAL;
     h->bw = bw;
     h->bg = bgrp;
+    return ISING_OK;
+}
+
+extern "C" int ising_set_item_lanes(ising_lattice* h, int32_t lanes)
+{
+    if (!h) return ISING_EINVAL;
+    if (h->layout != ISING_LAYOUT_ROW_PACKED) return ISING_EINVAL;   // row-packed words only
+    if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) return ISING_EINVAL;
+    h->item_lanes = lanes;
     return ISING_OK;
 }
 

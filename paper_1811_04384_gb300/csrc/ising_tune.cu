@@ -17,7 +17,7 @@ constexpr double kBetaTune = 1.0 / 2.269;   // timing point: the critical region
 constexpr uint64_t kSeedTune = 0x5eed;
 
 struct Candidate {
-    int bw, bg, path;
+    int bw, bg, path, lanes;   // lanes per thread item on the launch path
 };
 
 // Time `sweeps` sweeps of a fresh hot-start lattice with candidate c; the
@@ -36,6 +36,7 @@ int time_candidate(int32_t L, int32_t sweeps, const Candidate& c, double* ms, st
     if (rc == ISING_OK) rc = ising_set_stream(h, s);
     if (rc == ISING_OK) rc = ising_set_path(h, c.path);
     if (rc == ISING_OK && c.path == ISING_PATH_LAUNCHES) rc = ising_set_tiling(h, 4, c.bw, c.bg);
+    if (rc == ISING_OK && c.path == ISING_PATH_LAUNCHES) rc = ising_set_item_lanes(h, c.lanes);
     if (rc == ISING_OK) rc = ising_init_hot(h);
     if (rc == ISING_OK) rc = ising_set_beta(h, kBetaTune);
     if (rc == ISING_OK) rc = ising_sweep(h, 1);                  // warm-up (module load, caches)
@@ -62,17 +63,15 @@ int time_candidate(int32_t L, int32_t sweeps, const Candidate& c, double* ms, st
 }  // namespace
 
 extern "C" int ising_autotune(int32_t L, int32_t sweeps, int32_t* best_bw, int32_t* best_bg, int32_t* best_path,
-                              double* ns_per_update)
+                              int32_t* best_lanes, double* ns_per_update)
 {
     if (!ising::valid_side(L) || sweeps < 1 || sweeps > 100000) return ISING_EINVAL;
-    std::vector<Candidate> cands = {{0, 128, ISING_PATH_LAUNCHES},  {0, 64, ISING_PATH_LAUNCHES},
-                                    {0, 192, ISING_PATH_LAUNCHES},  {0, 256, ISING_PATH_LAUNCHES},
-                                    {32, 4, ISING_PATH_LAUNCHES},  {16, 2, ISING_PATH_LAUNCHES},
-                                    {16, 4, ISING_PATH_LAUNCHES},  {16, 8, ISING_PATH_LAUNCHES},
-                                    {16, 16, ISING_PATH_LAUNCHES}, {32, 1, ISING_PATH_LAUNCHES},
-                                    {32, 2, ISING_PATH_LAUNCHES},  {32, 8, ISING_PATH_LAUNCHES},
-                                    {64, 1, ISING_PATH_LAUNCHES},  {64, 2, ISING_PATH_LAUNCHES},
-                                    {64, 4, ISING_PATH_LAUNCHES},  {32, 4, ISING_PATH_RESIDENT}};
+    const int P = ISING_PATH_LAUNCHES;
+    std::vector<Candidate> cands = {{0, 128, P, 1},  {0, 64, P, 1},   {0, 192, P, 1},  {0, 256, P, 1},
+                                    {32, 4, P, 1},   {16, 2, P, 1},   {16, 4, P, 1},   {16, 8, P, 1},
+                                    {16, 16, P, 1},  {32, 1, P, 1},   {32, 2, P, 1},   {32, 8, P, 1},
+                                    {64, 1, P, 1},   {64, 2, P, 1},   {64, 4, P, 1},   {0, 128, P, 2},
+                                    {0, 128, P, 4},  {0, 128, P, 8},  {0, 128, ISING_PATH_RESIDENT, 0}};
     std::vector<uint64_t> ref, words;
     double best = -1.0;
     Candidate pick = cands[0];
@@ -91,6 +90,7 @@ extern "C" int ising_autotune(int32_t L, int32_t sweeps, int32_t* best_bw, int32
     if (best_bw) *best_bw = pick.bw;
     if (best_bg) *best_bg = pick.bg;
     if (best_path) *best_path = pick.path;
+    if (best_lanes) *best_lanes = pick.lanes;
     if (ns_per_update) *ns_per_update = best * 1e6 / ((double)sweeps * L * L);
     return ISING_OK;
 }

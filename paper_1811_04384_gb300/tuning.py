@@ -2,7 +2,7 @@
 include/ising.h), kept in a JSON table next to this file:
 
     {"device": "...", "lattice": {"<L>": {"block_words": .., "block_groups": ..,
-     "path": .., "ns_per_update": ..}}, "batch": {...}}
+     "path": .., "item_lanes": .., "ns_per_update": ..}}, "batch": {...}}
 
 `apply(lattice)` sets the tuned shape for the lattice's side when the table
 holds one for the current device.  Choosing a shape never changes results.
@@ -29,11 +29,12 @@ def _device_name() -> str:
 
 
 def tune_lattice(L: int, sweeps: int = 20) -> dict:
-    bw, bg, path = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    bw, bg, path, lanes = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     ns = ctypes.c_double()
     _check(load().ising_autotune(int(L), int(sweeps), ctypes.byref(bw), ctypes.byref(bg), ctypes.byref(path),
-                                 ctypes.byref(ns)), "ising_autotune")
-    return {"block_words": bw.value, "block_groups": bg.value, "path": path.value, "ns_per_update": ns.value}
+                                 ctypes.byref(lanes), ctypes.byref(ns)), "ising_autotune")
+    return {"block_words": bw.value, "block_groups": bg.value, "path": path.value, "item_lanes": lanes.value,
+            "ns_per_update": ns.value}
 
 
 def tune_batch(L, beta, seed, hot, sweeps: int = 50) -> dict:
@@ -81,4 +82,5 @@ def apply(lattice, table: dict | None = None) -> bool:
     lattice.set_path(entry["path"])
     if entry["path"] == 1:
         lattice.set_tiling(4, entry["block_words"], entry["block_groups"])
+        lattice.set_item_lanes(entry.get("item_lanes", 0))
     return True

@@ -179,6 +179,47 @@ def test_tiling_does_not_change_results(ising, tiling):
         np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("L", [4, 44, 46, 130, 258, 1026])
+@pytest.mark.parametrize("lanes", [2, 4, 8])
+def test_item_lanes_do_not_change_results(ising, L, lanes):
+    """Launch path with 2, 4 or 8 lanes per thread item (fields split over the
+    lanes, accept bits merged by shuffles) against one thread per item, with
+    records every sweep and a ragged last word / row group."""
+    def go(F):
+        with ising.Lattice(L, 21) as lat:
+            lat.set_path(ising.ISING_PATH_LAUNCHES)
+            lat.set_item_lanes(F)
+            lat.init_hot()
+            lat.set_beta(BETA_TC)
+            E, M = lat.sweep_record(7, 1)
+            return E, M, lat.get_spins()
+    for a, b in zip(go(1), go(lanes)):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_item_lanes_match_oracle(ising):
+    L = 46
+    with ising.Lattice(L, 8) as lat:
+        lat.set_path(ising.ISING_PATH_LAUNCHES)
+        lat.set_item_lanes(4)
+        lat.init_hot()
+        lat.set_beta(0.41)
+        E, M = lat.sweep_record(9, 3)
+        S = lat.get_spins()
+    s = oracle.init_hot(L, 8)
+    Eo, Mo = oracle.run(s, 8, 0.41, 0, 9, 3)
+    np.testing.assert_array_equal(E, Eo)
+    np.testing.assert_array_equal(M, Mo)
+    np.testing.assert_array_equal(S, s)
+
+
+def test_item_lanes_rejects_bad_values(ising):
+    with ising.Lattice(64, 1) as lat:
+        for bad in (3, 16, -1):
+            with pytest.raises(ising.IsingError):
+                lat.set_item_lanes(bad)
+
+
 def test_rejected_tilings(ising):
     with ising.Lattice(64, 1) as lat:
         for bad in [(8, 32, 4), (4, 48, 4), (4, 64, 8), (4, 16, 1), (4, 32, 3), (4, 0, 32), (4, 0, 96),

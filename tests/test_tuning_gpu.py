@@ -21,6 +21,7 @@ def test_autotune_lattice_choice_is_valid_and_neutral(ising, L):
     best = tuning.tune_lattice(L, sweeps=4)
     assert best["path"] in (ising.ISING_PATH_LAUNCHES, ising.ISING_PATH_RESIDENT)
     assert best["ns_per_update"] > 0
+    assert best["item_lanes"] in (0, 1, 2, 4, 8)
     if L > 740:
         assert best["path"] == ising.ISING_PATH_LAUNCHES
     table = {"device": tuning._device_name(), "lattice": {str(L): best}}
