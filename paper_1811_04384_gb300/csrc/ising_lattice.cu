@@ -722,8 +722,6 @@ static bool use_resident(const ising_lattice* h)
     return h->path == ISING_PATH_RESIDENT || ((h->g.L + 3) / 4) * h->g.W <= kResidentAutoMaxItems;
 }
 
-// n sweeps with the lattice resident in shared memory, E/M records (if any)
-// written as (E, M) pairs into the count buffer.
 // Lanes per item of the on-chip path (0: one thread per item,
 // resident_sweeps_kernel), from a GB300 sweep of 1000 recorded sweeps at
 // L = 16 .. 256 over 1, 2, 4, 8 and 32 lanes: one warp per item up to 12
@@ -766,6 +764,8 @@ static cudaError_t allow_group_smem()
     return e;
 }
 
+// n sweeps with the lattice resident in shared memory, E/M records (if any)
+// written as (E, M) pairs into the count buffer.
 static int run_resident(ising_lattice* h, int n, int every)
 {
     const Geom& g = h->g;
