@@ -145,10 +145,30 @@ int ising_magnetization(ising_lattice *h, int64_t *host_M);
  * row-major s[i*L + j], each +1 or -1 (set: any value > 0 counts as +1).
  * Packing and unpacking run on the device through an int8 L*L staging
  * buffer that the library allocates on first use (also for ising_create_on
- * lattices) and frees in ising_destroy.  n != L*L -> EINVAL.
+ * lattices) and frees in ising_destroy; ising_set_spins reads a pinned host
+ * array (cudaHostAlloc / cudaHostRegister) in place instead, in one pass.  n != L*L -> EINVAL.
  * Synchronises.  Neither changes t. */
 int ising_get_spins(ising_lattice *h, int8_t *host_out, size_t n);
 int ising_set_spins(ising_lattice *h, const int8_t *host_in, size_t n);
+
+/* Run a sequence of lattice states: for k = 0 .. nstates-1, ising_set_spins
+ * with states[k] (L*L int8, row-major, > 0 is up), then ising_sweep_record of
+ * `sweeps` sweeps with a record every `every`-th sweep, into E / M entries
+ * k*R .. k*R + R - 1, R = sweeps / every (caller-owned host arrays of
+ * nstates*R entries, either may be NULL).  The sweep counter continues
+ * across states, so the results are those of the calls made one after
+ * another.  The library copies state k + 1 to the device, on a copy stream
+ * and into a second input buffer, while the sweeps of state k run.  With
+ * pinned host arrays (cudaHostAlloc / cudaHostRegister) the copies overlap
+ * the sweeps; pageable arrays work but do not overlap.  The arrays must stay
+ * unchanged until the call returns.  On the on-chip path, with the
+ * interleaved layout, or with more than 1024 records per state, the calls
+ * run in turn.  No counterpart in the paper (input streaming).
+ * Synchronises.  Errors: EINVAL (null state, sweeps > 2^30, every out of
+ * 1..2^22), ENOMEM, ECUDA. */
+int ising_run_states(ising_lattice *h, const int8_t *const *states, int32_t nstates, int64_t sweeps,
+                     int64_t every, int64_t *E, int64_t *M);
+
 
 /* The packed colour arrays, for checkpoints: n64 = 2 * L * pitch words,
  * colour 0 first, each colour row-major with `pitch` words per row (see

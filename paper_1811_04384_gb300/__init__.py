@@ -151,6 +151,24 @@ class Lattice:
     def set_tiling(self, rows: int = 4, block_words: int = 0, block_groups: int = 128):
         _check(load().ising_set_tiling(self._h, rows, block_words, block_groups), "ising_set_tiling")
 
+    def run_states(self, states, sweeps: int, every: int = 1):
+        """ising_run_states: for each int8 L x L array in `states` (pinned host
+        memory overlaps its copy with the previous state's sweeps), set the
+        spins and run `sweeps` sweeps with a record every `every`; returns int64
+        E and M of shape (len(states), sweeps // every)."""
+        arrs = [np.ascontiguousarray(a, dtype=np.int8) for a in states]
+        for a in arrs:
+            assert a.size == self.L * self.L
+        n = len(arrs)
+        R = max(int(sweeps), 0) // max(int(every), 1)
+        E = np.zeros((n, R), dtype=np.int64)
+        M = np.zeros((n, R), dtype=np.int64)
+        ptrs = (ctypes.c_void_p * max(n, 1))(*[a.ctypes.data_as(ctypes.c_void_p).value for a in arrs])
+        _check(load().ising_run_states(self._h, ptrs, n, int(sweeps), int(every),
+                                       E.ctypes.data_as(ctypes.c_void_p), M.ctypes.data_as(ctypes.c_void_p)),
+               "ising_run_states")
+        return E, M
+
     def set_item_lanes(self, lanes: int = 0):
         """Lanes per thread item on the launch path: 1, 2, 4, 8 or 0 (auto)."""
         _check(load().ising_set_item_lanes(self._h, int(lanes)), "ising_set_item_lanes")

@@ -59,6 +59,7 @@ SYMBOLS = {
     "ising_set_sweep": (_int, [_vp, _u64]),
     "ising_set_stream": (_int, [_vp, _vp]),
     "ising_set_item_lanes": (_int, [_vp, _i32]),
+    "ising_run_states": (_int, [_vp, _vp, _i32, _i64, _i64, _vp, _vp]),
     "ising_set_tiling": (_int, [_vp, _i32, _i32, _i32]),
     "ising_device_words": (_int, [_vp, _i32, _pvp]),
     "ising_set_path": (_int, [_vp, _i32]),

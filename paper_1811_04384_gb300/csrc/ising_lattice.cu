@@ -56,25 +56,37 @@ __global__ void init_cold_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict
     w1[(size_t)i * g.P + w] = v;
 }
 
-// int8 spins (row-major L x L, > 0 is up) -> packed colour words.
-__global__ void pack_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom g,
-                            const int8_t* __restrict__ s)
+// int8 spins of row blockIdx.x (> 0 is up) -> that row's words of both
+// colours.  The row is first staged in shared memory (16-byte loads when
+// vec16: `in` 16-byte aligned and L % 16 == 0), so the input is read once
+// and coalesced; `in` may be device memory or pinned host memory mapped into
+// the device's address space.  Dynamic shared memory: L bytes.
+__global__ void pack_rows_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom g,
+                                 const int8_t* __restrict__ in, int vec16)
 {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y * blockDim.y + threadIdx.y;
-    const int c = blockIdx.z;
-    if (w >= g.P || i >= g.L) return;
-    uint64_t word = 0;
-    if (w < g.W) {
-        const int nf = (w == g.W - 1) ? g.rlast : kFields;
-        const int par = (i + c) & 1;
-        const int8_t* row = s + (size_t)i * g.L;
-        for (int k = 0; k < nf; ++k) {
-            const int j = 2 * (w * kFields + k) + par;
-            word |= (uint64_t)(row[j] > 0) << (3 * k);
-        }
+    extern __shared__ __align__(16) int8_t row_s[];
+    const int i = blockIdx.x;
+    const int8_t* src = in + (size_t)i * g.L;
+    if (vec16) {
+        const uint4* s4 = reinterpret_cast<const uint4*>(src);
+        uint4* d4 = reinterpret_cast<uint4*>(row_s);
+        for (int k = threadIdx.x; k < g.L / 16; k += blockDim.x) d4[k] = s4[k];
+    } else {
+        for (int k = threadIdx.x; k < g.L; k += blockDim.x) row_s[k] = src[k];
     }
-    (c ? w1 : w0)[(size_t)i * g.P + w] = word;
+    __syncthreads();
+    for (int t = threadIdx.x; t < 2 * g.P; t += blockDim.x) {
+        const int c = t >= g.P ? 1 : 0;
+        const int w = t - c * g.P;
+        uint64_t word = 0;
+        if (w < g.W) {
+            const int nf = (w == g.W - 1) ? g.rlast : kFields;
+            const int par = (i + c) & 1;
+            const int8_t* r = row_s + 2 * w * kFields + par;
+            for (int k = 0; k < nf; ++k) word |= (uint64_t)(r[2 * k] > 0) << (3 * k);
+        }
+        (c ? w1 : w0)[(size_t)i * g.P + w] = word;
+    }
 }
 
 // Packed colour words -> int8 spins (+1 / -1).
@@ -350,6 +362,9 @@ struct ising_lattice {
     unsigned long long* counts = nullptr;
     uint64_t* t_dev = nullptr;
     int8_t* staging = nullptr;   // lazily allocated int8 L*L (get/set spins)
+    int8_t* staging2 = nullptr;  // second input buffer of ising_run_states
+    cudaStream_t copy_stream = nullptr;          // ising_run_states: host -> device copies
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_packed[2] = {nullptr, nullptr};
     unsigned long long* host_counts = nullptr;   // pinned, kCountBytes
     int bw = 0, bg = 128;                        // half-sweep shape: linear items, 128 threads a block
     int path = ISING_PATH_AUTO;                  // multi-block launches or on-chip resident sweeps
@@ -512,6 +527,12 @@ static void free_handle(ising_lattice* h)
 {
     if (!h) return;
     if (h->staging) cudaFree(h->staging);
+    if (h->staging2) cudaFree(h->staging2);
+    for (int b = 0; b < 2; ++b) {
+        if (h->ev_copied[b]) cudaEventDestroy(h->ev_copied[b]);
+        if (h->ev_packed[b]) cudaEventDestroy(h->ev_packed[b]);
+    }
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     if (h->owns_mem && h->base) cudaFree(h->base);
     if (h->host_counts) cudaFreeHost(h->host_counts);
     delete h;
@@ -980,19 +1001,116 @@ extern "C" int ising_set_spins(ising_lattice* h, const int8_t* in, size_t n)
     int rc = ensure_staging(h);
     if (rc != ISING_OK) return rc;
     const Geom& g = h->g;
-    cudaError_t e = cudaMemcpyAsync(h->staging, in, n, cudaMemcpyHostToDevice, h->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync spins");
+    // Pinned host memory is read by the pack kernel itself (one pass over the
+    // host link); anything else is first copied to the device staging buffer.
+    const int8_t* src = h->staging;
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, in);
+    if (e == cudaSuccess && attr.type == cudaMemoryTypeHost && attr.devicePointer &&
+        h->layout == ISING_LAYOUT_ROW_PACKED) {
+        src = static_cast<const int8_t*>(attr.devicePointer);
+    } else {
+        cudaGetLastError();                          // a failed query is not an error here
+        e = cudaMemcpyAsync(h->staging, in, n, cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync spins");
+    }
     if (h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED) {
         e = ci_pack(h->words[0], g.L, h->staging, h->stream);
     } else {
-        dim3 block(32, 8);
-        dim3 grid((g.P + 31) / 32, (g.L + 7) / 8, 2);
-        pack_kernel<<<grid, block, 0, h->stream>>>(h->words[0], h->words[1], g, h->staging);
+        const int vec16 = ((uintptr_t)src % 16 == 0) && (g.L % 16 == 0);
+        pack_rows_kernel<<<g.L, 256, g.L, h->stream>>>(h->words[0], h->words[1], g, src, vec16);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return cuda_fail(e, "pack_kernel");
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return ISING_OK;
+}
+
+// Resources of ising_run_states (created on first use, kept): the second
+// input buffer, a copy stream and the events that order copies, packs and
+// sweeps.
+static int ensure_pipeline(ising_lattice* h)
+{
+    int rc = ensure_staging(h);
+    if (rc != ISING_OK) return rc;
+    cudaError_t e = cudaSuccess;
+    if (!h->staging2) {
+        e = cudaMalloc(&h->staging2, (size_t)h->g.L * h->g.L);
+        if (e != cudaSuccess) { h->staging2 = nullptr; cuda_fail(e, "cudaMalloc staging"); return ISING_ENOMEM; }
+    }
+    if (!h->copy_stream) e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        if (!h->ev_copied[b]) e = cudaEventCreateWithFlags(&h->ev_copied[b], cudaEventDisableTiming);
+        if (e == cudaSuccess && !h->ev_packed[b]) e = cudaEventCreateWithFlags(&h->ev_packed[b], cudaEventDisableTiming);
+    }
+    return e == cudaSuccess ? ISING_OK : cuda_fail(e, "run_states setup");
+}
+
+extern "C" int ising_run_states(ising_lattice* h, const int8_t* const* states, int32_t nstates, int64_t sweeps,
+                                int64_t every, int64_t* E, int64_t* M)
+{
+    TraceRange trace("ising_run_states");
+    if (!h || !states || nstates < 0 || sweeps < 0 || sweeps > (1 << 30) || every < 1 || every > (1 << 22))
+        return ISING_EINVAL;
+    for (int32_t k = 0; k < nstates; ++k)
+        if (!states[k]) return ISING_EINVAL;
+    const size_t nn = (size_t)h->g.L * h->g.L;
+    const int64_t R = sweeps / every;                          // records per state
+    if (h->layout != ISING_LAYOUT_ROW_PACKED || use_resident(h) || R > kRecordsPerChunk) {
+        // no overlap to gain (on-chip path) or records beyond one chunk: the same calls in turn
+        for (int32_t k = 0; k < nstates; ++k) {
+            int rc = ising_set_spins(h, states[k], nn);
+            if (rc == ISING_OK) rc = ising_sweep_record(h, sweeps, every, E ? E + k * R : nullptr, M ? M + k * R : nullptr);
+            if (rc != ISING_OK) return rc;
+        }
+        return ISING_OK;
+    }
+    int rc = ensure_pipeline(h);
+    if (rc != ISING_OK) return rc;
+    const Geom& g = h->g;
+    int8_t* stage[2] = {h->staging, h->staging2};
+    const size_t rec_words = (size_t)kCountSlots * 2;         // count slots of one record
+    const int64_t group = R > 0 ? std::max<int64_t>(1, kRecordsPerChunk / R) : (int64_t)nstates;
+    for (int64_t k0 = 0; k0 < nstates; k0 += group) {
+        const int64_t k1 = std::min<int64_t>(nstates, k0 + group);
+        cudaError_t e = cudaSuccess;
+        if (R > 0)
+            e = cudaMemsetAsync(h->counts, 0, (size_t)(k1 - k0) * R * rec_words * sizeof(unsigned long long),
+                                h->stream);
+        for (int64_t k = k0; k < k1 && e == cudaSuccess; ++k) {
+            const int b = (int)(k & 1);
+            // state k -> input buffer b, once the pack that last read buffer b is done;
+            // this copy runs while the sweeps of state k - 1 are on the device
+            e = cudaStreamWaitEvent(h->copy_stream, h->ev_packed[b], 0);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(stage[b], states[k], nn, cudaMemcpyHostToDevice, h->copy_stream);
+            if (e == cudaSuccess) e = cudaEventRecord(h->ev_copied[b], h->copy_stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0);
+            if (e != cudaSuccess) break;
+            const int vec16 = ((uintptr_t)stage[b] % 16 == 0) && (g.L % 16 == 0);
+            pack_rows_kernel<<<g.L, 256, g.L, h->stream>>>(h->words[0], h->words[1], g, stage[b], vec16);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(h->ev_packed[b], h->stream);
+            if (e != cudaSuccess) break;
+            const int64_t base = (k - k0) * R;
+            rc = run_sweeps(h, sweeps, [every, base](int64_t s) {
+                return (s % every == 0) ? (int)(base + s / every - 1) : -1;
+            });
+            if (rc != ISING_OK) return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "run_states");
+        if (R > 0) {
+            const size_t nrec = (size_t)(k1 - k0) * R;
+            e = cudaMemcpyAsync(h->host_counts, h->counts, nrec * rec_words * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync counts");
+        }
+        e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+        for (int64_t r = 0; r < (k1 - k0) * R; ++r)
+            counts_to_EM(h, h->host_counts + (size_t)r * rec_words, E ? E + k0 * R + r : nullptr,
+                         M ? M + k0 * R + r : nullptr);
+    }
     return ISING_OK;
 }
 

@@ -220,6 +220,69 @@ def test_item_lanes_rejects_bad_values(ising):
                 lat.set_item_lanes(bad)
 
 
+@pytest.mark.parametrize("L", [4, 46, 64, 1024, 1026])
+def test_set_spins_from_pinned_host_memory(ising, L):
+    """ising_set_spins reads pinned host memory directly in its pack kernel
+    and copies pageable memory through a device buffer: both give the same
+    words, the round trip returns the spins, and a chain continued from them
+    equals the oracle (small L)."""
+    import torch
+    rng = np.random.default_rng(L)
+    spins = np.where(rng.random((L, L)) < 0.4, 1, -1).astype(np.int8)
+    pinned = torch.empty((L, L), dtype=torch.int8, pin_memory=True)
+    pinned.numpy()[:] = spins
+    with ising.Lattice(L, 5) as a, ising.Lattice(L, 5) as b:
+        a.set_spins(spins)                   # pageable
+        b.set_spins(pinned.numpy())          # pinned, read in place
+        np.testing.assert_array_equal(a.get_words(), b.get_words())
+        np.testing.assert_array_equal(b.get_spins(), spins)
+        b.set_beta(0.45)
+        E, M = b.sweep_record(3, 1)
+    if L <= 64:
+        s = spins.copy()
+        Eo, Mo = oracle.run(s, 5, 0.45, 0, 3, 1)
+        np.testing.assert_array_equal(E, Eo)
+        np.testing.assert_array_equal(M, Mo)
+
+
+@pytest.mark.parametrize("L,sweeps,every", [(46, 7, 2), (260, 6, 3), (1026, 4, 2), (260, 3, 5)])
+def test_run_states_equals_calls_in_turn(ising, L, sweeps, every):
+    """ising_run_states (copies of the next state overlapping the sweeps) gives
+    the E/M series and final lattice of set_spins + sweep_record in turn, with
+    pinned and pageable inputs; L = 46 takes the on-chip path, 260 and 1026
+    the launch path; sweeps < every records nothing."""
+    import torch
+    rng = np.random.default_rng(L + sweeps)
+    states = []
+    for k in range(5):
+        a = np.where(rng.random((L, L)) < 0.3 + 0.1 * k, 1, -1).astype(np.int8)
+        if k % 2:
+            p = torch.empty((L, L), dtype=torch.int8, pin_memory=True)
+            p.numpy()[:] = a
+            a = p.numpy()
+        states.append(a)
+    R = sweeps // every
+    with ising.Lattice(L, 13) as ref:
+        ref.set_beta(0.43)
+        E0, M0 = [], []
+        for a in states:
+            ref.set_spins(a)
+            E, M = ref.sweep_record(sweeps, every)
+            E0.append(E)
+            M0.append(M)
+        S0, t0 = ref.get_spins(), ref.t
+    with ising.Lattice(L, 13) as lat:
+        lat.set_beta(0.43)
+        E1, M1 = lat.run_states(states, sweeps, every)
+        S1, t1 = lat.get_spins(), lat.t
+    assert E1.shape == (5, R)
+    for k in range(5):
+        np.testing.assert_array_equal(E1[k], E0[k])
+        np.testing.assert_array_equal(M1[k], M0[k])
+    np.testing.assert_array_equal(S1, S0)
+    assert t1 == t0 == 5 * sweeps
+
+
 def test_rejected_tilings(ising):
     with ising.Lattice(64, 1) as lat:
         for bad in [(8, 32, 4), (4, 48, 4), (4, 64, 8), (4, 16, 1), (4, 32, 3), (4, 0, 32), (4, 0, 96),
