@@ -43,7 +43,15 @@ struct SweepArgs {
     uint32_t rounds;           // Philox rounds of the sweep draws: 10 (default) or 7 (opt-in)
     PhiloxKeys rk;             // round keys of the key (lo32(seed), hi32(seed))
     unsigned long long* counts;  // E/M count slots of this record (RECORD only)
+    const uint32_t* rec_base;    // device record index added to `counts` (graph replays), or null
 };
+
+// The 32 count slots a RECORD launch adds to: `counts`, moved on by
+// *rec_base records when a replayed graph picks its slot on the device.
+__device__ __forceinline__ unsigned long long* record_counts(const SweepArgs& a)
+{
+    return a.rec_base ? a.counts + (size_t)(*a.rec_base) * 2 * kCountSlots : a.counts;
+}
 
 __device__ __forceinline__ int wrap_row(int i, int L)
 {
@@ -426,7 +434,7 @@ half_sweep_kernel(uint64_t* __restrict__ own, const uint64_t* __restrict__ other
     }
     if (RECORD) {
         const int slot = (blockIdx.x + gridDim.x * blockIdx.y) % kCountSlots;
-        block_add_counts(a.counts + 2 * slot, anti, up);
+        block_add_counts(record_counts(a) + 2 * slot, anti, up);
     }
 }
 

@@ -145,7 +145,7 @@ ci_half_sweep_kernel(uint64_t* __restrict__ S, int L, int N, SweepArgs a)
     }
     if (RECORD) {
         const int slot = (blockIdx.x + gridDim.x * blockIdx.y) % kCountSlots;
-        block_add_counts(a.counts + 2 * slot, anti, up);
+        block_add_counts(record_counts(a) + 2 * slot, anti, up);
     }
 }
 

@@ -113,6 +113,15 @@ __global__ void advance_sweep_kernel(uint64_t* t_base, uint64_t n)
     if (threadIdx.x == 0 && blockIdx.x == 0) *t_base += n;
 }
 
+// End of a replayed graph of sweeps: t_base += n, record index += inc.
+__global__ void advance_graph_kernel(uint64_t* t_base, uint64_t n, uint32_t* rec_base, uint32_t inc)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        *t_base += n;
+        *rec_base += inc;
+    }
+}
+
 __global__ void set_sweep_kernel(uint64_t* t_base, uint64_t t)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) *t_base = t;
@@ -278,7 +287,7 @@ half_sweep_lanes_kernel(uint64_t* __restrict__ own, const uint64_t* __restrict__
     uint32_t anti = 0, up = 0;
     sweep_item_lanes<C, RECORD, F, ROUNDS>(own, other, g, item, item < items, q, t, a.rk, a.thr0, a.thr1, a.all0,
                                            a.all1, anti, up);
-    if (RECORD) block_add_counts(a.counts + 2 * (blockIdx.x % kCountSlots), anti, up);
+    if (RECORD) block_add_counts(record_counts(a) + 2 * (blockIdx.x % kCountSlots), anti, up);
 }
 
 template <int F, int ROUNDS>
@@ -371,8 +380,14 @@ struct ising_lattice {
     int rounds = 10;                             // Philox rounds of the sweep draws
     int layout = ISING_LAYOUT_ROW_PACKED;        // or the paper's column-interleaved words
     int item_lanes = 0;                          // lanes per thread item on the launch path (0: auto)
+    cudaStream_t capture_stream = nullptr;       // graphs of sweep chunks are captured here
+    cudaGraphExec_t graph_plain = nullptr;       // kGraphSweeps sweeps, no record
+    cudaGraphExec_t graph_rec = nullptr;         // graph_rec_every sweeps, the last one recorded
+    int graph_rec_every = 0;
     bool resident_attr = false;                  // dynamic shared memory attribute set
 };
+
+static void drop_graphs(ising_lattice* h);
 
 extern "C" const char* ising_strerror(int code)
 {
@@ -458,6 +473,7 @@ SweepArgs make_sweep_args(uint64_t seed, const uint64_t thr[2], const uint64_t* 
     a.rounds = 10;
     a.rk = philox_keys((uint32_t)seed, (uint32_t)(seed >> 32));
     a.counts = nullptr;
+    a.rec_base = nullptr;
     return a;
 }
 
@@ -533,6 +549,9 @@ static void free_handle(ising_lattice* h)
         if (h->ev_packed[b]) cudaEventDestroy(h->ev_packed[b]);
     }
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    if (h->graph_plain) cudaGraphExecDestroy(h->graph_plain);
+    if (h->graph_rec) cudaGraphExecDestroy(h->graph_rec);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     if (h->owns_mem && h->base) cudaFree(h->base);
     if (h->host_counts) cudaFreeHost(h->host_counts);
     delete h;
@@ -665,6 +684,7 @@ extern "C" int ising_set_beta(ising_lattice* h, double beta)
     if (!h || std::isnan(beta) || beta < 0.0) return ISING_EINVAL;
     h->beta = beta;
     thresholds_for_beta(beta, h->thr);
+    drop_graphs(h);                              // the thresholds are launch operands of the graphs
     return ISING_OK;
 }
 
@@ -698,15 +718,107 @@ static int item_lanes(const ising_lattice* h)
 }
 
 // One half-sweep of the handle's lattice in its layout.
-static cudaError_t launch_hs(const ising_lattice* h, int colour, bool update, bool record, const SweepArgs& a)
+static cudaError_t launch_hs_on(const ising_lattice* h, cudaStream_t st, int colour, bool update, bool record,
+                                const SweepArgs& a)
 {
     if (h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED)
-        return ci_half_sweep(colour, update, record, h->words[0], h->g.L, a, h->stream);
+        return ci_half_sweep(colour, update, record, h->words[0], h->g.L, a, st);
     const int F = item_lanes(h);
     if (update && F > 1)
-        return launch_half_sweep_lanes(F, colour, record, h->words[colour], h->words[1 - colour], h->g, a, h->stream);
+        return launch_half_sweep_lanes(F, colour, record, h->words[colour], h->words[1 - colour], h->g, a, st);
     return launch_half_sweep(h->bw, h->bg, colour, update, record, h->words[colour], h->words[1 - colour], h->g, a,
-                             h->stream);
+                             st);
+}
+
+static cudaError_t launch_hs(const ising_lattice* h, int colour, bool update, bool record, const SweepArgs& a)
+{
+    return launch_hs_on(h, h->stream, colour, update, record, a);
+}
+
+// ---- Graph replay of sweep chunks (launch path, small and mid-size lattices)
+// Below about L = 2300 a half-sweep kernel runs for a few microseconds, about
+// as long as the host takes to launch it.  Chunks of sweeps are captured once
+// into CUDA graphs and replayed: graph_plain holds kGraphSweeps sweeps, and
+// graph_rec holds `every` sweeps whose last one records into the count slots
+// picked by the device record index (advanced by the graph itself, so one
+// graph serves every record of a chunk).  The kernels' launch operands
+// (thresholds, Philox rounds, launch shape) are baked into the graphs, so
+// every call that changes them drops the graphs.
+constexpr int kGraphSweeps = 32;
+constexpr int kGraphMaxEvery = 64;
+constexpr int kGraphMaxItems = 32768;
+
+static bool use_graphs(const ising_lattice* h)
+{
+    return h->layout == ISING_LAYOUT_ROW_PACKED && ((h->g.L + 3) / 4) * h->g.W <= kGraphMaxItems;
+}
+
+static void drop_graphs(ising_lattice* h)
+{
+    if (h->graph_plain) cudaGraphExecDestroy(h->graph_plain);
+    if (h->graph_rec) cudaGraphExecDestroy(h->graph_rec);
+    h->graph_plain = nullptr;
+    h->graph_rec = nullptr;
+    h->graph_rec_every = 0;
+}
+
+static uint32_t* rec_index(const ising_lattice* h) { return reinterpret_cast<uint32_t*>(h->t_dev + 1); }
+
+// Capture `n` sweeps (relative to the device counter) into *out.  every > 0:
+// sweeps every, 2 every, ... record into the count slots 0, 1, ... past the
+// device record index, which the graph then advances by n / every.
+static int capture_sweeps(ising_lattice* h, int n, int every, cudaGraphExec_t* out)
+{
+    cudaError_t e = cudaSuccess;
+    if (!h->capture_stream) e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { h->capture_stream = nullptr; return cuda_fail(e, "capture stream"); }
+    SweepArgs a = base_args(h);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    cudaError_t le = cudaSuccess;
+    for (int s = 1; s <= n && le == cudaSuccess; ++s) {
+        a.t_off = (uint32_t)s;
+        a.counts = nullptr;
+        a.rec_base = nullptr;
+        le = launch_hs_on(h, h->capture_stream, 0, true, false, a);
+        const bool rec = every > 0 && s % every == 0;
+        if (rec) {
+            a.counts = h->counts + (size_t)(s / every - 1) * kCountSlots * 2;
+            a.rec_base = rec_index(h);
+        }
+        if (le == cudaSuccess) le = launch_hs_on(h, h->capture_stream, 1, true, rec, a);
+    }
+    if (le == cudaSuccess) {
+        advance_graph_kernel<<<1, 1, 0, h->capture_stream>>>(h->t_dev, (uint64_t)n, rec_index(h),
+                                                            every > 0 ? (uint32_t)(n / every) : 0u);
+        le = cudaGetLastError();
+    }
+    e = cudaStreamEndCapture(h->capture_stream, &graph);
+    if (le != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(le, "sweep graph capture"); }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { *out = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+    return ISING_OK;
+}
+
+// n -> n % kGraphSweeps: the whole graph_plain chunks of n sweeps, replayed.
+static int replay_plain(ising_lattice* h, int64_t* n)
+{
+    const int64_t reps = *n / kGraphSweeps;
+    if (reps == 0) return ISING_OK;
+    if (!h->graph_plain) {
+        int rc = capture_sweeps(h, kGraphSweeps, 0, &h->graph_plain);
+        if (rc != ISING_OK) return rc;
+    }
+    for (int64_t r = 0; r < reps; ++r) {
+        cudaError_t e = cudaGraphLaunch(h->graph_plain, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    }
+    h->t += (uint64_t)(reps * kGraphSweeps);
+    *n -= reps * kGraphSweeps;
+    return ISING_OK;
 }
 
 // Run `n` sweeps relative to the device counter; sweep s (1-based) records into
@@ -733,6 +845,37 @@ static int run_sweeps(ising_lattice* h, int64_t n, RecOf rec_of)
     }
     return ISING_OK;
 }
+
+// `records` x `every` sweeps, record r into count slots r: graph_rec holds
+// per = max(1, kGraphSweeps / every) records; the records left over run as
+// plain launches into their slots.
+static int replay_records(ising_lattice* h, int64_t records, int every)
+{
+    const int per = std::max(1, kGraphSweeps / every);
+    if (h->graph_rec && h->graph_rec_every != every) {
+        cudaGraphExecDestroy(h->graph_rec);
+        h->graph_rec = nullptr;
+    }
+    if (!h->graph_rec) {
+        int rc = capture_sweeps(h, per * every, every, &h->graph_rec);
+        if (rc != ISING_OK) return rc;
+        h->graph_rec_every = every;
+    }
+    cudaError_t e = cudaMemsetAsync(rec_index(h), 0, sizeof(uint32_t), h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync record index");
+    const int64_t reps = records / per;
+    for (int64_t r = 0; r < reps; ++r) {
+        e = cudaGraphLaunch(h->graph_rec, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    }
+    h->t += (uint64_t)(reps * per * every);
+    const int64_t done = reps * per, rest = records - done;
+    if (rest == 0) return ISING_OK;
+    return run_sweeps(h, rest * every, [every, done](int64_t s) {
+        return (s % every == 0) ? (int)(done + s / every - 1) : -1;
+    });
+}
+
 
 static size_t resident_bytes(const Geom& g) { return 2 * (size_t)g.L * g.P * sizeof(uint64_t); }
 
@@ -836,6 +979,7 @@ extern "C" int ising_set_rng(ising_lattice* h, int32_t scheme)
     if (scheme == ISING_RNG_PHILOX4X32_10) h->rounds = 10;
     else if (scheme == ISING_RNG_PHILOX4X32_7) h->rounds = 7;
     else return ISING_EINVAL;
+    drop_graphs(h);
     return ISING_OK;
 }
 
@@ -861,6 +1005,10 @@ extern "C" int ising_sweep(ising_lattice* h, int64_t n)
             n -= c;
         }
         return ISING_OK;
+    }
+    if (use_graphs(h)) {
+        int rc = replay_plain(h, &n);
+        if (rc != ISING_OK) return rc;
     }
     // chunks keep t_off within 32 bits
     while (n > 0) {
@@ -915,9 +1063,13 @@ extern "C" int ising_sweep_record(ising_lattice* h, int64_t n, int64_t every, in
         const size_t bytes = (size_t)chunk * kCountSlots * 2 * sizeof(unsigned long long);
         cudaError_t e = cudaMemsetAsync(h->counts, 0, bytes, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync counts");
-        int rc = run_sweeps(h, chunk * every, [every](int64_t s) {
-            return (s % every == 0) ? (int)(s / every - 1) : -1;
-        });
+        int rc;
+        if (use_graphs(h) && every <= kGraphMaxEvery)
+            rc = replay_records(h, chunk, (int)every);
+        else
+            rc = run_sweeps(h, chunk * every, [every](int64_t s) {
+                return (s % every == 0) ? (int)(s / every - 1) : -1;
+            });
         if (rc != ISING_OK) return rc;
         e = cudaMemcpyAsync(h->host_counts, h->counts, bytes, cudaMemcpyDeviceToHost, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync counts");
@@ -1183,6 +1335,7 @@ extern "C" int ising_set_tiling(ising_lattice* h, int32_t rows, int32_t bw, int3
         if (bgrp != 64 && bgrp != 128 && bgrp != 192 && bgrp != 256) return ISING_EINVAL;
         h->bw = 0;
         h->bg = bgrp;
+        drop_graphs(h);
         return ISING_OK;
     }
     if (bw != 16 && bw != 32 && bw != 64) return ISING_EINVAL;
@@ -1190,6 +1343,7 @@ extern "C" int ising_set_tiling(ising_lattice* h, int32_t rows, int32_t bw, int3
     if (bw * bgrp > 256 || bw * bgrp < 32) return ISING_EINVAL;
     h->bw = bw;
     h->bg = bgrp;
+    drop_graphs(h);
     return ISING_OK;
 }
 
@@ -1199,6 +1353,7 @@ extern "C" int ising_set_item_lanes(ising_lattice* h, int32_t lanes)
     if (h->layout != ISING_LAYOUT_ROW_PACKED) return ISING_EINVAL;   // row-packed words only
     if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) return ISING_EINVAL;
     h->item_lanes = lanes;
+    drop_graphs(h);
     return ISING_OK;
 }
 

@@ -39,7 +39,7 @@ int time_candidate(int32_t L, int32_t sweeps, const Candidate& c, double* ms, st
     if (rc == ISING_OK && c.path == ISING_PATH_LAUNCHES) rc = ising_set_item_lanes(h, c.lanes);
     if (rc == ISING_OK) rc = ising_init_hot(h);
     if (rc == ISING_OK) rc = ising_set_beta(h, kBetaTune);
-    if (rc == ISING_OK) rc = ising_sweep(h, 1);                  // warm-up (module load, caches)
+    if (rc == ISING_OK) rc = ising_sweep(h, 33);                 // warm-up (module load, caches, graph capture)
     if (rc == ISING_OK && cudaEventRecord(e0, s) != cudaSuccess) rc = ISING_ECUDA;
     if (rc == ISING_OK) rc = ising_sweep(h, sweeps);
     if (rc == ISING_OK && cudaEventRecord(e1, s) != cudaSuccess) rc = ISING_ECUDA;

@@ -283,6 +283,47 @@ def test_run_states_equals_calls_in_turn(ising, L, sweeps, every):
     assert t1 == t0 == 5 * sweeps
 
 
+@pytest.mark.parametrize("L", [260, 516, 700])
+def test_graph_replays_equal_on_chip_path(ising, L):
+    """The launch path replays captured graphs for these sizes (32-sweep
+    chunks; record chunks for every <= 64, with the record slot picked on the
+    device): it equals the on-chip path, which launches no graphs, across
+    record intervals on both sides of the graph limit, a re-capture after
+    set_beta, and remainders."""
+    def go(path):
+        with ising.Lattice(L, 31) as lat:
+            lat.set_path(path)
+            lat.init_hot()
+            lat.set_beta(0.42)
+            out = [lat.sweep_record(70, 1), lat.sweep_record(70, 7), lat.sweep_record(130, 65)]
+            lat.sweep(100)
+            lat.set_beta(0.47)
+            out.append(lat.sweep_record(66, 64))
+            lat.sweep(33)
+            return out, lat.get_spins(), lat.t
+    a, sa, ta = go(ising.ISING_PATH_LAUNCHES)
+    b, sb, tb = go(ising.ISING_PATH_RESIDENT)
+    for (Ea, Ma), (Eb, Mb) in zip(a, b):
+        np.testing.assert_array_equal(Ea, Eb)
+        np.testing.assert_array_equal(Ma, Mb)
+    np.testing.assert_array_equal(sa, sb)
+    assert ta == tb == 70 + 70 + 130 + 100 + 66 + 33
+
+
+def test_graph_replays_match_oracle(ising):
+    L, seed, beta = 1026, 6, 0.44
+    with ising.Lattice(L, seed) as lat:
+        lat.init_hot()
+        lat.set_beta(beta)
+        E, M = lat.sweep_record(40, 4)
+        S = lat.get_spins()
+    s = oracle.init_hot(L, seed)
+    Eo, Mo = oracle.run(s, seed, beta, 0, 40, 4)
+    np.testing.assert_array_equal(E, Eo)
+    np.testing.assert_array_equal(M, Mo)
+    np.testing.assert_array_equal(S, s)
+
+
 def test_rejected_tilings(ising):
     with ising.Lattice(64, 1) as lat:
         for bad in [(8, 32, 4), (4, 48, 4), (4, 64, 8), (4, 16, 1), (4, 32, 3), (4, 0, 32), (4, 0, 96),
