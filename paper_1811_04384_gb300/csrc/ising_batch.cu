@@ -156,12 +156,12 @@ int capture_graph(ising_batch* b)
             const int nt = b->lane_ntiles[k];
             if (nt == 0) continue;
             const BatchTile* tiles = b->d_tiles + b->lane_tile0[k];
-            batch_half_sweep_kernel<0><<<nt, b->threads, 0, st[k]>>>(b->d_reps, tiles, b->d_chunk_base,
-                                                                   (uint32_t)s, 1u);
+            launch_pdl(batch_half_sweep_kernel<0>, dim3(nt), dim3(b->threads), st[k], (const BatchReplica*)b->d_reps,
+                       tiles, (const uint32_t*)b->d_chunk_base, (uint32_t)s, 1u);
             le = cudaGetLastError();
             if (le != cudaSuccess) break;
-            batch_half_sweep_kernel<1><<<nt, b->threads, 0, st[k]>>>(b->d_reps, tiles, b->d_chunk_base,
-                                                                   (uint32_t)s, 1u);
+            launch_pdl(batch_half_sweep_kernel<1>, dim3(nt), dim3(b->threads), st[k], (const BatchReplica*)b->d_reps,
+                       tiles, (const uint32_t*)b->d_chunk_base, (uint32_t)s, 1u);
             le = cudaGetLastError();
         }
     }

@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(256, 3)
 batch_half_sweep_kernel(const BatchReplica* __restrict__ reps, const BatchTile* __restrict__ tiles,
                         const uint32_t* __restrict__ chunk_base, uint32_t s_local, uint32_t one)
 {
+    pdl_enter();
     const BatchTile tile = tiles[blockIdx.x];
     const BatchReplica* R = reps + tile.rep;
     const uint32_t s = *chunk_base + s_local;      // sweep of this run, 1-based

@@ -53,6 +53,17 @@ __device__ __forceinline__ unsigned long long* record_counts(const SweepArgs& a)
     return a.rec_base ? a.counts + (size_t)(*a.rec_base) * 2 * kCountSlots : a.counts;
 }
 
+// Programmatic dependent launch: a half-sweep launched with programmatic
+// stream serialization lets the next half-sweep be launched and its blocks be
+// placed as soon as every block of this one has started (launch_dependents),
+// and waits, before its first read, until the previous grid has completed
+// and its writes are visible (wait).  Both are no-ops in a plain launch.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ __forceinline__ int wrap_row(int i, int L)
 {
     return i < 0 ? i + L : (i >= L ? i - L : i);
@@ -416,6 +427,7 @@ template <int C, bool UPDATE, bool RECORD, int ROUNDS = 10, bool LINEAR = true>
 __global__ void __launch_bounds__(256, 3)
 half_sweep_kernel(uint64_t* __restrict__ own, const uint64_t* __restrict__ other, Geom g, SweepArgs a)
 {
+    pdl_enter();
     int w, row0;
     if (LINEAR) {
         const uint32_t item = blockIdx.x * blockDim.x + threadIdx.x;

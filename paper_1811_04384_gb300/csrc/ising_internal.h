@@ -40,6 +40,34 @@ cudaError_t launch_init_hot(uint64_t* w0, uint64_t* w1, const Geom& g, uint64_t 
 cudaError_t launch_init_cold(uint64_t* w0, uint64_t* w1, const Geom& g, int up, cudaStream_t s);
 cudaError_t launch_unpack(const uint64_t* w0, const uint64_t* w1, const Geom& g, int8_t* out, cudaStream_t s);
 
+// Launch `kernel` with programmatic stream serialization (the kernel calls
+// pdl_enter before its first read): the next launch's setup overlaps the end
+// of the previous one.  On a stream that is being captured into a graph the
+// launch is a plain one: measured on GB300, programmatic edges made replayed
+// graphs of short half-sweeps slower (L = 2016: 531 -> 298 spin-updates/ns),
+// while plain stream launches gained (L = 16384: +2.7%, L = 4096: +19%).
+// Errors are left for cudaGetLastError.
+template <typename... Params, typename... Args>
+inline void launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, cudaStream_t s, Args... args)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusNone;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = cs == cudaStreamCaptureStatusNone ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Geometry checks shared by the entry points.
 bool valid_side(int32_t L);
 

@@ -280,6 +280,7 @@ template <int C, bool RECORD, int F, int ROUNDS>
 __global__ void __launch_bounds__(128, 4)
 half_sweep_lanes_kernel(uint64_t* __restrict__ own, const uint64_t* __restrict__ other, Geom g, SweepArgs a)
 {
+    pdl_enter();
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     const int item = (int)(k / F), q = (int)(k % F);
     const int items = ((g.L + 3) / 4) * g.W;
@@ -296,9 +297,9 @@ static void launch_lanes_r(int colour, bool record, uint64_t* own, const uint64_
 {
     const uint32_t threads = (uint32_t)(((g.L + 3) / 4) * g.W) * F;
     const dim3 block(128), grid((threads + 127) / 128);
-    if (colour == 0) half_sweep_lanes_kernel<0, false, F, ROUNDS><<<grid, block, 0, s>>>(own, other, g, a);
-    else if (record) half_sweep_lanes_kernel<1, true, F, ROUNDS><<<grid, block, 0, s>>>(own, other, g, a);
-    else half_sweep_lanes_kernel<1, false, F, ROUNDS><<<grid, block, 0, s>>>(own, other, g, a);
+    if (colour == 0) launch_pdl(half_sweep_lanes_kernel<0, false, F, ROUNDS>, grid, block, s, own, other, g, a);
+    else if (record) launch_pdl(half_sweep_lanes_kernel<1, true, F, ROUNDS>, grid, block, s, own, other, g, a);
+    else launch_pdl(half_sweep_lanes_kernel<1, false, F, ROUNDS>, grid, block, s, own, other, g, a);
 }
 
 // A half-sweep that updates, with F = 2, 4 or 8 lanes per item.
@@ -482,13 +483,13 @@ static void launch_half_sweep_r(dim3 grid, dim3 block, int colour, bool update, 
                                 const uint64_t* other, const Geom& g, const SweepArgs& a, cudaStream_t s)
 {
     if (colour == 0) {
-        if (record) half_sweep_kernel<0, true, true, ROUNDS, LIN><<<grid, block, 0, s>>>(own, other, g, a);
-        else half_sweep_kernel<0, true, false, ROUNDS, LIN><<<grid, block, 0, s>>>(own, other, g, a);
+        if (record) launch_pdl(half_sweep_kernel<0, true, true, ROUNDS, LIN>, grid, block, s, own, other, g, a);
+        else launch_pdl(half_sweep_kernel<0, true, false, ROUNDS, LIN>, grid, block, s, own, other, g, a);
     } else if (!update) {
         half_sweep_kernel<1, false, true, 10, LIN><<<grid, block, 0, s>>>(own, other, g, a);
     } else {
-        if (record) half_sweep_kernel<1, true, true, ROUNDS, LIN><<<grid, block, 0, s>>>(own, other, g, a);
-        else half_sweep_kernel<1, true, false, ROUNDS, LIN><<<grid, block, 0, s>>>(own, other, g, a);
+        if (record) launch_pdl(half_sweep_kernel<1, true, true, ROUNDS, LIN>, grid, block, s, own, other, g, a);
+        else launch_pdl(half_sweep_kernel<1, true, false, ROUNDS, LIN>, grid, block, s, own, other, g, a);
     }
 }
 

@@ -259,8 +259,10 @@ int run_epoch(ising_server* s, const std::vector<uint64_t>& run, std::vector<Job
         for (int k = 0; k < kLanes; ++k) {
             if (lane_nt[k] == 0) continue;
             const BatchTile* t = s->d_tiles + lane_tile0[k];
-            batch_half_sweep_kernel<0><<<lane_nt[k], threads, 0, st[k]>>>(s->d_reps, t, s->d_zero, n, 1u);
-            batch_half_sweep_kernel<1><<<lane_nt[k], threads, 0, st[k]>>>(s->d_reps, t, s->d_zero, n, 1u);
+            launch_pdl(batch_half_sweep_kernel<0>, dim3(lane_nt[k]), dim3(threads), st[k],
+                       (const BatchReplica*)s->d_reps, t, (const uint32_t*)s->d_zero, n, 1u);
+            launch_pdl(batch_half_sweep_kernel<1>, dim3(lane_nt[k]), dim3(threads), st[k],
+                       (const BatchReplica*)s->d_reps, t, (const uint32_t*)s->d_zero, n, 1u);
         }
     }
     e = cudaGetLastError();
