@@ -49,7 +49,7 @@ MULWIDE_PER_SM_CLK = 32         # 32x32->64 integer multiplies (IMAD.WIDE) per S
 # DRAM bytes (read + write) per half-sweep launch of the current kernel at
 # L = 16384, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum;
 # profiles/launches_large_L16384.md); None for other sizes and the 7-round scheme.
-MEASURED_TRAFFIC = {}              # refilled from the next ncu capture of this kernel
+MEASURED_TRAFFIC = {16384: 1.112e8}
 MULWIDE_PER_SITE = 4            # Philox4x32-10 with the counter-independent rounds hoisted:
                                 # 16 multiplies per call, one call per 4 sites (10 per call,
                                 # 2.5 per site, for the opt-in 7-round scheme)
