@@ -152,6 +152,47 @@ def oracle_sample(L: int, sweeps: int, beta: float, seed: int):
     return sweeps * L * L / (dt * 1e9), dt
 
 
+def host_cpu() -> str:
+    """CPU model and logical core count of this host, for the baseline lines."""
+    import platform
+    import subprocess
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return f"{model or platform.processor() or platform.machine()} x {os.cpu_count()}"
+
+
+def _oracle_worker(job):
+    """One host core: `sweeps` oracle sweeps of one lattice, E/M every sweep
+    (init excluded); returns (spin updates, seconds)."""
+    L, seed, beta, hot, sweeps = job
+    import oracle
+    s = oracle.init_hot(L, seed) if hot else oracle.init_cold(L, 1)
+    t0 = time.perf_counter()
+    oracle.run(s, seed, beta, 0, sweeps, 1)
+    return L * L * sweeps, time.perf_counter() - t0
+
+
+def oracle_all_cores(jobs):
+    """The oracle on all host cores at once, one independent lattice per core
+    (a spawn-context pool: no worker inherits the parent's CUDA state).
+    Returns the aggregate rate (sum of the concurrent per-core rates) and the
+    per-core mean, in spin-updates/ns."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    rates = [u / (dt * 1e9) for u, dt in res]
+    return sum(rates), sum(rates) / len(rates)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -177,7 +218,8 @@ def run_reference(args, rank, world):
         "data": "synthetic",
         "config": {"workload": "large: L=16384 periodic Ising, T=2.269, hot start seed 3, E/M every 10 sweeps",
                    "reference_step": sample},
-        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": host_cpu()},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -298,6 +340,16 @@ def run_batched(args, ising, local):
         upd_k += float(Ls[r]) ** 2 * sweeps
     dt_p = time.perf_counter() - t0
     b.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        cores = min(os.cpu_count() or 1, n)
+        jobs = [(int(Ls[r]), int(seeds[r]), float(betas[r]), True, max(1, int(round(1e8 / float(Ls[r]) ** 2))))
+                for r in range(cores)]
+        cpu_rate, cpu_core = oracle_all_cores(jobs)
+        cpu = {"value": cpu_rate, "unit": METRIC, "cores": cores, "kind": "oracle", "per_core": cpu_core,
+               "host": host_cpu(),
+               "sample": f"replicas 0..{cores - 1} of the batch, one per host core, concurrently, about 1e8 "
+                         "spin updates each (E/M every sweep)"}
     emit({"metric": METRIC, "value": updates / (dt_b * 1e9), "unit": METRIC, "n_gpus": 1, "steps": 1,
           "warmup": 1, "ms_per_step": dt_b * 1e3, "higher_is_better": True, "scaling": "weak",
           "vs_baseline": None, "dtype": "u64", "data": "synthetic",
@@ -308,7 +360,7 @@ def run_batched(args, ising, local):
                            "path": "one ising_lattice per replica, ising_sweep_record(sweeps, 1)",
                            "bit_exact_vs_batched": exact},
           "batched_over_per_instance": (updates / dt_b) / (upd_k / dt_p),
-          "clocks": clocks.summary(), "gpu_launches": batch_launches(n, sweeps)})
+          "cpu_baseline": cpu, "clocks": clocks.summary(), "gpu_launches": batch_launches(n, sweeps)})
 
 
 def run_scan(args, ising, local):
@@ -333,12 +385,20 @@ def run_scan(args, ising, local):
     for r in range(n):
         e, m = ising.means(E[r], M[r], L)
         per_T.append({"T": float(Ts[r]), "E_per_spin": e, "absM_per_spin": m})
+    cpu = None
+    if not args.no_cpu_baseline:
+        cores = min(os.cpu_count() or 1, n)
+        cpu_rate, cpu_core = oracle_all_cores([(L, 7, float(1.0 / Ts[k]), False, 100) for k in range(cores)])
+        cpu = {"value": cpu_rate, "unit": METRIC, "cores": cores, "kind": "oracle", "per_core": cpu_core,
+               "host": host_cpu(),
+               "sample": f"{cores} of the scan's lattices (L={L}, cold start, seed 7, T={Ts[0]}..{Ts[cores - 1]}), "
+                         "100 sweeps each with E/M every sweep, one per host core, concurrently"}
     emit({"metric": METRIC, "value": n * L * L * (therm + meas) / (dt * 1e9), "unit": METRIC, "n_gpus": 1,
           "steps": 1, "warmup": 0, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
           "vs_baseline": None, "dtype": "u64", "data": "synthetic",
           "config": {"workload": f"scan: L={L}, T=1.0..3.5 step 0.1 ({n} replicas in one batch), cold start, "
                                  f"seed 7, {therm}+{meas} sweeps, E/M every measured sweep"},
-          "per_T": per_T, "clocks": clocks.summary(),
+          "per_T": per_T, "cpu_baseline": cpu, "clocks": clocks.summary(),
           "gpu_launches": batch_launches(n, therm) + batch_launches(n, meas)})
 
 
@@ -625,7 +685,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt = oracle_sample(L, 1, BETA, SEED_LARGE)
-        cpu = {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+        cpu = {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle", "host": host_cpu(),
                "sample": f"1 sweep of the L={L} hot-start lattice (seed {SEED_LARGE}, T=2.269); init excluded; {dt:.1f} s"}
 
     if rank == 0:
