@@ -751,7 +751,7 @@ constexpr int kGraphMaxItems = 32768;
 
 static bool use_graphs(const ising_lattice* h)
 {
-    return h->layout == ISING_LAYOUT_ROW_PACKED && ((h->g.L + 3) / 4) * h->g.W <= kGraphMaxItems;
+    return ((h->g.L + 3) / 4) * h->g.W <= kGraphMaxItems;      // both layouts: the same thread count
 }
 
 static void drop_graphs(ising_lattice* h)

@@ -51,6 +51,14 @@ def test_paper_sizes_equal_row_packed(ising, L):
         np.testing.assert_array_equal(Ea, Eb)
         np.testing.assert_array_equal(Ma, Mb)
         np.testing.assert_array_equal(a.get_spins(), b.get_spins())
+        # long enough for the replayed graphs of both layouts (32-sweep chunks)
+        for lat in (a, b):
+            lat.sweep(40)
+        Ea2, Ma2 = a.sweep_record(70, 1)
+        Eb2, Mb2 = b.sweep_record(70, 1)
+        np.testing.assert_array_equal(Ea2, Eb2)
+        np.testing.assert_array_equal(Ma2, Mb2)
+        np.testing.assert_array_equal(a.get_spins(), b.get_spins())
     if L == 1008:
         s = oracle.init_hot(L, 11)
         Eo, _ = oracle.run(s, 11, 1.0 / 2.269, 0, 20, 1)
