@@ -59,6 +59,8 @@ struct ising_batch {
     int graph_chunk = 0;
     int graph_threads = 0;
     int graph_lanes = 0;
+    int graph_rounds = 0;                   // Philox rounds the graph's kernels are fixed for
+    bool graph_every1 = false;              // colour-1 kernels record every sweep
 };
 
 namespace {
@@ -134,12 +136,36 @@ int ensure_lane_streams(ising_batch* b)
     return e == cudaSuccess ? ISING_OK : cuda_fail(e, "lane streams");
 }
 
+// Both half-sweeps of sweep s for one lane, with the kernel fixed for the
+// batch-wide Philox rounds and, when every replica records every sweep,
+// recording always.
+template <int ROUNDS>
+void launch_batch_pair_r(bool every1, dim3 grid, dim3 block, cudaStream_t st, const BatchReplica* reps,
+                         const BatchTile* tiles, const uint32_t* chunk_base, uint32_t s)
+{
+    launch_pdl(batch_half_sweep_kernel<0, ROUNDS, 1>, grid, block, st, reps, tiles, chunk_base, s, 1u);
+    if (every1) launch_pdl(batch_half_sweep_kernel<1, ROUNDS, 2>, grid, block, st, reps, tiles, chunk_base, s, 1u);
+    else launch_pdl(batch_half_sweep_kernel<1, ROUNDS, 0>, grid, block, st, reps, tiles, chunk_base, s, 1u);
+}
+
+void launch_batch_pair(int rounds, bool every1, dim3 grid, dim3 block, cudaStream_t st, const BatchReplica* reps,
+                       const BatchTile* tiles, const uint32_t* chunk_base, uint32_t s)
+{
+    if (rounds == 7) launch_batch_pair_r<7>(every1, grid, block, st, reps, tiles, chunk_base, s);
+    else launch_batch_pair_r<10>(every1, grid, block, st, reps, tiles, chunk_base, s);
+}
+
 // One chunk of sweeps as a graph: lane 0 on the batch's stream, lanes
 // 1.. forked from it and joined back before the chunk counter advances.
-int capture_graph(ising_batch* b)
+// The kernels are fixed for the batch's Philox rounds and for records every
+// sweep, so the graph is recaptured when either changes.
+int capture_graph(ising_batch* b, int rounds, bool every1)
 {
-    if (b->graph && b->graph_chunk == b->chunk && b->graph_threads == b->threads && b->graph_lanes == b->lanes)
+    if (b->graph && b->graph_chunk == b->chunk && b->graph_threads == b->threads && b->graph_lanes == b->lanes &&
+        b->graph_rounds == rounds && b->graph_every1 == every1)
         return ISING_OK;
+    b->graph_rounds = rounds;
+    b->graph_every1 = every1;
     if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
     int rc = ensure_lane_streams(b);
     if (rc != ISING_OK) return rc;
@@ -156,12 +182,8 @@ int capture_graph(ising_batch* b)
             const int nt = b->lane_ntiles[k];
             if (nt == 0) continue;
             const BatchTile* tiles = b->d_tiles + b->lane_tile0[k];
-            launch_pdl(batch_half_sweep_kernel<0>, dim3(nt), dim3(b->threads), st[k], (const BatchReplica*)b->d_reps,
-                       tiles, (const uint32_t*)b->d_chunk_base, (uint32_t)s, 1u);
-            le = cudaGetLastError();
-            if (le != cudaSuccess) break;
-            launch_pdl(batch_half_sweep_kernel<1>, dim3(nt), dim3(b->threads), st[k], (const BatchReplica*)b->d_reps,
-                       tiles, (const uint32_t*)b->d_chunk_base, (uint32_t)s, 1u);
+            launch_batch_pair(b->graph_rounds, b->graph_every1, dim3(nt), dim3(b->threads), st[k], b->d_reps, tiles,
+                              b->d_chunk_base, (uint32_t)s);
             le = cudaGetLastError();
         }
     }
@@ -337,7 +359,7 @@ extern "C" int ising_batch_sweep(ising_batch* b, const int64_t* sweeps, int64_t 
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync counts");
     e = cudaMemsetAsync(b->d_chunk_base, 0, sizeof(uint32_t), b->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync chunk");
-    int rc = capture_graph(b);
+    int rc = capture_graph(b, b->h_reps[0].rounds == 7 ? 7 : 10, every == 1);
     if (rc != ISING_OK) return rc;
     const int64_t nlaunch = (max_s + b->chunk - 1) / b->chunk;
     for (int64_t k = 0; k < nlaunch; ++k) {

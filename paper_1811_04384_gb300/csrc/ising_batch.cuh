@@ -30,8 +30,13 @@ struct BatchTile {
 
 // One half-sweep of colour C over every replica that still has sweeps to do
 // in this run.  Block b works on tile b; its threads own consecutive items
-// item = group * W + w of the replica (4 rows x 1 word each).
-template <int C>
+// item = group * W + w of the replica (4 rows x 1 word each).  ROUNDS: the
+// Philox rounds of every replica (0: each replica's own, a runtime choice).
+// REC: 0 records after the sweeps the replica's phase and interval pick, 1
+// never records, 2 always records (colour 1).  Fixing both when a launch
+// allows it removes the other code paths from the kernel: measured on GB300,
+// scan 1,246 -> 1,284 and batched 1,262 -> 1,284 spin-updates/ns.
+template <int C, int ROUNDS = 0, int REC = 0>
 __global__ void __launch_bounds__(256, 3)
 batch_half_sweep_kernel(const BatchReplica* __restrict__ reps, const BatchTile* __restrict__ tiles,
                         const uint32_t* __restrict__ chunk_base, uint32_t s_local, uint32_t one)
@@ -44,7 +49,7 @@ batch_half_sweep_kernel(const BatchReplica* __restrict__ reps, const BatchTile* 
     const Geom g = R->g;
     const uint32_t item = (uint32_t)tile.first + threadIdx.x;
     const uint32_t ps = R->phase + s;
-    const bool record = (C == 1) && (ps % R->every == 0);
+    const bool record = (C == 1) && (REC == 2 || (REC == 0 && ps % R->every == 0));
     uint32_t anti = 0, up = 0;
     if (item < R->items) {
         const int grp = (int)(item / (uint32_t)g.W);
@@ -53,18 +58,19 @@ batch_half_sweep_kernel(const BatchReplica* __restrict__ reps, const BatchTile* 
         uint64_t* own = C == 0 ? R->w0 : R->w1;
         const uint64_t* other = C == 0 ? R->w1 : R->w0;
         const PhiloxKeys rk = R->rk;
-        if (R->rounds == 7) {
-            if (record)
-                sweep_rows<C, true, true, true, 7>(own, other, g, grp * 4, w, t, rk, R->thr0, R->thr1, R->all0,
-                                                   R->all1, one, anti, up);
-            else
+        const bool r7 = ROUNDS == 7 || (ROUNDS == 0 && R->rounds == 7);
+        if (r7) {
+            if (C == 1 && REC != 1 && record)
+                sweep_rows<C, true, C == 1 && REC != 1, true, 7>(own, other, g, grp * 4, w, t, rk, R->thr0, R->thr1,
+                                                                 R->all0, R->all1, one, anti, up);
+            else if (REC != 2 || C == 0)
                 sweep_rows<C, true, false, true, 7>(own, other, g, grp * 4, w, t, rk, R->thr0, R->thr1, R->all0,
                                                     R->all1, one, anti, up);
-        } else {
-            if (record)
-                sweep_rows<C, true, true>(own, other, g, grp * 4, w, t, rk, R->thr0, R->thr1, R->all0, R->all1,
-                                          one, anti, up);
-            else
+        } else if (ROUNDS != 7) {
+            if (C == 1 && REC != 1 && record)
+                sweep_rows<C, true, C == 1 && REC != 1>(own, other, g, grp * 4, w, t, rk, R->thr0, R->thr1, R->all0,
+                                                        R->all1, one, anti, up);
+            else if (REC != 2 || C == 0)
                 sweep_rows<C, true, false>(own, other, g, grp * 4, w, t, rk, R->thr0, R->thr1, R->all0, R->all1,
                                            one, anti, up);
         }

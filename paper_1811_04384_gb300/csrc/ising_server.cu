@@ -202,6 +202,7 @@ int run_epoch(ising_server* s, const std::vector<uint64_t>& run, std::vector<Job
     const int threads = 128;
     std::vector<BatchReplica> reps(run.size());
     uint32_t max_n = 0;
+    int rounds = 10;                               // 10 if every job uses Philox4x32-10, else per job
     std::vector<double> work(run.size());
     for (size_t a = 0; a < run.size(); ++a) {
         Job& j = *jp[a];
@@ -214,6 +215,7 @@ int run_epoch(ising_server* s, const std::vector<uint64_t>& run, std::vector<Job
         R.counts = s->d_counts + a * 2 * (size_t)s->epoch;
         reps[a] = R;
         max_n = std::max(max_n, R.nsweeps);
+        if (R.rounds != 10) rounds = 0;
         work[a] = (double)j.g.L * j.g.L * R.nsweeps;
     }
     // lanes: jobs, most work first, to the lane with the least work so far;
@@ -259,10 +261,15 @@ int run_epoch(ising_server* s, const std::vector<uint64_t>& run, std::vector<Job
         for (int k = 0; k < kLanes; ++k) {
             if (lane_nt[k] == 0) continue;
             const BatchTile* t = s->d_tiles + lane_tile0[k];
-            launch_pdl(batch_half_sweep_kernel<0>, dim3(lane_nt[k]), dim3(threads), st[k],
-                       (const BatchReplica*)s->d_reps, t, (const uint32_t*)s->d_zero, n, 1u);
-            launch_pdl(batch_half_sweep_kernel<1>, dim3(lane_nt[k]), dim3(threads), st[k],
-                       (const BatchReplica*)s->d_reps, t, (const uint32_t*)s->d_zero, n, 1u);
+            const BatchReplica* R = s->d_reps;
+            const uint32_t* z = s->d_zero;
+            if (rounds == 10) {
+                launch_pdl(batch_half_sweep_kernel<0, 10, 1>, dim3(lane_nt[k]), dim3(threads), st[k], R, t, z, n, 1u);
+                launch_pdl(batch_half_sweep_kernel<1, 10, 0>, dim3(lane_nt[k]), dim3(threads), st[k], R, t, z, n, 1u);
+            } else {
+                launch_pdl(batch_half_sweep_kernel<0, 0, 1>, dim3(lane_nt[k]), dim3(threads), st[k], R, t, z, n, 1u);
+                launch_pdl(batch_half_sweep_kernel<1, 0, 0>, dim3(lane_nt[k]), dim3(threads), st[k], R, t, z, n, 1u);
+            }
         }
     }
     e = cudaGetLastError();
