@@ -22,7 +22,7 @@ the data path (weak scaling).
 --impl reference times the oracle (plain single-threaded C) on the host on a
 bounded sample of the same workload: each step is one sweep of an L = 2048
 lattice at the same temperature (the oracle's cost per update does not depend
-on L, and the run stays within minutes for any --steps the driver passes).
+on L, and the run stays within minutes for any --steps value).
 """
 from __future__ import annotations
 
@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-csv", default=None, help="directory for the raw nvidia-smi clock samples")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the plain-vs-batched comparison")
     ap.add_argument("--tiling", default=None, help="rows,block_words,block_groups")
@@ -93,14 +94,19 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
+    # where the raw samples go: --clocks-csv DIR, else the system temp directory
+    csv_dir = None
+
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
         self.path = None
 
     def __enter__(self):
-        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{self.gpu}.csv")
+        import tempfile
+        d = ClockSampler.csv_dir or tempfile.gettempdir()
+        os.makedirs(d, exist_ok=True)
+        self.path = os.path.join(d, f"clocks_rank{self.gpu}.csv")
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -537,8 +543,8 @@ def run_paper(args, ising, local):
 
 
 def two_pipe_roofline(achieved_sites_per_ns: float, rng: int) -> dict:
-    """The bound of the survey's definition, beside the strict multiply-only
-    one: the integer work per site over both pipes it can use.  Per site,
+    """The two-pipe integer bound, beside the strict multiply-only one: the
+    integer work per site over both pipes it can use.  Per site,
     FMA-heavy only: the Philox multiplies, 2 issue slots each (4 per site;
     2.5 with 7 rounds); ALU only: the Philox three-input XORs (4.5; 3 with
     7 rounds), the two threshold compares and the word logic (1.1, per
@@ -558,6 +564,7 @@ def two_pipe_roofline(achieved_sites_per_ns: float, rng: int) -> dict:
 
 def main():
     args = parse()
+    ClockSampler.csv_dir = args.clocks_csv
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
