@@ -219,7 +219,8 @@ int ising_set_item_lanes(ising_lattice *h, int32_t lanes);
  * bounds small lattices.  Up to L = 168 the fields of each thread item are
  * split over 2, 4 or 32 lanes, so that a small lattice still gives all four
  * schedulers of the SM work.  ISING_PATH_AUTO (default): resident while
- * ceil(L/4) * ceil(L/42) <= 256 thread items (L <= 204).
+ * ceil(L/4) * ceil(L/42) <= 128 thread items (L <= 128); above that the
+ * launch path, whose replayed graphs are faster there.
  * Results are identical on every path. */
 #define ISING_PATH_AUTO 0
 #define ISING_PATH_LAUNCHES 1

@@ -255,26 +255,31 @@ __device__ __forceinline__ void sweep_rows(uint64_t* __restrict__ own, const uin
     }
 }
 
-// One warp per item, for lattices too small to fill the SM with one thread
-// per item.  Lane l draws field k = l / 3 when l % 3 == 0 (fields 0..10) and
-// k = (l + 32) / 3 when l % 3 == 1 (fields 11..20); the other lanes draw
-// nothing.  So the lane of field k is the bit position 3k of its spin within
-// the low or high 32-bit half of the word, and a warp ballot of the lanes'
-// comparisons is already the half of the accept mask in word layout.  Lane e
-// (e < 4) then updates row e of the item.  The draws and the accept rule are
-// those of sweep_rows, so the result is bit-identical.  The whole warp must
-// call this (ballots): `valid` = false runs the arithmetic on item 0 and
-// neither stores nor counts.  Plain (shared-memory) loads.
-template <int C, bool RECORD, int ROUNDS = 10>
-__device__ __forceinline__ void sweep_item_warp(uint64_t* __restrict__ own, const uint64_t* __restrict__ other,
-                                                const Geom& g, int item, bool valid, int lane, uint64_t t,
+// ---- Field-split forms of sweep_rows ------------------------------------
+// For lattices too small to fill the GPU (or one SM) with one thread per item,
+// several lanes share an item.  Each form has two parts: the accept masks of
+// an item (the Philox draws against the thresholds; they depend on the site,
+// sweep and colour only, never on the spins) and their application to the
+// item's rows.  A caller can therefore draw the masks of the next half-sweep
+// while it applies the current one.  The draws and the accept rule are those
+// of sweep_rows, so the results are bit-identical.  All lanes of a warp must
+// call the mask parts (shuffles, ballots); an item past the end (`valid` =
+// false) is drawn as item 0 and never applied.
+
+// One warp per item.  Lane l draws field k = l / 3 when l % 3 == 0 (fields
+// 0..10) and k = (l + 32) / 3 when l % 3 == 1 (fields 11..20); the other
+// lanes draw nothing.  So the lane of field k is the bit position 3k of its
+// spin within the low or high 32-bit half of the word, and a warp ballot of
+// the lanes' comparisons is already that half of the accept mask in word
+// layout.  Every lane gets all masks: a1[e] (r < thr1) and a0[e] (r < thr0)
+// of row e.
+template <int ROUNDS = 10>
+__device__ __forceinline__ void item_masks_warp(const Geom& g, int item, int lane, uint64_t t, int colour,
                                                 const PhiloxKeys& rk, uint32_t thr0, uint32_t thr1,
-                                                uint32_t all0w, uint32_t all1w, uint32_t& anti, uint32_t& up)
+                                                uint64_t a1[4], uint64_t a0[4])
 {
-    if (!valid) item = 0;
     const int grp = item / g.W;
     const int w = item - grp * g.W;
-    const int row0 = grp * 4;
     const int lm3 = lane % 3;
     const int k = lm3 == 0 ? lane / 3 : (lm3 == 1 ? (lane + 32) / 3 : kFields);
     const bool lo_lane = lm3 == 0;
@@ -282,11 +287,10 @@ __device__ __forceinline__ void sweep_item_warp(uint64_t* __restrict__ own, cons
     uint32_t r[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};   // never below a threshold
     if (k < kFields) {
         const uint32_t tl = (uint32_t)t;
-        const uint32_t th = ((uint32_t)(t >> 32) << 1) | (uint32_t)C;
+        const uint32_t th = ((uint32_t)(t >> 32) << 1) | (uint32_t)colour;
         const PhiloxRowKey pk = philox_row_key((uint32_t)grp, tl, th, rk);
         philox_row<ROUNDS>(pk, rk, (uint32_t)(w * kFields + k), r);
     }
-    uint64_t c1[4], c0[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const bool p1 = r[e] < thr1, p0 = r[e] < thr0;
@@ -294,67 +298,29 @@ __device__ __forceinline__ void sweep_item_warp(uint64_t* __restrict__ own, cons
         const uint32_t c1hi = __ballot_sync(0xffffffffu, p1 && hi_lane);
         const uint32_t c0lo = __ballot_sync(0xffffffffu, p0 && lo_lane);
         const uint32_t c0hi = __ballot_sync(0xffffffffu, p0 && hi_lane);
-        c1[e] = (uint64_t)c1hi << 32 | c1lo;
-        c0[e] = (uint64_t)c0hi << 32 | c0lo;
-    }
-    // lane e (< 4) takes row e: its masks by selection (no divergent per-row code)
-    const int e = lane & 3;
-    const uint64_t m1 = e == 0 ? c1[0] : (e == 1 ? c1[1] : (e == 2 ? c1[2] : c1[3]));
-    const uint64_t m0 = e == 0 ? c0[0] : (e == 1 ? c0[1] : (e == 2 ? c0[2] : c0[3]));
-    if (!valid || lane >= 4 || e >= g.L - row0) return;
-    const uint64_t live = live_mask(g, w);
-    const uint64_t all0 = ((uint64_t)all0w << 32 | all0w) & live;
-    const uint64_t all1 = ((uint64_t)all1w << 32 | all1w) & live;
-    const uint32_t P = (uint32_t)g.P;
-    const int i = row0 + e;
-    const uint32_t o = (uint32_t)i * P;
-    const uint64_t s = own[o + (uint32_t)w];
-    const uint64_t u = other[(uint32_t)wrap_row(i - 1, g.L) * P + (uint32_t)w];
-    const uint64_t d = other[(uint32_t)wrap_row(i + 1, g.L) * P + (uint32_t)w];
-    const uint64_t h0 = other[o + (uint32_t)w];
-    // horizontal neighbour at m - 1 ((i + C) even) or m + 1 (odd), as in sweep_rows
-    const bool left = ((e + C) & 1) == 0;                  // row0 is a multiple of 4
-    const int ws = left ? ((w > 0) ? w - 1 : g.W - 1) : ((w < g.W - 1) ? w + 1 : 0);
-    const int sh = (left ? (w > 0) : (w < g.W - 1)) ? 60 : 3 * (g.rlast - 1);
-    const uint64_t side = other[o + (uint32_t)ws];
-    const uint64_t h1 = left ? ((h0 << 3) | (side >> sh)) : ((h0 >> 3) | (side << sh));
-    const uint64_t x1 = s ^ u, x2 = s ^ d, x3 = s ^ h0, x4 = s ^ h1;
-    const uint64_t any = x1 | x2 | x3 | x4;
-    const uint64_t ge2 = (x1 & x2) | (x3 & x4) | ((x1 ^ x2) & (x3 ^ x4));
-    const uint64_t accept = ge2 | (any & (m1 | all1)) | (~any & (m0 | all0));
-    const uint64_t s_new = s ^ (accept & live);
-    own[o + (uint32_t)w] = s_new;
-    if (RECORD) {
-        anti += __popcll((s_new ^ u) & live) + __popcll((s_new ^ d) & live)
-              + __popcll((s_new ^ h0) & live) + __popcll((s_new ^ h1) & live);
-        up += __popcll(s_new & live) + __popcll(h0 & live);
+        a1[e] = (uint64_t)c1hi << 32 | c1lo;
+        a0[e] = (uint64_t)c0hi << 32 | c0lo;
     }
 }
 
 // F lanes per item (F = 2, 4 or 8; aligned groups of the warp): lane q draws
 // the fields k = q + jF, collects its accept bits at bit 3jF (compile-time
 // positions), shifts them by 3q to bit 3k and OR-merges the F lanes' masks
-// with shuffles.  Lane q then updates rows q, q + F, ... of the item (one
-// code path for all lanes).  Same draws and accept rule as sweep_rows, so
-// the result is bit-identical.  The whole warp must call this (shuffles):
-// `valid` = false runs the arithmetic on item 0 and neither stores nor
-// counts.  Plain (shared-memory) loads.
-template <int C, bool RECORD, int F, int ROUNDS = 10>
-__device__ __forceinline__ void sweep_item_lanes(uint64_t* __restrict__ own, const uint64_t* __restrict__ other,
-                                                 const Geom& g, int item, bool valid, int q, uint64_t t,
+// with shuffles.  Every lane of the group gets all masks.
+template <int F, int ROUNDS = 10>
+__device__ __forceinline__ void item_masks_lanes(const Geom& g, int item, int q, uint64_t t, int colour,
                                                  const PhiloxKeys& rk, uint32_t thr0, uint32_t thr1,
-                                                 uint32_t all0w, uint32_t all1w, uint32_t& anti, uint32_t& up)
+                                                 uint64_t a1[4], uint64_t a0[4])
 {
     static_assert(F == 2 || F == 4 || F == 8, "F: 2, 4 or 8 lanes per item");
     constexpr int J = (kFields + F - 1) / F;
-    if (!valid) item = 0;
     const int grp = item / g.W;
     const int w = item - grp * g.W;
-    const int row0 = grp * 4;
     const uint32_t tl = (uint32_t)t;
-    const uint32_t th = ((uint32_t)(t >> 32) << 1) | (uint32_t)C;
+    const uint32_t th = ((uint32_t)(t >> 32) << 1) | (uint32_t)colour;
     const PhiloxRowKey pk = philox_row_key((uint32_t)grp, tl, th, rk);
-    uint64_t a1[4] = {0, 0, 0, 0}, a0[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) a1[e] = a0[e] = 0;
 #pragma unroll
     for (int j = 0; j < J; ++j) {
         const int k = q + j * F;
@@ -381,13 +347,29 @@ __device__ __forceinline__ void sweep_item_lanes(uint64_t* __restrict__ own, con
             a0[e] |= __shfl_xor_sync(0xffffffffu, a0[e], d);
         }
     }
+}
+
+// Apply the masks of an item of colour C: lane q of its group (F lanes; a
+// warp for F = 32) updates rows q, q + F, ... below 4 (one code path for all
+// lanes, the row's masks picked by selection).  RECORD adds the item's
+// anti-aligned bonds and up spins to anti / up (colour 1).
+template <int C, bool RECORD, int F>
+__device__ __forceinline__ void item_apply(uint64_t* __restrict__ own, const uint64_t* __restrict__ other,
+                                           const Geom& g, int item, bool valid, int q, const uint64_t a1[4],
+                                           const uint64_t a0[4], uint32_t all0w, uint32_t all1w, uint32_t& anti,
+                                           uint32_t& up)
+{
+    constexpr int STEP = F < 4 ? F : 4;
     if (!valid) return;
+    const int grp = item / g.W;
+    const int w = item - grp * g.W;
+    const int row0 = grp * 4;
     const uint64_t live = live_mask(g, w);
     const uint64_t all0 = ((uint64_t)all0w << 32 | all0w) & live;
     const uint64_t all1 = ((uint64_t)all1w << 32 | all1w) & live;
     const uint32_t P = (uint32_t)g.P;
 #pragma unroll
-    for (int e0 = 0; e0 < 4; e0 += F) {
+    for (int e0 = 0; e0 < 4; e0 += STEP) {
         const int e = e0 + q;
         if (e >= 4 || e >= g.L - row0) break;
         const uint64_t m1 = e == 0 ? a1[0] : (e == 1 ? a1[1] : (e == 2 ? a1[2] : a1[3]));
@@ -398,6 +380,7 @@ __device__ __forceinline__ void sweep_item_lanes(uint64_t* __restrict__ own, con
         const uint64_t u = other[(uint32_t)wrap_row(i - 1, g.L) * P + (uint32_t)w];
         const uint64_t d = other[(uint32_t)wrap_row(i + 1, g.L) * P + (uint32_t)w];
         const uint64_t h0 = other[o + (uint32_t)w];
+        // horizontal neighbour at m - 1 ((i + C) even) or m + 1 (odd), as in sweep_rows
         const bool left = ((e + C) & 1) == 0;                  // row0 is a multiple of 4
         const int ws = left ? ((w > 0) ? w - 1 : g.W - 1) : ((w < g.W - 1) ? w + 1 : 0);
         const int sh = (left ? (w > 0) : (w < g.W - 1)) ? 60 : 3 * (g.rlast - 1);
@@ -415,6 +398,29 @@ __device__ __forceinline__ void sweep_item_lanes(uint64_t* __restrict__ own, con
             up += __popcll(s_new & live) + __popcll(h0 & live);
         }
     }
+}
+
+// Masks of an item with F lanes (F = 32: one warp).
+template <int F, int ROUNDS = 10>
+__device__ __forceinline__ void item_masks(const Geom& g, int item, bool valid, int q, uint64_t t, int colour,
+                                           const PhiloxKeys& rk, uint32_t thr0, uint32_t thr1, uint64_t a1[4],
+                                           uint64_t a0[4])
+{
+    if (!valid) item = 0;
+    if constexpr (F == 32) item_masks_warp<ROUNDS>(g, item, q, t, colour, rk, thr0, thr1, a1, a0);
+    else item_masks_lanes<F, ROUNDS>(g, item, q, t, colour, rk, thr0, thr1, a1, a0);
+}
+
+// Draw and apply in one step (the launch path's lanes kernel).
+template <int C, bool RECORD, int F, int ROUNDS = 10>
+__device__ __forceinline__ void sweep_item_lanes(uint64_t* __restrict__ own, const uint64_t* __restrict__ other,
+                                                 const Geom& g, int item, bool valid, int q, uint64_t t,
+                                                 const PhiloxKeys& rk, uint32_t thr0, uint32_t thr1,
+                                                 uint32_t all0w, uint32_t all1w, uint32_t& anti, uint32_t& up)
+{
+    uint64_t a1[4], a0[4];
+    item_masks<F, ROUNDS>(g, item, valid, q, t, C, rk, thr0, thr1, a1, a0);
+    item_apply<C, RECORD, F>(own, other, g, item, valid, q, a1, a0, all0w, all1w, anti, up);
 }
 
 // One half-sweep of colour C over one lattice.  LINEAR: a 1-D grid whose

@@ -190,27 +190,15 @@ resident_sweeps_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geo
     }
 }
 
-// One item's half-sweep on the on-chip path with F lanes per item: one warp
-// (F = 32, sweep_item_warp) or an aligned group of 2, 4 or 8 lanes
-// (sweep_item_lanes).
-template <int F, int C, bool RECORD, int ROUNDS>
-__device__ __forceinline__ void item_half_sweep(uint64_t* own, const uint64_t* other, const Geom& g, int item,
-                                                bool valid, int q, uint64_t t, const SweepArgs& a, uint32_t& anti,
-                                                uint32_t& up)
-{
-    if constexpr (F == 32)
-        sweep_item_warp<C, RECORD, ROUNDS>(own, other, g, item, valid, q, t, a.rk, a.thr0, a.thr1, a.all0, a.all1,
-                                           anti, up);
-    else
-        sweep_item_lanes<C, RECORD, F, ROUNDS>(own, other, g, item, valid, q, t, a.rk, a.thr0, a.thr1, a.all0,
-                                               a.all1, anti, up);
-}
-
-// The on-chip path for small lattices with F lanes per item: F times the
-// threads of resident_sweeps_kernel, each with 1/F of the Philox calls, so a
-// lattice of a few dozen items keeps all four schedulers of the SM busy
-// instead of one warp.  Groups loop over the items.  Same records and
-// results as resident_sweeps_kernel.  blockDim.x: a multiple of 32, <= 512.
+// The on-chip path for small lattices with F lanes per item (F = 32: one
+// warp per item; 2 or 4: item_masks_lanes): F times the threads of
+// resident_sweeps_kernel, each with 1/F of the Philox calls, so a lattice of
+// a few dozen items keeps all four schedulers of the SM busy instead of one
+// warp.  The accept masks of the next half-sweep are drawn while the current
+// one is applied (the draws do not depend on the spins), so the Philox work
+// fills the latency of the spin logic and the barriers.  One pass: the
+// block has a group of F lanes for every item (items * F <= 512).  Same
+// records and results as resident_sweeps_kernel.
 template <int F, int ROUNDS>
 __global__ void __launch_bounds__(512, 1)
 resident_group_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom g, SweepArgs a, uint64_t t0,
@@ -227,34 +215,31 @@ resident_group_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom
     }
     __syncthreads();
     const int items = ((g.L + 3) / 4) * g.W;
-    const int per_pass = (int)blockDim.x / F;
-    const int slot = (int)threadIdx.x / F, q = (int)threadIdx.x % F;
+    const int item = (int)threadIdx.x / F, q = (int)threadIdx.x % F;
+    const bool valid = item < items;
     const int nwarps = (int)blockDim.x / 32;
     const int warp = (int)threadIdx.x / 32, lane = (int)threadIdx.x % 32;
-    const int passes = (items + per_pass - 1) / per_pass;
     const long long N = (long long)g.L * g.L;
+    uint64_t m1[4], m0[4], n1[4], n0[4];          // masks of the current / next half-sweep
+    item_masks<F, ROUNDS>(g, item, valid, q, t0 + 1, 0, a.rk, a.thr0, a.thr1, m1, m0);
     for (int s = 1; s <= n; ++s) {
         const uint64_t t = t0 + (uint64_t)s;
         uint32_t dummy0 = 0, dummy1 = 0;
-        for (int p = 0; p < passes; ++p) {
-            const int it = p * per_pass + slot;
-            item_half_sweep<F, 0, false, ROUNDS>(s0, s1, g, it, it < items, q, t, a, dummy0, dummy1);
-        }
+        item_masks<F, ROUNDS>(g, item, valid, q, t, 1, a.rk, a.thr0, a.thr1, n1, n0);
+        item_apply<0, false, F>(s0, s1, g, item, valid, q, m1, m0, a.all0, a.all1, dummy0, dummy1);
         __syncthreads();
         const bool record = (s % every) == 0;
         uint32_t anti = 0, up = 0;
-        for (int p = 0; p < passes; ++p) {
-            const int it = p * per_pass + slot;
-            if (record) item_half_sweep<F, 1, true, ROUNDS>(s1, s0, g, it, it < items, q, t, a, anti, up);
-            else item_half_sweep<F, 1, false, ROUNDS>(s1, s0, g, it, it < items, q, t, a, anti, up);
-        }
+        item_masks<F, ROUNDS>(g, item, valid, q, t + 1, 0, a.rk, a.thr0, a.thr1, m1, m0);
+        if (record) item_apply<1, true, F>(s1, s0, g, item, valid, q, n1, n0, a.all0, a.all1, anti, up);
+        else item_apply<1, false, F>(s1, s0, g, item, valid, q, n1, n0, a.all0, a.all1, anti, up);
         if (record) {
             anti = __reduce_add_sync(0xffffffffu, anti);
             up = __reduce_add_sync(0xffffffffu, up);
             if (lane == 0) { red_anti[warp] = anti; red_up[warp] = up; }
         }
         __syncthreads();
-        if (record && warp == 0) {          // up to 32 warp sums, each below 2^31: fits 32 bits
+        if (record && warp == 0) {          // up to 16 warp sums, each below 2^31: fits 32 bits
             const unsigned int sa = __reduce_add_sync(0xffffffffu, lane < nwarps ? red_anti[lane] : 0u);
             const unsigned int su = __reduce_add_sync(0xffffffffu, lane < nwarps ? red_up[lane] : 0u);
             if (lane == 0) {
@@ -338,7 +323,7 @@ constexpr int kRecordsPerChunk = 1024;           // count slots resident on the 
 constexpr size_t kCountBytes = (size_t)kRecordsPerChunk * kCountSlots * 2 * sizeof(unsigned long long);
 constexpr size_t kAlign = 256;
 constexpr size_t kResidentMaxBytes = 220 * 1024;   // shared memory for the on-chip path
-constexpr int kResidentAutoMaxItems = 256;          // auto: on-chip while one block of 256 threads covers the items
+constexpr int kResidentAutoMaxItems = 128;          // auto: on-chip up to 128 items (L <= 128); graph replays above
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
