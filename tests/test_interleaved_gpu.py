@@ -101,3 +101,22 @@ def test_interleaved_rejects_sizes_and_row_packed_calls(ising):
             lat.set_path(ising.ISING_PATH_RESIDENT)
         with pytest.raises(ising.IsingError):
             lat.set_tiling(4, 32, 4)
+        with pytest.raises(ising.IsingError):
+            lat.set_item_lanes(4)
+
+
+def test_interleaved_run_states_equals_calls_in_turn(ising):
+    """ising_run_states on the paper's layout runs the calls in turn."""
+    L = 168
+    rng = np.random.default_rng(3)
+    states = [np.where(rng.random((L, L)) < 0.5, 1, -1).astype(np.int8) for _ in range(3)]
+    with interleaved(ising, L, 2) as a, interleaved(ising, L, 2) as b:
+        for lat in (a, b):
+            lat.set_beta(0.44)
+        E1, M1 = a.run_states(states, 6, 2)
+        for k, st in enumerate(states):
+            b.set_spins(st)
+            E, M = b.sweep_record(6, 2)
+            np.testing.assert_array_equal(E1[k], E)
+            np.testing.assert_array_equal(M1[k], M)
+        np.testing.assert_array_equal(a.get_spins(), b.get_spins())

@@ -324,6 +324,36 @@ def test_graph_replays_match_oracle(ising):
     np.testing.assert_array_equal(S, s)
 
 
+def test_run_states_edge_cases(ising):
+    """No states: nothing runs; NULL outputs; more records per state than one
+    device chunk (the calls then run in turn); bad arguments rejected."""
+    import ctypes
+    L = 260
+    st = np.where(np.random.default_rng(1).random((L, L)) < 0.5, 1, -1).astype(np.int8)
+    with ising.Lattice(L, 4) as lat, ising.Lattice(L, 4) as ref:
+        lat.set_beta(0.4)
+        ref.set_beta(0.4)
+        E, M = lat.run_states([], 10, 2)
+        assert E.shape == (0, 5) and lat.t == 0
+        lib = ising.load()
+        ptrs = (ctypes.c_void_p * 2)(st.ctypes.data, st.ctypes.data)
+        assert lib.ising_run_states(lat._h, ptrs, 2, 5, 1, None, None) == 0
+        ref.set_spins(st)
+        ref.sweep_record(5, 1)
+        ref.set_spins(st)
+        ref.sweep_record(5, 1)
+        np.testing.assert_array_equal(lat.get_spins(), ref.get_spins())
+        E1, M1 = lat.run_states([st], 1100, 1)            # 1100 records > 1024 per chunk
+        ref.set_spins(st)
+        E2, M2 = ref.sweep_record(1100, 1)
+        np.testing.assert_array_equal(E1[0], E2)
+        np.testing.assert_array_equal(M1[0], M2)
+        null_states = (ctypes.c_void_p * 1)(None)
+        assert lib.ising_run_states(lat._h, null_states, 1, 5, 1, None, None) == ising.ISING_EINVAL
+        assert lib.ising_run_states(lat._h, ptrs, 1, 5, 0, None, None) == ising.ISING_EINVAL
+        assert lib.ising_run_states(lat._h, ptrs, 1, -1, 1, None, None) == ising.ISING_EINVAL
+
+
 def test_rejected_tilings(ising):
     with ising.Lattice(64, 1) as lat:
         for bad in [(8, 32, 4), (4, 48, 4), (4, 64, 8), (4, 16, 1), (4, 32, 3), (4, 0, 32), (4, 0, 96),
