@@ -485,7 +485,8 @@ def run_plain(args, ising, local):
                                  "wall clock of ising_sweep_record(n, 1) (best of 3)"},
           "paths": {"resident_on_chip": rate["resident"], "launches": rate["launches"],
                     "graph_captured_batch": rate["graph"]},
-          "bit_exact_across_paths": exact})
+          "bit_exact_across_paths": exact,
+          "gpu_launches": 2})      # the timed on-chip call: one sweeps kernel, one sweep-counter kernel
 
 
 # The paper's test cases (Table 2): lattice side and iterations; an iteration
