@@ -35,10 +35,25 @@ SweepArgs make_sweep_args(uint64_t seed, const uint64_t thr[2], const uint64_t* 
 
 Geom lattice_geom(int L);
 
-// Stand-alone kernels of ising_lattice.cu, for other translation units.
+// Launchers of the kernels in ising_kernels.cu (errors: the launch's own).
 cudaError_t launch_init_hot(uint64_t* w0, uint64_t* w1, const Geom& g, uint64_t seed, cudaStream_t s);
 cudaError_t launch_init_cold(uint64_t* w0, uint64_t* w1, const Geom& g, int up, cudaStream_t s);
 cudaError_t launch_unpack(const uint64_t* w0, const uint64_t* w1, const Geom& g, int8_t* out, cudaStream_t s);
+// int8 spins (row-major L x L, device memory or mapped pinned host memory) -> words.
+cudaError_t launch_pack_rows(uint64_t* w0, uint64_t* w1, const Geom& g, const int8_t* src, cudaStream_t s);
+// Device sweep counter: += n; += n with the graph record index += inc; = t.
+cudaError_t launch_advance_sweep(uint64_t* t_base, uint64_t n, cudaStream_t s);
+cudaError_t launch_advance_graph(uint64_t* t_base, uint64_t n, uint32_t* rec_base, uint32_t inc, cudaStream_t s);
+cudaError_t launch_set_sweep(uint64_t* t_base, uint64_t t, cudaStream_t s);
+// Philox4x32-10 of n counters (4 words each) under key `seed` (test hook).
+cudaError_t launch_philox_blocks(const uint32_t* ctr, uint32_t* out, int64_t n, uint64_t seed, cudaStream_t s);
+// The on-chip path: allow `bytes` of dynamic shared memory for its kernels
+// (once), then run n sweeps from sweep t0 with `lanes` lanes per item (32, 4,
+// 2; anything else: one thread per item) and E/M records every `every`-th
+// sweep as (E, M) pairs into rec; `bytes` = both colour arrays.
+cudaError_t allow_resident_smem(int bytes);
+cudaError_t launch_resident(int lanes, uint64_t* w0, uint64_t* w1, const Geom& g, const SweepArgs& a, uint64_t t0,
+                            int n, int every, long long* rec, size_t bytes, cudaStream_t s);
 
 // Launch `kernel` with programmatic stream serialization (the kernel calls
 // pdl_enter before its first read): the next launch's setup overlaps the end

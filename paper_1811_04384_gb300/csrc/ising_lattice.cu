@@ -1,5 +1,6 @@
 // C ABI of the single-lattice path: handle management, initialisation,
-// sweeps with the fused energy/magnetisation reduction, spin I/O.
+// sweeps with the fused energy/magnetisation reduction (launches, graph
+// replays, the on-chip path), spin I/O.  The kernels: ising_kernels.cu.
 // Declarations and the contract of every function: include/ising.h.
 #include <cuda_runtime.h>
 
@@ -18,307 +19,9 @@
 
 using namespace ising;
 
-namespace ising {
-
-// Hot start: s = +1 iff the site's Philox draw at t = 0 is below 2^31.
-// Thread = (4-row group, word, colour).
-__global__ void init_hot_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom g,
-                                uint32_t key0, uint32_t key1)
-{
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    const int grp = blockIdx.y * blockDim.y + threadIdx.y;
-    const int c = blockIdx.z;
-    if (w >= g.W || grp * 4 >= g.L) return;
-    const uint64_t live = live_mask(g, w);
-    uint64_t word[4] = {0, 0, 0, 0};
-    for (int k = 0; k < kFields; ++k) {
-        uint32_t x[4] = {(uint32_t)grp, (uint32_t)(w * kFields + k), 0u, (uint32_t)c};
-        philox10(x, key0, key1);
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-            word[e] |= (uint64_t)((x[e] >> 31) ^ 1u) << (3 * k);
-    }
-    uint64_t* arr = c ? w1 : w0;
-    for (int e = 0; e < 4; ++e) {
-        const int i = grp * 4 + e;
-        if (i < g.L) arr[(size_t)i * g.P + w] = word[e] & live;
-    }
-}
-
-// Cold start (all up or all down); also zeroes the pitch padding.
-__global__ void init_cold_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom g, int up)
-{
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y * blockDim.y + threadIdx.y;
-    if (w >= g.P || i >= g.L) return;
-    const uint64_t v = (w < g.W && up) ? live_mask(g, w) : 0ull;
-    w0[(size_t)i * g.P + w] = v;
-    w1[(size_t)i * g.P + w] = v;
-}
-
-// int8 spins of row blockIdx.x (> 0 is up) -> that row's words of both
-// colours.  The row is first staged in shared memory (16-byte loads when
-// vec16: `in` 16-byte aligned and L % 16 == 0), so the input is read once
-// and coalesced; `in` may be device memory or pinned host memory mapped into
-// the device's address space.  Dynamic shared memory: L bytes.
-__global__ void pack_rows_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom g,
-                                 const int8_t* __restrict__ in, int vec16)
-{
-    extern __shared__ __align__(16) int8_t row_s[];
-    const int i = blockIdx.x;
-    const int8_t* src = in + (size_t)i * g.L;
-    if (vec16) {
-        const uint4* s4 = reinterpret_cast<const uint4*>(src);
-        uint4* d4 = reinterpret_cast<uint4*>(row_s);
-        for (int k = threadIdx.x; k < g.L / 16; k += blockDim.x) d4[k] = s4[k];
-    } else {
-        for (int k = threadIdx.x; k < g.L; k += blockDim.x) row_s[k] = src[k];
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < 2 * g.P; t += blockDim.x) {
-        const int c = t >= g.P ? 1 : 0;
-        const int w = t - c * g.P;
-        uint64_t word = 0;
-        if (w < g.W) {
-            const int nf = (w == g.W - 1) ? g.rlast : kFields;
-            const int par = (i + c) & 1;
-            const int8_t* r = row_s + 2 * w * kFields + par;
-            for (int k = 0; k < nf; ++k) word |= (uint64_t)(r[2 * k] > 0) << (3 * k);
-        }
-        (c ? w1 : w0)[(size_t)i * g.P + w] = word;
-    }
-}
-
-// Packed colour words -> int8 spins (+1 / -1).
-__global__ void unpack_kernel(const uint64_t* __restrict__ w0, const uint64_t* __restrict__ w1, Geom g,
-                              int8_t* __restrict__ s)
-{
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y * blockDim.y + threadIdx.y;
-    const int c = blockIdx.z;
-    if (w >= g.W || i >= g.L) return;
-    const uint64_t word = (c ? w1 : w0)[(size_t)i * g.P + w];
-    const int nf = (w == g.W - 1) ? g.rlast : kFields;
-    const int par = (i + c) & 1;
-    int8_t* row = s + (size_t)i * g.L;
-    for (int k = 0; k < nf; ++k) {
-        const int j = 2 * (w * kFields + k) + par;
-        row[j] = ((word >> (3 * k)) & 1ull) ? (int8_t)1 : (int8_t)-1;
-    }
-}
-
-// t_base += n (end of a chunk of sweeps).
-__global__ void advance_sweep_kernel(uint64_t* t_base, uint64_t n)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) *t_base += n;
-}
-
-// End of a replayed graph of sweeps: t_base += n, record index += inc.
-__global__ void advance_graph_kernel(uint64_t* t_base, uint64_t n, uint32_t* rec_base, uint32_t inc)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        *t_base += n;
-        *rec_base += inc;
-    }
-}
-
-__global__ void set_sweep_kernel(uint64_t* t_base, uint64_t t)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) *t_base = t;
-}
-
-// Temporal blocking with the whole lattice on chip: one block copies both
-// colour arrays into shared memory, runs sweeps t0+1 .. t0+n there (a block
-// barrier between half-sweeps), records E and M after every `every`-th sweep
-// with an on-chip reduction (records[2k] = E, records[2k+1] = M), and copies
-// the lattice back.  For lattices whose 2 L P words fit in shared memory.
-template <int ROUNDS>
-__global__ void __launch_bounds__(256, 1)
-resident_sweeps_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom g, SweepArgs a, uint64_t t0,
-                       int n, int every, long long* __restrict__ records)
-{
-    extern __shared__ __align__(16) uint64_t lattice[];
-    __shared__ unsigned int red_anti[8], red_up[8];
-    const size_t words = (size_t)g.L * g.P;
-    uint64_t* s0 = lattice;
-    uint64_t* s1 = lattice + words;
-    for (size_t k = threadIdx.x; k < words; k += blockDim.x) {
-        s0[k] = w0[k];
-        s1[k] = w1[k];
-    }
-    __syncthreads();
-    const int items = ((g.L + 3) / 4) * g.W;
-    const long long N = (long long)g.L * g.L;
-    for (int s = 1; s <= n; ++s) {
-        const uint64_t t = t0 + (uint64_t)s;
-        uint32_t dummy0 = 0, dummy1 = 0;
-        for (int it = threadIdx.x; it < items; it += blockDim.x) {
-            const int grp = it / g.W, w = it - grp * g.W;
-            sweep_rows<0, true, false, false, ROUNDS>(s0, s1, g, grp * 4, w, t, a.rk, a.thr0, a.thr1, a.all0,
-                                                      a.all1, a.one, dummy0, dummy1);
-        }
-        __syncthreads();
-        const bool record = (s % every) == 0;
-        uint32_t anti = 0, up = 0;
-        for (int it = threadIdx.x; it < items; it += blockDim.x) {
-            const int grp = it / g.W, w = it - grp * g.W;
-            if (record)
-                sweep_rows<1, true, true, false, ROUNDS>(s1, s0, g, grp * 4, w, t, a.rk, a.thr0, a.thr1, a.all0,
-                                                         a.all1, a.one, anti, up);
-            else
-                sweep_rows<1, true, false, false, ROUNDS>(s1, s0, g, grp * 4, w, t, a.rk, a.thr0, a.thr1, a.all0,
-                                                          a.all1, a.one, anti, up);
-        }
-        if (record) {
-            anti = __reduce_add_sync(0xffffffffu, anti);
-            up = __reduce_add_sync(0xffffffffu, up);
-            if ((threadIdx.x & 31) == 0) { red_anti[threadIdx.x >> 5] = anti; red_up[threadIdx.x >> 5] = up; }
-        }
-        __syncthreads();
-        if (record && threadIdx.x == 0) {
-            unsigned long long sa = 0, su = 0;
-            for (int k = 0; k < (int)(blockDim.x + 31) / 32; ++k) { sa += red_anti[k]; su += red_up[k]; }
-            const int rec = s / every - 1;
-            records[2 * rec] = 2 * (long long)sa - 2 * N;
-            records[2 * rec + 1] = 2 * (long long)su - N;
-        }
-    }
-    __syncthreads();
-    for (size_t k = threadIdx.x; k < words; k += blockDim.x) {
-        w0[k] = s0[k];
-        w1[k] = s1[k];
-    }
-}
-
-// The on-chip path for small lattices with F lanes per item (F = 32: one
-// warp per item; 2 or 4: item_masks_lanes): F times the threads of
-// resident_sweeps_kernel, each with 1/F of the Philox calls, so a lattice of
-// a few dozen items keeps all four schedulers of the SM busy instead of one
-// warp.  The accept masks of the next half-sweep are drawn while the current
-// one is applied (the draws do not depend on the spins), so the Philox work
-// fills the latency of the spin logic and the barriers.  One pass: the
-// block has a group of F lanes for every item (items * F <= 512).  Same
-// records and results as resident_sweeps_kernel.
-template <int F, int ROUNDS>
-__global__ void __launch_bounds__(512, 1)
-resident_group_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom g, SweepArgs a, uint64_t t0,
-                      int n, int every, long long* __restrict__ records)
-{
-    extern __shared__ __align__(16) uint64_t lattice[];
-    __shared__ unsigned int red_anti[32], red_up[32];
-    const size_t words = (size_t)g.L * g.P;
-    uint64_t* s0 = lattice;
-    uint64_t* s1 = lattice + words;
-    for (size_t k = threadIdx.x; k < words; k += blockDim.x) {
-        s0[k] = w0[k];
-        s1[k] = w1[k];
-    }
-    __syncthreads();
-    const int items = ((g.L + 3) / 4) * g.W;
-    const int item = (int)threadIdx.x / F, q = (int)threadIdx.x % F;
-    const bool valid = item < items;
-    const int nwarps = (int)blockDim.x / 32;
-    const int warp = (int)threadIdx.x / 32, lane = (int)threadIdx.x % 32;
-    const long long N = (long long)g.L * g.L;
-    uint64_t m1[4], m0[4], n1[4], n0[4];          // masks of the current / next half-sweep
-    item_masks<F, ROUNDS>(g, item, valid, q, t0 + 1, 0, a.rk, a.thr0, a.thr1, m1, m0);
-    for (int s = 1; s <= n; ++s) {
-        const uint64_t t = t0 + (uint64_t)s;
-        uint32_t dummy0 = 0, dummy1 = 0;
-        item_masks<F, ROUNDS>(g, item, valid, q, t, 1, a.rk, a.thr0, a.thr1, n1, n0);
-        item_apply<0, false, F>(s0, s1, g, item, valid, q, m1, m0, a.all0, a.all1, dummy0, dummy1);
-        __syncthreads();
-        const bool record = (s % every) == 0;
-        uint32_t anti = 0, up = 0;
-        item_masks<F, ROUNDS>(g, item, valid, q, t + 1, 0, a.rk, a.thr0, a.thr1, m1, m0);
-        if (record) item_apply<1, true, F>(s1, s0, g, item, valid, q, n1, n0, a.all0, a.all1, anti, up);
-        else item_apply<1, false, F>(s1, s0, g, item, valid, q, n1, n0, a.all0, a.all1, anti, up);
-        if (record) {
-            anti = __reduce_add_sync(0xffffffffu, anti);
-            up = __reduce_add_sync(0xffffffffu, up);
-            if (lane == 0) { red_anti[warp] = anti; red_up[warp] = up; }
-        }
-        __syncthreads();
-        if (record && warp == 0) {          // up to 16 warp sums, each below 2^31: fits 32 bits
-            const unsigned int sa = __reduce_add_sync(0xffffffffu, lane < nwarps ? red_anti[lane] : 0u);
-            const unsigned int su = __reduce_add_sync(0xffffffffu, lane < nwarps ? red_up[lane] : 0u);
-            if (lane == 0) {
-                const int rec = s / every - 1;
-                records[2 * rec] = 2 * (long long)sa - 2 * N;
-                records[2 * rec + 1] = 2 * (long long)su - N;
-            }
-        }
-    }
-    __syncthreads();
-    for (size_t k = threadIdx.x; k < words; k += blockDim.x) {
-        w0[k] = s0[k];
-        w1[k] = s1[k];
-    }
-}
-
-// One half-sweep of colour C over all SMs with F lanes per thread item
-// (sweep_item_lanes on the lattice in global memory): for lattices whose one
-// thread per item would leave SMs idle and each thread with a long chain of
-// 21 Philox calls.  Thread k of the grid is lane k % F of item k / F.  Same
-// results as half_sweep_kernel.
-template <int C, bool RECORD, int F, int ROUNDS>
-__global__ void __launch_bounds__(128, 4)
-half_sweep_lanes_kernel(uint64_t* __restrict__ own, const uint64_t* __restrict__ other, Geom g, SweepArgs a)
-{
-    pdl_enter();
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int item = (int)(k / F), q = (int)(k % F);
-    const int items = ((g.L + 3) / 4) * g.W;
-    const uint64_t t = *a.t_base + a.t_off;
-    uint32_t anti = 0, up = 0;
-    sweep_item_lanes<C, RECORD, F, ROUNDS>(own, other, g, item, item < items, q, t, a.rk, a.thr0, a.thr1, a.all0,
-                                           a.all1, anti, up);
-    if (RECORD) block_add_counts(record_counts(a) + 2 * (blockIdx.x % kCountSlots), anti, up);
-}
-
-template <int F, int ROUNDS>
-static void launch_lanes_r(int colour, bool record, uint64_t* own, const uint64_t* other, const Geom& g,
-                           const SweepArgs& a, cudaStream_t s)
-{
-    const uint32_t threads = (uint32_t)(((g.L + 3) / 4) * g.W) * F;
-    const dim3 block(128), grid((threads + 127) / 128);
-    if (colour == 0) launch_pdl(half_sweep_lanes_kernel<0, false, F, ROUNDS>, grid, block, s, own, other, g, a);
-    else if (record) launch_pdl(half_sweep_lanes_kernel<1, true, F, ROUNDS>, grid, block, s, own, other, g, a);
-    else launch_pdl(half_sweep_lanes_kernel<1, false, F, ROUNDS>, grid, block, s, own, other, g, a);
-}
-
-// A half-sweep that updates, with F = 2, 4 or 8 lanes per item.
-cudaError_t launch_half_sweep_lanes(int F, int colour, bool record, uint64_t* own, const uint64_t* other,
-                                    const Geom& g, const SweepArgs& a, cudaStream_t s)
-{
-    const bool r7 = a.rounds == 7;
-    switch (F) {
-    case 2: r7 ? launch_lanes_r<2, 7>(colour, record, own, other, g, a, s)
-               : launch_lanes_r<2, 10>(colour, record, own, other, g, a, s); break;
-    case 4: r7 ? launch_lanes_r<4, 7>(colour, record, own, other, g, a, s)
-               : launch_lanes_r<4, 10>(colour, record, own, other, g, a, s); break;
-    default: r7 ? launch_lanes_r<8, 7>(colour, record, own, other, g, a, s)
-                : launch_lanes_r<8, 10>(colour, record, own, other, g, a, s); break;
-    }
-    return cudaGetLastError();
-}
-
-// Test hook: Philox4x32-10 blocks of arbitrary counters.
-__global__ void philox_blocks_kernel(const uint32_t* __restrict__ ctr, uint32_t* __restrict__ out,
-                                     int64_t n, uint32_t key0, uint32_t key1)
-{
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n) return;
-    uint32_t x[4] = {ctr[4 * b], ctr[4 * b + 1], ctr[4 * b + 2], ctr[4 * b + 3]};
-    philox10(x, key0, key1);
-    for (int e = 0; e < 4; ++e) out[4 * b + e] = x[e];
-}
-
-}  // namespace ising
 
 namespace {
 
-constexpr int kMaxL = 32768;
 constexpr int kRecordsPerChunk = 1024;           // count slots resident on the device
 constexpr size_t kCountBytes = (size_t)kRecordsPerChunk * kCountSlots * 2 * sizeof(unsigned long long);
 constexpr size_t kAlign = 256;
@@ -327,18 +30,9 @@ constexpr int kResidentAutoMaxItems = 128;          // auto: on-chip up to 128 i
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-Geom make_geom(int L)
-{
-    Geom g;
-    g.L = L;
-    const int half = L / 2;
-    g.W = (half + kFields - 1) / kFields;
-    g.P = (g.W + 1) & ~1;
-    g.rlast = half - kFields * (g.W - 1);
-    return g;
-}
+Geom make_geom(int L) { return lattice_geom(L); }
 
-bool valid_L(int32_t L) { return L >= 4 && L <= kMaxL && (L % 2) == 0; }
+bool valid_L(int32_t L) { return valid_side(L); }
 
 size_t words_bytes(const Geom& g) { return (size_t)g.L * (size_t)g.P * sizeof(uint64_t); }
 
@@ -389,118 +83,7 @@ extern "C" const char* ising_strerror(int code)
     }
 }
 
-namespace ising {
 
-thread_local char g_last_cuda_error[256] = "";
-
-int cuda_fail(cudaError_t e, const char* where)
-{
-    snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "%s: %s", where, cudaGetErrorString(e));
-    return ISING_ECUDA;
-}
-
-// Integer thresholds of Sec. 2 step 3 with dE = 8 - 4a (Table 1).
-void thresholds_for_beta(double beta, uint64_t thr[2])
-{
-    const double two32 = 4294967296.0;
-    for (int a = 0; a < 2; ++a) {
-        const double dE = 8.0 - 4.0 * a;
-        double x = std::floor(std::exp(-dE * beta) * two32);
-        if (x > two32) x = two32;
-        if (!(x >= 0.0)) x = 0.0;
-        thr[a] = (uint64_t)x;
-    }
-}
-
-void fill_threshold_args(const uint64_t thr[2], SweepArgs& a)
-{
-    const uint64_t two32 = 1ull << 32;
-    a.thr0 = thr[0] >= two32 ? 0xFFFFFFFFu : (uint32_t)thr[0];
-    a.thr1 = thr[1] >= two32 ? 0xFFFFFFFFu : (uint32_t)thr[1];
-    a.all0 = thr[0] >= two32 ? 0xFFFFFFFFu : 0u;
-    a.all1 = thr[1] >= two32 ? 0xFFFFFFFFu : 0u;
-}
-
-Geom lattice_geom(int L) { return make_geom(L); }
-
-bool valid_side(int32_t L) { return valid_L(L); }
-
-cudaError_t launch_init_hot(uint64_t* w0, uint64_t* w1, const Geom& g, uint64_t seed, cudaStream_t s)
-{
-    dim3 block(32, 4);
-    dim3 grid((g.W + 31) / 32, ((g.L + 3) / 4 + 3) / 4, 2);
-    init_hot_kernel<<<grid, block, 0, s>>>(w0, w1, g, (uint32_t)seed, (uint32_t)(seed >> 32));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_init_cold(uint64_t* w0, uint64_t* w1, const Geom& g, int up, cudaStream_t s)
-{
-    dim3 block(32, 8);
-    dim3 grid((g.P + 31) / 32, (g.L + 7) / 8);
-    init_cold_kernel<<<grid, block, 0, s>>>(w0, w1, g, up);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_unpack(const uint64_t* w0, const uint64_t* w1, const Geom& g, int8_t* out, cudaStream_t s)
-{
-    dim3 block(32, 8);
-    dim3 grid((g.W + 31) / 32, (g.L + 7) / 8, 2);
-    unpack_kernel<<<grid, block, 0, s>>>(w0, w1, g, out);
-    return cudaGetLastError();
-}
-
-SweepArgs make_sweep_args(uint64_t seed, const uint64_t thr[2], const uint64_t* t_base)
-{
-    SweepArgs a;
-    a.t_base = t_base;
-    a.t_off = 0;
-    fill_threshold_args(thr, a);
-    a.one = 1;
-    a.rounds = 10;
-    a.rk = philox_keys((uint32_t)seed, (uint32_t)(seed >> 32));
-    a.counts = nullptr;
-    a.rec_base = nullptr;
-    return a;
-}
-
-template <int ROUNDS, bool LIN>
-static void launch_half_sweep_r(dim3 grid, dim3 block, int colour, bool update, bool record, uint64_t* own,
-                                const uint64_t* other, const Geom& g, const SweepArgs& a, cudaStream_t s)
-{
-    if (colour == 0) {
-        if (record) launch_pdl(half_sweep_kernel<0, true, true, ROUNDS, LIN>, grid, block, s, own, other, g, a);
-        else launch_pdl(half_sweep_kernel<0, true, false, ROUNDS, LIN>, grid, block, s, own, other, g, a);
-    } else if (!update) {
-        half_sweep_kernel<1, false, true, 10, LIN><<<grid, block, 0, s>>>(own, other, g, a);
-    } else {
-        if (record) launch_pdl(half_sweep_kernel<1, true, true, ROUNDS, LIN>, grid, block, s, own, other, g, a);
-        else launch_pdl(half_sweep_kernel<1, true, false, ROUNDS, LIN>, grid, block, s, own, other, g, a);
-    }
-}
-
-// bw == 0: linear items, bgrp threads per block; else bw x bgrp 2-D blocks.
-cudaError_t launch_half_sweep(int bw, int bgrp, int colour, bool update, bool record,
-                              uint64_t* own, const uint64_t* other, const Geom& g, const SweepArgs& a,
-                              cudaStream_t s)
-{
-    const int ngroups = (g.L + 3) / 4;
-    if (bw == 0) {
-        const uint32_t items = (uint32_t)ngroups * (uint32_t)g.W;
-        dim3 block(bgrp), grid((items + bgrp - 1) / bgrp);
-        if (a.rounds == 7) launch_half_sweep_r<7, true>(grid, block, colour, update, record, own, other, g, a, s);
-        else launch_half_sweep_r<10, true>(grid, block, colour, update, record, own, other, g, a, s);
-        return cudaGetLastError();
-    }
-    dim3 block(bw, bgrp);
-    dim3 grid((g.W + bw - 1) / bw, (ngroups + bgrp - 1) / bgrp);
-    if (a.rounds == 7) launch_half_sweep_r<7, false>(grid, block, colour, update, record, own, other, g, a, s);
-    else launch_half_sweep_r<10, false>(grid, block, colour, update, record, own, other, g, a, s);
-    return cudaGetLastError();
-}
-
-}  // namespace ising
-
-extern "C" const char* ising_last_cuda_error(void) { return g_last_cuda_error; }
 
 extern "C" size_t ising_bytes_required(int32_t L)
 {
@@ -619,8 +202,7 @@ extern "C" int ising_destroy(ising_lattice* h)
 
 static int reset_t(ising_lattice* h, uint64_t t)
 {
-    set_sweep_kernel<<<1, 1, 0, h->stream>>>(h->t_dev, t);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_set_sweep(h->t_dev, t, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "set_sweep_kernel");
     h->t = t;
     return ISING_OK;
@@ -639,11 +221,7 @@ extern "C" int ising_init_hot(ising_lattice* h)
     // zero everything first so the pitch padding is defined
     cudaError_t e = cudaMemsetAsync(h->words[0], 0, 2 * align_up(words_bytes(g), kAlign), h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    dim3 block(32, 4);
-    dim3 grid((g.W + 31) / 32, ((g.L + 3) / 4 + 3) / 4, 2);
-    init_hot_kernel<<<grid, block, 0, h->stream>>>(h->words[0], h->words[1], g, (uint32_t)h->seed,
-                                                   (uint32_t)(h->seed >> 32));
-    e = cudaGetLastError();
+    e = launch_init_hot(h->words[0], h->words[1], g, h->seed, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "init_hot_kernel");
     return reset_t(h, 0);
 }
@@ -656,11 +234,7 @@ extern "C" int ising_init_cold(ising_lattice* h, int8_t spin)
         if (e != cudaSuccess) return cuda_fail(e, "ci_init_cold");
         return reset_t(h, 0);
     }
-    const Geom& g = h->g;
-    dim3 block(32, 8);
-    dim3 grid((g.P + 31) / 32, (g.L + 7) / 8);
-    init_cold_kernel<<<grid, block, 0, h->stream>>>(h->words[0], h->words[1], g, spin > 0 ? 1 : 0);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_init_cold(h->words[0], h->words[1], h->g, spin > 0 ? 1 : 0, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "init_cold_kernel");
     return reset_t(h, 0);
 }
@@ -776,9 +350,8 @@ static int capture_sweeps(ising_lattice* h, int n, int every, cudaGraphExec_t* o
         if (le == cudaSuccess) le = launch_hs_on(h, h->capture_stream, 1, true, rec, a);
     }
     if (le == cudaSuccess) {
-        advance_graph_kernel<<<1, 1, 0, h->capture_stream>>>(h->t_dev, (uint64_t)n, rec_index(h),
-                                                            every > 0 ? (uint32_t)(n / every) : 0u);
-        le = cudaGetLastError();
+        le = launch_advance_graph(h->t_dev, (uint64_t)n, rec_index(h), every > 0 ? (uint32_t)(n / every) : 0u,
+                                  h->capture_stream);
     }
     e = cudaStreamEndCapture(h->capture_stream, &graph);
     if (le != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(le, "sweep graph capture"); }
@@ -824,8 +397,7 @@ static int run_sweeps(ising_lattice* h, int64_t n, RecOf rec_of)
         if (e != cudaSuccess) return cuda_fail(e, "half_sweep colour 1");
     }
     if (n > 0) {
-        advance_sweep_kernel<<<1, 1, 0, h->stream>>>(h->t_dev, (uint64_t)n);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_advance_sweep(h->t_dev, (uint64_t)n, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "advance_sweep_kernel");
         h->t += (uint64_t)n;
     }
@@ -887,73 +459,21 @@ static int resident_lanes(const Geom& g)
     return 0;
 }
 
-template <int F>
-static cudaError_t launch_resident_group(const ising_lattice* h, const SweepArgs& a, size_t bytes, int n, int every,
-                                         long long* rec)
-{
-    const Geom& g = h->g;
-    const int items = ((g.L + 3) / 4) * g.W;
-    const int threads = (items * F + 31) / 32 * 32;      // <= 416 by resident_lanes
-    if (a.rounds == 7)
-        resident_group_kernel<F, 7><<<1, threads, bytes, h->stream>>>(h->words[0], h->words[1], g, a, h->t, n, every,
-                                                                      rec);
-    else
-        resident_group_kernel<F, 10><<<1, threads, bytes, h->stream>>>(h->words[0], h->words[1], g, a, h->t, n,
-                                                                       every, rec);
-    return cudaGetLastError();
-}
-
-template <int F>
-static cudaError_t allow_group_smem()
-{
-    cudaError_t e = cudaFuncSetAttribute(resident_group_kernel<F, 10>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kResidentMaxBytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(resident_group_kernel<F, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kResidentMaxBytes);
-    return e;
-}
-
 // n sweeps with the lattice resident in shared memory, E/M records (if any)
 // written as (E, M) pairs into the count buffer.
 static int run_resident(ising_lattice* h, int n, int every)
 {
     const Geom& g = h->g;
-    const size_t bytes = resident_bytes(g);
     if (!h->resident_attr) {
-        cudaError_t e = cudaFuncSetAttribute(resident_sweeps_kernel<10>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kResidentMaxBytes);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(resident_sweeps_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kResidentMaxBytes);
-        if (e == cudaSuccess) e = allow_group_smem<2>();
-        if (e == cudaSuccess) e = allow_group_smem<4>();
-        if (e == cudaSuccess) e = allow_group_smem<32>();
+        cudaError_t e = allow_resident_smem((int)kResidentMaxBytes);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
         h->resident_attr = true;
     }
-    const int items = ((g.L + 3) / 4) * g.W;
-    SweepArgs a = base_args(h);
-    long long* rec = reinterpret_cast<long long*>(h->counts);
-    cudaError_t e = cudaSuccess;
-    switch (resident_lanes(g)) {
-    case 32: e = launch_resident_group<32>(h, a, bytes, n, every, rec); break;
-    case 4: e = launch_resident_group<4>(h, a, bytes, n, every, rec); break;
-    case 2: e = launch_resident_group<2>(h, a, bytes, n, every, rec); break;
-    default: {
-        const int threads = std::min(256, std::max(32, (items + 31) / 32 * 32));
-        if (a.rounds == 7)
-            resident_sweeps_kernel<7><<<1, threads, bytes, h->stream>>>(h->words[0], h->words[1], g, a, h->t, n,
-                                                                        every, rec);
-        else
-            resident_sweeps_kernel<10><<<1, threads, bytes, h->stream>>>(h->words[0], h->words[1], g, a, h->t, n,
-                                                                         every, rec);
-        e = cudaGetLastError();
-    }
-    }
+    const SweepArgs a = base_args(h);
+    cudaError_t e = launch_resident(resident_lanes(g), h->words[0], h->words[1], g, a, h->t, n, every,
+                                    reinterpret_cast<long long*>(h->counts), resident_bytes(g), h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "resident sweeps kernel");
-    advance_sweep_kernel<<<1, 1, 0, h->stream>>>(h->t_dev, (uint64_t)n);
-    e = cudaGetLastError();
+    e = launch_advance_sweep(h->t_dev, (uint64_t)n, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "advance_sweep_kernel");
     h->t += (uint64_t)n;
     return ISING_OK;
@@ -1119,10 +639,7 @@ extern "C" int ising_get_spins(ising_lattice* h, int8_t* out, size_t n)
     if (h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED) {
         e = ci_unpack(h->words[0], g.L, h->staging, h->stream);
     } else {
-        dim3 block(32, 8);
-        dim3 grid((g.W + 31) / 32, (g.L + 7) / 8, 2);
-        unpack_kernel<<<grid, block, 0, h->stream>>>(h->words[0], h->words[1], g, h->staging);
-        e = cudaGetLastError();
+        e = launch_unpack(h->words[0], h->words[1], g, h->staging, h->stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "unpack_kernel");
     e = cudaMemcpyAsync(out, h->staging, n, cudaMemcpyDeviceToHost, h->stream);
@@ -1155,9 +672,7 @@ extern "C" int ising_set_spins(ising_lattice* h, const int8_t* in, size_t n)
     if (h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED) {
         e = ci_pack(h->words[0], g.L, h->staging, h->stream);
     } else {
-        const int vec16 = ((uintptr_t)src % 16 == 0) && (g.L % 16 == 0);
-        pack_rows_kernel<<<g.L, 256, g.L, h->stream>>>(h->words[0], h->words[1], g, src, vec16);
-        e = cudaGetLastError();
+        e = launch_pack_rows(h->words[0], h->words[1], g, src, h->stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "pack_kernel");
     e = cudaStreamSynchronize(h->stream);
@@ -1225,9 +740,7 @@ extern "C" int ising_run_states(ising_lattice* h, const int8_t* const* states, i
             if (e == cudaSuccess) e = cudaEventRecord(h->ev_copied[b], h->copy_stream);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0);
             if (e != cudaSuccess) break;
-            const int vec16 = ((uintptr_t)stage[b] % 16 == 0) && (g.L % 16 == 0);
-            pack_rows_kernel<<<g.L, 256, g.L, h->stream>>>(h->words[0], h->words[1], g, stage[b], vec16);
-            e = cudaGetLastError();
+            e = launch_pack_rows(h->words[0], h->words[1], g, stage[b], h->stream);
             if (e == cudaSuccess) e = cudaEventRecord(h->ev_packed[b], h->stream);
             if (e != cudaSuccess) break;
             const int64_t base = (k - k0) * R;
@@ -1361,9 +874,7 @@ extern "C" int ising_philox_blocks(uint64_t seed, const uint32_t* host_ctr, uint
     int rc = ISING_OK;
     e = cudaMemcpy(d, host_ctr, (size_t)n * 4 * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        philox_blocks_kernel<<<(unsigned)((n + 255) / 256), 256>>>(d, d + 4 * n, n, (uint32_t)seed,
-                                                                  (uint32_t)(seed >> 32));
-        e = cudaGetLastError();
+        e = launch_philox_blocks(d, d + 4 * n, n, seed, nullptr);
     }
     if (e == cudaSuccess) e = cudaMemcpy(host_out, d + 4 * n, (size_t)n * 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) rc = cuda_fail(e, "philox_blocks");
