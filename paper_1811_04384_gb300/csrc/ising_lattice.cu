@@ -674,7 +674,7 @@ extern "C" int ising_set_spins(ising_lattice* h, const int8_t* in, size_t n)
     } else {
         e = launch_pack_rows(h->words[0], h->words[1], g, src, h->stream);
     }
-    if (e != cudaSuccess) return cuda_fail(e, "pack_kernel");
+    if (e != cudaSuccess) return cuda_fail(e, "pack_rows_kernel");
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return ISING_OK;
