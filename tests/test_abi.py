@@ -84,3 +84,14 @@ def test_product_path_has_no_oracle_dependency():
                 text = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in text and "from oracle" not in text, fn
                 assert "oracle.c" not in text and "liboracle" not in text, fn
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libising.so the binding raises instead of falling back."""
+    import paper_1811_04384_gb300 as p
+    monkeypatch.setattr(p, "_lib", None)
+    monkeypatch.setattr(p, "LIB_PATH", str(tmp_path / "libising.so"))
+    with pytest.raises(ImportError, match="no CPU fallback"):
+        p.load()
+    with pytest.raises(ImportError):
+        p.Lattice(64, 1)
