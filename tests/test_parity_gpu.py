@@ -478,6 +478,37 @@ def test_config_large_L16384_first_sweeps(ising):
         np.testing.assert_array_equal(lat.get_spins(), s)
 
 
+def test_config_large_L16384_run_states(ising):
+    """The bench's end-to-end form at full size: ising_run_states with pinned
+    int8 states of L = 16384 (the copy of state k+1 overlapping the sweeps of
+    state k) equals set_spins + sweep_record in turn; the first state's first
+    record also equals the oracle's."""
+    import torch
+    L = 16384
+    with ising.Lattice(L, 3) as lat, ising.Lattice(L, 3) as ref:
+        lat.init_hot()
+        base = lat.get_spins()
+        states = []
+        for k in range(3):
+            p = torch.empty((L, L), dtype=torch.int8, pin_memory=True)
+            a = p.numpy()
+            a[:] = base
+            a[k::7, :] *= -1                      # a different state each time
+            states.append(a)
+        for x in (lat, ref):
+            x.set_beta(BETA_TC)
+        E1, M1 = lat.run_states(states, 4, 2)
+        for k in range(3):
+            ref.set_spins(states[k])
+            E, M = ref.sweep_record(4, 2)
+            np.testing.assert_array_equal(E1[k], E)
+            np.testing.assert_array_equal(M1[k], M)
+        np.testing.assert_array_equal(lat.get_spins(), ref.get_spins())
+    s = states[0].copy()
+    Eo, Mo = oracle.run(s, 3, BETA_TC, 0, 2, 2)
+    assert E1[0][0] == Eo[0] and M1[0][0] == Mo[0]
+
+
 def test_max_size_lattice(ising):
     """L = 32768 (the largest allowed): properties that hold at any size."""
     L = 32768
