@@ -146,8 +146,8 @@ int ising_magnetization(ising_lattice *h, int64_t *host_M);
  * Packing and unpacking run on the device through an int8 L*L staging
  * buffer that the library allocates on first use (also for ising_create_on
  * lattices) and frees in ising_destroy; ising_set_spins reads a pinned host
- * array (cudaHostAlloc / cudaHostRegister) in place instead, in one pass.  n != L*L -> EINVAL.
- * Synchronises.  Neither changes t. */
+ * array (cudaHostAlloc / cudaHostRegister) in place instead, in one pass.
+ * n != L*L -> EINVAL.  Synchronises.  Neither changes t. */
 int ising_get_spins(ising_lattice *h, int8_t *host_out, size_t n);
 int ising_set_spins(ising_lattice *h, const int8_t *host_in, size_t n);
 
@@ -211,7 +211,13 @@ int ising_set_tiling(ising_lattice *h, int32_t rows_per_thread,
 int ising_set_item_lanes(ising_lattice *h, int32_t lanes);
 
 /* Execution path of ising_sweep / ising_sweep_record.  ISING_PATH_LAUNCHES:
- * two kernel launches per sweep, all SMs.  ISING_PATH_RESIDENT: temporal
+ * two kernel launches per sweep, all SMs; up to 32768 thread items (L up to
+ * about 2300, either layout) the launches of chunks of up to 32 sweeps are
+ * captured once into CUDA graphs and replayed (recaptured after
+ * ising_set_beta, ising_set_rng, ising_set_tiling, ising_set_item_lanes; a
+ * device record index picks the count slots of each replay), because there
+ * a half-sweep runs about as long as the host takes to launch it.
+ * ISING_PATH_RESIDENT: temporal
  * blocking with the whole lattice on chip -- one block copies both colour
  * arrays into shared memory and runs all requested sweeps there in one
  * launch (lattices with 2 L pitch 8 bytes <= 220 KB, i.e. L up to about
