@@ -39,6 +39,28 @@ def test_seven_rounds_match_oracle(ising, L, path):
     assert not np.array_equal(spins, s10)
 
 
+@pytest.mark.parametrize("L", [64, 258])
+def test_seven_rounds_through_graph_replays(ising, L):
+    """Long enough for the launch path's replayed graphs (record chunks and
+    32-sweep chunks) with the 7-round kernels and item lanes."""
+    beta = 0.45
+    with ising.Lattice(L, 7) as lat:
+        lat.set_rng(ising.ISING_RNG_PHILOX4X32_7)
+        lat.set_path(ising.ISING_PATH_LAUNCHES)
+        lat.init_hot()
+        lat.set_beta(beta)
+        E, M = lat.sweep_record(66, 3)
+        lat.sweep(40)
+        spins = lat.get_spins()
+    with oracle.sweep_rounds(7):
+        s = oracle.init_hot(L, 7)
+        Eo, Mo = oracle.run(s, 7, beta, 0, 66, 3)
+        oracle.run(s, 7, beta, 66, 40, 40)
+    np.testing.assert_array_equal(E, Eo)
+    np.testing.assert_array_equal(M, Mo)
+    np.testing.assert_array_equal(spins, s)
+
+
 def test_rng_scheme_rejects_unknown(ising):
     with ising.Lattice(64, 1) as lat:
         with pytest.raises(ising.IsingError):
