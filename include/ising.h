@@ -402,10 +402,11 @@ int ising_autotune(int32_t L, int32_t sweeps, int32_t *best_block_words, int32_t
 
 /* Batch (arguments as ising_batch_create): threads per tile {64, 128, 256}
  * x graph chunk {10, 50, 200} x lanes {1, 2, 4}, `sweeps` timed sweeps per
- * replica.  Outputs may be NULL. */
+ * replica with E/M every `every`-th sweep (1 <= every <= sweeps; the
+ * kernels differ for every == 1).  Outputs may be NULL. */
 int ising_batch_autotune(int32_t n, const int32_t *L, const double *beta, const uint64_t *seed,
-                         const uint8_t *hot, int64_t sweeps, int32_t *best_threads, int32_t *best_chunk,
-                         int32_t *best_lanes, double *ns_per_update);
+                         const uint8_t *hot, int64_t sweeps, int64_t every, int32_t *best_threads,
+                         int32_t *best_chunk, int32_t *best_lanes, double *ns_per_update);
 
 /* ---- Allocation-free record path ----------------------------------------
  * The paper has no counterpart to this entry point.  It is for callers that

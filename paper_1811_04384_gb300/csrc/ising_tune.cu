@@ -96,10 +96,11 @@ extern "C" int ising_autotune(int32_t L, int32_t sweeps, int32_t* best_bw, int32
 }
 
 extern "C" int ising_batch_autotune(int32_t n, const int32_t* L, const double* beta, const uint64_t* seed,
-                                    const uint8_t* hot, int64_t sweeps, int32_t* best_threads, int32_t* best_chunk,
-                                    int32_t* best_lanes, double* ns_per_update)
+                                    const uint8_t* hot, int64_t sweeps, int64_t every, int32_t* best_threads,
+                                    int32_t* best_chunk, int32_t* best_lanes, double* ns_per_update)
 {
-    if (n < 1 || !L || !beta || !seed || sweeps < 1 || sweeps > 100000) return ISING_EINVAL;
+    if (n < 1 || !L || !beta || !seed || sweeps < 1 || sweeps > 100000 || every < 1 || every > sweeps)
+        return ISING_EINVAL;
     const int threads[3] = {64, 128, 256};
     const int chunks[3] = {10, 50, 200};
     const int lanes[3] = {1, 2, 4};
@@ -119,10 +120,10 @@ extern "C" int ising_batch_autotune(int32_t n, const int32_t* L, const double* b
             rc = ising_batch_set_tiling(b, threads[ti], chunks[ci]);
             if (rc == ISING_OK) rc = ising_batch_set_lanes(b, lanes[li]);
             std::vector<int64_t> one(n, 1);
-            if (rc == ISING_OK) rc = ising_batch_sweep(b, one.data(), 1, nullptr, nullptr);   // warm-up, graph capture
+            if (rc == ISING_OK) rc = ising_batch_sweep(b, one.data(), every == 1 ? 1 : 2, nullptr, nullptr);   // warm-up
             // ising_batch_sweep synchronises the batch's stream, so the host clock times it
             const auto t0 = std::chrono::steady_clock::now();
-            if (rc == ISING_OK) rc = ising_batch_sweep(b, sw.data(), sweeps, nullptr, nullptr);
+            if (rc == ISING_OK) rc = ising_batch_sweep(b, sw.data(), every, nullptr, nullptr);
             const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
             for (int r = 0; rc == ISING_OK && r < n; ++r) {
                 got[r].resize((size_t)L[r] * L[r]);

@@ -2,10 +2,14 @@
 include/ising.h), kept in a JSON table next to this file:
 
     {"device": "...", "lattice": {"<L>": {"block_words": .., "block_groups": ..,
-     "path": .., "item_lanes": .., "ns_per_update": ..}}, "batch": {...}}
+     "path": .., "item_lanes": .., "ns_per_update": ..}},
+     "batch": {"<name>": {"threads_per_tile": .., "graph_chunk": .., "lanes": ..,
+     "ns_per_update": .., "workload": ".."}}}
 
-`apply(lattice)` sets the tuned shape for the lattice's side when the table
-holds one for the current device.  Choosing a shape never changes results.
+`apply(lattice)` sets the tuned shape for the lattice's side and
+`apply_batch(batch, name)` the tuned tiles of a named batch workload, when the
+table holds one for the current device.  Choosing a shape never changes
+results.
 """
 from __future__ import annotations
 
@@ -37,7 +41,7 @@ def tune_lattice(L: int, sweeps: int = 20) -> dict:
             "ns_per_update": ns.value}
 
 
-def tune_batch(L, beta, seed, hot, sweeps: int = 50) -> dict:
+def tune_batch(L, beta, seed, hot, sweeps: int = 50, every: int = 1) -> dict:
     L = np.ascontiguousarray(L, dtype=np.int32)
     beta = np.ascontiguousarray(beta, dtype=np.float64)
     seed = np.ascontiguousarray(seed, dtype=np.uint64)
@@ -47,7 +51,7 @@ def tune_batch(L, beta, seed, hot, sweeps: int = 50) -> dict:
     _check(load().ising_batch_autotune(len(L), L.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                        beta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                        seed.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
-                                       hot.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), int(sweeps),
+                                       hot.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), int(sweeps), int(every),
                                        ctypes.byref(th), ctypes.byref(ch), ctypes.byref(ln), ctypes.byref(ns)),
            "ising_batch_autotune")
     return {"threads_per_tile": th.value, "graph_chunk": ch.value, "lanes": ln.value, "ns_per_update": ns.value}
@@ -66,11 +70,41 @@ def save_table(table: dict, path: str = TABLE):
 
 
 def tune_all(Ls, sweeps: int = 20, path: str = TABLE) -> dict:
-    table = {"device": _device_name(), "lattice": {}}
+    table = load_table(path)
+    if table.get("device") != _device_name():
+        table = {}
+    table["device"] = _device_name()
+    table["lattice"] = {}
     for L in Ls:
         table["lattice"][str(int(L))] = tune_lattice(int(L), sweeps)
     save_table(table, path)
     return table
+
+
+def tune_named_batch(name: str, L, beta, seed, hot, sweeps: int = 20, every: int = 1, workload: str = "",
+                     path: str = TABLE) -> dict:
+    """Tune the batch tiles of one workload and store them under `name`."""
+    entry = tune_batch(L, beta, seed, hot, sweeps, every)
+    entry["workload"] = workload
+    table = load_table(path)
+    if table.get("device") != _device_name():
+        table = {"lattice": {}}
+    table["device"] = _device_name()
+    table.setdefault("batch", {})[name] = entry
+    save_table(table, path)
+    return entry
+
+
+def apply_batch(batch, name: str, table: dict | None = None) -> bool:
+    """Set the tuned tiles of batch workload `name` if the table has them for
+    this device."""
+    table = load_table() if table is None else table
+    entry = table.get("batch", {}).get(name)
+    if not entry or table.get("device") != _device_name():
+        return False
+    batch.set_tiling(entry["threads_per_tile"], entry["graph_chunk"])
+    batch.set_lanes(entry["lanes"])
+    return True
 
 
 def apply(lattice, table: dict | None = None) -> bool:
