@@ -54,7 +54,7 @@ enum {
                              NULL pointer, buffer too small, bad count */
     ISING_ENOMEM = -2,    /* device or host allocation failed */
     ISING_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
-    ISING_ETIMEOUT = -4,  /* a bounded device-side wait gave up */
+    ISING_ETIMEOUT = -4,  /* a bounded wait gave up (ising_server_wait); no kernel spin-waits */
     ISING_EBUSY = -5,     /* no free slot / budget (server admission) */
     ISING_ENOTFOUND = -6  /* unknown request id */
 };

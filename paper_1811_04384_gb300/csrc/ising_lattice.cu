@@ -19,7 +19,6 @@
 
 using namespace ising;
 
-
 namespace {
 
 constexpr int kRecordsPerChunk = 1024;           // count slots resident on the device
@@ -62,7 +61,7 @@ struct ising_lattice {
     int item_lanes = 0;                          // lanes per thread item on the launch path (0: auto)
     cudaStream_t capture_stream = nullptr;       // graphs of sweep chunks are captured here
     cudaGraphExec_t graph_plain = nullptr;       // kGraphSweeps sweeps, no record
-    cudaGraphExec_t graph_rec = nullptr;         // graph_rec_every sweeps, the last one recorded
+    cudaGraphExec_t graph_rec = nullptr;         // record intervals of graph_rec_every sweeps, each recorded
     int graph_rec_every = 0;
     bool resident_attr = false;                  // dynamic shared memory attribute set
 };
@@ -76,7 +75,7 @@ extern "C" const char* ising_strerror(int code)
     case ISING_EINVAL: return "invalid argument";
     case ISING_ENOMEM: return "out of memory";
     case ISING_ECUDA: return "CUDA error";
-    case ISING_ETIMEOUT: return "bounded device wait timed out";
+    case ISING_ETIMEOUT: return "timed out waiting";
     case ISING_EBUSY: return "busy: no free slot or memory budget";
     case ISING_ENOTFOUND: return "unknown request id";
     default: return "unknown error code";
@@ -299,9 +298,10 @@ static cudaError_t launch_hs(const ising_lattice* h, int colour, bool update, bo
 // Below about L = 2300 a half-sweep kernel runs for a few microseconds, about
 // as long as the host takes to launch it.  Chunks of sweeps are captured once
 // into CUDA graphs and replayed: graph_plain holds kGraphSweeps sweeps, and
-// graph_rec holds `every` sweeps whose last one records into the count slots
-// picked by the device record index (advanced by the graph itself, so one
-// graph serves every record of a chunk).  The kernels' launch operands
+// graph_rec holds max(1, kGraphSweeps / every) record intervals of `every`
+// sweeps, each recording into count slots offset by the device record index
+// (advanced by the graph itself, so one graph serves every record of a
+// chunk).  The kernels' launch operands
 // (thresholds, Philox rounds, launch shape) are baked into the graphs, so
 // every call that changes them drops the graphs.
 constexpr int kGraphSweeps = 32;
