@@ -75,6 +75,7 @@ def _stream_ptr(stream) -> ctypes.c_void_p:
 
 
 def bytes_required(L: int) -> int:
+    """Device bytes a lattice of side L needs (ising_bytes_required), for caller-owned buffers."""
     return int(load().ising_bytes_required(L))
 
 
@@ -104,6 +105,7 @@ class Lattice:
 
     # -- lifetime ---------------------------------------------------------------
     def close(self):
+        """Release the lattice (ising_destroy); also done by the context manager."""
         if getattr(self, "_h", None) is not None and self._h.value is not None:
             load().ising_destroy(self._h)
             self._h = None
@@ -122,21 +124,26 @@ class Lattice:
 
     # -- state ------------------------------------------------------------------
     def init_hot(self):
+        """Hot start (ising_init_hot): each spin from the site's Philox draw at t = 0; t = 0."""
         _check(load().ising_init_hot(self._h), "ising_init_hot")
 
     def init_cold(self, spin: int = 1):
+        """Cold start (ising_init_cold): every spin = spin (+1 or -1); t = 0."""
         _check(load().ising_init_cold(self._h, int(spin)), "ising_init_cold")
 
     def set_beta(self, beta: float):
+        """Inverse temperature (ising_set_beta); builds the integer thresholds."""
         _check(load().ising_set_beta(self._h, float(beta)), "ising_set_beta")
 
     def thresholds(self) -> tuple[int, int]:
+        """The two integer thresholds in use (ising_get_thresholds): (thr[a=0], thr[a=1])."""
         thr = (ctypes.c_uint64 * 2)()
         _check(load().ising_get_thresholds(self._h, thr), "ising_get_thresholds")
         return int(thr[0]), int(thr[1])
 
     @property
     def t(self) -> int:
+        """Sweep counter (ising_get_sweep / ising_set_sweep)."""
         v = ctypes.c_uint64()
         _check(load().ising_get_sweep(self._h, ctypes.byref(v)), "ising_get_sweep")
         return int(v.value)
@@ -146,9 +153,11 @@ class Lattice:
         _check(load().ising_set_sweep(self._h, int(value)), "ising_set_sweep")
 
     def set_stream(self, stream):
+        """CUDA stream for all further work (ising_set_stream): a torch.cuda.Stream, a handle or None."""
         _check(load().ising_set_stream(self._h, _stream_ptr(stream)), "ising_set_stream")
 
     def set_tiling(self, rows: int = 4, block_words: int = 0, block_groups: int = 128):
+        """Launch shape of the half-sweep kernels (ising_set_tiling); results do not depend on it."""
         _check(load().ising_set_tiling(self._h, rows, block_words, block_groups), "ising_set_tiling")
 
     def run_states(self, states, sweeps: int, every: int = 1):
@@ -182,15 +191,18 @@ class Lattice:
         _check(load().ising_set_path(self._h, int(path)), "ising_set_path")
 
     def layout(self) -> tuple[int, int, int]:
+        """(W, pitch, live fields of the last word) of the row-packed layout (ising_layout)."""
         W, P, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         _check(load().ising_layout(self._h, ctypes.byref(W), ctypes.byref(P), ctypes.byref(r)), "ising_layout")
         return W.value, P.value, r.value
 
     # -- dynamics ---------------------------------------------------------------
     def sweep(self, n: int = 1):
+        """Run n sweeps (ising_sweep); asynchronous on the lattice's stream."""
         _check(load().ising_sweep(self._h, int(n)), "ising_sweep")
 
     def sweep_record(self, n: int, every: int = 1):
+        """Run n sweeps; returns int64 arrays E, M recorded every `every` sweeps (ising_sweep_record)."""
         k = n // every
         E = np.zeros(max(k, 1), dtype=np.int64)
         M = np.zeros(max(k, 1), dtype=np.int64)
@@ -199,17 +211,20 @@ class Lattice:
         return E[:k], M[:k]
 
     def energy(self) -> int:
+        """Current energy, exact int64 (ising_energy)."""
         v = ctypes.c_int64()
         _check(load().ising_energy(self._h, ctypes.byref(v)), "ising_energy")
         return int(v.value)
 
     def magnetization(self) -> int:
+        """Current magnetisation, exact int64 (ising_magnetization)."""
         v = ctypes.c_int64()
         _check(load().ising_magnetization(self._h, ctypes.byref(v)), "ising_magnetization")
         return int(v.value)
 
     # -- spin I/O ---------------------------------------------------------------
     def get_spins(self, out: np.ndarray | None = None) -> np.ndarray:
+        """The spins as an L x L int8 array of +1 / -1 (ising_get_spins)."""
         if out is None:
             out = np.empty((self.L, self.L), dtype=np.int8)
         assert out.dtype == np.int8 and out.size == self.L * self.L and out.flags["C_CONTIGUOUS"]
@@ -218,12 +233,14 @@ class Lattice:
         return out
 
     def set_spins(self, s: np.ndarray):
+        """Set the spins from an L x L int8 array, > 0 is up (ising_set_spins); pinned arrays are read in place."""
         s = np.ascontiguousarray(s, dtype=np.int8)
         assert s.size == self.L * self.L
         _check(load().ising_set_spins(self._h, s.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), s.size),
                "ising_set_spins")
 
     def get_words(self) -> np.ndarray:
+        """The packed words of both colours, shape (2, L, pitch) (ising_get_words), for checkpoints."""
         _, P, _ = self.layout()
         out = np.empty(2 * self.L * P, dtype=np.uint64)
         _check(load().ising_get_words(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), out.size),
@@ -231,11 +248,13 @@ class Lattice:
         return out.reshape(2, self.L, P)
 
     def set_words(self, words: np.ndarray):
+        """Set the packed words of both colours (ising_set_words)."""
         w = np.ascontiguousarray(words, dtype=np.uint64).reshape(-1)
         _check(load().ising_set_words(self._h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), w.size),
                "ising_set_words")
 
     def device_words(self, c: int) -> int:
+        """Device address of colour c's packed words (ising_device_words)."""
         p = ctypes.c_void_p()
         _check(load().ising_device_words(self._h, int(c), ctypes.byref(p)), "ising_device_words")
         return int(p.value)
@@ -270,6 +289,7 @@ class Batch:
         self._h = h
 
     def close(self):
+        """Release the batch (ising_batch_destroy); also done by the context manager."""
         if getattr(self, "_h", None) is not None and self._h.value is not None:
             load().ising_batch_destroy(self._h)
             self._h = None
@@ -287,9 +307,11 @@ class Batch:
         self.close()
 
     def set_rng(self, scheme: int):
+        """Random-number scheme of every replica (ising_batch_set_rng)."""
         _check(load().ising_batch_set_rng(self._h, int(scheme)), "ising_batch_set_rng")
 
     def set_tiling(self, threads_per_tile: int = 128, graph_chunk: int = 50):
+        """Threads per tile and sweeps per captured graph (ising_batch_set_tiling); results do not depend on them."""
         _check(load().ising_batch_set_tiling(self._h, threads_per_tile, graph_chunk), "ising_batch_set_tiling")
 
     def set_lanes(self, lanes: int = 4):
@@ -309,6 +331,7 @@ class Batch:
         return (E, M) if record else None
 
     def get_spins(self, r: int) -> np.ndarray:
+        """Spins of replica r as an L x L int8 array (ising_batch_get_spins)."""
         L = int(self.L[r])
         out = np.empty((L, L), dtype=np.int8)
         _check(load().ising_batch_get_spins(self._h, int(r), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
@@ -316,6 +339,7 @@ class Batch:
         return out
 
     def t(self, r: int) -> int:
+        """Sweep counter of replica r (ising_batch_get_sweep)."""
         v = ctypes.c_uint64()
         _check(load().ising_batch_get_sweep(self._h, int(r), ctypes.byref(v)), "ising_batch_get_sweep")
         return int(v.value)
