@@ -491,7 +491,7 @@ def run_plain(args, ising, local):
           "paths": {"resident_on_chip": rate["resident"], "launches": rate["launches"],
                     "graph_captured_batch": rate["graph"]},
           "bit_exact_across_paths": exact,
-          "gpu_launches": 2})      # the timed on-chip call: one sweeps kernel, one sweep-counter kernel
+          "gpu_launches": 3})      # the timed on-chip call: mask draw, on-chip sweeps, sweep counter
 
 
 # The paper's test cases (Table 2): lattice side and iterations; an iteration

@@ -125,14 +125,17 @@ int ising_get_thresholds(ising_lattice *h, uint64_t host_thr[2]);
 
 /* Run n >= 0 full sweeps t+1 .. t+n (t += n).  A sweep is the paper's Monte
  * Carlo iteration (Sec. 2: every spin proposed once), in checkerboard order:
- * all colour-0 sites, then all colour-1 sites.  Asynchronous on the stream.
- * Errors: EINVAL (NULL, n < 0), ECUDA. */
+ * all colour-0 sites, then all colour-1 sites.  Asynchronous on the stream
+ * (the first call on the on-chip path allocates its mask buffer).
+ * Errors: EINVAL (NULL, n < 0), ENOMEM (that buffer), ECUDA. */
 int ising_sweep(ising_lattice *h, int64_t n);
 
 /* Run n sweeps and record E and M after sweeps t+every, t+2*every, ...:
  * host_E and host_M (caller-owned host arrays) receive n / every entries
  * each; either may be NULL.  n >= 0, 1 <= every <= 2^22.  Synchronises the stream.
- * The counts come from the reduction fused into the colour-1 half-sweep. */
+ * The counts come from the reduction fused into the colour-1 half-sweep.
+ * Errors: EINVAL (NULL, n < 0, every out of range), ENOMEM (the on-chip
+ * path's mask buffer), ECUDA. */
 int ising_sweep_record(ising_lattice *h, int64_t n, int64_t every,
                        int64_t *host_E, int64_t *host_M);
 
@@ -222,11 +225,12 @@ int ising_set_item_lanes(ising_lattice *h, int32_t lanes);
  * arrays into shared memory and runs all requested sweeps there in one
  * launch (lattices with 2 L pitch 8 bytes <= 220 KB, i.e. L up to about
  * 740; larger -> EINVAL); it removes the per-sweep launch latency that
- * bounds small lattices.  Up to L = 168 the fields of each thread item are
- * split over 2, 4 or 32 lanes, so that a small lattice still gives all four
- * schedulers of the SM work.  ISING_PATH_AUTO (default): resident while
- * ceil(L/4) * ceil(L/42) <= 128 thread items (L <= 128); above that the
- * launch path, whose replayed graphs are faster there.
+ * bounds small lattices.  Up to 512 thread items (ceil(L/4) * ceil(L/42),
+ * L <= 292) the accept masks of the requested sweeps are first drawn by all
+ * SMs into a device buffer the library allocates on first use (up to
+ * 16 MB), and the on-chip block only applies them, one or two rows per
+ * thread.  ISING_PATH_AUTO (default): resident up to 512 thread items; above
+ * that the launch path, which is faster there.
  * Results are identical on every path. */
 #define ISING_PATH_AUTO 0
 #define ISING_PATH_LAUNCHES 1

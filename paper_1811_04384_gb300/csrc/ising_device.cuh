@@ -255,53 +255,17 @@ __device__ __forceinline__ void sweep_rows(uint64_t* __restrict__ own, const uin
     }
 }
 
-// ---- Field-split forms of sweep_rows ------------------------------------
-// For lattices too small to fill the GPU (or one SM) with one thread per item,
-// several lanes share an item.  Each form has two parts: the accept masks of
-// an item (the Philox draws against the thresholds; they depend on the site,
-// sweep and colour only, never on the spins) and their application to the
-// item's rows.  A caller can therefore draw the masks of the next half-sweep
-// while it applies the current one.  The draws and the accept rule are those
-// of sweep_rows, so the results are bit-identical.  All lanes of a warp must
-// call the mask parts (shuffles, ballots); an item past the end (`valid` =
-// false) is drawn as item 0 and never applied.
-
-// One warp per item.  Lane l draws field k = l / 3 when l % 3 == 0 (fields
-// 0..10) and k = (l + 32) / 3 when l % 3 == 1 (fields 11..20); the other
-// lanes draw nothing.  So the lane of field k is the bit position 3k of its
-// spin within the low or high 32-bit half of the word, and a warp ballot of
-// the lanes' comparisons is already that half of the accept mask in word
-// layout.  Every lane gets all masks: a1[e] (r < thr1) and a0[e] (r < thr0)
-// of row e.
-template <int ROUNDS = 10>
-__device__ __forceinline__ void item_masks_warp(const Geom& g, int item, int lane, uint64_t t, int colour,
-                                                const PhiloxKeys& rk, uint32_t thr0, uint32_t thr1,
-                                                uint64_t a1[4], uint64_t a0[4])
-{
-    const int grp = item / g.W;
-    const int w = item - grp * g.W;
-    const int lm3 = lane % 3;
-    const int k = lm3 == 0 ? lane / 3 : (lm3 == 1 ? (lane + 32) / 3 : kFields);
-    const bool lo_lane = lm3 == 0;
-    const bool hi_lane = lm3 == 1 && k < kFields;
-    uint32_t r[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};   // never below a threshold
-    if (k < kFields) {
-        const uint32_t tl = (uint32_t)t;
-        const uint32_t th = ((uint32_t)(t >> 32) << 1) | (uint32_t)colour;
-        const PhiloxRowKey pk = philox_row_key((uint32_t)grp, tl, th, rk);
-        philox_row<ROUNDS>(pk, rk, (uint32_t)(w * kFields + k), r);
-    }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const bool p1 = r[e] < thr1, p0 = r[e] < thr0;
-        const uint32_t c1lo = __ballot_sync(0xffffffffu, p1 && lo_lane);
-        const uint32_t c1hi = __ballot_sync(0xffffffffu, p1 && hi_lane);
-        const uint32_t c0lo = __ballot_sync(0xffffffffu, p0 && lo_lane);
-        const uint32_t c0hi = __ballot_sync(0xffffffffu, p0 && hi_lane);
-        a1[e] = (uint64_t)c1hi << 32 | c1lo;
-        a0[e] = (uint64_t)c0hi << 32 | c0lo;
-    }
-}
+// ---- Split forms of sweep_rows -------------------------------------------
+// The work of an item in two parts: its accept masks (the Philox draws
+// against the thresholds; they depend on the site, sweep and colour only,
+// never on the spins) and their application to the item's rows.  So the
+// masks can be drawn by other threads than the ones that apply them, or
+// before the spins they apply to exist: F lanes per item on the launch path
+// for lattices too small to fill the GPU with one thread per item, and all
+// masks of a run drawn beforehand for the on-chip path.  The draws and the
+// accept rule are those of sweep_rows, so the results are bit-identical.  All
+// lanes of a warp must call the lane forms (shuffles); an item past the end
+// (`valid` = false) is drawn as item 0 and never applied.
 
 // F lanes per item (F = 2, 4 or 8; aligned groups of the warp): lane q draws
 // the fields k = q + jF, collects its accept bits at bit 3jF (compile-time
@@ -349,9 +313,43 @@ __device__ __forceinline__ void item_masks_lanes(const Geom& g, int item, int q,
     }
 }
 
-// Apply the masks of an item of colour C: lane q of its group (F lanes; a
-// warp for F = 32) updates rows q, q + F, ... below 4 (one code path for all
-// lanes, the row's masks picked by selection).  RECORD adds the item's
+// Apply the masks m1 (r < thr1) and m0 (r < thr0) of row i, word w of colour
+// C: the spin logic of sweep_rows for one row.  all0 / all1 are the "always"
+// masks (thresholds of 2^32) and live the row's live spin bits.  RECORD adds
+// the row's anti-aligned bonds and up spins to anti / up (colour 1).
+template <int C, bool RECORD>
+__device__ __forceinline__ void row_apply(uint64_t* __restrict__ own, const uint64_t* __restrict__ other,
+                                          const Geom& g, int i, int w, uint64_t live, uint64_t m1, uint64_t m0,
+                                          uint64_t all0, uint64_t all1, uint32_t& anti, uint32_t& up)
+{
+    const uint32_t P = (uint32_t)g.P;
+    const uint32_t o = (uint32_t)i * P;
+    const uint64_t s = own[o + (uint32_t)w];
+    const uint64_t u = other[(uint32_t)wrap_row(i - 1, g.L) * P + (uint32_t)w];
+    const uint64_t d = other[(uint32_t)wrap_row(i + 1, g.L) * P + (uint32_t)w];
+    const uint64_t h0 = other[o + (uint32_t)w];
+    // horizontal neighbour at m - 1 ((i + C) even) or m + 1 (odd), as in sweep_rows
+    const bool left = ((i + C) & 1) == 0;
+    const int ws = left ? ((w > 0) ? w - 1 : g.W - 1) : ((w < g.W - 1) ? w + 1 : 0);
+    const int sh = (left ? (w > 0) : (w < g.W - 1)) ? 60 : 3 * (g.rlast - 1);
+    const uint64_t side = other[o + (uint32_t)ws];
+    const uint64_t h1 = left ? ((h0 << 3) | (side >> sh)) : ((h0 >> 3) | (side << sh));
+    const uint64_t x1 = s ^ u, x2 = s ^ d, x3 = s ^ h0, x4 = s ^ h1;
+    const uint64_t any = x1 | x2 | x3 | x4;
+    const uint64_t ge2 = (x1 & x2) | (x3 & x4) | ((x1 ^ x2) & (x3 ^ x4));
+    const uint64_t accept = ge2 | (any & (m1 | all1)) | (~any & (m0 | all0));
+    const uint64_t s_new = s ^ (accept & live);
+    own[o + (uint32_t)w] = s_new;
+    if (RECORD) {
+        anti += __popcll((s_new ^ u) & live) + __popcll((s_new ^ d) & live)
+              + __popcll((s_new ^ h0) & live) + __popcll((s_new ^ h1) & live);
+        up += __popcll(s_new & live) + __popcll(h0 & live);
+    }
+}
+
+// Apply the masks of an item of colour C: lane q of its group of F lanes
+// updates rows q, q + F, ... below 4 (one code path for all lanes, the row's
+// masks picked by selection).  RECORD adds the item's
 // anti-aligned bonds and up spins to anti / up (colour 1).
 template <int C, bool RECORD, int F>
 __device__ __forceinline__ void item_apply(uint64_t* __restrict__ own, const uint64_t* __restrict__ other,
@@ -367,48 +365,50 @@ __device__ __forceinline__ void item_apply(uint64_t* __restrict__ own, const uin
     const uint64_t live = live_mask(g, w);
     const uint64_t all0 = ((uint64_t)all0w << 32 | all0w) & live;
     const uint64_t all1 = ((uint64_t)all1w << 32 | all1w) & live;
-    const uint32_t P = (uint32_t)g.P;
 #pragma unroll
     for (int e0 = 0; e0 < 4; e0 += STEP) {
         const int e = e0 + q;
         if (e >= 4 || e >= g.L - row0) break;
         const uint64_t m1 = e == 0 ? a1[0] : (e == 1 ? a1[1] : (e == 2 ? a1[2] : a1[3]));
         const uint64_t m0 = e == 0 ? a0[0] : (e == 1 ? a0[1] : (e == 2 ? a0[2] : a0[3]));
-        const int i = row0 + e;
-        const uint32_t o = (uint32_t)i * P;
-        const uint64_t s = own[o + (uint32_t)w];
-        const uint64_t u = other[(uint32_t)wrap_row(i - 1, g.L) * P + (uint32_t)w];
-        const uint64_t d = other[(uint32_t)wrap_row(i + 1, g.L) * P + (uint32_t)w];
-        const uint64_t h0 = other[o + (uint32_t)w];
-        // horizontal neighbour at m - 1 ((i + C) even) or m + 1 (odd), as in sweep_rows
-        const bool left = ((e + C) & 1) == 0;                  // row0 is a multiple of 4
-        const int ws = left ? ((w > 0) ? w - 1 : g.W - 1) : ((w < g.W - 1) ? w + 1 : 0);
-        const int sh = (left ? (w > 0) : (w < g.W - 1)) ? 60 : 3 * (g.rlast - 1);
-        const uint64_t side = other[o + (uint32_t)ws];
-        const uint64_t h1 = left ? ((h0 << 3) | (side >> sh)) : ((h0 >> 3) | (side << sh));
-        const uint64_t x1 = s ^ u, x2 = s ^ d, x3 = s ^ h0, x4 = s ^ h1;
-        const uint64_t any = x1 | x2 | x3 | x4;
-        const uint64_t ge2 = (x1 & x2) | (x3 & x4) | ((x1 ^ x2) & (x3 ^ x4));
-        const uint64_t accept = ge2 | (any & (m1 | all1)) | (~any & (m0 | all0));
-        const uint64_t s_new = s ^ (accept & live);
-        own[o + (uint32_t)w] = s_new;
-        if (RECORD) {
-            anti += __popcll((s_new ^ u) & live) + __popcll((s_new ^ d) & live)
-                  + __popcll((s_new ^ h0) & live) + __popcll((s_new ^ h1) & live);
-            up += __popcll(s_new & live) + __popcll(h0 & live);
-        }
+        row_apply<C, RECORD>(own, other, g, row0 + e, w, live, m1, m0, all0, all1, anti, up);
     }
 }
 
-// Masks of an item with F lanes (F = 32: one warp).
+// All accept masks of one item drawn by one thread, with the draws and
+// accumulators of sweep_rows: a1[e] (r < thr1) and a0[e] (r < thr0) of row e
+// at the spin bits 3k of the word.
+template <int ROUNDS = 10>
+__device__ __forceinline__ void item_masks_thread(const Geom& g, int item, uint64_t t, int colour,
+                                                  const PhiloxKeys& rk, uint32_t thr0, uint32_t thr1, uint32_t one,
+                                                  uint64_t a1[4], uint64_t a0[4])
+{
+    const int grp = item / g.W;
+    const int w = item - grp * g.W;
+    AcceptBits acc;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc.a[e][q] = 0;
+    const uint32_t tl = (uint32_t)t;
+    const uint32_t th = ((uint32_t)(t >> 32) << 1) | (uint32_t)colour;
+    const PhiloxRowKey pk = philox_row_key((uint32_t)grp, tl, th, rk);
+    FieldLoop<0, ROUNDS>::run(pk, rk, (uint32_t)w * kFields, acc, thr0, thr1, one);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        a1[e] = (uint64_t)acc.a[e][2] << 32 | acc.a[e][0];
+        a0[e] = ((uint64_t)acc.a[e][3] << 32 | acc.a[e][1]) >> 1;
+    }
+}
+
+// Masks of an item with F lanes; an item past the end is drawn as item 0.
 template <int F, int ROUNDS = 10>
 __device__ __forceinline__ void item_masks(const Geom& g, int item, bool valid, int q, uint64_t t, int colour,
                                            const PhiloxKeys& rk, uint32_t thr0, uint32_t thr1, uint64_t a1[4],
                                            uint64_t a0[4])
 {
     if (!valid) item = 0;
-    if constexpr (F == 32) item_masks_warp<ROUNDS>(g, item, q, t, colour, rk, thr0, thr1, a1, a0);
-    else item_masks_lanes<F, ROUNDS>(g, item, q, t, colour, rk, thr0, thr1, a1, a0);
+    item_masks_lanes<F, ROUNDS>(g, item, q, t, colour, rk, thr0, thr1, a1, a0);
 }
 
 // Draw and apply in one step (the launch path's lanes kernel).

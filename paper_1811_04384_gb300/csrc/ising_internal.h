@@ -48,12 +48,24 @@ cudaError_t launch_set_sweep(uint64_t* t_base, uint64_t t, cudaStream_t s);
 // Philox4x32-10 of n counters (4 words each) under key `seed` (test hook).
 cudaError_t launch_philox_blocks(const uint32_t* ctr, uint32_t* out, int64_t n, uint64_t seed, cudaStream_t s);
 // The on-chip path: allow `bytes` of dynamic shared memory for its kernels
-// (once), then run n sweeps from sweep t0 with `lanes` lanes per item (32, 4,
-// 2; anything else: one thread per item) and E/M records every `every`-th
-// sweep as (E, M) pairs into rec; `bytes` = both colour arrays.
+// (once), then run n sweeps from sweep t0 with one thread per item and E/M
+// records every `every`-th sweep as (E, M) pairs into rec; `bytes` = both
+// colour arrays.
 cudaError_t allow_resident_smem(int bytes);
-cudaError_t launch_resident(int lanes, uint64_t* w0, uint64_t* w1, const Geom& g, const SweepArgs& a, uint64_t t0,
-                            int n, int every, long long* rec, size_t bytes, cudaStream_t s);
+cudaError_t launch_resident(uint64_t* w0, uint64_t* w1, const Geom& g, const SweepArgs& a, uint64_t t0, int n,
+                            int every, long long* rec, size_t bytes, cudaStream_t s);
+// The on-chip path with masks drawn beforehand: draw nhalf half-sweeps' masks
+// after sweep t0 (nhalf * items * 4 entries), then run sweeps s_base+1 ..
+// s_base+n of a run reading them (at most kPremaskedMaxItems items, one or
+// two rows per thread of one block; `bytes` = both colour arrays, and
+// allow_resident_smem(bytes) leaves room for 1024 record counters).
+constexpr int kPremaskedMaxItems = 512;
+inline int premasked_rows_per_thread(int items) { return items <= 256 ? 1 : 2; }
+cudaError_t launch_mask_draw(const Geom& g, const SweepArgs& a, uint64_t t0, int nhalf, ulonglong2* masks,
+                             cudaStream_t s);
+cudaError_t launch_resident_premasked(uint64_t* w0, uint64_t* w1, const Geom& g, const SweepArgs& a, int s_base,
+                                      int n, int every, const ulonglong2* masks, long long* rec, size_t bytes,
+                                      cudaStream_t s);
 
 // Launch `kernel` with programmatic stream serialization (the kernel calls
 // pdl_enter before its first read): the next launch's setup overlaps the end

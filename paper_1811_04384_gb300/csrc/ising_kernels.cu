@@ -187,66 +187,135 @@ resident_sweeps_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geo
     }
 }
 
-// The on-chip path for small lattices with F lanes per item (F = 32: one
-// warp per item; 2 or 4: item_masks_lanes): F times the threads of
-// resident_sweeps_kernel, each with 1/F of the Philox calls, so a lattice of
-// a few dozen items keeps all four schedulers of the SM busy instead of one
-// warp.  The accept masks of the next half-sweep are drawn while the current
-// one is applied (the draws do not depend on the spins), so the Philox work
-// fills the latency of the spin logic and the barriers.  One pass: the
-// block has a group of F lanes for every item (items * F <= 512).  Same
-// records and results as resident_sweeps_kernel.
-template <int F, int ROUNDS>
-__global__ void __launch_bounds__(512, 1)
-resident_group_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom g, SweepArgs a, uint64_t t0,
-                      int n, int every, long long* __restrict__ records)
+// Accept masks of the half-sweeps h = 0 .. nhalf-1 that follow sweep t0
+// (half-sweep h: sweep t0 + h/2 + 1, colour h & 1), one thread per (h, item),
+// drawn exactly as sweep_rows draws them: masks[(h * items + item) * 4 + e]
+// = (r < thr1 mask, r < thr0 mask) of row e of the item.  The draws depend on
+// the site, sweep and colour only, so a whole run's masks can be drawn at
+// once by every SM before the spins are updated.
+template <int ROUNDS>
+__global__ void __launch_bounds__(128)
+mask_draw_kernel(Geom g, SweepArgs a, uint64_t t0, int nhalf, ulonglong2* __restrict__ masks)
+{
+    const int items = ((g.L + 3) / 4) * g.W;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)nhalf * items) return;
+    const int h = (int)(k / items);
+    const int item = (int)(k - (long long)h * items);
+    uint64_t a1[4], a0[4];
+    item_masks_thread<ROUNDS>(g, item, t0 + (uint64_t)(h / 2) + 1, h & 1, a.rk, a.thr0, a.thr1, a.one, a1, a0);
+    ulonglong2* out = masks + (size_t)k * 4;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) out[e] = make_ulonglong2(a1[e], a0[e]);
+}
+
+// The on-chip path with the masks drawn beforehand (mask_draw_kernel): one
+// block holds the lattice in shared memory and runs sweeps s_base+1 ..
+// s_base+n of a run.  Thread x updates the rows (item, e) numbered 4 item + e
+// = x, x + blockDim.x, ... (R of them) in every half-sweep.  Their masks are
+// read from global memory two sweeps ahead, so a half-sweep's critical path
+// is the spin logic of R rows and one barrier; the Philox work ran
+// beforehand on all SMs.  Each warp adds its E/M counts of a recorded sweep
+// to shared memory with one atomic per count; the records of the run (after
+// its sweeps s with s % every == 0) are written at the end to
+// records[2 (s / every - 1) ..] as (E, M).  rec_first is the first record
+// of this launch and nrec their number; the dynamic shared memory holds both
+// colour arrays and 2 nrec counters.  Same results as resident_sweeps_kernel.
+template <int R>
+__global__ void __launch_bounds__(1024, 1)
+resident_premasked_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom g, SweepArgs a, int s_base,
+                          int n, int every, int rec_first, int nrec, const ulonglong2* __restrict__ masks,
+                          long long* __restrict__ records)
 {
     extern __shared__ __align__(16) uint64_t lattice[];
-    __shared__ unsigned int red_anti[32], red_up[32];
     const size_t words = (size_t)g.L * g.P;
     uint64_t* s0 = lattice;
     uint64_t* s1 = lattice + words;
+    unsigned int* rec_sm = reinterpret_cast<unsigned int*>(lattice + 2 * words);
     for (size_t k = threadIdx.x; k < words; k += blockDim.x) {
         s0[k] = w0[k];
         s1[k] = w1[k];
     }
+    for (int k = threadIdx.x; k < 2 * nrec; k += blockDim.x) rec_sm[k] = 0;
     __syncthreads();
     const int items = ((g.L + 3) / 4) * g.W;
-    const int item = (int)threadIdx.x / F, q = (int)threadIdx.x % F;
-    const bool valid = item < items;
-    const int nwarps = (int)blockDim.x / 32;
-    const int warp = (int)threadIdx.x / 32, lane = (int)threadIdx.x % 32;
-    const long long N = (long long)g.L * g.L;
-    uint64_t m1[4], m0[4], n1[4], n0[4];          // masks of the current / next half-sweep
-    item_masks<F, ROUNDS>(g, item, valid, q, t0 + 1, 0, a.rk, a.thr0, a.thr1, m1, m0);
-    for (int s = 1; s <= n; ++s) {
-        const uint64_t t = t0 + (uint64_t)s;
-        uint32_t dummy0 = 0, dummy1 = 0;
-        item_masks<F, ROUNDS>(g, item, valid, q, t, 1, a.rk, a.thr0, a.thr1, n1, n0);
-        item_apply<0, false, F>(s0, s1, g, item, valid, q, m1, m0, a.all0, a.all1, dummy0, dummy1);
-        __syncthreads();
-        const bool record = (s % every) == 0;
-        uint32_t anti = 0, up = 0;
-        item_masks<F, ROUNDS>(g, item, valid, q, t + 1, 0, a.rk, a.thr0, a.thr1, m1, m0);
-        if (record) item_apply<1, true, F>(s1, s0, g, item, valid, q, n1, n0, a.all0, a.all1, anti, up);
-        else item_apply<1, false, F>(s1, s0, g, item, valid, q, n1, n0, a.all0, a.all1, anti, up);
-        if (record) {
-            anti = __reduce_add_sync(0xffffffffu, anti);
-            up = __reduce_add_sync(0xffffffffu, up);
-            if (lane == 0) { red_anti[warp] = anti; red_up[warp] = up; }
-        }
-        __syncthreads();
-        if (record && warp == 0) {          // up to 16 warp sums, each below 2^31: fits 32 bits
-            const unsigned int sa = __reduce_add_sync(0xffffffffu, lane < nwarps ? red_anti[lane] : 0u);
-            const unsigned int su = __reduce_add_sync(0xffffffffu, lane < nwarps ? red_up[lane] : 0u);
-            if (lane == 0) {
-                const int rec = s / every - 1;
-                records[2 * rec] = 2 * (long long)sa - 2 * N;
-                records[2 * rec + 1] = 2 * (long long)su - N;
+    const size_t stride = (size_t)items * 4;             // masks of one half-sweep
+    const ulonglong2 zero = make_ulonglong2(0, 0);
+    int row[R], col[R];
+    bool valid[R];
+    uint64_t live[R], all0[R], all1[R];
+    // masks of sweep s (c0, c1) and s + 1 (n0, n1) of each row
+    ulonglong2 c0[R], c1[R], n0[R], n1[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int x = (int)threadIdx.x + r * (int)blockDim.x;
+        const int item = x >> 2, e = x & 3;
+        const int grp = item / g.W;
+        col[r] = item - grp * g.W;
+        row[r] = grp * 4 + e;
+        valid[r] = item < items && row[r] < g.L;
+        live[r] = valid[r] ? live_mask(g, col[r]) : 0;
+        all0[r] = ((uint64_t)a.all0 << 32 | a.all0) & live[r];
+        all1[r] = ((uint64_t)a.all1 << 32 | a.all1) & live[r];
+        c0[r] = c1[r] = n0[r] = n1[r] = zero;
+        if (valid[r]) {
+            const ulonglong2* mp = masks + x;
+            c0[r] = __ldg(mp);
+            c1[r] = __ldg(mp + stride);
+            if (n >= 2) {
+                n0[r] = __ldg(mp + 2 * stride);
+                n1[r] = __ldg(mp + 3 * stride);
             }
         }
     }
-    __syncthreads();
+    // the next recorded sweep of this launch and its slot in rec_sm
+    int next = every - s_base % every;
+    int slot = 0;
+    for (int s = 1; s <= n; ++s) {
+        ulonglong2 f0[R], f1[R];
+        uint32_t anti = 0, up = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            f0[r] = f1[r] = zero;
+            if (valid[r] && s + 2 <= n) {
+                const ulonglong2* mp = masks + (threadIdx.x + r * blockDim.x);
+                f0[r] = __ldg(mp + (size_t)(2 * s + 2) * stride);
+                f1[r] = __ldg(mp + (size_t)(2 * s + 3) * stride);
+            }
+            if (valid[r])
+                row_apply<0, false>(s0, s1, g, row[r], col[r], live[r], c0[r].x, c0[r].y, all0[r], all1[r], anti, up);
+        }
+        __syncthreads();
+        const bool record = s == next;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (valid[r]) {
+                if (record)
+                    row_apply<1, true>(s1, s0, g, row[r], col[r], live[r], c1[r].x, c1[r].y, all0[r], all1[r], anti,
+                                       up);
+                else
+                    row_apply<1, false>(s1, s0, g, row[r], col[r], live[r], c1[r].x, c1[r].y, all0[r], all1[r],
+                                        anti, up);
+            }
+            c0[r] = n0[r]; c1[r] = n1[r]; n0[r] = f0[r]; n1[r] = f1[r];
+        }
+        if (record) {
+            anti = __reduce_add_sync(0xffffffffu, anti);
+            up = __reduce_add_sync(0xffffffffu, up);
+            if ((threadIdx.x & 31) == 0) {
+                atomicAdd(rec_sm + 2 * slot, anti);
+                atomicAdd(rec_sm + 2 * slot + 1, up);
+            }
+            next += every;
+            ++slot;
+        }
+        __syncthreads();
+    }
+    const long long N = (long long)g.L * g.L;
+    for (int k = threadIdx.x; k < nrec; k += blockDim.x) {
+        records[2 * (rec_first + k)] = 2 * (long long)rec_sm[2 * k] - 2 * N;
+        records[2 * (rec_first + k) + 1] = 2 * (long long)rec_sm[2 * k + 1] - N;
+    }
     for (size_t k = threadIdx.x; k < words; k += blockDim.x) {
         w0[k] = s0[k];
         w1[k] = s1[k];
@@ -469,56 +538,57 @@ cudaError_t launch_philox_blocks(const uint32_t* ctr, uint32_t* out, int64_t n, 
     return cudaGetLastError();
 }
 
-namespace {
-
-template <int F>
-cudaError_t allow_group_smem(int bytes)
-{
-    cudaError_t e = cudaFuncSetAttribute(resident_group_kernel<F, 10>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(resident_group_kernel<F, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return e;
-}
-
-template <int F>
-void launch_group(uint64_t* w0, uint64_t* w1, const Geom& g, const SweepArgs& a, uint64_t t0, int n, int every,
-                  long long* rec, size_t bytes, cudaStream_t s)
-{
-    const int items = ((g.L + 3) / 4) * g.W;
-    const int threads = (items * F + 31) / 32 * 32;      // <= 416 by the lane rule of the caller
-    if (a.rounds == 7) resident_group_kernel<F, 7><<<1, threads, bytes, s>>>(w0, w1, g, a, t0, n, every, rec);
-    else resident_group_kernel<F, 10><<<1, threads, bytes, s>>>(w0, w1, g, a, t0, n, every, rec);
-}
-
-}  // namespace
-
 cudaError_t allow_resident_smem(int bytes)
 {
     cudaError_t e = cudaFuncSetAttribute(resident_sweeps_kernel<10>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(resident_sweeps_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = allow_group_smem<2>(bytes);
-    if (e == cudaSuccess) e = allow_group_smem<4>(bytes);
-    if (e == cudaSuccess) e = allow_group_smem<32>(bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(resident_premasked_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(resident_premasked_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     return e;
 }
 
-cudaError_t launch_resident(int lanes, uint64_t* w0, uint64_t* w1, const Geom& g, const SweepArgs& a, uint64_t t0,
-                            int n, int every, long long* rec, size_t bytes, cudaStream_t s)
+cudaError_t launch_resident(uint64_t* w0, uint64_t* w1, const Geom& g, const SweepArgs& a, uint64_t t0, int n,
+                            int every, long long* rec, size_t bytes, cudaStream_t s)
 {
-    switch (lanes) {
-    case 32: launch_group<32>(w0, w1, g, a, t0, n, every, rec, bytes, s); break;
-    case 4: launch_group<4>(w0, w1, g, a, t0, n, every, rec, bytes, s); break;
-    case 2: launch_group<2>(w0, w1, g, a, t0, n, every, rec, bytes, s); break;
-    default: {
-        const int items = ((g.L + 3) / 4) * g.W;
-        const int threads = std::min(256, std::max(32, (items + 31) / 32 * 32));
-        if (a.rounds == 7) resident_sweeps_kernel<7><<<1, threads, bytes, s>>>(w0, w1, g, a, t0, n, every, rec);
-        else resident_sweeps_kernel<10><<<1, threads, bytes, s>>>(w0, w1, g, a, t0, n, every, rec);
-    }
-    }
+    const int items = ((g.L + 3) / 4) * g.W;
+    const int threads = std::min(256, std::max(32, (items + 31) / 32 * 32));
+    if (a.rounds == 7) resident_sweeps_kernel<7><<<1, threads, bytes, s>>>(w0, w1, g, a, t0, n, every, rec);
+    else resident_sweeps_kernel<10><<<1, threads, bytes, s>>>(w0, w1, g, a, t0, n, every, rec);
+    return cudaGetLastError();
+}
+
+// Masks of nhalf half-sweeps following sweep t0 into `masks`
+// (nhalf * items * 4 entries).
+cudaError_t launch_mask_draw(const Geom& g, const SweepArgs& a, uint64_t t0, int nhalf, ulonglong2* masks,
+                             cudaStream_t s)
+{
+    const long long threads = (long long)nhalf * (((g.L + 3) / 4) * g.W);
+    const unsigned blocks = (unsigned)((threads + 127) / 128);
+    if (a.rounds == 7) mask_draw_kernel<7><<<blocks, 128, 0, s>>>(g, a, t0, nhalf, masks);
+    else mask_draw_kernel<10><<<blocks, 128, 0, s>>>(g, a, t0, nhalf, masks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resident_premasked(uint64_t* w0, uint64_t* w1, const Geom& g, const SweepArgs& a, int s_base,
+                                      int n, int every, const ulonglong2* masks, long long* rec, size_t bytes,
+                                      cudaStream_t s)
+{
+    const int items = ((g.L + 3) / 4) * g.W;
+    const int R = premasked_rows_per_thread(items);
+    const int threads = ((4 * items + R - 1) / R + 31) / 32 * 32;
+    const int rec_first = s_base / every;
+    const int nrec = (s_base + n) / every - rec_first;
+    const size_t smem = bytes + 2 * (size_t)nrec * sizeof(unsigned int);
+    if (R == 1)
+        resident_premasked_kernel<1><<<1, threads, smem, s>>>(w0, w1, g, a, s_base, n, every, rec_first, nrec, masks,
+                                                              rec);
+    else
+        resident_premasked_kernel<2><<<1, threads, smem, s>>>(w0, w1, g, a, s_base, n, every, rec_first, nrec, masks,
+                                                              rec);
     return cudaGetLastError();
 }
 

@@ -25,7 +25,7 @@ constexpr int kRecordsPerChunk = 1024;           // count slots resident on the 
 constexpr size_t kCountBytes = (size_t)kRecordsPerChunk * kCountSlots * 2 * sizeof(unsigned long long);
 constexpr size_t kAlign = 256;
 constexpr size_t kResidentMaxBytes = 220 * 1024;   // shared memory for the on-chip path
-constexpr int kResidentAutoMaxItems = 128;          // auto: on-chip up to 128 items (L <= 128); graph replays above
+constexpr int kResidentAutoMaxItems = kPremaskedMaxItems;   // auto: on-chip up to 512 items (L <= 292); launches above
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -64,6 +64,8 @@ struct ising_lattice {
     cudaGraphExec_t graph_rec = nullptr;         // record intervals of graph_rec_every sweeps, each recorded
     int graph_rec_every = 0;
     bool resident_attr = false;                  // dynamic shared memory attribute set
+    ulonglong2* masks = nullptr;                 // lazily allocated: pre-drawn masks of the on-chip path
+    size_t mask_bytes = 0;
 };
 
 static void drop_graphs(ising_lattice* h);
@@ -112,6 +114,7 @@ static void free_handle(ising_lattice* h)
     if (!h) return;
     if (h->staging) cudaFree(h->staging);
     if (h->staging2) cudaFree(h->staging2);
+    if (h->masks) cudaFree(h->masks);
     for (int b = 0; b < 2; ++b) {
         if (h->ev_copied[b]) cudaEventDestroy(h->ev_copied[b]);
         if (h->ev_packed[b]) cudaEventDestroy(h->ev_packed[b]);
@@ -444,23 +447,15 @@ static bool use_resident(const ising_lattice* h)
     return h->path == ISING_PATH_RESIDENT || ((h->g.L + 3) / 4) * h->g.W <= kResidentAutoMaxItems;
 }
 
-// Lanes per item of the on-chip path (0: one thread per item,
-// resident_sweeps_kernel), from a GB300 sweep of 1000 recorded sweeps at
-// L = 16 .. 256 over 1, 2, 4, 8 and 32 lanes: one warp per item up to 12
-// items (L <= 42), 4 lanes up to 100 items (L <= 126), 2 lanes up to 200
-// (L <= 168); above that the extra merge work outweighs the parallelism.
-// Every choice gives the same results.  At most 416 threads (launch bound 512).
-static int resident_lanes(const Geom& g)
-{
-    const int items = ((g.L + 3) / 4) * g.W;
-    if (items <= 12) return 32;
-    if (items <= 100) return 4;
-    if (items <= 200) return 2;
-    return 0;
-}
+// Pre-drawn masks of the on-chip path: 128 B per item and sweep, drawn for
+// at most this many bytes of sweeps at a time.
+constexpr size_t kMaskBufMax = 16u << 20;
 
 // n sweeps with the lattice resident in shared memory, E/M records (if any)
-// written as (E, M) pairs into the count buffer.
+// written as (E, M) pairs into the count buffer.  Up to kPremaskedMaxItems
+// items the accept masks are drawn first by all SMs (mask_draw_kernel), in
+// pieces of at most kMaskBufMax bytes, and the on-chip kernel only applies
+// them; larger lattices draw inside the on-chip kernel.
 static int run_resident(ising_lattice* h, int n, int every)
 {
     const Geom& g = h->g;
@@ -470,10 +465,35 @@ static int run_resident(ising_lattice* h, int n, int every)
         h->resident_attr = true;
     }
     const SweepArgs a = base_args(h);
-    cudaError_t e = launch_resident(resident_lanes(g), h->words[0], h->words[1], g, a, h->t, n, every,
-                                    reinterpret_cast<long long*>(h->counts), resident_bytes(g), h->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "resident sweeps kernel");
-    e = launch_advance_sweep(h->t_dev, (uint64_t)n, h->stream);
+    long long* rec = reinterpret_cast<long long*>(h->counts);
+    const int items = ((g.L + 3) / 4) * g.W;
+    if (items <= kPremaskedMaxItems) {
+        const size_t per_sweep = (size_t)items * 2 * 4 * sizeof(ulonglong2);
+        const int max_sweeps = (int)std::max<size_t>(1, kMaskBufMax / per_sweep);
+        const size_t need = (size_t)std::min(n, max_sweeps) * per_sweep;
+        if (h->mask_bytes < need) {
+            if (h->masks) cudaFree(h->masks);
+            h->masks = nullptr;
+            h->mask_bytes = 0;
+            cudaError_t e = cudaMalloc(&h->masks, need);
+            if (e != cudaSuccess) { h->masks = nullptr; cuda_fail(e, "cudaMalloc masks"); return ISING_ENOMEM; }
+            h->mask_bytes = need;
+        }
+        for (int done = 0; done < n;) {
+            const int part = std::min(n - done, max_sweeps);
+            cudaError_t e = launch_mask_draw(g, a, h->t + (uint64_t)done, 2 * part, h->masks, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "mask_draw_kernel");
+            e = launch_resident_premasked(h->words[0], h->words[1], g, a, done, part, every, h->masks, rec,
+                                          resident_bytes(g), h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "resident_premasked_kernel");
+            done += part;
+        }
+    } else {
+        cudaError_t e = launch_resident(h->words[0], h->words[1], g, a, h->t, n, every, rec, resident_bytes(g),
+                                        h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "resident sweeps kernel");
+    }
+    cudaError_t e = launch_advance_sweep(h->t_dev, (uint64_t)n, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "advance_sweep_kernel");
     h->t += (uint64_t)n;
     return ISING_OK;
@@ -546,7 +566,8 @@ extern "C" int ising_sweep_record(ising_lattice* h, int64_t n, int64_t every, in
     int64_t done_rec = 0;
     if (use_resident(h)) {
         while (done_rec < nrec) {
-            const int64_t chunk = std::min<int64_t>(nrec - done_rec, kRecordsPerChunk);
+            // at most 2^30 sweeps a launch
+            const int64_t chunk = std::min<int64_t>({nrec - done_rec, (int64_t)kRecordsPerChunk, (1 << 30) / every});
             int rc = run_resident(h, (int)(chunk * every), (int)every);
             if (rc != ISING_OK) return rc;
             const size_t bytes = (size_t)chunk * 2 * sizeof(long long);

@@ -27,11 +27,12 @@ def run(ising, L, seed, beta, n, every, path, hot=True):
         return E, M, lat.get_spins(), lat.t, lat.energy()
 
 
-# Lanes per item on the on-chip path (items = ceil(L/4) * W): a warp up to 12
-# items (L <= 42), 4 lanes up to 100 items (L = 44 .. 126), 2 lanes up to 200
-# (L = 128 .. 168), one thread per item above (L >= 170).
+# The on-chip forms by thread items (ceil(L/4) * W): masks drawn beforehand
+# with one row a thread up to 256 items (L <= 204), two rows a thread up to
+# 512 (L = 206 .. 292), the draws inside the on-chip kernel (one thread per
+# item) above (L >= 294).  W = 1 up to L = 42, so both wraps fall in one word.
 @pytest.mark.parametrize("L", [4, 6, 10, 42, 44, 46, 64, 66, 84, 86, 100, 126, 128, 130, 168, 170, 200,
-                               256, 300, 512, 700])
+                               204, 206, 256, 292, 294, 300, 512, 700])
 def test_resident_equals_launches(ising, L):
     beta = 0.3 + (L % 7) * 0.05
     a = run(ising, L, 40 + L, beta, 25, 3, ising.ISING_PATH_RESIDENT)
@@ -71,6 +72,17 @@ def test_resident_many_records_and_chunks(ising):
     b = run(ising, 32, 5, 0.44, 2600, 2, ising.ISING_PATH_LAUNCHES)
     for x, y in zip(a, b):
         np.testing.assert_array_equal(x, y)
+
+
+def test_resident_masks_drawn_in_pieces(ising):
+    # L = 292 (511 items): the 16 MB mask buffer holds 255 sweeps, so 600
+    # sweeps are drawn and applied in three pieces; records every 7 sweeps
+    # straddle the piece boundaries
+    a = run(ising, 292, 8, 0.43, 600, 7, ising.ISING_PATH_RESIDENT)
+    b = run(ising, 292, 8, 0.43, 600, 7, ising.ISING_PATH_LAUNCHES)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+    assert a[3] == 603
 
 
 def test_resident_rejects_lattices_that_do_not_fit(ising):
