@@ -376,12 +376,13 @@ __device__ __forceinline__ void item_apply(uint64_t* __restrict__ own, const uin
 }
 
 // All accept masks of one item drawn by one thread, with the draws and
-// accumulators of sweep_rows: a1[e] (r < thr1) and a0[e] (r < thr0) of row e
-// at the spin bits 3k of the word.
+// accumulators of sweep_rows, packed one word per row: packed[e] has r < thr1
+// of field k at bit 3k and r < thr0 at bit 3k + 1.  For row_apply, m1 =
+// packed and m0 = packed >> 1: their other bits fall on no spin bit.
 template <int ROUNDS = 10>
 __device__ __forceinline__ void item_masks_thread(const Geom& g, int item, uint64_t t, int colour,
                                                   const PhiloxKeys& rk, uint32_t thr0, uint32_t thr1, uint32_t one,
-                                                  uint64_t a1[4], uint64_t a0[4])
+                                                  uint64_t packed[4])
 {
     const int grp = item / g.W;
     const int w = item - grp * g.W;
@@ -395,10 +396,8 @@ __device__ __forceinline__ void item_masks_thread(const Geom& g, int item, uint6
     const PhiloxRowKey pk = philox_row_key((uint32_t)grp, tl, th, rk);
     FieldLoop<0, ROUNDS>::run(pk, rk, (uint32_t)w * kFields, acc, thr0, thr1, one);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        a1[e] = (uint64_t)acc.a[e][2] << 32 | acc.a[e][0];
-        a0[e] = ((uint64_t)acc.a[e][3] << 32 | acc.a[e][1]) >> 1;
-    }
+    for (int e = 0; e < 4; ++e)
+        packed[e] = (uint64_t)(acc.a[e][2] | acc.a[e][3]) << 32 | (acc.a[e][0] | acc.a[e][1]);
 }
 
 // Masks of an item with F lanes; an item past the end is drawn as item 0.

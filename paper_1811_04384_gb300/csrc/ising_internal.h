@@ -54,14 +54,14 @@ cudaError_t launch_philox_blocks(const uint32_t* ctr, uint32_t* out, int64_t n, 
 cudaError_t allow_resident_smem(int bytes);
 cudaError_t launch_resident(uint64_t* w0, uint64_t* w1, const Geom& g, const SweepArgs& a, uint64_t t0, int n,
                             int every, long long* rec, size_t bytes, cudaStream_t s);
-// The on-chip path with masks drawn beforehand: draw nhalf half-sweeps' masks
-// after sweep t0 (nhalf * items * 4 entries), then run sweeps s_base+1 ..
+// The on-chip path with masks drawn beforehand: draw the masks of the nsweeps
+// sweeps after sweep t0 (nsweeps * items * 4 entries), then run sweeps s_base+1 ..
 // s_base+n of a run reading them (at most kPremaskedMaxItems items, one or
 // two rows per thread of one block; `bytes` = both colour arrays, and
 // allow_resident_smem(bytes) leaves room for 1024 record counters).
 constexpr int kPremaskedMaxItems = 512;
 inline int premasked_rows_per_thread(int items) { return items <= 256 ? 1 : 2; }
-cudaError_t launch_mask_draw(const Geom& g, const SweepArgs& a, uint64_t t0, int nhalf, ulonglong2* masks,
+cudaError_t launch_mask_draw(const Geom& g, const SweepArgs& a, uint64_t t0, int nsweeps, ulonglong2* masks,
                              cudaStream_t s);
 cudaError_t launch_resident_premasked(uint64_t* w0, uint64_t* w1, const Geom& g, const SweepArgs& a, int s_base,
                                       int n, int every, const ulonglong2* masks, long long* rec, size_t bytes,

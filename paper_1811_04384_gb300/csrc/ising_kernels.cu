@@ -187,33 +187,36 @@ resident_sweeps_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geo
     }
 }
 
-// Accept masks of the half-sweeps h = 0 .. nhalf-1 that follow sweep t0
-// (half-sweep h: sweep t0 + h/2 + 1, colour h & 1), one thread per (h, item),
-// drawn exactly as sweep_rows draws them: masks[(h * items + item) * 4 + e]
-// = (r < thr1 mask, r < thr0 mask) of row e of the item.  The draws depend on
-// the site, sweep and colour only, so a whole run's masks can be drawn at
-// once by every SM before the spins are updated.
+// Accept masks of the sweeps j = 0 .. nsweeps-1 that follow sweep t0 (sweep
+// t0 + j + 1), one thread per (j, item), drawn exactly as sweep_rows draws
+// them: masks[(j * items + item) * 4 + e] = (colour-0, colour-1 packed masks)
+// of row e of the item (item_masks_thread).  The draws depend on the site,
+// sweep and colour only, so a whole run's masks can be drawn at once by every
+// SM before the spins are updated.
 template <int ROUNDS>
 __global__ void __launch_bounds__(128)
-mask_draw_kernel(Geom g, SweepArgs a, uint64_t t0, int nhalf, ulonglong2* __restrict__ masks)
+mask_draw_kernel(Geom g, SweepArgs a, uint64_t t0, int nsweeps, ulonglong2* __restrict__ masks)
 {
     const int items = ((g.L + 3) / 4) * g.W;
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (long long)nhalf * items) return;
-    const int h = (int)(k / items);
-    const int item = (int)(k - (long long)h * items);
-    uint64_t a1[4], a0[4];
-    item_masks_thread<ROUNDS>(g, item, t0 + (uint64_t)(h / 2) + 1, h & 1, a.rk, a.thr0, a.thr1, a.one, a1, a0);
+    if (k >= (long long)nsweeps * items) return;
+    const int j = (int)(k / items);
+    const int item = (int)(k - (long long)j * items);
+    uint64_t p0[4], p1[4];
+    const uint64_t t = t0 + (uint64_t)j + 1;
+    item_masks_thread<ROUNDS>(g, item, t, 0, a.rk, a.thr0, a.thr1, a.one, p0);
+    item_masks_thread<ROUNDS>(g, item, t, 1, a.rk, a.thr0, a.thr1, a.one, p1);
     ulonglong2* out = masks + (size_t)k * 4;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) out[e] = make_ulonglong2(a1[e], a0[e]);
+    for (int e = 0; e < 4; ++e) out[e] = make_ulonglong2(p0[e], p1[e]);
 }
 
 // The on-chip path with the masks drawn beforehand (mask_draw_kernel): one
 // block holds the lattice in shared memory and runs sweeps s_base+1 ..
 // s_base+n of a run.  Thread x updates the rows (item, e) numbered 4 item + e
-// = x, x + blockDim.x, ... (R of them) in every half-sweep.  Their masks are
-// read from global memory two sweeps ahead, so a half-sweep's critical path
+// = x, x + blockDim.x, ... (R of them) in every half-sweep.  Their masks (one
+// 16-byte load per row and sweep) are read from global memory two sweeps
+// ahead, so a half-sweep's critical path
 // is the spin logic of R rows and one barrier; the Philox work ran
 // beforehand on all SMs.  Each warp adds its E/M counts of a recorded sweep
 // to shared memory with one atomic per count; the records of the run (after
@@ -239,13 +242,13 @@ resident_premasked_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, 
     for (int k = threadIdx.x; k < 2 * nrec; k += blockDim.x) rec_sm[k] = 0;
     __syncthreads();
     const int items = ((g.L + 3) / 4) * g.W;
-    const size_t stride = (size_t)items * 4;             // masks of one half-sweep
+    const size_t stride = (size_t)items * 4;             // masks of one sweep
     const ulonglong2 zero = make_ulonglong2(0, 0);
     int row[R], col[R];
     bool valid[R];
     uint64_t live[R], all0[R], all1[R];
-    // masks of sweep s (c0, c1) and s + 1 (n0, n1) of each row
-    ulonglong2 c0[R], c1[R], n0[R], n1[R];
+    // packed masks (colour 0, colour 1) of sweep s (c) and s + 1 (nx) of each row
+    ulonglong2 c[R], nx[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int x = (int)threadIdx.x + r * (int)blockDim.x;
@@ -257,33 +260,26 @@ resident_premasked_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, 
         live[r] = valid[r] ? live_mask(g, col[r]) : 0;
         all0[r] = ((uint64_t)a.all0 << 32 | a.all0) & live[r];
         all1[r] = ((uint64_t)a.all1 << 32 | a.all1) & live[r];
-        c0[r] = c1[r] = n0[r] = n1[r] = zero;
+        c[r] = nx[r] = zero;
         if (valid[r]) {
-            const ulonglong2* mp = masks + x;
-            c0[r] = __ldg(mp);
-            c1[r] = __ldg(mp + stride);
-            if (n >= 2) {
-                n0[r] = __ldg(mp + 2 * stride);
-                n1[r] = __ldg(mp + 3 * stride);
-            }
+            c[r] = __ldg(masks + x);
+            if (n >= 2) nx[r] = __ldg(masks + stride + x);
         }
     }
     // the next recorded sweep of this launch and its slot in rec_sm
     int next = every - s_base % every;
     int slot = 0;
     for (int s = 1; s <= n; ++s) {
-        ulonglong2 f0[R], f1[R];
+        ulonglong2 f[R];
         uint32_t anti = 0, up = 0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            f0[r] = f1[r] = zero;
-            if (valid[r] && s + 2 <= n) {
-                const ulonglong2* mp = masks + (threadIdx.x + r * blockDim.x);
-                f0[r] = __ldg(mp + (size_t)(2 * s + 2) * stride);
-                f1[r] = __ldg(mp + (size_t)(2 * s + 3) * stride);
-            }
+            f[r] = zero;
+            if (valid[r] && s + 2 <= n)
+                f[r] = __ldg(masks + (size_t)(s + 1) * stride + (threadIdx.x + r * blockDim.x));
             if (valid[r])
-                row_apply<0, false>(s0, s1, g, row[r], col[r], live[r], c0[r].x, c0[r].y, all0[r], all1[r], anti, up);
+                row_apply<0, false>(s0, s1, g, row[r], col[r], live[r], c[r].x, c[r].x >> 1, all0[r], all1[r], anti,
+                                    up);
         }
         __syncthreads();
         const bool record = s == next;
@@ -291,13 +287,14 @@ resident_premasked_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, 
         for (int r = 0; r < R; ++r) {
             if (valid[r]) {
                 if (record)
-                    row_apply<1, true>(s1, s0, g, row[r], col[r], live[r], c1[r].x, c1[r].y, all0[r], all1[r], anti,
-                                       up);
+                    row_apply<1, true>(s1, s0, g, row[r], col[r], live[r], c[r].y, c[r].y >> 1, all0[r], all1[r],
+                                       anti, up);
                 else
-                    row_apply<1, false>(s1, s0, g, row[r], col[r], live[r], c1[r].x, c1[r].y, all0[r], all1[r],
+                    row_apply<1, false>(s1, s0, g, row[r], col[r], live[r], c[r].y, c[r].y >> 1, all0[r], all1[r],
                                         anti, up);
             }
-            c0[r] = n0[r]; c1[r] = n1[r]; n0[r] = f0[r]; n1[r] = f1[r];
+            c[r] = nx[r];
+            nx[r] = f[r];
         }
         if (record) {
             anti = __reduce_add_sync(0xffffffffu, anti);
@@ -561,15 +558,15 @@ cudaError_t launch_resident(uint64_t* w0, uint64_t* w1, const Geom& g, const Swe
     return cudaGetLastError();
 }
 
-// Masks of nhalf half-sweeps following sweep t0 into `masks`
-// (nhalf * items * 4 entries).
-cudaError_t launch_mask_draw(const Geom& g, const SweepArgs& a, uint64_t t0, int nhalf, ulonglong2* masks,
+// Masks of the nsweeps sweeps following sweep t0 into `masks`
+// (nsweeps * items * 4 entries).
+cudaError_t launch_mask_draw(const Geom& g, const SweepArgs& a, uint64_t t0, int nsweeps, ulonglong2* masks,
                              cudaStream_t s)
 {
-    const long long threads = (long long)nhalf * (((g.L + 3) / 4) * g.W);
+    const long long threads = (long long)nsweeps * (((g.L + 3) / 4) * g.W);
     const unsigned blocks = (unsigned)((threads + 127) / 128);
-    if (a.rounds == 7) mask_draw_kernel<7><<<blocks, 128, 0, s>>>(g, a, t0, nhalf, masks);
-    else mask_draw_kernel<10><<<blocks, 128, 0, s>>>(g, a, t0, nhalf, masks);
+    if (a.rounds == 7) mask_draw_kernel<7><<<blocks, 128, 0, s>>>(g, a, t0, nsweeps, masks);
+    else mask_draw_kernel<10><<<blocks, 128, 0, s>>>(g, a, t0, nsweeps, masks);
     return cudaGetLastError();
 }
 

@@ -447,7 +447,7 @@ static bool use_resident(const ising_lattice* h)
     return h->path == ISING_PATH_RESIDENT || ((h->g.L + 3) / 4) * h->g.W <= kResidentAutoMaxItems;
 }
 
-// Pre-drawn masks of the on-chip path: 128 B per item and sweep, drawn for
+// Pre-drawn masks of the on-chip path: 64 B per item and sweep, drawn for
 // at most this many bytes of sweeps at a time.
 constexpr size_t kMaskBufMax = 16u << 20;
 
@@ -468,7 +468,7 @@ static int run_resident(ising_lattice* h, int n, int every)
     long long* rec = reinterpret_cast<long long*>(h->counts);
     const int items = ((g.L + 3) / 4) * g.W;
     if (items <= kPremaskedMaxItems) {
-        const size_t per_sweep = (size_t)items * 2 * 4 * sizeof(ulonglong2);
+        const size_t per_sweep = (size_t)items * 4 * sizeof(ulonglong2);
         const int max_sweeps = (int)std::max<size_t>(1, kMaskBufMax / per_sweep);
         const size_t need = (size_t)std::min(n, max_sweeps) * per_sweep;
         if (h->mask_bytes < need) {
@@ -481,7 +481,7 @@ static int run_resident(ising_lattice* h, int n, int every)
         }
         for (int done = 0; done < n;) {
             const int part = std::min(n - done, max_sweeps);
-            cudaError_t e = launch_mask_draw(g, a, h->t + (uint64_t)done, 2 * part, h->masks, h->stream);
+            cudaError_t e = launch_mask_draw(g, a, h->t + (uint64_t)done, part, h->masks, h->stream);
             if (e != cudaSuccess) return cuda_fail(e, "mask_draw_kernel");
             e = launch_resident_premasked(h->words[0], h->words[1], g, a, done, part, every, h->masks, rec,
                                           resident_bytes(g), h->stream);
