@@ -55,14 +55,19 @@ cudaError_t allow_resident_smem(int bytes);
 cudaError_t launch_resident(uint64_t* w0, uint64_t* w1, const Geom& g, const SweepArgs& a, uint64_t t0, int n,
                             int every, long long* rec, size_t bytes, cudaStream_t s);
 // The on-chip path with masks drawn beforehand: draw the masks of the nsweeps
-// sweeps after sweep t0 (nsweeps * items * 4 entries), then run sweeps s_base+1 ..
+// sweeps after sweep (t_base ? *t_base : 0) + t0 (nsweeps * items * 4
+// entries), then run sweeps s_base+1 ..
 // s_base+n of a run reading them (at most kPremaskedMaxItems items, one or
 // two rows per thread of one block; `bytes` = both colour arrays, and
 // allow_resident_smem(bytes) leaves room for 1024 record counters).
 constexpr int kPremaskedMaxItems = 512;
 inline int premasked_rows_per_thread(int items) { return items <= 256 ? 1 : 2; }
-cudaError_t launch_mask_draw(const Geom& g, const SweepArgs& a, uint64_t t0, int nsweeps, ulonglong2* masks,
-                             cudaStream_t s);
+cudaError_t launch_mask_draw(const Geom& g, const SweepArgs& a, const uint64_t* t_base, uint64_t t0, int nsweeps,
+                             ulonglong2* masks, cudaStream_t s);
+// One half-sweep that applies masks drawn by launch_mask_draw (`masks`: the
+// entries of its sweep), one thread per row.
+cudaError_t launch_half_sweep_apply(int colour, bool record, uint64_t* own, const uint64_t* other, const Geom& g,
+                                    const SweepArgs& a, const ulonglong2* masks, cudaStream_t s);
 cudaError_t launch_resident_premasked(uint64_t* w0, uint64_t* w1, const Geom& g, const SweepArgs& a, int s_base,
                                       int n, int every, const ulonglong2* masks, long long* rec, size_t bytes,
                                       cudaStream_t s);

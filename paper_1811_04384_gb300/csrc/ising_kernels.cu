@@ -193,9 +193,11 @@ resident_sweeps_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geo
 // of row e of the item (item_masks_thread).  The draws depend on the site,
 // sweep and colour only, so a whole run's masks can be drawn at once by every
 // SM before the spins are updated.
+// t_base (device memory, or null) is added to t0: a graph that is replayed
+// draws for the sweeps after the device sweep counter.
 template <int ROUNDS>
 __global__ void __launch_bounds__(128)
-mask_draw_kernel(Geom g, SweepArgs a, uint64_t t0, int nsweeps, ulonglong2* __restrict__ masks)
+mask_draw_kernel(Geom g, SweepArgs a, const uint64_t* t_base, uint64_t t0, int nsweeps, ulonglong2* __restrict__ masks)
 {
     const int items = ((g.L + 3) / 4) * g.W;
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -203,7 +205,7 @@ mask_draw_kernel(Geom g, SweepArgs a, uint64_t t0, int nsweeps, ulonglong2* __re
     const int j = (int)(k / items);
     const int item = (int)(k - (long long)j * items);
     uint64_t p0[4], p1[4];
-    const uint64_t t = t0 + (uint64_t)j + 1;
+    const uint64_t t = (t_base ? *t_base : 0) + t0 + (uint64_t)j + 1;
     item_masks_thread<ROUNDS>(g, item, t, 0, a.rk, a.thr0, a.thr1, a.one, p0);
     item_masks_thread<ROUNDS>(g, item, t, 1, a.rk, a.thr0, a.thr1, a.one, p1);
     ulonglong2* out = masks + (size_t)k * 4;
@@ -317,6 +319,45 @@ resident_premasked_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, 
         w0[k] = s0[k];
         w1[k] = s1[k];
     }
+}
+
+// One half-sweep of colour C over all SMs with the masks drawn beforehand
+// (mask_draw_kernel): thread k updates row k & 3 of item k >> 2 with the
+// packed masks masks[k] (.x colour 0, .y colour 1), so a launch is short:
+// no Philox work, one row of spin logic per thread.  Same results as
+// half_sweep_kernel.
+template <int C, bool RECORD>
+__global__ void __launch_bounds__(128)
+half_sweep_apply_kernel(uint64_t* __restrict__ own, const uint64_t* __restrict__ other, Geom g, SweepArgs a,
+                        const ulonglong2* __restrict__ masks)
+{
+    pdl_enter();
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int items = ((g.L + 3) / 4) * g.W;
+    const int item = (int)(k >> 2), e = (int)(k & 3);
+    const int grp = item / g.W;
+    const int w = item - grp * g.W;
+    const int i = grp * 4 + e;
+    uint32_t anti = 0, up = 0;
+    if (item < items && i < g.L) {
+        const uint64_t live = live_mask(g, w);
+        const uint64_t all0 = ((uint64_t)a.all0 << 32 | a.all0) & live;
+        const uint64_t all1 = ((uint64_t)a.all1 << 32 | a.all1) & live;
+        const uint64_t p = C == 0 ? __ldg(&masks[k].x) : __ldg(&masks[k].y);
+        row_apply<C, RECORD>(own, other, g, i, w, live, p, p >> 1, all0, all1, anti, up);
+    }
+    if (RECORD) block_add_counts(record_counts(a) + 2 * (blockIdx.x % kCountSlots), anti, up);
+}
+
+cudaError_t launch_half_sweep_apply(int colour, bool record, uint64_t* own, const uint64_t* other, const Geom& g,
+                                    const SweepArgs& a, const ulonglong2* masks, cudaStream_t s)
+{
+    const uint32_t threads = (uint32_t)(((g.L + 3) / 4) * g.W) * 4;
+    const dim3 block(128), grid((threads + 127) / 128);
+    if (colour == 0) launch_pdl(half_sweep_apply_kernel<0, false>, grid, block, s, own, other, g, a, masks);
+    else if (record) launch_pdl(half_sweep_apply_kernel<1, true>, grid, block, s, own, other, g, a, masks);
+    else launch_pdl(half_sweep_apply_kernel<1, false>, grid, block, s, own, other, g, a, masks);
+    return cudaGetLastError();
 }
 
 // One half-sweep of colour C over all SMs with F lanes per thread item
@@ -558,15 +599,15 @@ cudaError_t launch_resident(uint64_t* w0, uint64_t* w1, const Geom& g, const Swe
     return cudaGetLastError();
 }
 
-// Masks of the nsweeps sweeps following sweep t0 into `masks`
-// (nsweeps * items * 4 entries).
-cudaError_t launch_mask_draw(const Geom& g, const SweepArgs& a, uint64_t t0, int nsweeps, ulonglong2* masks,
-                             cudaStream_t s)
+// Masks of the nsweeps sweeps following sweep (t_base ? *t_base : 0) + t0
+// into `masks` (nsweeps * items * 4 entries).
+cudaError_t launch_mask_draw(const Geom& g, const SweepArgs& a, const uint64_t* t_base, uint64_t t0, int nsweeps,
+                             ulonglong2* masks, cudaStream_t s)
 {
     const long long threads = (long long)nsweeps * (((g.L + 3) / 4) * g.W);
     const unsigned blocks = (unsigned)((threads + 127) / 128);
-    if (a.rounds == 7) mask_draw_kernel<7><<<blocks, 128, 0, s>>>(g, a, t0, nsweeps, masks);
-    else mask_draw_kernel<10><<<blocks, 128, 0, s>>>(g, a, t0, nsweeps, masks);
+    if (a.rounds == 7) mask_draw_kernel<7><<<blocks, 128, 0, s>>>(g, a, t_base, t0, nsweeps, masks);
+    else mask_draw_kernel<10><<<blocks, 128, 0, s>>>(g, a, t_base, t0, nsweeps, masks);
     return cudaGetLastError();
 }
 

@@ -66,6 +66,7 @@ struct ising_lattice {
     bool resident_attr = false;                  // dynamic shared memory attribute set
     ulonglong2* masks = nullptr;                 // lazily allocated: pre-drawn masks of the on-chip path
     size_t mask_bytes = 0;
+    ulonglong2* graph_masks = nullptr;           // masks of kDrawSweeps sweeps, drawn inside the graphs
 };
 
 static void drop_graphs(ising_lattice* h);
@@ -115,6 +116,7 @@ static void free_handle(ising_lattice* h)
     if (h->staging) cudaFree(h->staging);
     if (h->staging2) cudaFree(h->staging2);
     if (h->masks) cudaFree(h->masks);
+    if (h->graph_masks) cudaFree(h->graph_masks);
     for (int b = 0; b < 2; ++b) {
         if (h->ev_copied[b]) cudaEventDestroy(h->ev_copied[b]);
         if (h->ev_packed[b]) cudaEventDestroy(h->ev_packed[b]);
@@ -304,12 +306,17 @@ static cudaError_t launch_hs(const ising_lattice* h, int colour, bool update, bo
 // graph_rec holds max(1, kGraphSweeps / every) record intervals of `every`
 // sweeps, each recording into count slots offset by the device record index
 // (advanced by the graph itself, so one graph serves every record of a
-// chunk).  The kernels' launch operands
-// (thresholds, Philox rounds, launch shape) are baked into the graphs, so
-// every call that changes them drops the graphs.
+// chunk).  In the row-packed layout a graph first draws the accept masks of
+// kDrawSweeps sweeps at a time on all SMs (mask_draw_kernel, from the device
+// sweep counter), and its half-sweeps only apply them
+// (half_sweep_apply_kernel): at these sizes one thread per item leaves most
+// SMs idle while each runs its 21 Philox calls in a row.  The kernels'
+// launch operands (thresholds, Philox rounds, launch shape) are baked into
+// the graphs, so every call that changes them drops the graphs.
 constexpr int kGraphSweeps = 32;
 constexpr int kGraphMaxEvery = 64;
 constexpr int kGraphMaxItems = 32768;
+constexpr int kDrawSweeps = 16;
 
 static bool use_graphs(const ising_lattice* h)
 {
@@ -335,6 +342,12 @@ static int capture_sweeps(ising_lattice* h, int n, int every, cudaGraphExec_t* o
     cudaError_t e = cudaSuccess;
     if (!h->capture_stream) e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) { h->capture_stream = nullptr; return cuda_fail(e, "capture stream"); }
+    const size_t stride = (size_t)(((h->g.L + 3) / 4) * h->g.W) * 4;      // mask entries of one sweep
+    if (h->layout == ISING_LAYOUT_ROW_PACKED && !h->graph_masks) {
+        e = cudaMalloc(&h->graph_masks, kDrawSweeps * stride * sizeof(ulonglong2));
+        if (e != cudaSuccess) { h->graph_masks = nullptr; cuda_fail(e, "cudaMalloc graph masks"); return ISING_ENOMEM; }
+    }
+    const bool draw_first = h->layout == ISING_LAYOUT_ROW_PACKED;
     SweepArgs a = base_args(h);
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
@@ -344,13 +357,26 @@ static int capture_sweeps(ising_lattice* h, int n, int every, cudaGraphExec_t* o
         a.t_off = (uint32_t)s;
         a.counts = nullptr;
         a.rec_base = nullptr;
-        le = launch_hs_on(h, h->capture_stream, 0, true, false, a);
+        const ulonglong2* m = draw_first ? h->graph_masks + (size_t)((s - 1) % kDrawSweeps) * stride : nullptr;
+        if (draw_first) {
+            // sweeps s .. s + kDrawSweeps - 1 past the device counter
+            if ((s - 1) % kDrawSweeps == 0)
+                le = launch_mask_draw(h->g, a, h->t_dev, (uint64_t)(s - 1), std::min(kDrawSweeps, n - s + 1),
+                                      h->graph_masks, h->capture_stream);
+            if (le == cudaSuccess)
+                le = launch_half_sweep_apply(0, false, h->words[0], h->words[1], h->g, a, m, h->capture_stream);
+        } else {
+            le = launch_hs_on(h, h->capture_stream, 0, true, false, a);
+        }
         const bool rec = every > 0 && s % every == 0;
         if (rec) {
             a.counts = h->counts + (size_t)(s / every - 1) * kCountSlots * 2;
             a.rec_base = rec_index(h);
         }
-        if (le == cudaSuccess) le = launch_hs_on(h, h->capture_stream, 1, true, rec, a);
+        if (le == cudaSuccess) {
+            le = draw_first ? launch_half_sweep_apply(1, rec, h->words[1], h->words[0], h->g, a, m, h->capture_stream)
+                            : launch_hs_on(h, h->capture_stream, 1, true, rec, a);
+        }
     }
     if (le == cudaSuccess) {
         le = launch_advance_graph(h->t_dev, (uint64_t)n, rec_index(h), every > 0 ? (uint32_t)(n / every) : 0u,
@@ -481,7 +507,7 @@ static int run_resident(ising_lattice* h, int n, int every)
         }
         for (int done = 0; done < n;) {
             const int part = std::min(n - done, max_sweeps);
-            cudaError_t e = launch_mask_draw(g, a, h->t + (uint64_t)done, part, h->masks, h->stream);
+            cudaError_t e = launch_mask_draw(g, a, nullptr, h->t + (uint64_t)done, part, h->masks, h->stream);
             if (e != cudaSuccess) return cuda_fail(e, "mask_draw_kernel");
             e = launch_resident_premasked(h->words[0], h->words[1], g, a, done, part, every, h->masks, rec,
                                           resident_bytes(g), h->stream);
