@@ -66,7 +66,9 @@ struct ising_lattice {
     bool resident_attr = false;                  // dynamic shared memory attribute set
     ulonglong2* masks = nullptr;                 // lazily allocated: pre-drawn masks of the on-chip path
     size_t mask_bytes = 0;
-    ulonglong2* graph_masks = nullptr;           // masks of kDrawSweeps sweeps, drawn inside the graphs
+    ulonglong2* graph_masks = nullptr;           // two buffers of kDrawSweeps sweeps' masks, drawn inside the graphs
+    cudaStream_t draw_stream = nullptr;          // the graphs' mask draws are captured here, beside the half-sweeps
+    cudaEvent_t fork_ev = nullptr, draw_ev[8] = {}, apply_ev[8] = {};
 };
 
 static void drop_graphs(ising_lattice* h);
@@ -125,6 +127,10 @@ static void free_handle(ising_lattice* h)
     if (h->graph_plain) cudaGraphExecDestroy(h->graph_plain);
     if (h->graph_rec) cudaGraphExecDestroy(h->graph_rec);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    if (h->draw_stream) cudaStreamDestroy(h->draw_stream);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    for (cudaEvent_t ev : h->draw_ev) if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : h->apply_ev) if (ev) cudaEventDestroy(ev);
     if (h->owns_mem && h->base) cudaFree(h->base);
     if (h->host_counts) cudaFreeHost(h->host_counts);
     delete h;
@@ -306,17 +312,21 @@ static cudaError_t launch_hs(const ising_lattice* h, int colour, bool update, bo
 // graph_rec holds max(1, kGraphSweeps / every) record intervals of `every`
 // sweeps, each recording into count slots offset by the device record index
 // (advanced by the graph itself, so one graph serves every record of a
-// chunk).  In the row-packed layout a graph first draws the accept masks of
+// chunk).  In the row-packed layout a graph draws the accept masks of
 // kDrawSweeps sweeps at a time on all SMs (mask_draw_kernel, from the device
 // sweep counter), and its half-sweeps only apply them
 // (half_sweep_apply_kernel): at these sizes one thread per item leaves most
-// SMs idle while each runs its 21 Philox calls in a row.  The kernels'
-// launch operands (thresholds, Philox rounds, launch shape) are baked into
-// the graphs, so every call that changes them drops the graphs.
+// SMs idle while each runs its 21 Philox calls in a row.  The draws run on a
+// second branch of the graph, one piece ahead, into two alternating buffers:
+// piece k + 1 is drawn while piece k is applied, and a piece is drawn into a
+// buffer only after the half-sweeps of the piece before have read it.  The
+// kernels' launch operands (thresholds, Philox rounds, launch shape) are
+// baked into the graphs, so every call that changes them drops the graphs.
 constexpr int kGraphSweeps = 32;
 constexpr int kGraphMaxEvery = 64;
 constexpr int kGraphMaxItems = 32768;
-constexpr int kDrawSweeps = 16;
+constexpr int kDrawSweeps = 8;
+constexpr int kMaxPieces = 8;          // a graph holds at most kGraphMaxEvery sweeps
 
 static bool use_graphs(const ising_lattice* h)
 {
@@ -342,47 +352,77 @@ static int capture_sweeps(ising_lattice* h, int n, int every, cudaGraphExec_t* o
     cudaError_t e = cudaSuccess;
     if (!h->capture_stream) e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) { h->capture_stream = nullptr; return cuda_fail(e, "capture stream"); }
-    const size_t stride = (size_t)(((h->g.L + 3) / 4) * h->g.W) * 4;      // mask entries of one sweep
-    if (h->layout == ISING_LAYOUT_ROW_PACKED && !h->graph_masks) {
-        e = cudaMalloc(&h->graph_masks, kDrawSweeps * stride * sizeof(ulonglong2));
-        if (e != cudaSuccess) { h->graph_masks = nullptr; cuda_fail(e, "cudaMalloc graph masks"); return ISING_ENOMEM; }
-    }
     const bool draw_first = h->layout == ISING_LAYOUT_ROW_PACKED;
+    const size_t stride = (size_t)(((h->g.L + 3) / 4) * h->g.W) * 4;      // mask entries of one sweep
+    if (draw_first) {
+        if (!h->graph_masks) {
+            e = cudaMalloc(&h->graph_masks, 2 * kDrawSweeps * stride * sizeof(ulonglong2));
+            if (e != cudaSuccess) { h->graph_masks = nullptr; cuda_fail(e, "cudaMalloc graph masks"); return ISING_ENOMEM; }
+        }
+        if (!h->draw_stream) e = cudaStreamCreateWithFlags(&h->draw_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { h->draw_stream = nullptr; return cuda_fail(e, "draw stream"); }
+        if (!h->fork_ev) e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming);
+        for (int k = 0; k < kMaxPieces && e == cudaSuccess; ++k) {
+            if (!h->draw_ev[k]) e = cudaEventCreateWithFlags(&h->draw_ev[k], cudaEventDisableTiming);
+            if (e == cudaSuccess && !h->apply_ev[k]) e = cudaEventCreateWithFlags(&h->apply_ev[k], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "graph events");
+    }
     SweepArgs a = base_args(h);
+    cudaStream_t A = h->capture_stream;
     cudaGraph_t graph = nullptr;
-    e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
+    e = cudaStreamBeginCapture(A, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     cudaError_t le = cudaSuccess;
-    for (int s = 1; s <= n && le == cudaSuccess; ++s) {
+    // the half-sweeps of sweep s (relative to the device counter); masks: its
+    // entries in the mask buffers, or null for the fused kernels
+    auto sweep = [&](int s, const ulonglong2* m) {
         a.t_off = (uint32_t)s;
         a.counts = nullptr;
         a.rec_base = nullptr;
-        const ulonglong2* m = draw_first ? h->graph_masks + (size_t)((s - 1) % kDrawSweeps) * stride : nullptr;
-        if (draw_first) {
-            // sweeps s .. s + kDrawSweeps - 1 past the device counter
-            if ((s - 1) % kDrawSweeps == 0)
-                le = launch_mask_draw(h->g, a, h->t_dev, (uint64_t)(s - 1), std::min(kDrawSweeps, n - s + 1),
-                                      h->graph_masks, h->capture_stream);
-            if (le == cudaSuccess)
-                le = launch_half_sweep_apply(0, false, h->words[0], h->words[1], h->g, a, m, h->capture_stream);
-        } else {
-            le = launch_hs_on(h, h->capture_stream, 0, true, false, a);
-        }
+        cudaError_t r = m ? launch_half_sweep_apply(0, false, h->words[0], h->words[1], h->g, a, m, A)
+                          : launch_hs_on(h, A, 0, true, false, a);
         const bool rec = every > 0 && s % every == 0;
         if (rec) {
             a.counts = h->counts + (size_t)(s / every - 1) * kCountSlots * 2;
             a.rec_base = rec_index(h);
         }
-        if (le == cudaSuccess) {
-            le = draw_first ? launch_half_sweep_apply(1, rec, h->words[1], h->words[0], h->g, a, m, h->capture_stream)
-                            : launch_hs_on(h, h->capture_stream, 1, true, rec, a);
+        if (r == cudaSuccess)
+            r = m ? launch_half_sweep_apply(1, rec, h->words[1], h->words[0], h->g, a, m, A)
+                  : launch_hs_on(h, A, 1, true, rec, a);
+        return r;
+    };
+    if (draw_first) {
+        cudaStream_t B = h->draw_stream;
+        const int np = (n + kDrawSweeps - 1) / kDrawSweeps;      // <= kMaxPieces
+        auto draw = [&](int k) {       // piece k: sweeps k D + 1 .. into buffer k & 1
+            const int first = k * kDrawSweeps;
+            cudaError_t r = launch_mask_draw(h->g, a, h->t_dev, (uint64_t)first, std::min(kDrawSweeps, n - first),
+                                             h->graph_masks + (size_t)(k & 1) * kDrawSweeps * stride, B);
+            if (r == cudaSuccess) r = cudaEventRecord(h->draw_ev[k], B);
+            return r;
+        };
+        le = cudaEventRecord(h->fork_ev, A);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(B, h->fork_ev, 0);
+        if (le == cudaSuccess) le = draw(0);
+        for (int k = 0; k < np && le == cudaSuccess; ++k) {
+            if (k + 1 < np) {
+                if (k >= 1) le = cudaStreamWaitEvent(B, h->apply_ev[k - 1], 0);    // buffer (k + 1) & 1 is read
+                if (le == cudaSuccess) le = draw(k + 1);
+            }
+            if (le == cudaSuccess) le = cudaStreamWaitEvent(A, h->draw_ev[k], 0);
+            const ulonglong2* buf = h->graph_masks + (size_t)(k & 1) * kDrawSweeps * stride;
+            for (int s = k * kDrawSweeps + 1; s <= std::min(n, (k + 1) * kDrawSweeps) && le == cudaSuccess; ++s)
+                le = sweep(s, buf + (size_t)(s - 1 - k * kDrawSweeps) * stride);
+            if (le == cudaSuccess) le = cudaEventRecord(h->apply_ev[k], A);
         }
+    } else {
+        for (int s = 1; s <= n && le == cudaSuccess; ++s) le = sweep(s, nullptr);
     }
     if (le == cudaSuccess) {
-        le = launch_advance_graph(h->t_dev, (uint64_t)n, rec_index(h), every > 0 ? (uint32_t)(n / every) : 0u,
-                                  h->capture_stream);
+        le = launch_advance_graph(h->t_dev, (uint64_t)n, rec_index(h), every > 0 ? (uint32_t)(n / every) : 0u, A);
     }
-    e = cudaStreamEndCapture(h->capture_stream, &graph);
+    e = cudaStreamEndCapture(A, &graph);
     if (le != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(le, "sweep graph capture"); }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
     e = cudaGraphInstantiate(out, graph, 0);

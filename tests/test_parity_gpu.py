@@ -310,6 +310,54 @@ def test_graph_replays_equal_on_chip_path(ising, L):
     assert ta == tb == 70 + 70 + 130 + 100 + 66 + 33
 
 
+@pytest.mark.parametrize("beta", [0.0, 1e-18, BETA_TC, 6.0, math.inf])
+def test_graphs_drawing_masks_first_at_threshold_limits(ising, beta):
+    """Graph replays, which draw the masks of 16 sweeps at a time and then
+    apply them, at the threshold limits: 2^32 (beta = 0: every site flips),
+    just below 2^32, 0 (beta >= 5.55: only dE <= 0 flips).  70 sweeps span two
+    32-sweep graphs, the 16-sweep draw pieces and a plain remainder."""
+    L, seed = 300, 12
+    with ising.Lattice(L, seed) as lat:
+        lat.set_path(ising.ISING_PATH_LAUNCHES)
+        lat.init_hot()
+        lat.set_beta(beta)
+        E, M = lat.sweep_record(70, 1)
+        lat.sweep(70)
+        S = lat.get_spins()
+    s = oracle.init_hot(L, seed)
+    Eo, Mo = oracle.run(s, seed, beta, 0, 70, 1)
+    oracle.run(s, seed, beta, 70, 70, 70)
+    np.testing.assert_array_equal(E, Eo)
+    np.testing.assert_array_equal(M, Mo)
+    np.testing.assert_array_equal(S, s)
+
+
+@pytest.mark.parametrize("L", [300, 1026])
+def test_graphs_drawing_masks_first_keep_dead_fields_zero(ising, L):
+    """Canary for the apply-only half-sweeps of the graphs: after graph
+    replays at beta = 0 and at T_c the dead fields, bit 63 and the pitch
+    padding of both colour arrays are still zero, and at beta = 0 every
+    sweep negates every spin."""
+    with ising.Lattice(L, 3) as lat:
+        lat.set_path(ising.ISING_PATH_LAUNCHES)
+        lat.init_hot()
+        W, P, r = lat.layout()
+        live_last = sum(1 << (3 * k) for k in range(r))
+        s0 = lat.get_spins()
+        lat.set_beta(0.0)
+        E, M = lat.sweep_record(64, 1)
+        assert (E == E[0]).all()
+        assert (M[::2] == -M[1::2]).all() and M[1] == int(s0.sum())
+        np.testing.assert_array_equal(lat.get_spins(), s0)
+        for beta in (0.0, BETA_TC):
+            lat.set_beta(beta)
+            lat.sweep(64)
+            w = lat.get_words()
+            assert ((w[:, :, W - 1] & ~np.uint64(live_last)) == 0).all()
+            assert ((w[:, :, :W - 1] & ~np.uint64(0x1249249249249249)) == 0).all()
+            assert (w[:, :, W:] == 0).all()
+
+
 def test_graph_replays_match_oracle(ising):
     L, seed, beta = 1026, 6, 0.44
     with ising.Lattice(L, seed) as lat:
