@@ -126,16 +126,16 @@ int ising_get_thresholds(ising_lattice *h, uint64_t host_thr[2]);
 /* Run n >= 0 full sweeps t+1 .. t+n (t += n).  A sweep is the paper's Monte
  * Carlo iteration (Sec. 2: every spin proposed once), in checkerboard order:
  * all colour-0 sites, then all colour-1 sites.  Asynchronous on the stream
- * (the first call on the on-chip path allocates its mask buffer).
- * Errors: EINVAL (NULL, n < 0), ENOMEM (that buffer), ECUDA. */
+ * (the first call on the on-chip path or with graph replays allocates its
+ * mask buffer).  Errors: EINVAL (NULL, n < 0), ENOMEM (that buffer), ECUDA. */
 int ising_sweep(ising_lattice *h, int64_t n);
 
 /* Run n sweeps and record E and M after sweeps t+every, t+2*every, ...:
  * host_E and host_M (caller-owned host arrays) receive n / every entries
  * each; either may be NULL.  n >= 0, 1 <= every <= 2^22.  Synchronises the stream.
  * The counts come from the reduction fused into the colour-1 half-sweep.
- * Errors: EINVAL (NULL, n < 0, every out of range), ENOMEM (the on-chip
- * path's mask buffer), ECUDA. */
+ * Errors: EINVAL (NULL, n < 0, every out of range), ENOMEM (the mask
+ * buffer of the on-chip path or of the graph replays), ECUDA. */
 int ising_sweep_record(ising_lattice *h, int64_t n, int64_t every,
                        int64_t *host_E, int64_t *host_M);
 
@@ -219,7 +219,10 @@ int ising_set_item_lanes(ising_lattice *h, int32_t lanes);
  * captured once into CUDA graphs and replayed (recaptured after
  * ising_set_beta, ising_set_rng, ising_set_tiling, ising_set_item_lanes; a
  * device record index picks the count slots of each replay), because there
- * a half-sweep runs about as long as the host takes to launch it.
+ * a half-sweep runs about as long as the host takes to launch it.  In the
+ * row-packed layout these graphs draw the accept masks of 8 sweeps at a time
+ * on all SMs, into two buffers the library allocates on first use (128 B per
+ * thread item, at most 33.5 MB), and their half-sweeps only apply them.
  * ISING_PATH_RESIDENT: temporal
  * blocking with the whole lattice on chip -- one block copies both colour
  * arrays into shared memory and runs all requested sweeps there in one
