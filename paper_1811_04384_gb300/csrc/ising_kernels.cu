@@ -192,9 +192,9 @@ resident_sweeps_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geo
 // them: masks[(j * items + item) * 4 + e] = (colour-0, colour-1 packed masks)
 // of row e of the item (item_masks_thread).  The draws depend on the site,
 // sweep and colour only, so a whole run's masks can be drawn at once by every
-// SM before the spins are updated.
-// t_base (device memory, or null) is added to t0: a graph that is replayed
-// draws for the sweeps after the device sweep counter.
+// SM before the spins are updated.  t_base (device memory, or null) is added
+// to t0: a graph that is replayed draws for the sweeps after the device sweep
+// counter.
 template <int ROUNDS>
 __global__ void __launch_bounds__(128)
 mask_draw_kernel(Geom g, SweepArgs a, const uint64_t* t_base, uint64_t t0, int nsweeps, ulonglong2* __restrict__ masks)
@@ -218,14 +218,14 @@ mask_draw_kernel(Geom g, SweepArgs a, const uint64_t* t_base, uint64_t t0, int n
 // s_base+n of a run.  Thread x updates the rows (item, e) numbered 4 item + e
 // = x, x + blockDim.x, ... (R of them) in every half-sweep.  Their masks (one
 // 16-byte load per row and sweep) are read from global memory two sweeps
-// ahead, so a half-sweep's critical path
-// is the spin logic of R rows and one barrier; the Philox work ran
-// beforehand on all SMs.  Each warp adds its E/M counts of a recorded sweep
-// to shared memory with one atomic per count; the records of the run (after
-// its sweeps s with s % every == 0) are written at the end to
-// records[2 (s / every - 1) ..] as (E, M).  rec_first is the first record
-// of this launch and nrec their number; the dynamic shared memory holds both
-// colour arrays and 2 nrec counters.  Same results as resident_sweeps_kernel.
+// ahead, so a half-sweep's critical path is the spin logic of R rows and one
+// barrier; the Philox work ran beforehand on all SMs.  Each warp adds its
+// E/M counts of a recorded sweep to shared memory with one atomic per count;
+// the records of the run (after its sweeps s with s % every == 0) are
+// written at the end to records[2 (s / every - 1) ..] as (E, M).  rec_first
+// is the first record of this launch and nrec their number; the dynamic
+// shared memory holds both colour arrays and 2 nrec counters.  Same results
+// as resident_sweeps_kernel.
 template <int R>
 __global__ void __launch_bounds__(1024, 1)
 resident_premasked_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom g, SweepArgs a, int s_base,
