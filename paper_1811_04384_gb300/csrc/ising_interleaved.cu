@@ -76,15 +76,59 @@ __global__ void ci_unpack_kernel(const uint64_t* __restrict__ S, int L, int N, i
         s[(size_t)(I + k * N) * L + J] = ((word >> (3 * k)) & 1ull) ? (int8_t)1 : (int8_t)-1;
 }
 
+// Accept masks of the words of thread (m, q) of ci_half_sweep_kernel for
+// sweep t, colour C: Philox call k (counter (q + kN/4, m, t, C)) gives the
+// draws of field k of the four words.  packed[e] holds r < thr1 of field k
+// at bit 3k and r < thr0 at bit 3k + 1.
+template <int ROUNDS>
+__device__ __forceinline__ void ci_masks(int N, int q, int m, uint64_t t, int C, const SweepArgs& a,
+                                         uint64_t packed[4])
+{
+    const uint32_t tl = (uint32_t)t;
+    const uint32_t th = ((uint32_t)(t >> 32) << 1) | (uint32_t)C;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) packed[e] = 0;
+    for (int k = 0; k < 21; ++k) {
+        const PhiloxRowKey pk = philox_row_key((uint32_t)(q + k * (N / 4)), tl, th, a.rk);
+        uint32_t r[4];
+        philox_row<ROUNDS>(pk, a.rk, (uint32_t)m, r);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            packed[e] |= (uint64_t)(r[e] < a.thr1) << (3 * k) | (uint64_t)(r[e] < a.thr0) << (3 * k + 1);
+    }
+}
+
+// The masks of ci_half_sweep_kernel for the sweeps j = 0 .. nsweeps-1 after
+// sweep (t_base ? *t_base : 0) + t0, drawn ahead on all SMs: one thread per
+// (j, colour, q, m), masks[(((j * 2 + colour) * N/4 + q) * L/2 + m) * 4 + e]
+// = packed masks of word row 4q + e.
+template <int ROUNDS>
+__global__ void __launch_bounds__(128)
+ci_mask_draw_kernel(int L, int N, SweepArgs a, const uint64_t* t_base, uint64_t t0, int nsweeps,
+                    uint64_t* __restrict__ masks)
+{
+    const long long Q = N / 4, M = L / 2;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)nsweeps * 2 * Q * M) return;
+    const int m = (int)(k % M);
+    const int q = (int)((k / M) % Q);
+    const int colour = (int)((k / (M * Q)) & 1);
+    const int j = (int)(k / (2 * M * Q));
+    uint64_t packed[4];
+    ci_masks<ROUNDS>(N, q, m, (t_base ? *t_base : 0) + t0 + (uint64_t)j + 1, colour, a, packed);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) masks[(size_t)k * 4 + e] = packed[e];
+}
+
 // One half-sweep of colour C.  Thread (m, q) owns word rows 4q .. 4q+3 and the
 // column pair 2m, 2m+1; in each row it updates the colour-C word
-// J_e = 2m + ((I_e + C) & 1).  Philox call k (counter (q + kN/4, m, t, C))
-// gives the draws of field k of the four words.  RECORD (colour 1) also
-// counts the anti-aligned bonds of the four colour-1 words and the up spins
-// of all eight words of the block.
-template <int C, bool UPDATE, bool RECORD, int ROUNDS>
+// J_e = 2m + ((I_e + C) & 1).  Its accept masks come from ci_masks, or with
+// PRE from `masks` (this sweep and colour's block of ci_mask_draw_kernel).
+// RECORD (colour 1) also counts the anti-aligned bonds of the four colour-1
+// words and the up spins of all eight words of the block.
+template <int C, bool UPDATE, bool RECORD, int ROUNDS, bool PRE = false>
 __global__ void __launch_bounds__(128)
-ci_half_sweep_kernel(uint64_t* __restrict__ S, int L, int N, SweepArgs a)
+ci_half_sweep_kernel(uint64_t* __restrict__ S, int L, int N, SweepArgs a, const uint64_t* __restrict__ masks)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int q = blockIdx.y * blockDim.y + threadIdx.y;
@@ -106,20 +150,21 @@ ci_half_sweep_kernel(uint64_t* __restrict__ S, int L, int N, SweepArgs a)
             xu[e] = I == 0 ? rotate_up(__ldg(S + (size_t)(N - 1) * L + J[e])) : __ldg(S + (size_t)(I - 1) * L + J[e]);
             xd[e] = I == N - 1 ? rotate_down(__ldg(S + J[e])) : __ldg(S + (size_t)(I + 1) * L + J[e]);
         }
+        // c1: r < thr1 at the spin bits; c0 >> 1 of the same word: r < thr0 there
+        // (its other bits fall on no spin bit and are masked below)
         uint64_t c0[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0};
         if (UPDATE) {
-            const uint64_t t = *a.t_base + a.t_off;
-            const uint32_t tl = (uint32_t)t;
-            const uint32_t th = ((uint32_t)(t >> 32) << 1) | (uint32_t)C;
-            for (int k = 0; k < 21; ++k) {
-                const PhiloxRowKey pk = philox_row_key((uint32_t)(q + k * (N / 4)), tl, th, a.rk);
-                uint32_t r[4];
-                philox_row<ROUNDS>(pk, a.rk, (uint32_t)m, r);
+            uint64_t packed[4];
+            if (PRE) {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    c0[e] |= (uint64_t)(r[e] < a.thr0) << (3 * k);
-                    c1[e] |= (uint64_t)(r[e] < a.thr1) << (3 * k);
-                }
+                for (int e = 0; e < 4; ++e) packed[e] = __ldg(masks + ((size_t)q * (L / 2) + m) * 4 + e);
+            } else {
+                ci_masks<ROUNDS>(N, q, m, *a.t_base + a.t_off, C, a, packed);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                c1[e] = packed[e];
+                c0[e] = packed[e] >> 1;
             }
         }
         const uint64_t all0 = ((uint64_t)a.all0 << 32 | a.all0) & kAllFields;
@@ -192,13 +237,13 @@ static void ci_launch_r(dim3 grid, dim3 block, int colour, bool update, bool rec
                         const SweepArgs& a, cudaStream_t s)
 {
     if (colour == 0) {
-        if (record) ci_half_sweep_kernel<0, true, true, ROUNDS><<<grid, block, 0, s>>>(S, L, N, a);
-        else ci_half_sweep_kernel<0, true, false, ROUNDS><<<grid, block, 0, s>>>(S, L, N, a);
+        if (record) ci_half_sweep_kernel<0, true, true, ROUNDS><<<grid, block, 0, s>>>(S, L, N, a, nullptr);
+        else ci_half_sweep_kernel<0, true, false, ROUNDS><<<grid, block, 0, s>>>(S, L, N, a, nullptr);
     } else if (!update) {
-        ci_half_sweep_kernel<1, false, true, 10><<<grid, block, 0, s>>>(S, L, N, a);
+        ci_half_sweep_kernel<1, false, true, 10><<<grid, block, 0, s>>>(S, L, N, a, nullptr);
     } else {
-        if (record) ci_half_sweep_kernel<1, true, true, ROUNDS><<<grid, block, 0, s>>>(S, L, N, a);
-        else ci_half_sweep_kernel<1, true, false, ROUNDS><<<grid, block, 0, s>>>(S, L, N, a);
+        if (record) ci_half_sweep_kernel<1, true, true, ROUNDS><<<grid, block, 0, s>>>(S, L, N, a, nullptr);
+        else ci_half_sweep_kernel<1, true, false, ROUNDS><<<grid, block, 0, s>>>(S, L, N, a, nullptr);
     }
 }
 
@@ -210,6 +255,32 @@ cudaError_t ci_half_sweep(int colour, bool update, bool record, uint64_t* S, int
     dim3 grid((L / 2 + 31) / 32, (N / 4 + 3) / 4);
     if (a.rounds == 7) ci_launch_r<7>(grid, block, colour, update, record, S, L, N, a, s);
     else ci_launch_r<10>(grid, block, colour, update, record, S, L, N, a, s);
+    return cudaGetLastError();
+}
+
+size_t ci_mask_bytes_per_sweep(int L) { return (size_t)8 * (L / 21) * L; }
+
+cudaError_t ci_mask_draw(int L, const SweepArgs& a, const uint64_t* t_base, uint64_t t0, int nsweeps,
+                         uint64_t* masks, cudaStream_t s)
+{
+    const int N = L / 21;
+    const long long threads = (long long)nsweeps * 2 * (N / 4) * (L / 2);
+    const unsigned blocks = (unsigned)((threads + 127) / 128);
+    if (a.rounds == 7) ci_mask_draw_kernel<7><<<blocks, 128, 0, s>>>(L, N, a, t_base, t0, nsweeps, masks);
+    else ci_mask_draw_kernel<10><<<blocks, 128, 0, s>>>(L, N, a, t_base, t0, nsweeps, masks);
+    return cudaGetLastError();
+}
+
+cudaError_t ci_half_sweep_pre(int colour, bool record, uint64_t* S, int L, const SweepArgs& a,
+                              const uint64_t* sweep_masks, cudaStream_t s)
+{
+    const int N = L / 21;
+    dim3 block(32, 4);
+    dim3 grid((L / 2 + 31) / 32, (N / 4 + 3) / 4);
+    const uint64_t* m = sweep_masks + (size_t)colour * (N / 4) * (L / 2) * 4;
+    if (colour == 0) ci_half_sweep_kernel<0, true, false, 10, true><<<grid, block, 0, s>>>(S, L, N, a, m);
+    else if (record) ci_half_sweep_kernel<1, true, true, 10, true><<<grid, block, 0, s>>>(S, L, N, a, m);
+    else ci_half_sweep_kernel<1, true, false, 10, true><<<grid, block, 0, s>>>(S, L, N, a, m);
     return cudaGetLastError();
 }
 

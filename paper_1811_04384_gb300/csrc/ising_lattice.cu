@@ -312,11 +312,12 @@ static cudaError_t launch_hs(const ising_lattice* h, int colour, bool update, bo
 // graph_rec holds max(1, kGraphSweeps / every) record intervals of `every`
 // sweeps, each recording into count slots offset by the device record index
 // (advanced by the graph itself, so one graph serves every record of a
-// chunk).  In the row-packed layout a graph draws the accept masks of
-// kDrawSweeps sweeps at a time on all SMs (mask_draw_kernel, from the device
-// sweep counter), and its half-sweeps only apply them
-// (half_sweep_apply_kernel): at these sizes one thread per item leaves most
-// SMs idle while each runs its 21 Philox calls in a row.  The draws run on a
+// chunk).  A graph draws the accept masks of kDrawSweeps sweeps at a time on
+// all SMs (mask_draw_kernel, or ci_mask_draw in the column-interleaved
+// layout, from the device sweep counter), and its half-sweeps only apply
+// them (half_sweep_apply_kernel, ci_half_sweep_pre): at these sizes one
+// thread per item leaves most SMs idle while each runs its 21 Philox calls
+// in a row.  The draws run on a
 // second branch of the graph, one piece ahead, into two alternating buffers:
 // piece k + 1 is drawn while piece k is applied, and a piece is drawn into a
 // buffer only after the half-sweeps of the piece before have read it.  The
@@ -352,72 +353,74 @@ static int capture_sweeps(ising_lattice* h, int n, int every, cudaGraphExec_t* o
     cudaError_t e = cudaSuccess;
     if (!h->capture_stream) e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) { h->capture_stream = nullptr; return cuda_fail(e, "capture stream"); }
-    const bool draw_first = h->layout == ISING_LAYOUT_ROW_PACKED;
-    const size_t stride = (size_t)(((h->g.L + 3) / 4) * h->g.W) * 4;      // mask entries of one sweep
-    if (draw_first) {
-        if (!h->graph_masks) {
-            e = cudaMalloc(&h->graph_masks, 2 * kDrawSweeps * stride * sizeof(ulonglong2));
-            if (e != cudaSuccess) { h->graph_masks = nullptr; cuda_fail(e, "cudaMalloc graph masks"); return ISING_ENOMEM; }
-        }
-        if (!h->draw_stream) e = cudaStreamCreateWithFlags(&h->draw_stream, cudaStreamNonBlocking);
-        if (e != cudaSuccess) { h->draw_stream = nullptr; return cuda_fail(e, "draw stream"); }
-        if (!h->fork_ev) e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming);
-        for (int k = 0; k < kMaxPieces && e == cudaSuccess; ++k) {
-            if (!h->draw_ev[k]) e = cudaEventCreateWithFlags(&h->draw_ev[k], cudaEventDisableTiming);
-            if (e == cudaSuccess && !h->apply_ev[k]) e = cudaEventCreateWithFlags(&h->apply_ev[k], cudaEventDisableTiming);
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "graph events");
+    const bool ci = h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED;
+    const size_t sweep_bytes = ci ? ci_mask_bytes_per_sweep(h->g.L)
+                                  : (size_t)(((h->g.L + 3) / 4) * h->g.W) * 4 * sizeof(ulonglong2);
+    if (!h->graph_masks) {
+        e = cudaMalloc(&h->graph_masks, 2 * kDrawSweeps * sweep_bytes);
+        if (e != cudaSuccess) { h->graph_masks = nullptr; cuda_fail(e, "cudaMalloc graph masks"); return ISING_ENOMEM; }
     }
+    if (!h->draw_stream) e = cudaStreamCreateWithFlags(&h->draw_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { h->draw_stream = nullptr; return cuda_fail(e, "draw stream"); }
+    if (!h->fork_ev) e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming);
+    for (int k = 0; k < kMaxPieces && e == cudaSuccess; ++k) {
+        if (!h->draw_ev[k]) e = cudaEventCreateWithFlags(&h->draw_ev[k], cudaEventDisableTiming);
+        if (e == cudaSuccess && !h->apply_ev[k]) e = cudaEventCreateWithFlags(&h->apply_ev[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "graph events");
     SweepArgs a = base_args(h);
     cudaStream_t A = h->capture_stream;
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(A, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     cudaError_t le = cudaSuccess;
-    // the half-sweeps of sweep s (relative to the device counter); masks: its
-    // entries in the mask buffers, or null for the fused kernels
-    auto sweep = [&](int s, const ulonglong2* m) {
+    char* const buffers = reinterpret_cast<char*>(h->graph_masks);
+    // one half-sweep of sweep s from its masks m (this sweep's block in a mask buffer)
+    auto half = [&](int colour, bool rec, const char* m) {
+        if (ci) return ci_half_sweep_pre(colour, rec, h->words[0], h->g.L, a, reinterpret_cast<const uint64_t*>(m), A);
+        return launch_half_sweep_apply(colour, rec, h->words[colour], h->words[1 - colour], h->g, a,
+                                       reinterpret_cast<const ulonglong2*>(m), A);
+    };
+    // the half-sweeps of sweep s (relative to the device counter)
+    auto sweep = [&](int s, const char* m) {
         a.t_off = (uint32_t)s;
         a.counts = nullptr;
         a.rec_base = nullptr;
-        cudaError_t r = m ? launch_half_sweep_apply(0, false, h->words[0], h->words[1], h->g, a, m, A)
-                          : launch_hs_on(h, A, 0, true, false, a);
+        cudaError_t r = half(0, false, m);
         const bool rec = every > 0 && s % every == 0;
         if (rec) {
             a.counts = h->counts + (size_t)(s / every - 1) * kCountSlots * 2;
             a.rec_base = rec_index(h);
         }
-        if (r == cudaSuccess)
-            r = m ? launch_half_sweep_apply(1, rec, h->words[1], h->words[0], h->g, a, m, A)
-                  : launch_hs_on(h, A, 1, true, rec, a);
+        if (r == cudaSuccess) r = half(1, rec, m);
         return r;
     };
-    if (draw_first) {
-        cudaStream_t B = h->draw_stream;
-        const int np = (n + kDrawSweeps - 1) / kDrawSweeps;      // <= kMaxPieces
-        auto draw = [&](int k) {       // piece k: sweeps k D + 1 .. into buffer k & 1
-            const int first = k * kDrawSweeps;
-            cudaError_t r = launch_mask_draw(h->g, a, h->t_dev, (uint64_t)first, std::min(kDrawSweeps, n - first),
-                                             h->graph_masks + (size_t)(k & 1) * kDrawSweeps * stride, B);
-            if (r == cudaSuccess) r = cudaEventRecord(h->draw_ev[k], B);
-            return r;
-        };
-        le = cudaEventRecord(h->fork_ev, A);
-        if (le == cudaSuccess) le = cudaStreamWaitEvent(B, h->fork_ev, 0);
-        if (le == cudaSuccess) le = draw(0);
-        for (int k = 0; k < np && le == cudaSuccess; ++k) {
-            if (k + 1 < np) {
-                if (k >= 1) le = cudaStreamWaitEvent(B, h->apply_ev[k - 1], 0);    // buffer (k + 1) & 1 is read
-                if (le == cudaSuccess) le = draw(k + 1);
-            }
-            if (le == cudaSuccess) le = cudaStreamWaitEvent(A, h->draw_ev[k], 0);
-            const ulonglong2* buf = h->graph_masks + (size_t)(k & 1) * kDrawSweeps * stride;
-            for (int s = k * kDrawSweeps + 1; s <= std::min(n, (k + 1) * kDrawSweeps) && le == cudaSuccess; ++s)
-                le = sweep(s, buf + (size_t)(s - 1 - k * kDrawSweeps) * stride);
-            if (le == cudaSuccess) le = cudaEventRecord(h->apply_ev[k], A);
+    cudaStream_t B = h->draw_stream;
+    const int np = (n + kDrawSweeps - 1) / kDrawSweeps;      // <= kMaxPieces
+    auto draw = [&](int k) {       // piece k: sweeps k D + 1 .. into buffer k & 1
+        const int first = k * kDrawSweeps;
+        const int count = std::min(kDrawSweeps, n - first);
+        char* buf = buffers + (size_t)(k & 1) * kDrawSweeps * sweep_bytes;
+        cudaError_t r = ci ? ci_mask_draw(h->g.L, a, h->t_dev, (uint64_t)first, count,
+                                          reinterpret_cast<uint64_t*>(buf), B)
+                           : launch_mask_draw(h->g, a, h->t_dev, (uint64_t)first, count,
+                                              reinterpret_cast<ulonglong2*>(buf), B);
+        if (r == cudaSuccess) r = cudaEventRecord(h->draw_ev[k], B);
+        return r;
+    };
+    le = cudaEventRecord(h->fork_ev, A);
+    if (le == cudaSuccess) le = cudaStreamWaitEvent(B, h->fork_ev, 0);
+    if (le == cudaSuccess) le = draw(0);
+    for (int k = 0; k < np && le == cudaSuccess; ++k) {
+        if (k + 1 < np) {
+            if (k >= 1) le = cudaStreamWaitEvent(B, h->apply_ev[k - 1], 0);    // buffer (k + 1) & 1 is read
+            if (le == cudaSuccess) le = draw(k + 1);
         }
-    } else {
-        for (int s = 1; s <= n && le == cudaSuccess; ++s) le = sweep(s, nullptr);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(A, h->draw_ev[k], 0);
+        const char* buf = buffers + (size_t)(k & 1) * kDrawSweeps * sweep_bytes;
+        for (int s = k * kDrawSweeps + 1; s <= std::min(n, (k + 1) * kDrawSweeps) && le == cudaSuccess; ++s)
+            le = sweep(s, buf + (size_t)(s - 1 - k * kDrawSweeps) * sweep_bytes);
+        if (le == cudaSuccess) le = cudaEventRecord(h->apply_ev[k], A);
     }
     if (le == cudaSuccess) {
         le = launch_advance_graph(h->t_dev, (uint64_t)n, rec_index(h), every > 0 ? (uint32_t)(n / every) : 0u, A);

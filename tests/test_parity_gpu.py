@@ -310,14 +310,17 @@ def test_graph_replays_equal_on_chip_path(ising, L):
     assert ta == tb == 70 + 70 + 130 + 100 + 66 + 33
 
 
+@pytest.mark.parametrize("layout", ["row_packed", "column_interleaved"])
 @pytest.mark.parametrize("beta", [0.0, 1e-18, BETA_TC, 6.0, math.inf])
-def test_graphs_drawing_masks_first_at_threshold_limits(ising, beta):
-    """Graph replays, which draw the masks of 16 sweeps at a time and then
-    apply them, at the threshold limits: 2^32 (beta = 0: every site flips),
-    just below 2^32, 0 (beta >= 5.55: only dE <= 0 flips).  70 sweeps span two
-    32-sweep graphs, the 16-sweep draw pieces and a plain remainder."""
-    L, seed = 300, 12
-    with ising.Lattice(L, seed) as lat:
+def test_graphs_drawing_masks_first_at_threshold_limits(ising, beta, layout):
+    """Graph replays, which draw the masks of 8 sweeps at a time one piece
+    ahead and then apply them, at the threshold limits: 2^32 (beta = 0: every
+    site flips), just below 2^32, 0 (beta >= 5.55: only dE <= 0 flips), in
+    both word layouts.  70 sweeps span two 32-sweep graphs, the draw pieces
+    and a plain remainder."""
+    L, seed = (300, 12) if layout == "row_packed" else (336, 12)
+    code = ising.ISING_LAYOUT_ROW_PACKED if layout == "row_packed" else ising.ISING_LAYOUT_COLUMN_INTERLEAVED
+    with ising.Lattice(L, seed, layout=code) as lat:
         lat.set_path(ising.ISING_PATH_LAUNCHES)
         lat.init_hot()
         lat.set_beta(beta)
