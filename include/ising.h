@@ -219,10 +219,10 @@ int ising_set_item_lanes(ising_lattice *h, int32_t lanes);
  * captured once into CUDA graphs and replayed (recaptured after
  * ising_set_beta, ising_set_rng, ising_set_tiling, ising_set_item_lanes; a
  * device record index picks the count slots of each replay), because there
- * a half-sweep runs about as long as the host takes to launch it.  In the
- * row-packed layout these graphs draw the accept masks of 8 sweeps at a time
- * on all SMs, into two buffers the library allocates on first use (1 KB per
- * thread item, at most 33.5 MB), and their half-sweeps only apply them.
+ * a half-sweep runs about as long as the host takes to launch it.  These
+ * graphs draw the accept masks of 8 sweeps at a time on all SMs, into two
+ * buffers the library allocates on first use (1 KB per thread item, at most
+ * 33.5 MB), and their half-sweeps only apply them.
  * ISING_PATH_RESIDENT: temporal
  * blocking with the whole lattice on chip -- one block copies both colour
  * arrays into shared memory and runs all requested sweeps there in one
