@@ -198,7 +198,9 @@ int ising_set_stream(ising_lattice *h, void *stream);
  * grid: block_words (threads along a row) in {16, 32, 64}; block_groups
  * (threads down the columns) in {1, 2, 4, 8, 16}; 32 <= block_words *
  * block_groups <= 256.  Default 4, 0, 128 (1-D, 128 threads).  Results do
- * not depend on the shape (the draws are keyed by site). */
+ * not depend on the shape (the draws are keyed by site).  It shapes the
+ * launches that draw inside the half-sweep: above 32768 thread items, and
+ * the sweeps left over after the graph replays below that. */
 int ising_set_tiling(ising_lattice *h, int32_t rows_per_thread,
                      int32_t block_words, int32_t block_groups);
 
@@ -208,9 +210,11 @@ int ising_set_tiling(ising_lattice *h, int32_t rows_per_thread,
  * (4 rows x 1 word) draws the fields q, q + F, ... and the lanes merge their
  * accept bits with warp shuffles: F times the threads, each with 1/F of the
  * item's Philox calls.  This fills the GPU for lattices whose one thread
- * per item would leave SMs idle.  No counterpart in the paper (a scheduling
- * choice); results do not depend on it.  Row-packed layout only (EINVAL
- * otherwise; EINVAL for other values). */
+ * per item would leave SMs idle.  It applies to the launches that draw
+ * inside the half-sweep (the sweeps left over after the graph replays,
+ * whose half-sweeps apply masks drawn ahead).  No counterpart in the paper
+ * (a scheduling choice); results do not depend on it.  Row-packed layout
+ * only (EINVAL otherwise; EINVAL for other values). */
 int ising_set_item_lanes(ising_lattice *h, int32_t lanes);
 
 /* Execution path of ising_sweep / ising_sweep_record.  ISING_PATH_LAUNCHES:
