@@ -347,6 +347,46 @@ __device__ __forceinline__ void row_apply(uint64_t* __restrict__ own, const uint
     }
 }
 
+// row_apply for one 32-bit half of the row: hf = 0 holds fields 0..10 (bits
+// 0..31), hf = 1 fields 11..20 (bits 32..63); m1, m0, live, all0 and all1
+// are that half of the row's words.  The two halves of a word are updated by
+// different threads with 32-bit stores; the neighbour words of the other
+// colour are read whole, since the shifted one carries a field across the
+// halves.
+template <int C, bool RECORD>
+__device__ __forceinline__ void row_half_apply(uint64_t* __restrict__ own, const uint64_t* __restrict__ other,
+                                               const Geom& g, int i, int w, int hf, uint32_t live, uint32_t m1,
+                                               uint32_t m0, uint32_t all0, uint32_t all1, uint32_t& anti,
+                                               uint32_t& up)
+{
+    const uint32_t P = (uint32_t)g.P;
+    const uint32_t o = (uint32_t)i * P;
+    uint32_t* own32 = reinterpret_cast<uint32_t*>(own);
+    const uint32_t* other32 = reinterpret_cast<const uint32_t*>(other);
+    const uint32_t s = own32[2 * (o + (uint32_t)w) + hf];
+    const uint32_t u = other32[2 * ((uint32_t)wrap_row(i - 1, g.L) * P + (uint32_t)w) + hf];
+    const uint32_t d = other32[2 * ((uint32_t)wrap_row(i + 1, g.L) * P + (uint32_t)w) + hf];
+    const uint64_t h0w = other[o + (uint32_t)w];
+    // horizontal neighbour at m - 1 ((i + C) even) or m + 1 (odd), as in sweep_rows
+    const bool left = ((i + C) & 1) == 0;
+    const int ws = left ? ((w > 0) ? w - 1 : g.W - 1) : ((w < g.W - 1) ? w + 1 : 0);
+    const int sh = (left ? (w > 0) : (w < g.W - 1)) ? 60 : 3 * (g.rlast - 1);
+    const uint64_t side = other[o + (uint32_t)ws];
+    const uint64_t h1w = left ? ((h0w << 3) | (side >> sh)) : ((h0w >> 3) | (side << sh));
+    const uint32_t h0 = (uint32_t)(h0w >> (32 * hf)), h1 = (uint32_t)(h1w >> (32 * hf));
+    const uint32_t x1 = s ^ u, x2 = s ^ d, x3 = s ^ h0, x4 = s ^ h1;
+    const uint32_t any = x1 | x2 | x3 | x4;
+    const uint32_t ge2 = (x1 & x2) | (x3 & x4) | ((x1 ^ x2) & (x3 ^ x4));
+    const uint32_t accept = ge2 | (any & (m1 | all1)) | (~any & (m0 | all0));
+    const uint32_t s_new = s ^ (accept & live);
+    own32[2 * (o + (uint32_t)w) + hf] = s_new;
+    if (RECORD) {
+        anti += __popc((s_new ^ u) & live) + __popc((s_new ^ d) & live) + __popc((s_new ^ h0) & live)
+              + __popc((s_new ^ h1) & live);
+        up += __popc(s_new & live) + __popc(h0 & live);
+    }
+}
+
 // Apply the masks of an item of colour C: lane q of its group of F lanes
 // updates rows q, q + F, ... below 4 (one code path for all lanes, the row's
 // masks picked by selection).  RECORD adds the item's

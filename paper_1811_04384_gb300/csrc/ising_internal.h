@@ -62,6 +62,11 @@ cudaError_t launch_resident(uint64_t* w0, uint64_t* w1, const Geom& g, const Swe
 // allow_resident_smem(bytes) leaves room for 1024 record counters).
 constexpr int kPremaskedMaxItems = 512;
 inline int premasked_rows_per_thread(int items) { return items <= 256 ? 1 : 2; }
+// Two threads per row (one per 32-bit half of its word) up to 100 items: on
+// GB300, 1000 recorded sweeps took 0.36 / 0.35 / 0.41 / 0.78 ms at L = 16 /
+// 32 / 64 / 100 against 0.57 / 0.44 / 0.45 / 0.87 with one, but 0.99
+// against 0.92 at L = 128 (128 items, 32 warps).
+inline int premasked_threads_per_row(int items) { return items <= 100 ? 2 : 1; }
 cudaError_t launch_mask_draw(const Geom& g, const SweepArgs& a, const uint64_t* t_base, uint64_t t0, int nsweeps,
                              ulonglong2* masks, cudaStream_t s);
 // One half-sweep that applies masks drawn by launch_mask_draw (`masks`: the

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdint>
+#include <type_traits>
 
 #include "../../include/ising.h"
 #include "ising_device.cuh"
@@ -225,8 +226,10 @@ mask_draw_kernel(Geom g, SweepArgs a, const uint64_t* t_base, uint64_t t0, int n
 // written at the end to records[2 (s / every - 1) ..] as (E, M).  rec_first
 // is the first record of this launch and nrec their number; the dynamic
 // shared memory holds both colour arrays and 2 nrec counters.  Same results
-// as resident_sweeps_kernel.
-template <int R>
+// as resident_sweeps_kernel.  H = 2 splits every row over two threads, one
+// per 32-bit half of its word (row_half_apply): twice the warps for a small
+// lattice, each with half of the spin logic.
+template <int R, int H>
 __global__ void __launch_bounds__(1024, 1)
 resident_premasked_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom g, SweepArgs a, int s_base,
                           int n, int every, int rec_first, int nrec, const ulonglong2* __restrict__ masks,
@@ -251,10 +254,13 @@ resident_premasked_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, 
     uint64_t live[R], all0[R], all1[R];
     // packed masks (colour 0, colour 1) of sweep s (c) and s + 1 (nx) of each row
     ulonglong2 c[R], nx[R];
+    int mi[R], hf[R];                    // the unit's mask entry (its row) and word half (H = 2)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int x = (int)threadIdx.x + r * (int)blockDim.x;
-        const int item = x >> 2, e = x & 3;
+        mi[r] = x / H;
+        hf[r] = x % H;
+        const int item = mi[r] >> 2, e = mi[r] & 3;
         const int grp = item / g.W;
         col[r] = item - grp * g.W;
         row[r] = grp * 4 + e;
@@ -264,10 +270,24 @@ resident_premasked_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, 
         all1[r] = ((uint64_t)a.all1 << 32 | a.all1) & live[r];
         c[r] = nx[r] = zero;
         if (valid[r]) {
-            c[r] = __ldg(masks + x);
-            if (n >= 2) nx[r] = __ldg(masks + stride + x);
+            c[r] = __ldg(masks + mi[r]);
+            if (n >= 2) nx[r] = __ldg(masks + stride + mi[r]);
         }
     }
+    // one half-sweep of unit r with the packed masks p of its row
+    auto apply = [&](auto colour, auto rec, int r, uint64_t p, uint32_t& anti, uint32_t& up) {
+        constexpr int C = decltype(colour)::value;
+        constexpr bool REC = decltype(rec)::value;
+        if constexpr (H == 1) {
+            row_apply<C, REC>(C == 0 ? s0 : s1, C == 0 ? s1 : s0, g, row[r], col[r], live[r], p, p >> 1, all0[r],
+                              all1[r], anti, up);
+        } else {
+            const int sh = 32 * hf[r];
+            row_half_apply<C, REC>(C == 0 ? s0 : s1, C == 0 ? s1 : s0, g, row[r], col[r], hf[r],
+                                   (uint32_t)(live[r] >> sh), (uint32_t)(p >> sh), (uint32_t)((p >> 1) >> sh),
+                                   (uint32_t)(all0[r] >> sh), (uint32_t)(all1[r] >> sh), anti, up);
+        }
+    };
     // the next recorded sweep of this launch and its slot in rec_sm
     int next = every - s_base % every;
     int slot = 0;
@@ -277,23 +297,16 @@ resident_premasked_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, 
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             f[r] = zero;
-            if (valid[r] && s + 2 <= n)
-                f[r] = __ldg(masks + (size_t)(s + 1) * stride + (threadIdx.x + r * blockDim.x));
-            if (valid[r])
-                row_apply<0, false>(s0, s1, g, row[r], col[r], live[r], c[r].x, c[r].x >> 1, all0[r], all1[r], anti,
-                                    up);
+            if (valid[r] && s + 2 <= n) f[r] = __ldg(masks + (size_t)(s + 1) * stride + mi[r]);
+            if (valid[r]) apply(std::integral_constant<int, 0>(), std::false_type(), r, c[r].x, anti, up);
         }
         __syncthreads();
         const bool record = s == next;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (valid[r]) {
-                if (record)
-                    row_apply<1, true>(s1, s0, g, row[r], col[r], live[r], c[r].y, c[r].y >> 1, all0[r], all1[r],
-                                       anti, up);
-                else
-                    row_apply<1, false>(s1, s0, g, row[r], col[r], live[r], c[r].y, c[r].y >> 1, all0[r], all1[r],
-                                        anti, up);
+                if (record) apply(std::integral_constant<int, 1>(), std::true_type(), r, c[r].y, anti, up);
+                else apply(std::integral_constant<int, 1>(), std::false_type(), r, c[r].y, anti, up);
             }
             c[r] = nx[r];
             nx[r] = f[r];
@@ -583,9 +596,11 @@ cudaError_t allow_resident_smem(int bytes)
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(resident_sweeps_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(resident_premasked_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        e = cudaFuncSetAttribute(resident_premasked_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(resident_premasked_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        e = cudaFuncSetAttribute(resident_premasked_kernel<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(resident_premasked_kernel<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     return e;
 }
 
@@ -616,17 +631,21 @@ cudaError_t launch_resident_premasked(uint64_t* w0, uint64_t* w1, const Geom& g,
                                       cudaStream_t s)
 {
     const int items = ((g.L + 3) / 4) * g.W;
+    const int H = premasked_threads_per_row(items);
     const int R = premasked_rows_per_thread(items);
-    const int threads = ((4 * items + R - 1) / R + 31) / 32 * 32;
+    const int threads = ((4 * H * items + R - 1) / R + 31) / 32 * 32;
     const int rec_first = s_base / every;
     const int nrec = (s_base + n) / every - rec_first;
     const size_t smem = bytes + 2 * (size_t)nrec * sizeof(unsigned int);
-    if (R == 1)
-        resident_premasked_kernel<1><<<1, threads, smem, s>>>(w0, w1, g, a, s_base, n, every, rec_first, nrec, masks,
-                                                              rec);
+    if (H == 2)
+        resident_premasked_kernel<1, 2><<<1, threads, smem, s>>>(w0, w1, g, a, s_base, n, every, rec_first, nrec,
+                                                                 masks, rec);
+    else if (R == 1)
+        resident_premasked_kernel<1, 1><<<1, threads, smem, s>>>(w0, w1, g, a, s_base, n, every, rec_first, nrec,
+                                                                 masks, rec);
     else
-        resident_premasked_kernel<2><<<1, threads, smem, s>>>(w0, w1, g, a, s_base, n, every, rec_first, nrec, masks,
-                                                              rec);
+        resident_premasked_kernel<2, 1><<<1, threads, smem, s>>>(w0, w1, g, a, s_base, n, every, rec_first, nrec,
+                                                                 masks, rec);
     return cudaGetLastError();
 }
 
