@@ -85,6 +85,21 @@ def test_resident_masks_drawn_in_pieces(ising):
     assert a[3] == 603
 
 
+def test_resident_plain_sweeps_in_pieces(ising):
+    # 600 sweeps without records in three mask pieces, then the energy: the
+    # same state as the launch path's graph replays and leftovers
+    def go(path):
+        with ising.Lattice(292, 4) as lat:
+            lat.set_path(path)
+            lat.init_hot()
+            lat.set_beta(0.41)
+            lat.sweep(600)
+            return lat.get_spins(), lat.energy(), lat.magnetization(), lat.t
+    a, b = go(ising.ISING_PATH_RESIDENT), go(ising.ISING_PATH_LAUNCHES)
+    np.testing.assert_array_equal(a[0], b[0])
+    assert a[1:] == b[1:] and a[3] == 600
+
+
 def test_resident_rejects_lattices_that_do_not_fit(ising):
     with ising.Lattice(1024, 1) as lat:
         with pytest.raises(ising.IsingError):
