@@ -199,7 +199,7 @@ int ising_set_stream(ising_lattice *h, void *stream);
  * (threads down the columns) in {1, 2, 4, 8, 16}; 32 <= block_words *
  * block_groups <= 256.  Default 4, 0, 128 (1-D, 128 threads).  Results do
  * not depend on the shape (the draws are keyed by site).  It shapes the
- * launches that draw inside the half-sweep: above 32768 thread items, and
+ * launches that draw inside the half-sweep: above 102400 thread items, and
  * the sweeps left over after the graph replays below that. */
 int ising_set_tiling(ising_lattice *h, int32_t rows_per_thread,
                      int32_t block_words, int32_t block_groups);
@@ -218,15 +218,15 @@ int ising_set_tiling(ising_lattice *h, int32_t rows_per_thread,
 int ising_set_item_lanes(ising_lattice *h, int32_t lanes);
 
 /* Execution path of ising_sweep / ising_sweep_record.  ISING_PATH_LAUNCHES:
- * two kernel launches per sweep, all SMs; up to 32768 thread items (L up to
- * about 2300, either layout) the launches of chunks of up to 32 sweeps are
+ * two kernel launches per sweep, all SMs; up to 102400 thread items (L up
+ * to about 4100, either layout) the launches of chunks of up to 32 sweeps are
  * captured once into CUDA graphs and replayed (recaptured after
  * ising_set_beta, ising_set_rng, ising_set_tiling, ising_set_item_lanes; a
  * device record index picks the count slots of each replay), because there
  * a half-sweep runs about as long as the host takes to launch it.  These
- * graphs draw the accept masks of 8 sweeps at a time on all SMs, into two
- * buffers the library allocates on first use (1 KB per thread item, at most
- * 33.5 MB), and their half-sweeps only apply them.
+ * graphs draw the accept masks of up to 8 sweeps at a time on all SMs, into
+ * two buffers the library allocates on first use (at most 33.5 MB), and
+ * their half-sweeps only apply them.
  * ISING_PATH_RESIDENT: temporal
  * blocking with the whole lattice on chip -- one block copies both colour
  * arrays into shared memory and runs all requested sweeps there in one

@@ -66,9 +66,9 @@ struct ising_lattice {
     bool resident_attr = false;                  // dynamic shared memory attribute set
     ulonglong2* masks = nullptr;                 // lazily allocated: pre-drawn masks of the on-chip path
     size_t mask_bytes = 0;
-    ulonglong2* graph_masks = nullptr;           // two buffers of kDrawSweeps sweeps' masks, drawn inside the graphs
+    ulonglong2* graph_masks = nullptr;           // two buffers of draw_sweeps() sweeps' masks, drawn inside the graphs
     cudaStream_t draw_stream = nullptr;          // the graphs' mask draws are captured here, beside the half-sweeps
-    cudaEvent_t fork_ev = nullptr, draw_ev[8] = {}, apply_ev[8] = {};
+    cudaEvent_t fork_ev = nullptr, draw_ev[64] = {}, apply_ev[64] = {};   // kMaxPieces each
 };
 
 static void drop_graphs(ising_lattice* h);
@@ -306,28 +306,40 @@ static cudaError_t launch_hs(const ising_lattice* h, int colour, bool update, bo
 }
 
 // ---- Graph replay of sweep chunks (launch path, small and mid-size lattices)
-// Below about L = 2300 a half-sweep kernel runs for a few microseconds, about
-// as long as the host takes to launch it.  Chunks of sweeps are captured once
-// into CUDA graphs and replayed: graph_plain holds kGraphSweeps sweeps, and
+// Up to about L = 4100 (102400 thread items) the launch path runs chunks of
+// sweeps as captured CUDA graphs: graph_plain holds kGraphSweeps sweeps, and
 // graph_rec holds max(1, kGraphSweeps / every) record intervals of `every`
 // sweeps, each recording into count slots offset by the device record index
 // (advanced by the graph itself, so one graph serves every record of a
-// chunk).  A graph draws the accept masks of kDrawSweeps sweeps at a time on
-// all SMs (mask_draw_kernel, or ci_mask_draw in the column-interleaved
+// chunk).  A graph draws the accept masks of draw_sweeps(h) sweeps at a time
+// on all SMs (mask_draw_kernel, or ci_mask_draw in the column-interleaved
 // layout, from the device sweep counter), and its half-sweeps only apply
 // them (half_sweep_apply_kernel, ci_half_sweep_pre): at these sizes one
-// thread per item leaves most SMs idle while each runs its 21 Philox calls
-// in a row.  The draws run on a
-// second branch of the graph, one piece ahead, into two alternating buffers:
-// piece k + 1 is drawn while piece k is applied, and a piece is drawn into a
-// buffer only after the half-sweeps of the piece before have read it.  The
-// kernels' launch operands (thresholds, Philox rounds, launch shape) are
-// baked into the graphs, so every call that changes them drops the graphs.
+// thread per item leaves SMs idle while each runs its 21 Philox calls in a
+// row, and a half-sweep runs about as long as the host takes to launch it.
+// The draws run on a second branch of the graph, one piece ahead, into two
+// alternating buffers: piece k + 1 is drawn while piece k is applied, and a
+// piece is drawn into a buffer only after the half-sweeps of the piece before
+// have read it.  The kernels' launch operands (thresholds, Philox rounds,
+// launch shape) are baked into the graphs, so every call that changes them
+// drops the graphs.  Measured on GB300, sweeps without records,
+// spin-updates/ns, graphs against plain launches: L = 2600: 814 / 406;
+// L = 3000: 889 / 575; L = 3500: 951 / 729; L = 4096: 996 / 966; but
+// L = 4300: 1010 / 1082, where one thread per item fills the GPU.
 constexpr int kGraphSweeps = 32;
 constexpr int kGraphMaxEvery = 64;
-constexpr int kGraphMaxItems = 32768;
-constexpr int kDrawSweeps = 8;
-constexpr int kMaxPieces = 8;          // a graph holds at most kGraphMaxEvery sweeps
+constexpr int kGraphMaxItems = 102400;
+constexpr int kMaxDrawSweeps = 8;
+constexpr size_t kGraphMaskBytes = 32u << 20;    // both buffers
+constexpr int kMaxPieces = kGraphMaxEvery;       // a graph holds at most kGraphMaxEvery sweeps
+
+// Sweeps per drawn piece: 8, fewer where two buffers of 8 would pass 32 MB
+// (64 B per item and sweep).
+static int draw_sweeps(const ising_lattice* h)
+{
+    const size_t items = (size_t)((h->g.L + 3) / 4) * h->g.W;
+    return (int)std::max<size_t>(1, std::min<size_t>(kMaxDrawSweeps, kGraphMaskBytes / (2 * 64 * items)));
+}
 
 static bool use_graphs(const ising_lattice* h)
 {
@@ -356,8 +368,9 @@ static int capture_sweeps(ising_lattice* h, int n, int every, cudaGraphExec_t* o
     const bool ci = h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED;
     const size_t sweep_bytes = ci ? ci_mask_bytes_per_sweep(h->g.L)
                                   : (size_t)(((h->g.L + 3) / 4) * h->g.W) * 4 * sizeof(ulonglong2);
+    const int D = draw_sweeps(h);
     if (!h->graph_masks) {
-        e = cudaMalloc(&h->graph_masks, 2 * kDrawSweeps * sweep_bytes);
+        e = cudaMalloc(&h->graph_masks, 2 * D * sweep_bytes);
         if (e != cudaSuccess) { h->graph_masks = nullptr; cuda_fail(e, "cudaMalloc graph masks"); return ISING_ENOMEM; }
     }
     if (!h->draw_stream) e = cudaStreamCreateWithFlags(&h->draw_stream, cudaStreamNonBlocking);
@@ -396,11 +409,11 @@ static int capture_sweeps(ising_lattice* h, int n, int every, cudaGraphExec_t* o
         return r;
     };
     cudaStream_t B = h->draw_stream;
-    const int np = (n + kDrawSweeps - 1) / kDrawSweeps;      // <= kMaxPieces
+    const int np = (n + D - 1) / D;      // <= kMaxPieces
     auto draw = [&](int k) {       // piece k: sweeps k D + 1 .. into buffer k & 1
-        const int first = k * kDrawSweeps;
-        const int count = std::min(kDrawSweeps, n - first);
-        char* buf = buffers + (size_t)(k & 1) * kDrawSweeps * sweep_bytes;
+        const int first = k * D;
+        const int count = std::min(D, n - first);
+        char* buf = buffers + (size_t)(k & 1) * D * sweep_bytes;
         cudaError_t r = ci ? ci_mask_draw(h->g.L, a, h->t_dev, (uint64_t)first, count,
                                           reinterpret_cast<uint64_t*>(buf), B)
                            : launch_mask_draw(h->g, a, h->t_dev, (uint64_t)first, count,
@@ -417,9 +430,9 @@ static int capture_sweeps(ising_lattice* h, int n, int every, cudaGraphExec_t* o
             if (le == cudaSuccess) le = draw(k + 1);
         }
         if (le == cudaSuccess) le = cudaStreamWaitEvent(A, h->draw_ev[k], 0);
-        const char* buf = buffers + (size_t)(k & 1) * kDrawSweeps * sweep_bytes;
-        for (int s = k * kDrawSweeps + 1; s <= std::min(n, (k + 1) * kDrawSweeps) && le == cudaSuccess; ++s)
-            le = sweep(s, buf + (size_t)(s - 1 - k * kDrawSweeps) * sweep_bytes);
+        const char* buf = buffers + (size_t)(k & 1) * D * sweep_bytes;
+        for (int s = k * D + 1; s <= std::min(n, (k + 1) * D) && le == cudaSuccess; ++s)
+            le = sweep(s, buf + (size_t)(s - 1 - k * D) * sweep_bytes);
         if (le == cudaSuccess) le = cudaEventRecord(h->apply_ev[k], A);
     }
     if (le == cudaSuccess) {

@@ -361,6 +361,30 @@ def test_graphs_drawing_masks_first_keep_dead_fields_zero(ising, L):
             assert (w[:, :, W:] == 0).all()
 
 
+@pytest.mark.parametrize("L", [2600, 4096])
+def test_graphs_with_short_pieces_equal_fused_launches(ising, L):
+    """Above 32,768 thread items a graph draws fewer sweeps per piece (6 at
+    L = 2600, 2 at L = 4096, so that the mask buffers stay within 32 MB):
+    64 recorded sweeps through graph replays equal the same sweeps run one
+    call at a time, which use the fused half-sweeps (no graph)."""
+    def go(graphs):
+        with ising.Lattice(L, 17) as lat:
+            lat.set_path(ising.ISING_PATH_LAUNCHES)
+            lat.init_hot()
+            lat.set_beta(0.43)
+            if graphs:
+                E, M = lat.sweep_record(64, 1)
+            else:
+                parts = [lat.sweep_record(1, 1) for _ in range(64)]
+                E = np.concatenate([p[0] for p in parts])
+                M = np.concatenate([p[1] for p in parts])
+            return E, M, lat.get_spins(), lat.t
+    a, b = go(True), go(False)
+    for x, y in zip(a[:3], b[:3]):
+        np.testing.assert_array_equal(x, y)
+    assert a[3] == b[3] == 64
+
+
 def test_graph_replays_match_oracle(ising):
     L, seed, beta = 1026, 6, 0.44
     with ising.Lattice(L, seed) as lat:
