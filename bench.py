@@ -43,12 +43,10 @@ SEED_LARGE = 3
 BETA = 1.0 / 2.269
 SWEEPS_PER_STEP = 10
 METRIC = "spin-updates/ns"
-SM_COUNT = 152
-SM_MAX_MHZ = 2070.0
-MULWIDE_PER_SM_CLK = 32         # 32x32->64 integer multiplies (IMAD.WIDE) per SM per clock
+NOMINAL_SM_MAX_MHZ = 2070.0     # used only if neither nvidia-smi nor MEASURED_PEAKS.json gives the clock
 # DRAM bytes (read + write) per half-sweep launch of the current kernel at
-# L = 16384, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum;
-# profiles/launches_large_L16384.md); None for other sizes and the 7-round scheme.
+# L = 16384, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum);
+# None for other sizes and the 7-round scheme.
 MEASURED_TRAFFIC = {16384: 1.112e8}
 MULWIDE_PER_SITE = 4            # Philox4x32-10 with the counter-independent rounds hoisted:
                                 # 16 multiplies per call, one call per 4 sites (10 per call,
@@ -548,7 +546,25 @@ def run_paper(args, ising, local):
           "cases": cases, "clocks": clocks.summary()})
 
 
-def two_pipe_roofline(achieved_sites_per_ns: float, rng: int) -> dict:
+def integer_peaks(ising, clocks_summary: dict) -> dict:
+    """The integer peaks of this device: the SM count and the per-SM, per-clock
+    rates of 32x32->64 multiply-adds, 32-bit multiply-adds and three-input
+    XORs measured by ising_probe_int_pipes (the SM's cycle counter, so
+    independent of the clock), times the maximum SM clock that nvidia-smi
+    reported during the timed region (clocks.max.sm), else the driver-written
+    MEASURED_PEAKS.json's sm_max_mhz, else the nominal 2070 MHz."""
+    probe = ising.probe_int_pipes()
+    mhz, src = clocks_summary.get("sm_max_mhz"), "nvidia-smi clocks.max.sm during the timed region"
+    if not mhz:
+        peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(peaks_path) and json.load(open(peaks_path)).get("sm_max_mhz"):
+            mhz, src = float(json.load(open(peaks_path))["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+        else:
+            mhz, src = NOMINAL_SM_MAX_MHZ, "nominal"
+    return dict(probe, sm_max_mhz=float(mhz), clock_source=src)
+
+
+def two_pipe_roofline(achieved_sites_per_ns: float, rng: int, peaks: dict) -> dict:
     """The two-pipe integer bound, beside the strict multiply-only one: the
     integer work per site over both pipes it can use.  Per site,
     FMA-heavy only: the Philox multiplies, 2 issue slots each (4 per site;
@@ -559,13 +575,21 @@ def two_pipe_roofline(achieved_sites_per_ns: float, rng: int) -> dict:
     half of the total."""
     mul = MULWIDE_PER_SITE if rng == 10 else 2.5
     xors = 4.5 if rng == 10 else 3.0
-    fma_only, alu_only, either = 2 * mul, xors + 2 + 1.1, 2.0
+    # issue slots in units of one 32-bit multiply-add (the FMA-heavy pipe's
+    # lane rate); a 32x32->64 product takes mad32 / mulwide of them
+    lanes = peaks["mad32_per_sm_clk"]
+    fma_only = mul * lanes / peaks["mulwide_per_sm_clk"]
+    alu_only = (xors + 2 + 1.1) * lanes / peaks["lop3_per_sm_clk"]
+    either = 2.0
     slots = max(fma_only, alu_only, (fma_only + alu_only + either) / 2)
-    peak = SM_COUNT * 64 * SM_MAX_MHZ * 1e6 / slots / 1e9
+    peak = peaks["sm_count"] * lanes * peaks["sm_max_mhz"] * 1e6 / slots / 1e9
     return {"peak_spin_updates_per_ns": peak, "frac": achieved_sites_per_ns / peak,
             "slots_per_site_per_pipe": slots,
-            "basis": "FMA-heavy only 2 x mul.wide per site, ALU only Philox XORs + 2 compares + word logic, "
-                     "2 inserts on either pipe, balanced; 152 SMs x 64 lanes/clk per pipe x 2070 MHz"}
+            "basis": (f"FMA-heavy only {mul} x mul.wide per site, ALU only Philox XORs + 2 compares + word logic, "
+                      f"2 inserts on either pipe, balanced; {peaks['sm_count']} SMs x measured lane rates "
+                      f"(mul.wide {peaks['mulwide_per_sm_clk']:.1f}, mad32 {peaks['mad32_per_sm_clk']:.1f}, "
+                      f"lop3 {peaks['lop3_per_sm_clk']:.1f} per SM per clock, ising_probe_int_pipes) x "
+                      f"{peaks['sm_max_mhz']:.0f} MHz ({peaks['clock_source']})")}
 
 
 def main():
@@ -649,7 +673,9 @@ def main():
     sites_per_launch = L * L // 2
     mul_per_site = MULWIDE_PER_SITE if args.rng == 10 else 2.5
     achieved_mul = sites_per_launch * mul_per_site / half_sweep_s / 1e12
-    peak_mul = SM_COUNT * MULWIDE_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    cs = clocks.summary()
+    peaks = integer_peaks(ising, cs)
+    peak_mul = peaks["sm_count"] * peaks["mulwide_per_sm_clk"] * peaks["sm_max_mhz"] * 1e6 / 1e12
     W = (L // 2 + 20) // 21
     P = W + (W & 1)
     hbm_bytes_per_launch = 3 * L * P * 8          # read own + write own + read other colour
@@ -702,7 +728,6 @@ def main():
                "sample": f"1 sweep of the L={L} hot-start lattice (seed {SEED_LARGE}, T=2.269); init excluded; {dt:.1f} s"}
 
     if rank == 0:
-        cs = clocks.summary()
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_s * 1e3 / args.steps, "higher_is_better": True,
@@ -720,9 +745,13 @@ def main():
                          "kernel": "half_sweep_kernel",
                          "achieved_spin_updates_per_ns": sites_per_launch / half_sweep_s / 1e9,
                          "peak_spin_updates_per_ns": peak_mul * 1e12 / mul_per_site / 1e9,
-                         "peak_basis": ("152 SMs x 32 IMAD.WIDE/clk/SM x 2070 MHz (of nominal clock); "
-                                        "4 per site (16 per Philox4x32-10 call, 4 sites per call)"),
-                         "two_pipe": two_pipe_roofline(sites_per_launch / half_sweep_s / 1e9, args.rng),
+                         "peak_basis": (f"{peaks['sm_count']} SMs x {peaks['mulwide_per_sm_clk']:.1f} "
+                                        "mul.wide.u32 per SM per clock (measured, ising_probe_int_pipes) x "
+                                        f"{peaks['sm_max_mhz']:.0f} MHz ({peaks['clock_source']}); "
+                                        f"{mul_per_site} per site (16 per Philox4x32-10 call after hoisting, "
+                                        "4 sites per call)"),
+                         "int_pipes": peaks,
+                         "two_pipe": two_pipe_roofline(sites_per_launch / half_sweep_s / 1e9, args.rng, peaks),
                          "hbm_achieved_gbs": hbm_bytes_per_launch / half_sweep_s / 1e9,
                          "hbm_peak_gbs": hbm_peak,
                          "hbm_frac": hbm_bytes_per_launch / half_sweep_s / 1e9 / hbm_peak},

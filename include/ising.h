@@ -56,7 +56,9 @@ enum {
     ISING_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
     ISING_ETIMEOUT = -4,  /* a bounded wait gave up (ising_server_wait); no kernel spin-waits */
     ISING_EBUSY = -5,     /* no free slot / budget (server admission) */
-    ISING_ENOTFOUND = -6  /* unknown request id */
+    ISING_ENOTFOUND = -6, /* unknown request id */
+    ISING_EINTERNAL = -7  /* a host exception inside the server's worker thread
+                             (an allocation failure, or ising_server_inject_fault) */
 };
 
 typedef struct ising_lattice ising_lattice;   /* opaque, library-owned */
@@ -143,6 +145,21 @@ int ising_sweep_record(ising_lattice *h, int64_t n, int64_t every,
  * Errors: EINVAL (NULL), ECUDA. */
 int ising_energy(ising_lattice *h, int64_t *host_E);
 int ising_magnetization(ising_lattice *h, int64_t *host_M);
+
+/* Eq. 2: the averages over n recorded sweeps of an L x L lattice, per spin:
+ * *mean_e = (sum_t E_t) / (n L^2) and *mean_absm = (sum_t |M_t|) / (n L^2)
+ * (the paper averages the per-iteration energies; the mean of |M_t| is the
+ * magnetisation counterpart).  host_E and host_M are caller-owned host
+ * arrays of n exact int64 records (as ising_sweep_record returns); either
+ * may be NULL when its output is NULL.  The sums are exact (128-bit
+ * integers) and each mean is one IEEE double division of the sum by n L^2,
+ * so it is the correctly rounded quotient while |sum| and n L^2 are below
+ * 2^53 (any run of fewer than about 2^21 records of the largest lattice).
+ * Pure host arithmetic: no device work, no synchronisation.
+ * Errors: EINVAL (n < 1, L invalid as for ising_create, an output whose
+ * input array is NULL, both outputs NULL). */
+int ising_means(const int64_t *host_E, const int64_t *host_M, int64_t n, int32_t L,
+                double *mean_e, double *mean_absm);
 
 /* Copy the spins to / from a caller-owned host array of n = L*L int8 values,
  * row-major s[i*L + j], each +1 or -1 (set: any value > 0 counts as +1).
@@ -361,11 +378,21 @@ typedef struct ising_result {
 } ising_result;
 
 /* Create a server on the current device with an arena of hbm_budget_bytes
- * (allocated once), at most max_jobs concurrently running jobs (1..4096) and
- * epochs of epoch_sweeps sweeps (1..100000), max_jobs * epoch_sweeps <= 2^22.
+ * (allocated once; at least 256 bytes, rounded down to a multiple of 256), at
+ * most ISING_SERVER_DEFAULT_MAX_JOBS (256) concurrently running jobs and epochs
+ * of ISING_SERVER_DEFAULT_EPOCH_SWEEPS (50) sweeps.  *out receives the handle.
+ * Errors: EINVAL (out NULL, budget < 256), ENOMEM, ECUDA. */
+#define ISING_SERVER_DEFAULT_MAX_JOBS 256
+#define ISING_SERVER_DEFAULT_EPOCH_SWEEPS 50
+int ising_server_create(size_t hbm_budget_bytes, ising_server **out);
+
+/* ising_server_create with the two scheduling limits chosen by the caller:
+ * at most max_jobs concurrently running jobs (1..4096) and epochs of
+ * epoch_sweeps sweeps (1..100000), max_jobs * epoch_sweeps <= 2^22 (the
+ * device record buffer of one epoch).  Results do not depend on either.
  * Errors: EINVAL, ENOMEM, ECUDA. */
-int ising_server_create(size_t hbm_budget_bytes, int32_t max_jobs, int32_t epoch_sweeps,
-                        ising_server **out);
+int ising_server_create_ex(size_t hbm_budget_bytes, int32_t max_jobs, int32_t epoch_sweeps,
+                           ising_server **out);
 
 /* Queue a job (copied); *id receives its id.  Thread-safe.  Errors: EINVAL
  * (bad job), ENOMEM (the job alone exceeds the whole arena). */
@@ -394,6 +421,16 @@ int ising_server_stats(ising_server *srv, int64_t *jobs_done, double *spin_updat
  * ones (state cancelled), free the arena.  Jobs still running are failed. */
 int ising_server_destroy(ising_server *srv);
 
+/* Failure-injection hook for tests (no counterpart in the paper): after
+ * `epochs` more epochs (0: the next one), the worker throws a host exception
+ * at the start of an epoch, before that epoch's device work.  The worker
+ * catches it, waits for its streams, marks every running job failed with
+ * status ISING_EINTERNAL, returns their arena blocks and goes on admitting
+ * and running the queued jobs.  epochs = -1 disarms the hook.  Nothing
+ * touches the device: no kernel is made to fault or hang.  Thread-safe.
+ * Errors: EINVAL (NULL, epochs < -1). */
+int ising_server_inject_fault(ising_server *srv, int32_t epochs);
+
 /* ---- Autotuning ---------------------------------------------------------
  * No counterpart in the paper.  Time the candidate launch shapes on the current device and return the
  * fastest.  Every candidate must leave a bit-identical lattice (the draws are
@@ -418,6 +455,18 @@ int ising_autotune(int32_t L, int32_t sweeps, int32_t *best_block_words, int32_t
 int ising_batch_autotune(int32_t n, const int32_t *L, const double *beta, const uint64_t *seed,
                          const uint8_t *hot, int64_t sweeps, int64_t every, int32_t *best_threads,
                          int32_t *best_chunk, int32_t *best_lanes, double *ns_per_update);
+
+/* Throughput probe of the integer instructions the sweep is made of, for the
+ * roofline (no counterpart in the paper): on the current device, one block
+ * of 1024 threads per SM runs 8 independent dependency chains per thread of
+ * (a) 32x32 -> 64-bit multiply-adds (the Philox product, both halves),
+ * (b) 32-bit multiply-adds and (c) three-input XORs, timed with the SM's
+ * cycle counter.  Outputs (any may be NULL): lane operations per SM per clock
+ * of each kind (the median over the SMs), and the SM count.  Takes a few
+ * milliseconds; allocates and frees about 0.6 MB of device memory and
+ * synchronises the device.  Errors: ENOMEM, ECUDA. */
+int ising_probe_int_pipes(double *mulwide_per_sm_clk, double *mad32_per_sm_clk, double *lop3_per_sm_clk,
+                          int32_t *sm_count);
 
 /* ---- Allocation-free record path ----------------------------------------
  * The paper has no counterpart to this entry point.  It is for callers that
@@ -445,10 +494,18 @@ int ising_batch_autotune(int32_t n, const int32_t *L, const double *beta, const 
  * ISING_NOALLOC_MAX_RECORDS records per call; n / every above that returns
  * ISING_EINVAL before any device work.  The first call on each device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call
- * shares the array, which keeps the previous call's contents (each call
- * clears the slots it uses first): calls that overlap on the GPU, on any
- * streams, race and give wrong results.
+ * current; make that first call before any stream capture.  That address
+ * is cached per device for the life of the process: after cudaDeviceReset
+ * (or a reset of the device's primary context) the cached address is stale,
+ * so do not call this entry point on that device again in the same process.
+ * Every call shares the array, which keeps the previous call's contents
+ * (each call clears the slots it uses first): calls that overlap on the GPU,
+ * on any streams, race and give wrong results.
+ *
+ * Execution: two plain half-sweep launches per sweep with a fixed 2-D shape
+ * (32 words x 4 row groups per block), no CUDA graphs and no on-chip path,
+ * so small lattices run at the plain-launch rate, far below
+ * ising_sweep_record's; results are identical (the draws are keyed by site).
  * Errors: EINVAL (NULL words, bad L, n < 0, every < 1, beta < 0 or NaN, too
  * many records), ECUDA. */
 #define ISING_NOALLOC_MAX_RECORDS 1024

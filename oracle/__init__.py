@@ -13,6 +13,7 @@ Eq. 2 (averages over iterations).
 from __future__ import annotations
 
 import ctypes
+import multiprocessing as mp
 import os
 import subprocess
 import threading
@@ -263,3 +264,30 @@ def means(E: np.ndarray, M: np.ndarray, L: int) -> tuple[float, float]:
     sE = int(np.sum(E.astype(object)))
     sM = int(np.sum(np.abs(M).astype(object)))
     return sE / (n * L * L), sM / (n * L * L)
+
+
+# --- independent jobs on several host cores ---------------------------------------
+
+def run_job(job):
+    """One independent oracle run: job = (L, seed, beta, hot, sweeps, every).
+    Hot start from `seed` (else all +1), sweeps 1..sweeps; returns the
+    (E, M) series recorded every `every` sweeps and the final spins."""
+    L, seed, beta, hot, sweeps, every = job
+    s = init_hot(L, seed) if hot else init_cold(L, 1)
+    E, M = run(s, seed, beta, 0, sweeps, every)
+    return E, M, s
+
+
+def run_jobs(jobs, processes: int | None = None):
+    """run_job over a list of jobs, in a spawn-context process pool (a
+    spawned worker inherits no CUDA state of the caller, so this may be
+    called after GPU work).  Results come back in the order of `jobs`."""
+    jobs = list(jobs)
+    if not jobs:
+        return []
+    build()
+    n = max(1, min(len(jobs), processes or os.cpu_count() or 1))
+    if n == 1:
+        return [run_job(j) for j in jobs]
+    with mp.get_context("spawn").Pool(n) as pool:
+        return pool.map(run_job, jobs, chunksize=1)

@@ -25,6 +25,7 @@ ISING_ECUDA = -3
 ISING_ETIMEOUT = -4
 ISING_EBUSY = -5
 ISING_ENOTFOUND = -6
+ISING_EINTERNAL = -7
 ISING_LAYOUT_ROW_PACKED = 0
 ISING_LAYOUT_COLUMN_INTERLEAVED = 1
 ISING_RNG_PHILOX4X32_10 = 0
@@ -377,10 +378,26 @@ def philox_blocks(seed: int, ctr: np.ndarray) -> np.ndarray:
     return out
 
 
+def probe_int_pipes() -> dict:
+    """Integer instruction throughput of the current device (ising_probe_int_pipes):
+    lane operations per SM per clock of 32x32->64 multiply-adds, 32-bit
+    multiply-adds and three-input XORs, and the SM count."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    n = ctypes.c_int32()
+    _check(load().ising_probe_int_pipes(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(n)),
+           "ising_probe_int_pipes")
+    return {"mulwide_per_sm_clk": a.value, "mad32_per_sm_clk": b.value, "lop3_per_sm_clk": c.value,
+            "sm_count": n.value}
+
+
 def means(E: np.ndarray, M: np.ndarray, L: int) -> tuple[float, float]:
-    """Eq. 2: <E>/N and <|M|>/N over the recorded sweeps, from exact integer sums
-    and one FP64 division each."""
-    n = len(E)
-    sE = int(np.sum(np.asarray(E, dtype=np.int64).astype(object)))
-    sM = int(np.sum(np.abs(np.asarray(M, dtype=np.int64)).astype(object)))
-    return sE / (n * L * L), sM / (n * L * L)
+    """Eq. 2 (ising_means): <E>/N and <|M|>/N over the recorded sweeps, from
+    exact integer sums and one FP64 division each."""
+    e = np.ascontiguousarray(E, dtype=np.int64)
+    m = np.ascontiguousarray(M, dtype=np.int64)
+    assert e.shape == m.shape and e.ndim == 1
+    me, mm = ctypes.c_double(), ctypes.c_double()
+    _check(load().ising_means(e.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                              m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), e.size, int(L),
+                              ctypes.byref(me), ctypes.byref(mm)), "ising_means")
+    return me.value, mm.value

@@ -50,6 +50,7 @@ SYMBOLS = {
     "ising_sweep_record": (_int, [_vp, _i64, _i64, _pi64, _pi64]),
     "ising_energy": (_int, [_vp, _pi64]),
     "ising_magnetization": (_int, [_vp, _pi64]),
+    "ising_means": (_int, [_pi64, _pi64, _i64, _i32, _pd, _pd]),
     "ising_get_spins": (_int, [_vp, _pi8, _sz]),
     "ising_set_spins": (_int, [_vp, _pi8, _sz]),
     "ising_get_words": (_int, [_vp, _pu64, _sz]),
@@ -74,7 +75,9 @@ SYMBOLS = {
     "ising_batch_set_rng": (_int, [_vp, _i32]),
     "ising_batch_set_lanes": (_int, [_vp, _i32]),
     "ising_batch_run": (_int, [_i32, _pi32, _pd, _pu64, _pu8, _pi64, _i64, _vp, _vp, _vp]),
-    "ising_server_create": (_int, [_sz, _i32, _i32, _pvp]),
+    "ising_server_create": (_int, [_sz, _pvp]),
+    "ising_server_create_ex": (_int, [_sz, _i32, _i32, _pvp]),
+    "ising_server_inject_fault": (_int, [_vp, _i32]),
     "ising_server_submit": (_int, [_vp, ctypes.POINTER(IsingJob), _pu64]),
     "ising_server_poll": (_int, [_vp, _u64, ctypes.POINTER(IsingResult)]),
     "ising_server_wait": (_int, [_vp, _u64, _i64, ctypes.POINTER(IsingResult)]),
@@ -83,6 +86,7 @@ SYMBOLS = {
     "ising_server_stats": (_int, [_vp, _pi64, _pd, _pi64, _pd]),
     "ising_server_destroy": (_int, [_vp]),
     "ising_autotune": (_int, [_i32, _i32, _pi32, _pi32, _pi32, _pi32, _pd]),
+    "ising_probe_int_pipes": (_int, [_pd, _pd, _pd, _pi32]),
     "ising_batch_autotune": (_int, [_i32, _pi32, _pd, _pu64, _pu8, _i64, _i64, _pi32, _pi32, _pi32, _pd]),
     "ising_sweep_record_noalloc": (_int, [_vp, _vp, _i32, _u64, _dbl, _u64, _i64, _i64, _pi64, _pi64, _vp]),
 }

@@ -83,6 +83,7 @@ extern "C" const char* ising_strerror(int code)
     case ISING_ETIMEOUT: return "timed out waiting";
     case ISING_EBUSY: return "busy: no free slot or memory budget";
     case ISING_ENOTFOUND: return "unknown request id";
+    case ISING_EINTERNAL: return "internal host error in the server worker";
     default: return "unknown error code";
     }
 }
@@ -721,6 +722,27 @@ extern "C" int ising_magnetization(ising_lattice* h, int64_t* M)
 {
     if (!h || !M) return ISING_EINVAL;
     return measure(h, nullptr, M);
+}
+
+// Eq. 2: exact 128-bit sums of the records, then one IEEE double division
+// each (the integer count n L^2 converted once).
+extern "C" int ising_means(const int64_t* E, const int64_t* M, int64_t n, int32_t L, double* mean_e,
+                           double* mean_absm)
+{
+    if (n < 1 || !valid_L(L) || (!mean_e && !mean_absm) || (mean_e && !E) || (mean_absm && !M))
+        return ISING_EINVAL;
+    const double count = (double)((__int128)n * L * L);
+    if (mean_e) {
+        __int128 sum = 0;
+        for (int64_t k = 0; k < n; ++k) sum += E[k];
+        *mean_e = (double)sum / count;
+    }
+    if (mean_absm) {
+        __int128 sum = 0;
+        for (int64_t k = 0; k < n; ++k) sum += M[k] < 0 ? -(__int128)M[k] : (__int128)M[k];
+        *mean_absm = (double)sum / count;
+    }
+    return ISING_OK;
 }
 
 static int ensure_staging(ising_lattice* h)

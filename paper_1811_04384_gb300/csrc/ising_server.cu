@@ -16,6 +16,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <stdexcept>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -108,6 +109,7 @@ struct ising_server {
     int device = 0;
     int max_jobs = 0;
     int epoch = 0;
+    int fault_after = -1;             // test hook: epochs until an injected host exception (-1: none)
     std::chrono::steady_clock::time_point t0;
     // totals
     int64_t jobs_done = 0, epochs = 0;
@@ -147,18 +149,36 @@ int valid_job(const ising_job* j)
     return 1;
 }
 
-// Mark every running job failed (after a device error).
+// Mark every running job failed (after a device error or a host exception in
+// the worker) and return its arena block, so that the queued jobs can still
+// be admitted.
 void fail_running(ising_server* s, int status)
 {
     std::lock_guard<std::mutex> lock(s->mu);
     for (uint64_t id : s->running) {
-        Job& j = s->jobs[id];
+        auto it = s->jobs.find(id);
+        if (it == s->jobs.end()) continue;
+        Job& j = it->second;
         j.state = kFailed;
         j.status = status;
         j.done_s = s->now();
+        s->alloc->release(j.off, j.bytes);
     }
     s->running.clear();
     s->done_cv.notify_all();
+}
+
+// Test hook (ising_server_inject_fault): throw a host exception at the start
+// of the epoch the hook asked for, before any device work of that epoch.
+void maybe_inject_fault(ising_server* s)
+{
+    bool fire = false;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (s->fault_after == 0) fire = true;
+        if (s->fault_after >= 0) s->fault_after -= 1;
+    }
+    if (fire) throw std::runtime_error("injected server fault");
 }
 
 // Admit queued jobs in arrival order while a slot and arena space are free.
@@ -167,8 +187,9 @@ std::vector<uint64_t> admit(ising_server* s)
     std::vector<uint64_t> admitted;
     while (!s->queue.empty() && (int)s->running.size() < s->max_jobs) {
         const uint64_t id = s->queue.front();
-        Job& j = s->jobs[id];
-        if (j.state != kQueued) { s->queue.pop_front(); continue; }
+        auto it = s->jobs.find(id);
+        if (it == s->jobs.end() || it->second.state != kQueued) { s->queue.pop_front(); continue; }
+        Job& j = it->second;
         size_t off;
         if (!s->alloc->alloc(j.bytes, &off)) break;
         s->queue.pop_front();
@@ -320,6 +341,16 @@ int copy_spins(ising_server* s, Job& j)
     return e == cudaSuccess ? ISING_OK : cuda_fail(e, "server spins");
 }
 
+// Wait for every stream of the server (used before failing the running jobs,
+// so that no kernel still writes their arena blocks).
+void drain_streams(ising_server* s)
+{
+    for (int k = 1; k < kLanes; ++k)
+        if (s->lane_stream[k]) cudaStreamSynchronize(s->lane_stream[k]);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    cudaGetLastError();
+}
+
 void worker_main(ising_server* s)
 {
     cudaSetDevice(s->device);
@@ -341,60 +372,76 @@ void worker_main(ising_server* s)
             s->cv.wait_for(lock, std::chrono::milliseconds(5));
             continue;
         }
-        // initialise the newly admitted jobs
-        int rc = ISING_OK;
-        for (uint64_t id : admitted) {
-            Job* j = nullptr;
+        try {
+            // initialise the newly admitted jobs
+            int rc = ISING_OK;
+            for (uint64_t id : admitted) {
+                Job* j = nullptr;
+                {
+                    std::lock_guard<std::mutex> lock(s->mu);
+                    j = &s->jobs[id];
+                }
+                uint64_t* w0 = reinterpret_cast<uint64_t*>(s->arena + j->off);
+                uint64_t* w1 = reinterpret_cast<uint64_t*>(s->arena + j->off + j->bytes / 2);
+                cudaError_t e = cudaMemsetAsync(w0, 0, j->bytes, s->stream);
+                if (e == cudaSuccess)
+                    e = j->spec.hot ? launch_init_hot(w0, w1, j->g, j->spec.seed, s->stream)
+                                    : launch_init_cold(w0, w1, j->g, 1, s->stream);
+                if (e != cudaSuccess) { rc = cuda_fail(e, "server init"); break; }
+                j->rep.w0 = w0;
+                j->rep.w1 = w1;
+            }
+            const double t_begin = s->now();
+            if (rc == ISING_OK) maybe_inject_fault(s);
+            if (rc == ISING_OK) rc = run_epoch(s, run, jp);
+            if (rc != ISING_OK) {
+                fail_running(s, rc);
+                continue;
+            }
+            // retire finished jobs
+            std::vector<Job*> finished;
+            for (Job* j : jp)
+                if (j->t >= j->spec.sweeps) finished.push_back(j);
+            for (Job* j : finished)
+                j->status = j->spec.host_spins ? copy_spins(s, *j) : ISING_OK;
             {
                 std::lock_guard<std::mutex> lock(s->mu);
-                j = &s->jobs[id];
+                s->busy_s += s->now() - t_begin;
+                s->epochs += 1;
+                for (Job* j : finished) {
+                    j->state = j->status == ISING_OK ? kDone : kFailed;
+                    j->done_s = s->now();
+                    s->alloc->release(j->off, j->bytes);
+                    s->jobs_done += 1;
+                }
+                s->running.erase(std::remove_if(s->running.begin(), s->running.end(),
+                                                [&](uint64_t id) {
+                                                    auto it = s->jobs.find(id);
+                                                    return it == s->jobs.end() || it->second.state != kRunning;
+                                                }),
+                                 s->running.end());
+                if (!finished.empty()) s->done_cv.notify_all();
             }
-            uint64_t* w0 = reinterpret_cast<uint64_t*>(s->arena + j->off);
-            uint64_t* w1 = reinterpret_cast<uint64_t*>(s->arena + j->off + j->bytes / 2);
-            cudaError_t e = cudaMemsetAsync(w0, 0, j->bytes, s->stream);
-            if (e == cudaSuccess)
-                e = j->spec.hot ? launch_init_hot(w0, w1, j->g, j->spec.seed, s->stream)
-                                : launch_init_cold(w0, w1, j->g, 1, s->stream);
-            if (e != cudaSuccess) { rc = cuda_fail(e, "server init"); break; }
-            j->rep.w0 = w0;
-            j->rep.w1 = w1;
-        }
-        const double t_begin = s->now();
-        if (rc == ISING_OK) rc = run_epoch(s, run, jp);
-        if (rc != ISING_OK) {
-            fail_running(s, rc);
-            continue;
-        }
-        // retire finished jobs
-        std::vector<Job*> finished;
-        for (Job* j : jp)
-            if (j->t >= j->spec.sweeps) finished.push_back(j);
-        for (Job* j : finished)
-            j->status = j->spec.host_spins ? copy_spins(s, *j) : ISING_OK;
-        {
-            std::lock_guard<std::mutex> lock(s->mu);
-            s->busy_s += s->now() - t_begin;
-            s->epochs += 1;
-            for (Job* j : finished) {
-                j->state = j->status == ISING_OK ? kDone : kFailed;
-                j->done_s = s->now();
-                s->alloc->release(j->off, j->bytes);
-                s->jobs_done += 1;
-            }
-            s->running.erase(std::remove_if(s->running.begin(), s->running.end(),
-                                            [&](uint64_t id) { return s->jobs[id].state != kRunning; }),
-                             s->running.end());
-            if (!finished.empty()) s->done_cv.notify_all();
+        } catch (...) {
+            // A host exception in the worker (an allocation failure, or the
+            // injected test fault): let the device finish what was launched,
+            // fail the running jobs, and go on serving the queue.
+            drain_streams(s);
+            fail_running(s, ISING_EINTERNAL);
         }
     }
     // stopping: queued jobs are cancelled, running ones failed
     std::lock_guard<std::mutex> lock(s->mu);
     for (uint64_t id : s->queue) {
-        Job& j = s->jobs[id];
+        auto it = s->jobs.find(id);
+        if (it == s->jobs.end()) continue;
+        Job& j = it->second;
         if (j.state == kQueued) { j.state = kCancelled; j.status = ISING_EBUSY; }
     }
     for (uint64_t id : s->running) {
-        Job& j = s->jobs[id];
+        auto it = s->jobs.find(id);
+        if (it == s->jobs.end()) continue;
+        Job& j = it->second;
         j.state = kFailed;
         j.status = ISING_EBUSY;
     }
@@ -435,7 +482,7 @@ void free_server(ising_server* s)
 
 }  // namespace
 
-extern "C" int ising_server_create(size_t budget, int32_t max_jobs, int32_t epoch_sweeps, ising_server** out)
+extern "C" int ising_server_create_ex(size_t budget, int32_t max_jobs, int32_t epoch_sweeps, ising_server** out)
 {
     if (!out || budget < kAlign || max_jobs < 1 || max_jobs > 4096 || epoch_sweeps < 1 || epoch_sweeps > 100000)
         return ISING_EINVAL;
@@ -475,6 +522,19 @@ extern "C" int ising_server_create(size_t budget, int32_t max_jobs, int32_t epoc
         return ISING_ENOMEM;
     }
     *out = s;
+    return ISING_OK;
+}
+
+extern "C" int ising_server_create(size_t budget, ising_server** out)
+{
+    return ising_server_create_ex(budget, ISING_SERVER_DEFAULT_MAX_JOBS, ISING_SERVER_DEFAULT_EPOCH_SWEEPS, out);
+}
+
+extern "C" int ising_server_inject_fault(ising_server* s, int32_t epochs)
+{
+    if (!s || epochs < -1) return ISING_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->fault_after = epochs;
     return ISING_OK;
 }
 
@@ -542,6 +602,7 @@ extern "C" int ising_server_cancel(ising_server* s, uint64_t id)
     if (it->second.state != kQueued) return ISING_EBUSY;
     it->second.state = kCancelled;
     it->second.status = ISING_EBUSY;
+    s->queue.erase(std::remove(s->queue.begin(), s->queue.end(), id), s->queue.end());
     s->done_cv.notify_all();
     return ISING_OK;
 }

@@ -4,6 +4,7 @@
 // bit-identical lattice, and reports the fastest.  Contract: include/ising.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 #include <vector>
@@ -146,5 +147,116 @@ extern "C" int ising_batch_autotune(int32_t n, const int32_t* L, const double* b
     if (best_chunk) *best_chunk = bc;
     if (best_lanes) *best_lanes = bl;
     if (ns_per_update) *ns_per_update = best * 1e6 / updates;
+    return ISING_OK;
+}
+
+// ---- Integer pipe probe ---------------------------------------------------
+// Throughput of the three integer instruction kinds the sweep is made of, in
+// lane operations per SM per clock, read from the SM's own cycle counter (so
+// it does not depend on the clock the GPU runs at): one block of 1024 threads
+// per SM (its dynamic shared memory keeps a second block off the SM), each
+// thread running kProbeChains independent dependency chains.
+namespace {
+
+constexpr int kProbeChains = 8;
+constexpr int kProbeIters = 2048;
+constexpr int kProbeThreads = 1024;
+constexpr int kProbeSmem = 160 * 1024;
+
+// KIND 0: 32x32 -> 64-bit multiply-add (a Philox product: both halves);
+// KIND 1: 32-bit multiply-add (low half only); KIND 2: three-input XOR.
+template <int KIND>
+__global__ void __launch_bounds__(kProbeThreads, 1)
+int_pipe_probe_kernel(uint32_t seed, uint32_t* sink, long long* cycles)
+{
+    extern __shared__ uint32_t probe_pad[];
+    uint64_t acc[kProbeChains];
+    uint32_t x[kProbeChains], y[kProbeChains], z[kProbeChains];
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) {
+        x[c] = seed ^ (threadIdx.x * kProbeChains + c);
+        y[c] = x[c] * 0x9E3779B9u;
+        z[c] = x[c] ^ 0xBB67AE85u;
+        acc[c] = x[c];
+    }
+    if (threadIdx.x == 0) probe_pad[0] = seed;
+    __syncthreads();
+    const long long t0 = clock64();
+#pragma unroll 4
+    for (int it = 0; it < kProbeIters; ++it) {
+#pragma unroll
+        for (int c = 0; c < kProbeChains; ++c) {
+            if (KIND == 0) {
+                acc[c] = (uint64_t)(uint32_t)acc[c] * 0xD2511F53u + acc[c];
+            } else if (KIND == 1) {
+                x[c] = x[c] * x[c] + y[c];           // a square: no two steps fold into one
+            } else {
+                const uint32_t n = x[c] ^ y[c] ^ z[c];
+                x[c] = y[c];
+                y[c] = z[c];
+                z[c] = n;
+            }
+        }
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    uint32_t r = probe_pad[0];
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) r ^= (uint32_t)acc[c] ^ (uint32_t)(acc[c] >> 32) ^ x[c] ^ y[c] ^ z[c];
+    sink[blockIdx.x * kProbeThreads + threadIdx.x] = r;
+    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
+template <int KIND>
+int run_probe(int nsm, uint32_t* sink, long long* d_cycles, double* rate)
+{
+    cudaError_t e = cudaFuncSetAttribute(int_pipe_probe_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kProbeSmem);
+    if (e != cudaSuccess) return ising::cuda_fail(e, "probe attribute");
+    for (int rep = 0; rep < 2; ++rep) {            // the first launch loads the module
+        int_pipe_probe_kernel<KIND><<<nsm, kProbeThreads, kProbeSmem>>>(0x1234u + KIND, sink, d_cycles);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return ising::cuda_fail(e, "int_pipe_probe_kernel");
+    }
+    std::vector<long long> cyc(nsm);
+    e = cudaMemcpy(cyc.data(), d_cycles, nsm * sizeof(long long), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return ising::cuda_fail(e, "probe cycles");
+    std::sort(cyc.begin(), cyc.end());
+    const double ops = (double)kProbeThreads * kProbeChains * kProbeIters;
+    *rate = cyc[nsm / 2] > 0 ? ops / (double)cyc[nsm / 2] : 0.0;
+    return ISING_OK;
+}
+
+}  // namespace
+
+extern "C" int ising_probe_int_pipes(double* mulwide_per_sm_clk, double* mad32_per_sm_clk, double* lop3_per_sm_clk,
+                                     int32_t* sm_count)
+{
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return ising::cuda_fail(e, "probe device");
+    if (nsm < 1) return ISING_ECUDA;
+    uint32_t* sink = nullptr;
+    long long* d_cycles = nullptr;
+    e = cudaMalloc(&sink, (size_t)nsm * kProbeThreads * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&d_cycles, (size_t)nsm * sizeof(long long));
+    if (e != cudaSuccess) {
+        cudaFree(sink);
+        ising::cuda_fail(e, "cudaMalloc probe");
+        return ISING_ENOMEM;
+    }
+    double r0 = 0, r1 = 0, r2 = 0;
+    int rc = run_probe<0>(nsm, sink, d_cycles, &r0);
+    if (rc == ISING_OK) rc = run_probe<1>(nsm, sink, d_cycles, &r1);
+    if (rc == ISING_OK) rc = run_probe<2>(nsm, sink, d_cycles, &r2);
+    cudaFree(sink);
+    cudaFree(d_cycles);
+    if (rc != ISING_OK) return rc;
+    if (mulwide_per_sm_clk) *mulwide_per_sm_clk = r0;
+    if (mad32_per_sm_clk) *mad32_per_sm_clk = r1;
+    if (lop3_per_sm_clk) *lop3_per_sm_clk = r2;
+    if (sm_count) *sm_count = nsm;
     return ISING_OK;
 }

@@ -39,11 +39,17 @@ class Request:
 
 
 class Server:
-    def __init__(self, hbm_budget_bytes: int, max_jobs: int = 256, epoch_sweeps: int = 50):
+    def __init__(self, hbm_budget_bytes: int, max_jobs: int | None = None, epoch_sweeps: int | None = None):
+        """A server with an arena of hbm_budget_bytes.  With neither limit given
+        this is ising_server_create (256 running jobs, 50-sweep epochs);
+        otherwise ising_server_create_ex with the missing limit at its default."""
         lib = load()
         h = ctypes.c_void_p()
-        _check(lib.ising_server_create(int(hbm_budget_bytes), int(max_jobs), int(epoch_sweeps), ctypes.byref(h)),
-               "ising_server_create")
+        if max_jobs is None and epoch_sweeps is None:
+            _check(lib.ising_server_create(int(hbm_budget_bytes), ctypes.byref(h)), "ising_server_create")
+        else:
+            _check(lib.ising_server_create_ex(int(hbm_budget_bytes), int(max_jobs or 256), int(epoch_sweeps or 50),
+                                              ctypes.byref(h)), "ising_server_create_ex")
         self._h = h
         self._live = {}
 
@@ -73,6 +79,11 @@ class Server:
     def release(self, jid: int):
         _check(load().ising_server_release(self._h, int(jid)), "ising_server_release")
         self._live.pop(int(jid), None)
+
+    def inject_fault(self, epochs: int = 0):
+        """Test hook (ising_server_inject_fault): a host exception in the worker
+        at the start of the epoch `epochs` epochs from now; -1 disarms it."""
+        _check(load().ising_server_inject_fault(self._h, int(epochs)), "ising_server_inject_fault")
 
     def stats(self):
         jobs, eps = ctypes.c_int64(), ctypes.c_int64()

@@ -71,6 +71,13 @@ def test_invalid_arguments_are_rejected_before_any_device_call(lib):
     assert lib.ising_sweep(None, 1) == p.ISING_EINVAL
     assert lib.ising_set_beta(None, 0.5) == p.ISING_EINVAL
     assert lib.ising_philox_blocks(1, None, None, 4) == p.ISING_EINVAL
+    # the serving entry points of the boundary, in the two-argument form
+    assert lib.ising_server_create(1 << 20, None) == p.ISING_EINVAL
+    assert lib.ising_server_create(255, ctypes.byref(h)) == p.ISING_EINVAL
+    assert lib.ising_server_create_ex(1 << 20, 0, 50, ctypes.byref(h)) == p.ISING_EINVAL
+    assert lib.ising_server_create_ex(1 << 20, 256, 1 << 17, ctypes.byref(h)) == p.ISING_EINVAL
+    assert lib.ising_server_inject_fault(None, 0) == p.ISING_EINVAL
+    assert lib.ising_strerror(p.ISING_EINTERNAL) == b"internal host error in the server worker"
 
 
 def test_product_path_has_no_oracle_dependency():

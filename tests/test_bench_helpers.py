@@ -39,13 +39,19 @@ def test_batch_launch_count():
 
 
 def test_two_pipe_roofline_arithmetic():
-    r = bench.two_pipe_roofline(1376.0, 10)
+    peaks = {"sm_count": 152, "mulwide_per_sm_clk": 32.0, "mad32_per_sm_clk": 64.0, "lop3_per_sm_clk": 64.0,
+             "sm_max_mhz": 2070.0, "clock_source": "test"}
+    r = bench.two_pipe_roofline(1376.0, 10, peaks)
     # FMA-heavy only 8, ALU only 7.6, either 2: balanced 8.8 slots per pipe
     assert r["slots_per_site_per_pipe"] == pytest.approx(8.8)
     assert r["peak_spin_updates_per_ns"] == pytest.approx(152 * 64 * 2070e6 / 8.8 / 1e9)
     assert r["frac"] == pytest.approx(1376.0 / r["peak_spin_updates_per_ns"])
-    r7 = bench.two_pipe_roofline(1.0, 7)
+    r7 = bench.two_pipe_roofline(1.0, 7, peaks)
     assert r7["slots_per_site_per_pipe"] == pytest.approx((5.0 + 6.1 + 2.0) / 2)
+    # a device whose wide product ran at the 32-bit rate: FMA-heavy only 4
+    # slots, so the ALU-only work (7.6) binds
+    r_fast = bench.two_pipe_roofline(1.0, 10, dict(peaks, mulwide_per_sm_clk=64.0))
+    assert r_fast["slots_per_site_per_pipe"] == pytest.approx(7.6)
 
 
 def test_default_arguments(monkeypatch):

@@ -385,6 +385,36 @@ def test_graphs_with_short_pieces_equal_fused_launches(ising, L):
     assert a[3] == b[3] == 64
 
 
+def test_graphs_with_short_pieces_match_oracle(ising):
+    """The graph replays with short drawn pieces against the oracle:
+    L = 2600 (6 sweeps per piece) with a record after each of 32 sweeps (one
+    replay of the record graph, six pieces), L = 3000 (4 sweeps per piece)
+    with a record every 2nd sweep (one replay of 16 records), and L = 2600
+    through the no-record graph (32 sweeps) followed by 2 recorded sweeps:
+    E/M at every record and the final spins."""
+    seed, beta = 23, 0.43
+    cases = [(2600, 32, 1, False), (3000, 32, 2, False), (2600, 34, 1, True)]
+    got = []
+    for L, n, every, plain_graph in cases:
+        with ising.Lattice(L, seed) as lat:
+            lat.set_path(ising.ISING_PATH_LAUNCHES)
+            lat.init_hot()
+            lat.set_beta(beta)
+            if plain_graph:
+                lat.sweep(32)
+                E, M = lat.sweep_record(n - 32, every)
+            else:
+                E, M = lat.sweep_record(n, every)
+            got.append((E, M, lat.get_spins()))
+    ora = oracle.run_jobs([(L, seed, beta, True, n, every) for (L, n, every, _) in cases])
+    for (E, M, S), (Eo, Mo, so), (L, n, every, plain_graph) in zip(got, ora, cases):
+        if plain_graph:
+            Eo, Mo = Eo[-len(E):], Mo[-len(M):]
+        np.testing.assert_array_equal(E, Eo)
+        np.testing.assert_array_equal(M, Mo)
+        np.testing.assert_array_equal(S, so)
+
+
 def test_graph_replays_match_oracle(ising):
     L, seed, beta = 1026, 6, 0.44
     with ising.Lattice(L, seed) as lat:

@@ -45,16 +45,41 @@ def test_mix_equals_alone(serving):
             res = srv.wait(r.id)
             assert res.status == 0 and serving.STATES[res.state] == "done"
             assert res.sweeps_done == r.sweeps
-    for r, (L, b, s, n, e, hot) in zip(reqs, specs):
+    # every served job (all L <= 512) against the oracle, and against the same job alone
+    ora = oracle.run_jobs([(L, s, b, hot, n, e) for (L, b, s, n, e, hot) in specs])
+    for r, (L, b, s, n, e, hot), (Eo, Mo, so) in zip(reqs, specs, ora):
+        np.testing.assert_array_equal(r.E, Eo)
+        np.testing.assert_array_equal(r.M, Mo)
+        np.testing.assert_array_equal(r.spins, so)
         E, M, S = alone(L, b, s, n, e, hot)
         np.testing.assert_array_equal(r.E, E)
-        np.testing.assert_array_equal(r.M, M)
         np.testing.assert_array_equal(r.spins, S)
-        if L <= 64:
-            so = oracle.init_hot(L, s) if hot else oracle.init_cold(L, 1)
-            Eo, Mo = oracle.run(so, s, b, 0, n, e)
-            np.testing.assert_array_equal(r.E, Eo)
-            np.testing.assert_array_equal(r.spins, so)
+
+
+def test_large_served_jobs_equal_oracle(serving):
+    """Sixteen served jobs of L = 1024 .. 4096 (the serving stream's large
+    sizes), 4 to 8 sweeps each, run in one mix with small jobs and compared
+    with the oracle: E, M every sweep and the final spins."""
+    rng = np.random.default_rng(17)
+    specs = []
+    for k in range(16):
+        L = [1024, 2048, 4096][k % 3] if k < 15 else 4096
+        n = 8 if L == 1024 else (6 if L == 2048 else 4)
+        specs.append((L, float(rng.uniform(1 / 3.5, 1 / 1.5)), int(rng.integers(1, 2**62)), n, 1, bool(k % 4)))
+    small = [serving.Request(64, 0.44, 100 + k, 300, 10) for k in range(6)]
+    reqs = [serving.Request(L, b, s, n, e, hot, want_spins=True) for (L, b, s, n, e, hot) in specs]
+    with serving.Server(2 << 30, max_jobs=32, epoch_sweeps=3) as srv:
+        for k, r in enumerate(reqs):
+            srv.submit(r)
+            if k < len(small):
+                srv.submit(small[k])
+        for r in reqs + small:
+            assert srv.wait(r.id).status == 0
+    ora = oracle.run_jobs([(L, s, b, hot, n, e) for (L, b, s, n, e, hot) in specs])
+    for r, (Eo, Mo, so) in zip(reqs, ora):
+        np.testing.assert_array_equal(r.E, Eo)
+        np.testing.assert_array_equal(r.M, Mo)
+        np.testing.assert_array_equal(r.spins, so)
 
 
 def test_jobs_arriving_while_others_run_overlap(serving):
@@ -121,3 +146,82 @@ def test_cancel_timeout_and_bad_jobs(serving):
         srv.release(long.id)
         with pytest.raises(p.IsingError):
             srv.poll(long.id)
+
+
+def test_boundary_create_form_serves_a_job(serving):
+    """ising_server_create(budget, &srv): the two-argument form of the
+    boundary, with the default limits, serves a job bit-exactly."""
+    with serving.Server(64 << 20) as srv:
+        r = serving.Request(96, 0.4, 21, 60, 4, want_spins=True)
+        srv.submit(r)
+        res = srv.wait(r.id)
+        assert res.status == 0 and res.sweeps_done == 60
+    so = oracle.init_hot(96, 21)
+    Eo, Mo = oracle.run(so, 21, 0.4, 0, 60, 4)
+    np.testing.assert_array_equal(r.E, Eo)
+    np.testing.assert_array_equal(r.M, Mo)
+    np.testing.assert_array_equal(r.spins, so)
+
+
+def test_cancel_then_release_keeps_serving(serving):
+    """A queued job that is cancelled and then released leaves no trace: the
+    worker skips its id, later jobs still run, and the totals count only the
+    jobs that ran."""
+    with serving.Server(256 << 20, max_jobs=1, epoch_sweeps=10) as srv:
+        long = serving.Request(1024, 0.44, 1, 4000, 1000)
+        queued = serving.Request(64, 0.44, 2, 10)
+        srv.submit(long)
+        srv.submit(queued)
+        srv.cancel(queued.id)
+        srv.release(queued.id)
+        after = serving.Request(64, 0.44, 3, 20, 2)
+        srv.submit(after)
+        assert srv.wait(long.id).status == 0
+        assert srv.wait(after.id).status == 0
+        st = srv.stats()
+        assert st["jobs_done"] == 2
+        assert st["spin_updates"] == 1024 * 1024 * 4000 + 64 * 64 * 20
+    so = oracle.init_hot(64, 3)
+    Eo, Mo = oracle.run(so, 3, 0.44, 0, 20, 2)
+    np.testing.assert_array_equal(after.E, Eo)
+    np.testing.assert_array_equal(after.M, Mo)
+
+
+def test_injected_worker_fault(serving):
+    """A host exception thrown in the worker between epochs (the test hook;
+    nothing faults on the device): the running jobs are reported failed with
+    ISING_EINTERNAL, their arena blocks come back, the queued job is then
+    admitted and runs bit-exactly, and destroy returns."""
+    import paper_1811_04384_gb300 as p
+    per_job = 2 * 512 * 14 * 8                 # L = 512: both colours, pitch 14
+    budget = 2 * per_job + 4096                # room for two such jobs at a time
+    srv = serving.Server(budget, max_jobs=4, epoch_sweeps=10)
+    try:
+        a = serving.Request(512, 0.44, 1, 100000, 1000)
+        b = serving.Request(512, 0.44, 2, 100000, 1000)
+        c = serving.Request(512, 0.44, 3, 40, 4)
+        srv.submit(a)
+        srv.submit(b)
+        for _ in range(5000):
+            if all(serving.STATES[srv.poll(r.id).state] == "running" for r in (a, b)):
+                break
+            time.sleep(0.001)
+        assert all(serving.STATES[srv.poll(r.id).state] == "running" for r in (a, b))
+        srv.submit(c)                          # no arena room until a or b leaves
+        assert serving.STATES[srv.poll(c.id).state] == "queued"
+        srv.inject_fault(0)
+        for r in (a, b):
+            res = srv.wait(r.id, timeout_ms=60000)
+            assert serving.STATES[res.state] == "failed"
+            assert res.status == p.ISING_EINTERNAL
+        res = srv.wait(c.id, timeout_ms=60000)
+        assert res.status == 0 and serving.STATES[res.state] == "done"
+        assert srv.stats()["jobs_done"] == 1
+    finally:
+        t0 = time.perf_counter()
+        srv.close()
+        assert time.perf_counter() - t0 < 30
+    so = oracle.init_hot(512, 3)
+    Eo, Mo = oracle.run(so, 3, 0.44, 0, 40, 4)
+    np.testing.assert_array_equal(c.E, Eo)
+    np.testing.assert_array_equal(c.M, Mo)
