@@ -459,9 +459,9 @@ int ising_batch_autotune(int32_t n, const int32_t *L, const double *beta, const 
 /* Throughput probe of the integer instructions the sweep is made of, for the
  * roofline (no counterpart in the paper): on the current device, one block
  * of 1024 threads per SM runs 8 independent dependency chains per thread of
- * (a) 32x32 -> 64-bit multiply-adds (the Philox product, both halves),
- * (b) 32-bit multiply-adds and (c) three-input XORs, timed with the SM's
- * cycle counter.  Outputs (any may be NULL): lane operations per SM per clock
+ * (a) 32x32 -> 64-bit products as a Philox round forms them (both halves,
+ * folded back by an XOR on the other pipe), (b) 32-bit multiply-adds and
+ * (c) three-input logic ops, timed with the SM's cycle counter.  Outputs (any may be NULL): lane operations per SM per clock
  * of each kind (the median over the SMs), and the SM count.  Takes a few
  * milliseconds; allocates and frees about 0.6 MB of device memory and
  * synchronises the device.  Errors: ENOMEM, ECUDA. */

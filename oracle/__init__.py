@@ -8,7 +8,8 @@ and shares nothing with the CUDA library.
 Every function cites the part of Hassani & Rafibakhsh (arXiv:1811.04384) it
 follows: Eq. 1 (Hamiltonian), Sec. 2 (Metropolis rule), Eq. 3 and Table 1
 (group value a and dE = 8 - 4a), Sec. 5.3 (energy as right + down bonds),
-Eq. 2 (averages over iterations).
+Eq. 2 (averages over iterations), Sec. 4-5 and Appendix A (the paper's own
+chain of random memory-word updates in two column phases, rw_*).
 """
 from __future__ import annotations
 
@@ -77,6 +78,17 @@ def _load():
                                  ctypes.c_double, i64p]),
             "ora_run": (None, [ctypes.c_int, i8p, ctypes.c_uint64, ctypes.c_double,
                                ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, i64p, i64p]),
+            "ora_rw_select": (None, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+            "ora_rw_step": (None, [ctypes.c_int, ctypes.c_int, i8p, ctypes.c_uint64, ctypes.c_uint64,
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
+                                   u64p, i64p]),
+            "ora_rw_iteration": (None, [ctypes.c_int, ctypes.c_int, i8p, ctypes.c_uint64, ctypes.c_uint64,
+                                        ctypes.c_int, u64p, ctypes.c_int, i64p]),
+            "ora_rw_run": (None, [ctypes.c_int, ctypes.c_int, i8p, ctypes.c_uint64, ctypes.c_double,
+                                  ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, i64p, i64p,
+                                  i64p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -254,6 +266,68 @@ def run(s: np.ndarray, seed: int, beta: float, t0: int, n: int, every: int = 1):
     M = np.zeros(max(k, 1), dtype=np.int64)
     _load().ora_run(L, _ptr(s, ctypes.c_int8), seed, float(beta), t0, n, every,
                     _ptr(E, ctypes.c_int64), _ptr(M, ctypes.c_int64))
+    return E[:k], M[:k]
+
+
+# --- the paper's own chain: random memory words (Sec. 4-5, Appendix A) ----------
+
+def rw_check(L: int, F: int, nstrips: int):
+    assert 1 <= F <= 22 and L % F == 0 and L // F >= (2 if F > 1 else 1), (L, F)
+    assert nstrips >= 1 and L % nstrips == 0 and L // nstrips >= 2, (L, nstrips)
+
+
+def rw_select(seed: int, t: int, phase: int, strip: int, step: int, N: int, col0: int, h: int):
+    """(row, column) of the word that update `step` of strip `strip` in phase
+    `phase` of iteration t picks from the half strip [col0, col0 + h)."""
+    I, J = ctypes.c_int(), ctypes.c_int()
+    _load().ora_rw_select(seed, t, phase, strip, step, N, col0, h, ctypes.byref(I), ctypes.byref(J))
+    return I.value, J.value
+
+
+def rw_step(s: np.ndarray, seed: int, t: int, phase: int, strip: int, step: int, col0: int, h: int,
+            thr0: int, thr1: int, F: int = 21) -> None:
+    """One word update of the random-word chain in place: update `step` of
+    strip `strip` in phase `phase` of iteration t, on the half strip
+    [col0, col0 + h), with the integer thresholds given directly."""
+    L = s.shape[0]
+    _check(L, s)
+    thr = np.array([thr0, thr1], dtype=np.uint64)
+    _load().ora_rw_step(L, F, _ptr(s, ctypes.c_int8), seed, t, phase, strip, step, col0, h,
+                        _ptr(thr, ctypes.c_uint64), None)
+
+
+def rw_iteration(s: np.ndarray, seed: int, t: int, beta: float, nstrips: int, F: int = 21,
+                 reverse: bool = False, stats: np.ndarray | None = None) -> None:
+    """One iteration t of the random-word chain in place (both phases, every
+    strip); reverse runs the strips of each phase in the opposite order."""
+    L = s.shape[0]
+    _check(L, s)
+    rw_check(L, F, nstrips)
+    thr = np.array(thresholds(beta), dtype=np.uint64)
+    sp = None
+    if stats is not None:
+        assert stats.dtype == np.int64 and stats.shape == (10,)
+        sp = _ptr(stats, ctypes.c_int64)
+    _load().ora_rw_iteration(L, F, _ptr(s, ctypes.c_int8), seed, t, nstrips, _ptr(thr, ctypes.c_uint64),
+                             1 if reverse else 0, sp)
+
+
+def rw_run(s: np.ndarray, seed: int, beta: float, t0: int, n: int, nstrips: int, every: int = 1, F: int = 21,
+           stats: np.ndarray | None = None):
+    """Iterations t0+1 .. t0+n of the random-word chain in place; returns the
+    int64 (E, M) series recorded after iterations t0+every, t0+2*every, ..."""
+    L = s.shape[0]
+    _check(L, s)
+    rw_check(L, F, nstrips)
+    k = n // every if every > 0 else 0
+    E = np.zeros(max(k, 1), dtype=np.int64)
+    M = np.zeros(max(k, 1), dtype=np.int64)
+    sp = None
+    if stats is not None:
+        assert stats.dtype == np.int64 and stats.shape == (10,)
+        sp = _ptr(stats, ctypes.c_int64)
+    _load().ora_rw_run(L, F, _ptr(s, ctypes.c_int8), seed, float(beta), t0, n, every, nstrips,
+                       _ptr(E, ctypes.c_int64), _ptr(M, ctypes.c_int64), sp)
     return E[:k], M[:k]
 
 

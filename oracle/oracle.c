@@ -287,3 +287,129 @@ void ora_run(int L, int8_t *s, uint64_t seed, double beta, uint64_t t0,
         }
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* The paper's own chain: random memory words (Sec. 4 and 5, Appendix A).
+ *
+ * The lattice is L x L with L = F N: the paper packs F = 21 spins into a
+ * memory word and has N word rows.  Memory word (I, J), 0 <= I < N,
+ * 0 <= J < L, holds the spins (I + kN, J), k = 0 .. F-1 (Sec. 3).  With
+ * N >= 2 none of them neighbours another (their rows differ by multiples of
+ * N, and the wrap from I + (F-1)N to I is N rows), so one word update can
+ * decide all F spins from the configuration before it, as the paper's
+ * `update` does.
+ *
+ * One Monte Carlo iteration t: the L word columns are split into nstrips
+ * strips of NC = L / nstrips columns (the paper's processes, Sec. 4);
+ * phase 0 updates the left floor(NC/2) columns of every strip, phase 1 the
+ * remaining ones (Sec. 5.2).  In phase p a strip performs 10 N h_p word
+ * updates, h_p being its number of columns in that phase (the paper's
+ * noOfUpdatesP1 / noOfUpdatesP2: ten times the words of the half), each on
+ * a word drawn uniformly with replacement from the half strip: a row from
+ * 0 .. N-1 and a column from the h_p columns (Appendix A's row and column
+ * generators).  A word update applies the Metropolis rule of Sec. 2 to each
+ * of its spins: with a the number of anti-aligned neighbours (Eq. 3,
+ * Table 1), a >= 2 flips, a in {0, 1} flips iff the spin's draw is below
+ * thr[a].  The strips of one phase never update neighbouring words (a half
+ * strip's neighbour columns belong to the other phase), so the order in
+ * which they run does not change the result; the oracle runs them in order
+ * 0, 1, ... (reverse != 0: in the opposite order, to test that claim).
+ *
+ * Draws (a reading: the paper reseeds ranlux48 from random_device, so its
+ * runs cannot be replayed): update s of strip q in phase p of iteration t
+ * takes the 24 words w[4b + e] of the Philox4x32-10 blocks b = 0 .. 5 with
+ * key (lo32(seed), hi32(seed)) and counter
+ * (s, 8q + b, lo32(t), 2^31 | hi32(t) << 1 | p).  Row I = floor(w[0] N / 2^32),
+ * column = the half strip's first column + floor(w[1] h_p / 2^32), and spin
+ * k of the word uses w[2 + k].  (The top counter bit keeps these draws apart
+ * from the checkerboard chain's for every t < 2^62.)
+ *
+ * stats (may be NULL): int64[10], [0..4] proposals by a, [5..9] flips by a. */
+
+static void rw_draws(uint64_t seed, uint64_t t, int phase, int strip, uint32_t step, uint32_t w[24])
+{
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    for (int b = 0; b < 6; ++b) {
+        uint32_t ctr[4] = { step, (uint32_t)strip * 8u + (uint32_t)b, (uint32_t)t,
+                            0x80000000u | ((uint32_t)(t >> 32) << 1) | (uint32_t)phase };
+        ora_philox4x32_10(ctr, key, w + 4 * b);
+    }
+}
+
+/* The word a draw selects: row and column of the half strip [col0, col0 + h). */
+void ora_rw_select(uint64_t seed, uint64_t t, int phase, int strip, uint32_t step, int N, int col0, int h,
+                   int *I, int *J)
+{
+    uint32_t w[24];
+    rw_draws(seed, t, phase, strip, step, w);
+    *I = (int)(((uint64_t)w[0] * (uint64_t)N) >> 32);
+    *J = col0 + (int)(((uint64_t)w[1] * (uint64_t)h) >> 32);
+}
+
+/* One word update: spins (I + kN, J), k = 0 .. F-1, decided together. */
+static void rw_update_word(int L, int F, int8_t *s, int I, int J, const uint32_t w[24],
+                           const uint64_t thr[2], int64_t *stats)
+{
+    const int N = L / F;
+    int flip[22];
+    for (int k = 0; k < F; ++k) {
+        int i = I + k * N;
+        int a = ora_group_value(L, s, i, J);
+        if (a >= 2) flip[k] = 1;
+        else flip[k] = ((uint64_t)w[2 + k] < thr[a]);
+        if (stats) {
+            stats[a] += 1;
+            stats[5 + a] += flip[k];
+        }
+    }
+    for (int k = 0; k < F; ++k)
+        if (flip[k]) s[(I + k * N) * L + J] = (int8_t)(-s[(I + k * N) * L + J]);
+}
+
+/* Update `step` of strip q in phase p of iteration t: choose the word in the
+ * half strip [col0, col0 + h), then update it. */
+void ora_rw_step(int L, int F, int8_t *s, uint64_t seed, uint64_t t, int phase, int q, uint32_t step,
+                 int col0, int h, const uint64_t thr[2], int64_t *stats)
+{
+    const int N = L / F;
+    uint32_t w[24];
+    rw_draws(seed, t, phase, q, step, w);
+    const int I = (int)(((uint64_t)w[0] * (uint64_t)N) >> 32);
+    const int J = col0 + (int)(((uint64_t)w[1] * (uint64_t)h) >> 32);
+    rw_update_word(L, F, s, I, J, w, thr, stats);
+}
+
+void ora_rw_iteration(int L, int F, int8_t *s, uint64_t seed, uint64_t t, int nstrips,
+                      const uint64_t thr[2], int reverse, int64_t *stats)
+{
+    const int N = L / F;
+    const int NC = L / nstrips;
+    for (int phase = 0; phase < 2; ++phase) {
+        const int h = phase == 0 ? NC / 2 : NC - NC / 2;
+        const uint32_t updates = 10u * (uint32_t)N * (uint32_t)h;
+        for (int n = 0; n < nstrips; ++n) {
+            const int q = reverse ? nstrips - 1 - n : n;
+            const int col0 = q * NC + (phase == 0 ? 0 : NC / 2);
+            for (uint32_t step = 0; step < updates; ++step)
+                ora_rw_step(L, F, s, seed, t, phase, q, step, col0, h, thr, stats);
+        }
+    }
+}
+
+/* Iterations t0+1 .. t0+n at inverse temperature beta; E, M after every
+ * `every`-th iteration (n / every entries), as ora_run does for sweeps. */
+void ora_rw_run(int L, int F, int8_t *s, uint64_t seed, double beta, uint64_t t0, int64_t n,
+                int64_t every, int nstrips, int64_t *E, int64_t *M, int64_t *stats)
+{
+    uint64_t thr[2];
+    ora_thresholds(beta, thr);
+    int64_t k = 0;
+    for (int64_t it = 1; it <= n; ++it) {
+        ora_rw_iteration(L, F, s, seed, t0 + (uint64_t)it, nstrips, thr, 0, stats);
+        if (every > 0 && it % every == 0) {
+            E[k] = ora_energy(L, s);
+            M[k] = ora_magnetization(L, s);
+            ++k;
+        }
+    }
+}

@@ -163,21 +163,19 @@ constexpr int kProbeIters = 2048;
 constexpr int kProbeThreads = 1024;
 constexpr int kProbeSmem = 160 * 1024;
 
-// KIND 0: 32x32 -> 64-bit multiply-add (a Philox product: both halves);
-// KIND 1: 32-bit multiply-add (low half only); KIND 2: three-input XOR.
+// KIND 0: the 32x32 -> 64-bit product of a Philox round (both halves);
+// KIND 1: 32-bit multiply-add (low half only); KIND 2: three-input logic.
 template <int KIND>
 __global__ void __launch_bounds__(kProbeThreads, 1)
 int_pipe_probe_kernel(uint32_t seed, uint32_t* sink, long long* cycles)
 {
     extern __shared__ uint32_t probe_pad[];
-    uint64_t acc[kProbeChains];
     uint32_t x[kProbeChains], y[kProbeChains], z[kProbeChains];
 #pragma unroll
     for (int c = 0; c < kProbeChains; ++c) {
         x[c] = seed ^ (threadIdx.x * kProbeChains + c);
         y[c] = x[c] * 0x9E3779B9u;
         z[c] = x[c] ^ 0xBB67AE85u;
-        acc[c] = x[c];
     }
     if (threadIdx.x == 0) probe_pad[0] = seed;
     __syncthreads();
@@ -187,11 +185,17 @@ int_pipe_probe_kernel(uint32_t seed, uint32_t* sink, long long* cycles)
 #pragma unroll
         for (int c = 0; c < kProbeChains; ++c) {
             if (KIND == 0) {
-                acc[c] = (uint64_t)(uint32_t)acc[c] * 0xD2511F53u + acc[c];
+                // the Philox round's product: both halves of M x, folded back
+                // into x by an XOR (which issues on the other pipe)
+                uint32_t hi, lo;
+                ising::mul_hilo(ising::kPhiloxM0, x[c], hi, lo);
+                x[c] = hi ^ lo;
             } else if (KIND == 1) {
                 x[c] = x[c] * x[c] + y[c];           // a square: no two steps fold into one
             } else {
-                const uint32_t n = x[c] ^ y[c] ^ z[c];
+                // (x & y) ^ z: one three-input logic op, not linear, so no
+                // sequence of steps simplifies into fewer
+                const uint32_t n = (x[c] & y[c]) ^ z[c];
                 x[c] = y[c];
                 y[c] = z[c];
                 z[c] = n;
@@ -202,7 +206,7 @@ int_pipe_probe_kernel(uint32_t seed, uint32_t* sink, long long* cycles)
     const long long t1 = clock64();
     uint32_t r = probe_pad[0];
 #pragma unroll
-    for (int c = 0; c < kProbeChains; ++c) r ^= (uint32_t)acc[c] ^ (uint32_t)(acc[c] >> 32) ^ x[c] ^ y[c] ^ z[c];
+    for (int c = 0; c < kProbeChains; ++c) r ^= x[c] ^ y[c] ^ z[c];
     sink[blockIdx.x * kProbeThreads + threadIdx.x] = r;
     if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }

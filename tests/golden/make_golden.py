@@ -23,7 +23,7 @@ def main():
         e, m, _, _ = exact.exact_means(4, beta)
         lines.append(f"enum_e_per_spin 4 {beta!r} {e!r}")
         lines.append(f"enum_absm_per_spin 4 {beta!r} {m!r}")
-    for L, beta in ((16, BETA_TC), (8, 0.3), (8, 0.6)):
+    for L, beta in ((16, BETA_TC), (8, 0.3), (8, 0.6), (42, 0.3), (42, 0.6), (42, BETA_TC)):
         lines.append(f"kaufman_e_per_spin {L} {beta!r} {exact.kaufman_energy(L, beta)!r}")
     for T in (1.0, 1.5, 2.0, 2.5, 3.0, 3.5):
         beta = 1.0 / T
