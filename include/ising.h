@@ -261,6 +261,32 @@ int ising_set_item_lanes(ising_lattice *h, int32_t lanes);
 #define ISING_PATH_RESIDENT 2
 int ising_set_path(ising_lattice *h, int32_t path);
 
+/* Which Markov chain ising_sweep and ising_sweep_record run.
+ * ISING_CHAIN_CHECKERBOARD (default): the checkerboard sweeps of the
+ * conventions above (nstrips ignored).  ISING_CHAIN_RANDOM_WORDS: the paper's
+ * own chain (Sec. 4 and 5, Appendix A), on a column-interleaved lattice only
+ * (EINVAL otherwise): memory word (I, J) holds the spins (I + kN, J),
+ * k = 0..20, N = L / 21; the L word columns form nstrips strips of
+ * NC = L / nstrips >= 2 columns (the paper's processes; nstrips = 1 is its
+ * one-process program); an iteration is phase 0, in which every strip
+ * performs 10 N floor(NC/2) updates of words drawn uniformly with
+ * replacement from its left floor(NC/2) columns, then phase 1 on its other
+ * NC - floor(NC/2) columns.  An update applies the Metropolis rule to all 21
+ * spins of its word at once.  Draws: update s of strip q in phase p of
+ * iteration t takes the 24 words w[4b + e] of the Philox4x32-10 blocks
+ * b = 0..5 with key (lo32(seed), hi32(seed)) and counter
+ * (s, 8q + b, lo32(t), 2^31 | hi32(t) << 1 | p): row floor(w[0] N / 2^32),
+ * column floor(w[1] h / 2^32) of the half strip's h columns, and w[2 + k]
+ * for spin k (always 10 rounds, whatever ising_set_rng chose).  With this
+ * chain the functions' "sweep" is the paper's iteration (10 update attempts
+ * per spin on average, Table 2), and t counts iterations.  The strips of a
+ * phase run in parallel, each strip's updates in its own sequence order, so
+ * the result equals the sequential chain's.  Errors: EINVAL (bad chain,
+ * nstrips not dividing L or L / nstrips < 2, a row-packed lattice). */
+#define ISING_CHAIN_CHECKERBOARD 0
+#define ISING_CHAIN_RANDOM_WORDS 1
+int ising_set_chain(ising_lattice *h, int32_t chain, int32_t nstrips);
+
 /* Random-number scheme of the sweeps.  ISING_RNG_PHILOX4X32_10 (default) is
  * the generator of the conventions above.  ISING_RNG_PHILOX4X32_7 is an
  * opt-in cheaper member of the same family: the same keying and counters,

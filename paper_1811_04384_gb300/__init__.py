@@ -30,6 +30,8 @@ ISING_LAYOUT_ROW_PACKED = 0
 ISING_LAYOUT_COLUMN_INTERLEAVED = 1
 ISING_RNG_PHILOX4X32_10 = 0
 ISING_RNG_PHILOX4X32_7 = 1
+ISING_CHAIN_CHECKERBOARD = 0
+ISING_CHAIN_RANDOM_WORDS = 1
 ISING_PATH_AUTO = 0
 ISING_PATH_LAUNCHES = 1
 ISING_PATH_RESIDENT = 2
@@ -186,6 +188,11 @@ class Lattice:
     def set_rng(self, scheme: int):
         """ISING_RNG_PHILOX4X32_10 (default) or the opt-in ISING_RNG_PHILOX4X32_7."""
         _check(load().ising_set_rng(self._h, int(scheme)), "ising_set_rng")
+
+    def set_chain(self, chain: int, nstrips: int = 1):
+        """ISING_CHAIN_CHECKERBOARD (default) or the paper's ISING_CHAIN_RANDOM_WORDS
+        with `nstrips` column strips (column-interleaved lattices only)."""
+        _check(load().ising_set_chain(self._h, int(chain), int(nstrips)), "ising_set_chain")
 
     def set_path(self, path: int):
         """ISING_PATH_AUTO, ISING_PATH_LAUNCHES or ISING_PATH_RESIDENT."""

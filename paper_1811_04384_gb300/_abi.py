@@ -65,6 +65,7 @@ SYMBOLS = {
     "ising_device_words": (_int, [_vp, _i32, _pvp]),
     "ising_set_path": (_int, [_vp, _i32]),
     "ising_set_rng": (_int, [_vp, _i32]),
+    "ising_set_chain": (_int, [_vp, _i32, _i32]),
     "ising_philox_blocks": (_int, [_u64, _pu32, _pu32, _i64]),
     "ising_batch_create": (_int, [_i32, _pi32, _pd, _pu64, _pu8, _pvp]),
     "ising_batch_destroy": (_int, [_vp]),

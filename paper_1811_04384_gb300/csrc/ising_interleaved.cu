@@ -194,9 +194,169 @@ ci_half_sweep_kernel(uint64_t* __restrict__ S, int L, int N, SweepArgs a, const 
     }
 }
 
+// ---- The paper's own chain: random memory words (Sec. 4-5, Appendix A) ----
+// One phase of one Monte Carlo iteration: each block is one strip (the
+// paper's process) and runs that strip's sequence of 10 N h word updates on
+// its half strip [col0, col0 + h) in sequence order, where update s picks
+// the word drawn from (seed, t, phase, strip, s) and applies the Metropolis
+// rule to its 21 spins.  Strips of one phase touch no common or neighbouring
+// words, so the blocks are independent.
+//
+// Within a strip the updates run as a window of kRwWindow pending ones, in
+// sequence order (slot 0 the oldest).  In each round every pending update
+// whose word and four neighbour words no older pending update touches runs;
+// the others wait for the next round, and the freed slots take the next
+// updates of the sequence.  An update that runs has every older update on
+// its word or a neighbouring word already applied, and none of the updates
+// of one round reads a word another one writes, so the result is the
+// sequential chain's, word for word.  The oldest pending update can always
+// run, so every round makes progress and the loop ends after at most 10 N h
+// rounds.  "Touches" is tracked in a shared-memory table of kRwBuckets
+// claims indexed by the word's index in the half strip modulo kRwBuckets: two
+// words sharing a bucket only make an update wait longer, never run early.
+// A slot's draws (the chosen word and the accept masks of its 21 spins)
+// depend on the update's counter only, so they are made when the update
+// enters the window and move with it.
+constexpr int kRwWindow = 256;
+constexpr int kRwBuckets = 8192;
+
+// The 24 draw words of update `step` (6 Philox4x32-10 blocks) reduced to
+// the chosen word (row I, column jr of the half strip) and the accept masks
+// (draw < thr1 at the spin bit of field k in c1, draw < thr0 in c0).
+__device__ __forceinline__ void rw_draw(const SweepArgs& a, uint32_t step, uint32_t strip, uint32_t tl,
+                                        uint32_t x3, int N, int h, uint32_t& I, uint32_t& jr, uint64_t& c1,
+                                        uint64_t& c0)
+{
+    uint32_t w[24];
+#pragma unroll
+    for (int b = 0; b < 6; ++b) {
+        uint32_t x0 = step, x1 = strip * 8u + (uint32_t)b, x2 = tl, y3 = x3;
+#pragma unroll
+        for (int r = 0; r < 10; ++r) philox_round(x0, x1, x2, y3, a.rk.k0[r], a.rk.k1[r]);
+        w[4 * b] = x0; w[4 * b + 1] = x1; w[4 * b + 2] = x2; w[4 * b + 3] = y3;
+    }
+    I = __umulhi(w[0], (uint32_t)N);
+    jr = __umulhi(w[1], (uint32_t)h);
+    uint64_t m1 = 0, m0 = 0;
+#pragma unroll
+    for (int k = 0; k < 21; ++k) {
+        m1 |= (uint64_t)(w[2 + k] < a.thr1) << (3 * k);
+        m0 |= (uint64_t)(w[2 + k] < a.thr0) << (3 * k);
+    }
+    c1 = m1 | (((uint64_t)a.all1 << 32 | a.all1) & kAllFields);
+    c0 = m0 | (((uint64_t)a.all0 << 32 | a.all0) & kAllFields);
+}
+
+__global__ void __launch_bounds__(kRwWindow)
+ci_rw_phase_kernel(uint64_t* S, int L, int N, int NC, int phase, SweepArgs a)
+{
+    __shared__ uint32_t claim[kRwBuckets];
+    __shared__ uint32_t sl_word[2][kRwWindow];          // I << 16 | column in the half strip
+    __shared__ uint64_t sl_c1[2][kRwWindow], sl_c0[2][kRwWindow];
+    __shared__ uint32_t warp_keep[kRwWindow / 32];
+    const int tid = threadIdx.x;
+    const uint32_t q = blockIdx.x;
+    const int h = phase == 0 ? NC / 2 : NC - NC / 2;
+    const int col0 = (int)q * NC + (phase == 0 ? 0 : NC / 2);
+    const uint32_t U = 10u * (uint32_t)N * (uint32_t)h;
+    const uint64_t t = *a.t_base + a.t_off;
+    const uint32_t tl = (uint32_t)t;
+    const uint32_t x3 = 0x80000000u | ((uint32_t)(t >> 32) << 1) | (uint32_t)phase;
+    constexpr uint32_t B = kRwBuckets - 1;
+    for (int i = tid; i < kRwBuckets; i += kRwWindow) claim[i] = 0xFFFFFFFFu;
+    uint32_t next = 0;
+    int cnt = 0, buf = 0;
+    __syncthreads();
+    for (;;) {
+        // the free slots cnt .. take the next updates of the sequence
+        const uint32_t fill = min((uint32_t)(kRwWindow - cnt), U - next);
+        if (tid >= cnt && (uint32_t)(tid - cnt) < fill) {
+            uint32_t I, jr;
+            uint64_t c1, c0;
+            rw_draw(a, next + (uint32_t)(tid - cnt), q, tl, x3, N, h, I, jr, c1, c0);
+            sl_word[buf][tid] = I << 16 | jr;
+            sl_c1[buf][tid] = c1;
+            sl_c0[buf][tid] = c0;
+        }
+        next += fill;
+        cnt += (int)fill;
+        if (cnt == 0) break;
+        __syncthreads();
+        // every pending update claims its word; the oldest claim wins
+        const bool live = tid < cnt;
+        uint32_t wI = 0, wj = 0, widx = 0;
+        if (live) {
+            const uint32_t word = sl_word[buf][tid];
+            wI = word >> 16;
+            wj = word & 0xFFFFu;
+            widx = wI * (uint32_t)h + wj;
+            atomicMin(&claim[widx & B], (uint32_t)tid);
+        }
+        __syncthreads();
+        // it runs if no older pending update claims its word or a neighbour
+        bool ready = false;
+        if (live) {
+            const uint32_t up = (wI == 0 ? (uint32_t)N - 1 : wI - 1) * (uint32_t)h + wj;
+            const uint32_t dn = (wI == (uint32_t)N - 1 ? 0 : wI + 1) * (uint32_t)h + wj;
+            ready = claim[widx & B] == (uint32_t)tid && claim[up & B] >= (uint32_t)tid &&
+                    claim[dn & B] >= (uint32_t)tid;
+            if (wj > 0) ready = ready && claim[(widx - 1) & B] >= (uint32_t)tid;
+            if (wj + 1 < (uint32_t)h) ready = ready && claim[(widx + 1) & B] >= (uint32_t)tid;
+        }
+        __syncthreads();
+        if (live) claim[widx & B] = 0xFFFFFFFFu;
+        if (ready) {
+            const int J = col0 + (int)wj;
+            uint64_t* row = S + (size_t)wI * L;
+            const uint64_t s = row[J];
+            const uint64_t xl = row[J == 0 ? L - 1 : J - 1];
+            const uint64_t xr = row[J == L - 1 ? 0 : J + 1];
+            const uint64_t xu = wI == 0 ? rotate_up(S[(size_t)(N - 1) * L + J]) : S[(size_t)(wI - 1) * L + J];
+            const uint64_t xd = wI == (uint32_t)N - 1 ? rotate_down(S[J]) : S[(size_t)(wI + 1) * L + J];
+            // Eq. 3: the 3-bit field sums hold a = 0..4 without carries
+            const uint64_t A = (s ^ xu) + (s ^ xd) + (s ^ xl) + (s ^ xr);
+            const uint64_t ge2 = ((A >> 1) | (A >> 2)) & kAllFields;
+            const uint64_t any = (A | (A >> 1) | (A >> 2)) & kAllFields;
+            const uint64_t accept = ge2 | (any & sl_c1[buf][tid]) | (~any & sl_c0[buf][tid]);
+            row[J] = s ^ (accept & kAllFields);
+        }
+        __syncthreads();
+        // the updates that did not run keep their order at the front
+        const bool keep = live && !ready;
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        const int lane = tid & 31, warp = tid >> 5;
+        if (lane == 0) warp_keep[warp] = (uint32_t)__popc(bal);
+        __syncthreads();
+        int off = 0, total = 0;
+#pragma unroll
+        for (int k = 0; k < kRwWindow / 32; ++k) {
+            const int v = (int)warp_keep[k];
+            off += k < warp ? v : 0;
+            total += v;
+        }
+        if (keep) {
+            const int pos = off + __popc(bal & ((1u << lane) - 1u));
+            sl_word[buf ^ 1][pos] = sl_word[buf][tid];
+            sl_c1[buf ^ 1][pos] = sl_c1[buf][tid];
+            sl_c0[buf ^ 1][pos] = sl_c0[buf][tid];
+        }
+        buf ^= 1;
+        cnt = total;
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 bool ci_valid_side(int32_t L) { return L >= 84 && L <= 32760 && L % 84 == 0; }
+
+bool ci_valid_strips(int32_t L, int32_t nstrips) { return nstrips >= 1 && L % nstrips == 0 && L / nstrips >= 2; }
+
+cudaError_t ci_random_words_phase(uint64_t* S, int L, int nstrips, int phase, const SweepArgs& a, cudaStream_t s)
+{
+    ci_rw_phase_kernel<<<nstrips, kRwWindow, 0, s>>>(S, L, L / 21, L / nstrips, phase, a);
+    return cudaGetLastError();
+}
 
 cudaError_t ci_init_hot(uint64_t* S, int L, uint64_t seed, cudaStream_t s)
 {

@@ -59,6 +59,8 @@ struct ising_lattice {
     int rounds = 10;                             // Philox rounds of the sweep draws
     int layout = ISING_LAYOUT_ROW_PACKED;        // or the paper's column-interleaved words
     int item_lanes = 0;                          // lanes per thread item on the launch path (0: auto)
+    int chain = ISING_CHAIN_CHECKERBOARD;        // or the paper's random-word chain (interleaved layout)
+    int nstrips = 1;                             // strips of the random-word chain
     cudaStream_t capture_stream = nullptr;       // graphs of sweep chunks are captured here
     cudaGraphExec_t graph_plain = nullptr;       // kGraphSweeps sweeps, no record
     cudaGraphExec_t graph_rec = nullptr;         // record intervals of graph_rec_every sweeps, each recorded
@@ -602,10 +604,64 @@ extern "C" int ising_set_path(ising_lattice* h, int32_t path)
     return ISING_OK;
 }
 
+// The paper's random-word chain: iterations t+1 .. t+n (relative to the
+// device counter), each its two phases; iteration s (1-based) is followed by
+// an E/M measurement into count slot rec_of(s) when rec_of(s) >= 0.
+template <typename RecOf>
+static int run_random_words(ising_lattice* h, int64_t n, RecOf rec_of)
+{
+    SweepArgs a = base_args(h);
+    for (int64_t it = 1; it <= n; ++it) {
+        a.t_off = (uint32_t)it;
+        a.counts = nullptr;
+        for (int phase = 0; phase < 2; ++phase) {
+            cudaError_t e = ci_random_words_phase(h->words[0], h->g.L, h->nstrips, phase, a, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "ci_rw_phase_kernel");
+        }
+        const int rec = rec_of(it);
+        if (rec >= 0) {
+            a.counts = h->counts + (size_t)rec * kCountSlots * 2;
+            cudaError_t e = ci_half_sweep(1, false, true, h->words[0], h->g.L, a, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "measure");
+        }
+    }
+    if (n > 0) {
+        cudaError_t e = launch_advance_sweep(h->t_dev, (uint64_t)n, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "advance_sweep_kernel");
+        h->t += (uint64_t)n;
+    }
+    return ISING_OK;
+}
+
+extern "C" int ising_set_chain(ising_lattice* h, int32_t chain, int32_t nstrips)
+{
+    if (!h) return ISING_EINVAL;
+    if (chain == ISING_CHAIN_CHECKERBOARD) {
+        h->chain = chain;
+        h->nstrips = 1;
+        return ISING_OK;
+    }
+    if (chain != ISING_CHAIN_RANDOM_WORDS || h->layout != ISING_LAYOUT_COLUMN_INTERLEAVED ||
+        !ci_valid_strips(h->g.L, nstrips))
+        return ISING_EINVAL;
+    h->chain = chain;
+    h->nstrips = nstrips;
+    return ISING_OK;
+}
+
 extern "C" int ising_sweep(ising_lattice* h, int64_t n)
 {
     TraceRange trace("ising_sweep");
     if (!h || n < 0) return ISING_EINVAL;
+    if (h->chain == ISING_CHAIN_RANDOM_WORDS) {
+        while (n > 0) {
+            const int64_t c = n > (1 << 30) ? (1 << 30) : n;
+            int rc = run_random_words(h, c, [](int64_t) { return -1; });
+            if (rc != ISING_OK) return rc;
+            n -= c;
+        }
+        return ISING_OK;
+    }
     if (use_resident(h)) {
         while (n > 0) {
             const int c = (int)std::min<int64_t>(n, 1 << 30);
@@ -647,7 +703,7 @@ extern "C" int ising_sweep_record(ising_lattice* h, int64_t n, int64_t every, in
     if (!h || n < 0 || every < 1 || every > (1 << 22)) return ISING_EINVAL;   // a chunk's offsets fit 32 bits
     const int64_t nrec = n / every;
     int64_t done_rec = 0;
-    if (use_resident(h)) {
+    if (use_resident(h) && h->chain == ISING_CHAIN_CHECKERBOARD) {
         while (done_rec < nrec) {
             // at most 2^30 sweeps a launch
             const int64_t chunk = std::min<int64_t>({nrec - done_rec, (int64_t)kRecordsPerChunk, (1 << 30) / every});
@@ -674,7 +730,11 @@ extern "C" int ising_sweep_record(ising_lattice* h, int64_t n, int64_t every, in
         cudaError_t e = cudaMemsetAsync(h->counts, 0, bytes, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync counts");
         int rc;
-        if (use_graphs(h) && every <= kGraphMaxEvery)
+        if (h->chain == ISING_CHAIN_RANDOM_WORDS)
+            rc = run_random_words(h, chunk * every, [every](int64_t s) {
+                return (s % every == 0) ? (int)(s / every - 1) : -1;
+            });
+        else if (use_graphs(h) && every <= kGraphMaxEvery)
             rc = replay_records(h, chunk, (int)every);
         else
             rc = run_sweeps(h, chunk * every, [every](int64_t s) {
@@ -835,7 +895,8 @@ extern "C" int ising_run_states(ising_lattice* h, const int8_t* const* states, i
         if (!states[k]) return ISING_EINVAL;
     const size_t nn = (size_t)h->g.L * h->g.L;
     const int64_t R = sweeps / every;                          // records per state
-    if (h->layout != ISING_LAYOUT_ROW_PACKED || use_resident(h) || R > kRecordsPerChunk) {
+    if (h->layout != ISING_LAYOUT_ROW_PACKED || use_resident(h) || R > kRecordsPerChunk ||
+        h->chain != ISING_CHAIN_CHECKERBOARD) {
         // no overlap to gain (on-chip path) or records beyond one chunk: the same calls in turn
         for (int32_t k = 0; k < nstates; ++k) {
             int rc = ising_set_spins(h, states[k], nn);

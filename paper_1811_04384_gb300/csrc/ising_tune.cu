@@ -194,11 +194,12 @@ int_pipe_probe_kernel(uint32_t seed, uint32_t* sink, long long* cycles)
                 x[c] = x[c] * x[c] + y[c];           // a square: no two steps fold into one
             } else {
                 // (x & y) ^ z: one three-input logic op, not linear, so no
-                // sequence of steps simplifies into fewer
-                const uint32_t n = (x[c] & y[c]) ^ z[c];
-                x[c] = y[c];
-                y[c] = z[c];
-                z[c] = n;
+                // sequence of steps simplifies into fewer; three steps per
+                // iteration, each overwriting the oldest value, so that no
+                // register moves are needed
+                x[c] = (x[c] & y[c]) ^ z[c];
+                y[c] = (y[c] & z[c]) ^ x[c];
+                z[c] = (z[c] & x[c]) ^ y[c];
             }
         }
     }
@@ -227,7 +228,7 @@ int run_probe(int nsm, uint32_t* sink, long long* d_cycles, double* rate)
     e = cudaMemcpy(cyc.data(), d_cycles, nsm * sizeof(long long), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return ising::cuda_fail(e, "probe cycles");
     std::sort(cyc.begin(), cyc.end());
-    const double ops = (double)kProbeThreads * kProbeChains * kProbeIters;
+    const double ops = (double)kProbeThreads * kProbeChains * kProbeIters * (KIND == 2 ? 3 : 1);
     *rate = cyc[nsm / 2] > 0 ? ops / (double)cyc[nsm / 2] : 0.0;
     return ISING_OK;
 }
