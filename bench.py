@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=None, help="override the workload's sweep count")
     ap.add_argument("--rng", type=int, default=10, choices=[10, 7],
                     help="Philox rounds of the sweep draws: 10 (default scheme) or the opt-in 7")
+    ap.add_argument("--rate", type=float, default=200.0,
+                    help="serving: mean arrival rate of the Poisson request stream (req/s)")
     ap.add_argument("--instances", type=int, default=None,
                     help="batched: compare with per-instance launches on the first N replicas only")
     return ap.parse_args()
@@ -415,7 +417,7 @@ def run_serving(args, ising, local):
     import numpy as np
     from paper_1811_04384_gb300 import serving
     n = args.instances or 400
-    stream = serving.poisson_stream(n, rate=200.0, seed=13)
+    stream = serving.poisson_stream(n, rate=args.rate, seed=13)
     budget = 4 << 30
     with ClockSampler(local) as clocks:
         reqs, stats = serving.serve_stream(stream, budget, max_jobs=256, epoch_sweeps=50, every=1)
@@ -437,12 +439,13 @@ def run_serving(args, ising, local):
     emit({"metric": METRIC, "value": updates / (span * 1e9), "unit": METRIC, "n_gpus": 1, "steps": 1,
           "warmup": 0, "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak",
           "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-          "config": {"workload": f"serving: {n} Poisson arrivals (200 req/s, seed 13), L in {{64..4096}}, "
+          "config": {"workload": f"serving: {n} Poisson arrivals ({args.rate:g} req/s, seed 13), L in {{64..4096}}, "
                                  "T in [1.5,3.5], sweeps log-uniform 100..10000, hot starts, E/M every sweep",
-                     "hbm_budget_bytes": budget, "max_jobs": 256, "epoch_sweeps": 50},
+                     "rate_req_per_s": args.rate, "hbm_budget_bytes": budget, "max_jobs": 256, "epoch_sweeps": 50},
           "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                         "mean": float(lat.mean()), "queue_wait_p50": float(np.percentile(wait, 50))},
           "offered_updates_per_ns": updates / (stream[-1][0] * 1e9),
+          "offered_over_achieved": (updates / stream[-1][0]) / (updates / span),
           "device_busy_updates_per_ns": stats["spin_updates"] / (stats["busy_s"] * 1e9),
           "epochs": stats["epochs"], "all_ok": ok,
           "alone_vs_mix": {"jobs_checked": checked, "bit_exact": exact},
@@ -495,6 +498,7 @@ def run_plain(args, ising, local):
 # The paper's test cases (Table 2): lattice side and iterations; an iteration
 # is 10 update attempts per spin, i.e. 10 sweeps of the checkerboard chain.
 PAPER_CASES = [("case 1", 2016, 5000), ("case 2", 2016, 4500), ("case 3", 1008, 4500)]
+PAPER_STRIPS = 72       # the paper's largest run: 9 nodes x 8 cores, one column strip each
 
 
 def run_paper(args, ising, local):
@@ -531,6 +535,25 @@ def run_paper(args, ising, local):
                 if lname == "row_packed":
                     total_updates += L * L * sweeps
                     total_s += dt
+            # the paper's own chain: random memory-word updates in two column phases,
+            # 72 strips (the paper's largest run, 9 nodes x 8 cores), E/M every iteration
+            with ising.Lattice(L, SEED_LARGE, stream=stream, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
+                lat.init_hot()
+                lat.set_beta(BETA)
+                lat.set_chain(ising.ISING_CHAIN_RANDOM_WORDS, PAPER_STRIPS)
+                lat.sweep_record(2, 1)                           # warm-up (module load)
+                lat.init_hot()
+                lat.t = 0
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                Er, Mr = lat.sweep_record(sweeps // 10, 1)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                dt = e0.elapsed_time(e1) / 1e3
+            entry["random_words"] = {"strips": PAPER_STRIPS, "iterations": sweeps // 10, "seconds": dt,
+                                     "value": L * L * sweeps / (dt * 1e9),
+                                     "E_per_spin_last": float(Er[-1]) / (L * L)}
             entry["bit_exact_across_layouts"] = bool(np.array_equal(series["row_packed"][0],
                                                                     series["column_interleaved"][0]) and
                                                      np.array_equal(series["row_packed"][1],
@@ -542,7 +565,8 @@ def run_paper(args, ising, local):
           "vs_baseline": None, "dtype": "u64", "data": "synthetic",
           "config": {"workload": "paper: the three test cases of Table 2 (L = 2016, 2016, 1008; 5000, 4500, "
                                  "4500 iterations of 10 sweeps), T=2.269, hot start seed 3, E/M every iteration; "
-                                 "value = row-packed layout over all three cases (CUDA events)"},
+                                 "value = row-packed layout over all three cases (CUDA events); each case also "
+                                 "runs the paper's own random-word chain (72 strips) for the same iterations"},
           "cases": cases, "clocks": clocks.summary()})
 
 

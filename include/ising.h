@@ -494,6 +494,20 @@ int ising_batch_autotune(int32_t n, const int32_t *L, const double *beta, const 
 int ising_probe_int_pipes(double *mulwide_per_sm_clk, double *mad32_per_sm_clk, double *lop3_per_sm_clk,
                           int32_t *sm_count);
 
+/* Memory-safety check of the checked build (no counterpart in the paper).  A
+ * library built with -DISING_CHECKED (paper_1811_04384_gb300.build.build(
+ * checked=True), libising_checked.so) range-checks every lattice-word index of
+ * the sweep, apply, batch, on-chip, column-interleaved and random-word
+ * kernels against the array it indexes; an index out of range is not
+ * accessed (loads give 0, stores are dropped, nothing traps) and the first
+ * one is recorded on the device.  *checked = 1 for that build, 0 for the
+ * normal one (whose kernels check nothing).  *first_violation = 0 if no index
+ * was out of range since the previous call, else bit 63 set, the source line
+ * of the access in bits 40..62 and the low 40 bits of the index; the call
+ * clears the record.  Synchronises the device.  Either output may be NULL.
+ * Errors: ECUDA. */
+int ising_check_status(int32_t *checked, uint64_t *first_violation);
+
 /* ---- Allocation-free record path ----------------------------------------
  * The paper has no counterpart to this entry point.  It is for callers that
  * cannot call cudaMalloc: for example a plug-in running inside a host program

@@ -16,7 +16,9 @@ import numpy as np
 from ._abi import declare, SYMBOLS  # noqa: F401
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_build", "libising.so")
+# ISING_LIBRARY selects another build of the library (the checked one,
+# _build/libising_checked.so); the default is the normal build
+LIB_PATH = os.environ.get("ISING_LIBRARY") or os.path.join(_PKG, "_build", "libising.so")
 
 ISING_OK = 0
 ISING_EINVAL = -1
@@ -383,6 +385,14 @@ def philox_blocks(seed: int, ctr: np.ndarray) -> np.ndarray:
                                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), c.shape[0]),
            "ising_philox_blocks")
     return out
+
+
+def check_status() -> tuple[bool, int]:
+    """(checked build?, first out-of-range index record or 0) from
+    ising_check_status; reading clears the record."""
+    c, v = ctypes.c_int32(), ctypes.c_uint64()
+    _check(load().ising_check_status(ctypes.byref(c), ctypes.byref(v)), "ising_check_status")
+    return bool(c.value), int(v.value)
 
 
 def probe_int_pipes() -> dict:

@@ -88,6 +88,7 @@ SYMBOLS = {
     "ising_server_destroy": (_int, [_vp]),
     "ising_autotune": (_int, [_i32, _i32, _pi32, _pi32, _pi32, _pi32, _pd]),
     "ising_probe_int_pipes": (_int, [_pd, _pd, _pd, _pi32]),
+    "ising_check_status": (_int, [_pi32, _pu64]),
     "ising_batch_autotune": (_int, [_i32, _pi32, _pd, _pu64, _pu8, _i64, _i64, _pi32, _pi32, _pi32, _pd]),
     "ising_sweep_record_noalloc": (_int, [_vp, _vp, _i32, _u64, _dbl, _u64, _i64, _i64, _pi64, _pi64, _vp]),
 }

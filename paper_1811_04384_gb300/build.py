@@ -1,10 +1,14 @@
 """Build libising.so (all CUDA sources in csrc/, sm_103a only) in-tree.
 
-    python -m paper_1811_04384_gb300.build
+    python -m paper_1811_04384_gb300.build [--checked]
 
 Each translation unit compiles in parallel with nvcc, then one link step
 writes paper_1811_04384_gb300/_build/libising.so.  No cmake, no torch
 extension machinery: the library exports a plain C ABI (include/ising.h).
+With checked=True (--checked) the same sources compile with -DISING_CHECKED
+into _build/libising_checked.so: every lattice-word index is range-checked
+and an out-of-range one is recorded instead of accessed (ising_check_status).
+Setting ISING_LIBRARY to that file's path makes the binding load it.
 """
 from __future__ import annotations
 
@@ -20,6 +24,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libising.so")
+LIB_CHECKED = os.path.join(BUILD, "libising_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          f"-I{os.path.join(ROOT, 'include')}"]
@@ -41,22 +46,26 @@ def _deps():
         os.path.join(ROOT, "include", "ising.h"), os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(checked: bool = False) -> bool:
+    lib = LIB_CHECKED if checked else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(os.path.join(BUILD, "obj"), exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    if not force and up_to_date(checked):
+        return lib
+    objdir = os.path.join(BUILD, "obj_checked" if checked else "obj")
+    os.makedirs(objdir, exist_ok=True)
     nvcc = _nvcc()
+    extra = ["-DISING_CHECKED"] if checked else []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, "obj", os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(objdir, os.path.basename(src) + ".o")
+        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -67,14 +76,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcuda"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))

@@ -13,6 +13,7 @@
 // other-colour rows i-1 / i+1; left/right are fields m and m-1 of row i when
 // (i + c) is even, fields m and m+1 when it is odd (periodic in m over L/2).
 #pragma once
+#include <cuda_runtime.h>
 #include <cstdint>
 #include "philox.cuh"
 
@@ -63,6 +64,75 @@ __device__ __forceinline__ void pdl_enter()
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
+
+// ---- Checked build (compiled with -DISING_CHECKED) -------------------------
+// Every lattice-word access of the sweep routines goes through word_ld /
+// word_st with the length of the array it indexes.  In a checked build an
+// index at or past that length is not accessed (a load gives 0, a store is
+// dropped) and the first such index is recorded, with the source line of the
+// access, in this translation unit's device word g_check_word; the host reads
+// and clears the words of every translation unit (ising_check_status).
+// Nothing traps or asserts, so a bad index leaves the context usable.  In the
+// normal build these are plain accesses.
+#ifdef ISING_CHECKED
+static __device__ unsigned long long g_check_word;
+
+__device__ __forceinline__ bool check_index(uint64_t idx, uint64_t n, uint32_t line)
+{
+    if (idx < n) return true;
+    atomicCAS(&g_check_word, 0ull, (1ull << 63) | ((uint64_t)(line & 0x7FFFFFu) << 40) | (idx & 0xFFFFFFFFFFull));
+    return false;
+}
+
+// Host side: this translation unit's word, read and cleared (registered with
+// the library's list of readers when the library loads).
+bool register_check_reader(int (*reader)(unsigned long long*));
+static int read_check_word(unsigned long long* out)
+{
+    const unsigned long long zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_check_word, sizeof(zero));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_check_word, &zero, sizeof(zero));
+    return e == cudaSuccess ? 0 : -1;
+}
+static const bool g_check_reader_registered = register_check_reader(&read_check_word);
+#endif
+
+// A lattice word p[idx] of an array of n words: through the read-only cache
+// (LDG) or a plain load.
+template <bool LDG>
+__device__ __forceinline__ uint64_t word_ld(const uint64_t* p, uint64_t idx, uint64_t n, uint32_t line)
+{
+#ifdef ISING_CHECKED
+    if (!check_index(idx, n, line)) return 0;
+#endif
+    return LDG ? __ldg(p + idx) : p[idx];
+}
+
+__device__ __forceinline__ void word_st(uint64_t* p, uint64_t idx, uint64_t v, uint64_t n, uint32_t line)
+{
+#ifdef ISING_CHECKED
+    if (!check_index(idx, n, line)) return;
+#endif
+    p[idx] = v;
+}
+
+__device__ __forceinline__ uint32_t half_ld(const uint32_t* p, uint64_t idx, uint64_t n, uint32_t line)
+{
+#ifdef ISING_CHECKED
+    if (!check_index(idx, n, line)) return 0;
+#endif
+    return p[idx];
+}
+
+__device__ __forceinline__ void half_st(uint32_t* p, uint64_t idx, uint32_t v, uint64_t n, uint32_t line)
+{
+#ifdef ISING_CHECKED
+    if (!check_index(idx, n, line)) return;
+#endif
+    p[idx] = v;
+}
+
+__device__ __forceinline__ uint64_t lattice_words(const Geom& g) { return (uint64_t)g.L * (uint64_t)g.P; }
 
 __device__ __forceinline__ int wrap_row(int i, int L)
 {
@@ -182,18 +252,19 @@ __device__ __forceinline__ void sweep_rows(uint64_t* __restrict__ own, const uin
     const uint32_t wl = (uint32_t)((w > 0) ? w - 1 : g.W - 1);
     const uint32_t wr = (uint32_t)((w < g.W - 1) ? w + 1 : 0);
 
+    const uint64_t n = lattice_words(g);
     // All loads first: their latency overlaps the Philox work below.
     // oc[r] = other-colour row row0 - 1 + r (periodic), column w.
     uint64_t oc[ROWS + 2], sw[ROWS], side[ROWS];
-    oc[0] = GLOBAL ? __ldg(other + up_off) : other[up_off];
+    oc[0] = word_ld<GLOBAL>(other, up_off, n, __LINE__);
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
         if (r < nrows) {
             const uint32_t o = base + (uint32_t)r * P;
-            oc[r + 1] = GLOBAL ? __ldg(other + o) : other[o];
-            sw[r] = own[o];
+            oc[r + 1] = word_ld<GLOBAL>(other, o, n, __LINE__);
+            sw[r] = word_ld<false>(own, o, n, __LINE__);
             const uint32_t os = o - (uint32_t)w + ((((r + C) & 1) == 0) ? wl : wr);   // row0 is a multiple of 4
-            side[r] = GLOBAL ? __ldg(other + os) : other[os];
+            side[r] = word_ld<GLOBAL>(other, os, n, __LINE__);
         } else {
             oc[r + 1] = 0;
             sw[r] = 0;
@@ -201,7 +272,7 @@ __device__ __forceinline__ void sweep_rows(uint64_t* __restrict__ own, const uin
         }
     }
     {
-        const uint64_t dn = GLOBAL ? __ldg(other + dn_off) : other[dn_off];   // row below the last present row
+        const uint64_t dn = word_ld<GLOBAL>(other, dn_off, n, __LINE__);   // row below the last present row
 #pragma unroll
         for (int r = 0; r < ROWS; ++r)
             if (r + 1 == nrows) oc[r + 2] = dn;
@@ -244,7 +315,7 @@ __device__ __forceinline__ void sweep_rows(uint64_t* __restrict__ own, const uin
                 const uint64_t c0 = (((uint64_t)acc.a[r][3] << 32 | acc.a[r][1]) >> 1) | all0;
                 const uint64_t accept = ge2 | (any & c1) | (~any & c0);
                 s_new = s ^ (accept & live);
-                own[base + (uint32_t)r * P] = s_new;
+                word_st(own, base + (uint32_t)r * P, s_new, n, __LINE__);
             }
             if (RECORD) {
                 anti += __popcll((s_new ^ u) & live) + __popcll((s_new ^ d) & live)
@@ -324,22 +395,23 @@ __device__ __forceinline__ void row_apply(uint64_t* __restrict__ own, const uint
 {
     const uint32_t P = (uint32_t)g.P;
     const uint32_t o = (uint32_t)i * P;
-    const uint64_t s = own[o + (uint32_t)w];
-    const uint64_t u = other[(uint32_t)wrap_row(i - 1, g.L) * P + (uint32_t)w];
-    const uint64_t d = other[(uint32_t)wrap_row(i + 1, g.L) * P + (uint32_t)w];
-    const uint64_t h0 = other[o + (uint32_t)w];
+    const uint64_t n = lattice_words(g);
+    const uint64_t s = word_ld<false>(own, o + (uint32_t)w, n, __LINE__);
+    const uint64_t u = word_ld<false>(other, (uint32_t)wrap_row(i - 1, g.L) * P + (uint32_t)w, n, __LINE__);
+    const uint64_t d = word_ld<false>(other, (uint32_t)wrap_row(i + 1, g.L) * P + (uint32_t)w, n, __LINE__);
+    const uint64_t h0 = word_ld<false>(other, o + (uint32_t)w, n, __LINE__);
     // horizontal neighbour at m - 1 ((i + C) even) or m + 1 (odd), as in sweep_rows
     const bool left = ((i + C) & 1) == 0;
     const int ws = left ? ((w > 0) ? w - 1 : g.W - 1) : ((w < g.W - 1) ? w + 1 : 0);
     const int sh = (left ? (w > 0) : (w < g.W - 1)) ? 60 : 3 * (g.rlast - 1);
-    const uint64_t side = other[o + (uint32_t)ws];
+    const uint64_t side = word_ld<false>(other, o + (uint32_t)ws, n, __LINE__);
     const uint64_t h1 = left ? ((h0 << 3) | (side >> sh)) : ((h0 >> 3) | (side << sh));
     const uint64_t x1 = s ^ u, x2 = s ^ d, x3 = s ^ h0, x4 = s ^ h1;
     const uint64_t any = x1 | x2 | x3 | x4;
     const uint64_t ge2 = (x1 & x2) | (x3 & x4) | ((x1 ^ x2) & (x3 ^ x4));
     const uint64_t accept = ge2 | (any & (m1 | all1)) | (~any & (m0 | all0));
     const uint64_t s_new = s ^ (accept & live);
-    own[o + (uint32_t)w] = s_new;
+    word_st(own, o + (uint32_t)w, s_new, n, __LINE__);
     if (RECORD) {
         anti += __popcll((s_new ^ u) & live) + __popcll((s_new ^ d) & live)
               + __popcll((s_new ^ h0) & live) + __popcll((s_new ^ h1) & live);
@@ -361,17 +433,18 @@ __device__ __forceinline__ void row_half_apply(uint64_t* __restrict__ own, const
 {
     const uint32_t P = (uint32_t)g.P;
     const uint32_t o = (uint32_t)i * P;
+    const uint64_t n = lattice_words(g);
     uint32_t* own32 = reinterpret_cast<uint32_t*>(own);
     const uint32_t* other32 = reinterpret_cast<const uint32_t*>(other);
-    const uint32_t s = own32[2 * (o + (uint32_t)w) + hf];
-    const uint32_t u = other32[2 * ((uint32_t)wrap_row(i - 1, g.L) * P + (uint32_t)w) + hf];
-    const uint32_t d = other32[2 * ((uint32_t)wrap_row(i + 1, g.L) * P + (uint32_t)w) + hf];
-    const uint64_t h0w = other[o + (uint32_t)w];
+    const uint32_t s = half_ld(own32, 2 * (o + (uint32_t)w) + hf, 2 * n, __LINE__);
+    const uint32_t u = half_ld(other32, 2 * ((uint32_t)wrap_row(i - 1, g.L) * P + (uint32_t)w) + hf, 2 * n, __LINE__);
+    const uint32_t d = half_ld(other32, 2 * ((uint32_t)wrap_row(i + 1, g.L) * P + (uint32_t)w) + hf, 2 * n, __LINE__);
+    const uint64_t h0w = word_ld<false>(other, o + (uint32_t)w, n, __LINE__);
     // horizontal neighbour at m - 1 ((i + C) even) or m + 1 (odd), as in sweep_rows
     const bool left = ((i + C) & 1) == 0;
     const int ws = left ? ((w > 0) ? w - 1 : g.W - 1) : ((w < g.W - 1) ? w + 1 : 0);
     const int sh = (left ? (w > 0) : (w < g.W - 1)) ? 60 : 3 * (g.rlast - 1);
-    const uint64_t side = other[o + (uint32_t)ws];
+    const uint64_t side = word_ld<false>(other, o + (uint32_t)ws, n, __LINE__);
     const uint64_t h1w = left ? ((h0w << 3) | (side >> sh)) : ((h0w >> 3) | (side << sh));
     const uint32_t h0 = (uint32_t)(h0w >> (32 * hf)), h1 = (uint32_t)(h1w >> (32 * hf));
     const uint32_t x1 = s ^ u, x2 = s ^ d, x3 = s ^ h0, x4 = s ^ h1;
@@ -379,7 +452,7 @@ __device__ __forceinline__ void row_half_apply(uint64_t* __restrict__ own, const
     const uint32_t ge2 = (x1 & x2) | (x3 & x4) | ((x1 ^ x2) & (x3 ^ x4));
     const uint32_t accept = ge2 | (any & (m1 | all1)) | (~any & (m0 | all0));
     const uint32_t s_new = s ^ (accept & live);
-    own32[2 * (o + (uint32_t)w) + hf] = s_new;
+    half_st(own32, 2 * (o + (uint32_t)w) + hf, s_new, 2 * n, __LINE__);
     if (RECORD) {
         anti += __popc((s_new ^ u) & live) + __popc((s_new ^ d) & live) + __popc((s_new ^ h0) & live)
               + __popc((s_new ^ h1) & live);

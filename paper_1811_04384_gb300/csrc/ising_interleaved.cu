@@ -134,6 +134,7 @@ ci_half_sweep_kernel(uint64_t* __restrict__ S, int L, int N, SweepArgs a, const 
     const int q = blockIdx.y * blockDim.y + threadIdx.y;
     uint32_t anti = 0, up = 0;
     if (m < L / 2 && q < N / 4) {
+        const uint64_t n = (uint64_t)N * L;
         uint64_t s[4], xl[4], xr[4], xu[4], xd[4], other[4];
         int J[4];
 #pragma unroll
@@ -142,13 +143,15 @@ ci_half_sweep_kernel(uint64_t* __restrict__ S, int L, int N, SweepArgs a, const 
             J[e] = 2 * m + ((I + C) & 1);
             const int Jl = J[e] == 0 ? L - 1 : J[e] - 1;
             const int Jr = J[e] == L - 1 ? 0 : J[e] + 1;
-            const uint64_t* row = S + (size_t)I * L;
-            s[e] = row[J[e]];
-            xl[e] = __ldg(row + Jl);
-            xr[e] = __ldg(row + Jr);
+            const uint64_t row = (uint64_t)I * L;
+            s[e] = word_ld<false>(S, row + J[e], n, __LINE__);
+            xl[e] = word_ld<true>(S, row + Jl, n, __LINE__);
+            xr[e] = word_ld<true>(S, row + Jr, n, __LINE__);
             other[e] = (J[e] & 1) ? xl[e] : xr[e];    // the other word of the column pair
-            xu[e] = I == 0 ? rotate_up(__ldg(S + (size_t)(N - 1) * L + J[e])) : __ldg(S + (size_t)(I - 1) * L + J[e]);
-            xd[e] = I == N - 1 ? rotate_down(__ldg(S + J[e])) : __ldg(S + (size_t)(I + 1) * L + J[e]);
+            xu[e] = I == 0 ? rotate_up(word_ld<true>(S, (uint64_t)(N - 1) * L + J[e], n, __LINE__))
+                           : word_ld<true>(S, (uint64_t)(I - 1) * L + J[e], n, __LINE__);
+            xd[e] = I == N - 1 ? rotate_down(word_ld<true>(S, (uint64_t)J[e], n, __LINE__))
+                               : word_ld<true>(S, (uint64_t)(I + 1) * L + J[e], n, __LINE__);
         }
         // c1: r < thr1 at the spin bits; c0 >> 1 of the same word: r < thr0 there
         // (its other bits fall on no spin bit and are masked below)
@@ -180,7 +183,7 @@ ci_half_sweep_kernel(uint64_t* __restrict__ S, int L, int N, SweepArgs a, const 
                 const uint64_t any = (A | (A >> 1) | (A >> 2)) & kAllFields;       // a >= 1
                 const uint64_t accept = ge2 | (any & (c1[e] | all1)) | (~any & (c0[e] | all0));
                 sn = s[e] ^ (accept & kAllFields);
-                S[(size_t)I * L + J[e]] = sn;
+                word_st(S, (uint64_t)I * L + J[e], sn, n, __LINE__);
             }
             if (RECORD) {
                 anti += __popcll(sn ^ xu[e]) + __popcll(sn ^ xd[e]) + __popcll(sn ^ xl[e]) + __popcll(sn ^ xr[e]);
@@ -306,19 +309,22 @@ ci_rw_phase_kernel(uint64_t* S, int L, int N, int NC, int phase, SweepArgs a)
         __syncthreads();
         if (live) claim[widx & B] = 0xFFFFFFFFu;
         if (ready) {
+            const uint64_t n = (uint64_t)N * L;
             const int J = col0 + (int)wj;
-            uint64_t* row = S + (size_t)wI * L;
-            const uint64_t s = row[J];
-            const uint64_t xl = row[J == 0 ? L - 1 : J - 1];
-            const uint64_t xr = row[J == L - 1 ? 0 : J + 1];
-            const uint64_t xu = wI == 0 ? rotate_up(S[(size_t)(N - 1) * L + J]) : S[(size_t)(wI - 1) * L + J];
-            const uint64_t xd = wI == (uint32_t)N - 1 ? rotate_down(S[J]) : S[(size_t)(wI + 1) * L + J];
+            const uint64_t row = (uint64_t)wI * L;
+            const uint64_t s = word_ld<false>(S, row + J, n, __LINE__);
+            const uint64_t xl = word_ld<false>(S, row + (J == 0 ? L - 1 : J - 1), n, __LINE__);
+            const uint64_t xr = word_ld<false>(S, row + (J == L - 1 ? 0 : J + 1), n, __LINE__);
+            const uint64_t xu = wI == 0 ? rotate_up(word_ld<false>(S, (uint64_t)(N - 1) * L + J, n, __LINE__))
+                                        : word_ld<false>(S, (uint64_t)(wI - 1) * L + J, n, __LINE__);
+            const uint64_t xd = wI == (uint32_t)N - 1 ? rotate_down(word_ld<false>(S, (uint64_t)J, n, __LINE__))
+                                                      : word_ld<false>(S, (uint64_t)(wI + 1) * L + J, n, __LINE__);
             // Eq. 3: the 3-bit field sums hold a = 0..4 without carries
             const uint64_t A = (s ^ xu) + (s ^ xd) + (s ^ xl) + (s ^ xr);
             const uint64_t ge2 = ((A >> 1) | (A >> 2)) & kAllFields;
             const uint64_t any = (A | (A >> 1) | (A >> 2)) & kAllFields;
             const uint64_t accept = ge2 | (any & sl_c1[buf][tid]) | (~any & sl_c0[buf][tid]);
-            row[J] = s ^ (accept & kAllFields);
+            word_st(S, row + J, s ^ (accept & kAllFields), n, __LINE__);
         }
         __syncthreads();
         // the updates that did not run keep their order at the front

@@ -18,6 +18,29 @@
 
 namespace ising {
 
+// The checked build's readers of each translation unit's out-of-range word
+// (see check_index in ising_device.cuh); a function-local table, so that the
+// registrations made while the library loads need no initialisation order.
+namespace {
+constexpr int kMaxCheckReaders = 16;
+struct CheckReaders {
+    int (*fn[kMaxCheckReaders])(unsigned long long*) = {};
+    int n = 0;
+};
+CheckReaders& check_readers()
+{
+    static CheckReaders r;
+    return r;
+}
+}  // namespace
+
+bool register_check_reader(int (*reader)(unsigned long long*))
+{
+    CheckReaders& r = check_readers();
+    if (r.n < kMaxCheckReaders) r.fn[r.n++] = reader;
+    return true;
+}
+
 // Hot start: s = +1 iff the site's Philox draw at t = 0 is below 2^31.
 // Thread = (4-row group, word, colour).
 __global__ void init_hot_kernel(uint64_t* __restrict__ w0, uint64_t* __restrict__ w1, Geom g,
@@ -652,3 +675,23 @@ cudaError_t launch_resident_premasked(uint64_t* w0, uint64_t* w1, const Geom& g,
 }  // namespace ising
 
 extern "C" const char* ising_last_cuda_error(void) { return ising::g_last_cuda_error; }
+
+extern "C" int ising_check_status(int32_t* checked, uint64_t* first_violation)
+{
+#ifdef ISING_CHECKED
+    if (checked) *checked = 1;
+#else
+    if (checked) *checked = 0;
+#endif
+    if (first_violation) *first_violation = 0;
+    ising::CheckReaders& r = ising::check_readers();
+    if (r.n == 0) return ISING_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return ising::cuda_fail(e, "ising_check_status");
+    for (int k = 0; k < r.n; ++k) {
+        unsigned long long word = 0;
+        if (r.fn[k](&word) != 0) return ising::cuda_fail(cudaGetLastError(), "ising_check_status");
+        if (word && first_violation && *first_violation == 0) *first_violation = word;
+    }
+    return ISING_OK;
+}

@@ -58,6 +58,8 @@ def test_host_only_entry_points(lib):
         assert lib.ising_bytes_required(L) >= 2 * L * P * 8
         assert lib.ising_bytes_required(L) < 2 * L * P * 8 + (1 << 20)
     assert lib.ising_destroy(None) == 0
+    # the normal build checks no indices: the status call touches no device
+    assert p.check_status() == (False, 0)
 
 
 def test_invalid_arguments_are_rejected_before_any_device_call(lib):
