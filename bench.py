@@ -47,7 +47,7 @@ NOMINAL_SM_MAX_MHZ = 2070.0     # used only if neither nvidia-smi nor MEASURED_P
 # DRAM bytes (read + write) per half-sweep launch of the current kernel at
 # L = 16384, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum);
 # None for other sizes and the 7-round scheme.
-MEASURED_TRAFFIC = {16384: 1.112e8}
+MEASURED_TRAFFIC = {16384: 1.103e8}
 MULWIDE_PER_SITE = 4            # Philox4x32-10 with the counter-independent rounds hoisted:
                                 # 16 multiplies per call, one call per 4 sites (10 per call,
                                 # 2.5 per site, for the opt-in 7-round scheme)
