@@ -281,8 +281,14 @@ int ising_set_path(ising_lattice *h, int32_t path);
  * chain the functions' "sweep" is the paper's iteration (10 update attempts
  * per spin on average, Table 2), and t counts iterations.  The strips of a
  * phase run in parallel, each strip's updates in its own sequence order, so
- * the result equals the sequential chain's.  Errors: EINVAL (bad chain,
- * nstrips not dividing L or L / nstrips < 2, a row-packed lattice). */
+ * the result equals the sequential chain's.  Execution: the draws of an
+ * iteration's updates are made first on all SMs, into a buffer of
+ * 160 L^2 / 21 bytes the library allocates on first use (up to 256 MB,
+ * L <= about 5900); with ISING_PATH_LAUNCHES, or above that size, each strip
+ * draws its own updates.  A strip whose words fit in shared memory (N (h + 2)
+ * words <= 160 KB) keeps them there for the phase.  Results are the same on
+ * every form.  Errors: EINVAL (bad chain, nstrips not dividing L or
+ * L / nstrips < 2, a row-packed lattice). */
 #define ISING_CHAIN_CHECKERBOARD 0
 #define ISING_CHAIN_RANDOM_WORDS 1
 int ising_set_chain(ising_lattice *h, int32_t chain, int32_t nstrips);

@@ -217,18 +217,28 @@ ci_half_sweep_kernel(uint64_t* __restrict__ S, int L, int N, SweepArgs a, const 
 // rounds.  "Touches" is tracked in a shared-memory table of kRwBuckets
 // claims indexed by the word's index in the half strip modulo kRwBuckets: two
 // words sharing a bucket only make an update wait longer, never run early.
-// A slot's draws (the chosen word and the accept masks of its 21 spins)
-// depend on the update's counter only, so they are made when the update
-// enters the window and move with it.
+//
+// An update's draws (the chosen word and the accept masks of its 21 spins)
+// depend on its counter only.  ci_rw_draw_kernel makes those of a whole
+// iteration beforehand on all SMs (PRE), so a window slot only loads them;
+// lattices whose draws would pass kRwDrawBytesMax draw them in the block
+// instead, when an update enters the window.  With WIN the block keeps its
+// half strip and the two columns beside it in shared memory for the phase
+// (the columns beside it are not updated in this phase), so a round touches
+// no global memory; strips too wide for shared memory work on the lattice in
+// global memory.
 constexpr int kRwWindow = 256;
+constexpr int kRwRing = 4 * kRwWindow;                  // pre-drawn updates staged ahead in shared memory
 constexpr int kRwBuckets = 8192;
+constexpr size_t kRwWinBytesMax = 160 * 1024;         // dynamic shared memory of the WIN form
+constexpr size_t kRwDrawBytesMax = (size_t)256 << 20;  // pre-drawn updates of one iteration
 
 // The 24 draw words of update `step` (6 Philox4x32-10 blocks) reduced to
 // the chosen word (row I, column jr of the half strip) and the accept masks
-// (draw < thr1 at the spin bit of field k in c1, draw < thr0 in c0).
+// packed in one word: draw < thr1 at the spin bit of field k, draw < thr0
+// one bit above it.
 __device__ __forceinline__ void rw_draw(const SweepArgs& a, uint32_t step, uint32_t strip, uint32_t tl,
-                                        uint32_t x3, int N, int h, uint32_t& I, uint32_t& jr, uint64_t& c1,
-                                        uint64_t& c0)
+                                        uint32_t x3, int N, int h, uint32_t& I, uint32_t& jr, uint64_t& packed)
 {
     uint32_t w[24];
 #pragma unroll
@@ -240,23 +250,53 @@ __device__ __forceinline__ void rw_draw(const SweepArgs& a, uint32_t step, uint3
     }
     I = __umulhi(w[0], (uint32_t)N);
     jr = __umulhi(w[1], (uint32_t)h);
-    uint64_t m1 = 0, m0 = 0;
+    uint64_t m = 0;
 #pragma unroll
-    for (int k = 0; k < 21; ++k) {
-        m1 |= (uint64_t)(w[2 + k] < a.thr1) << (3 * k);
-        m0 |= (uint64_t)(w[2 + k] < a.thr0) << (3 * k);
-    }
-    c1 = m1 | (((uint64_t)a.all1 << 32 | a.all1) & kAllFields);
-    c0 = m0 | (((uint64_t)a.all0 << 32 | a.all0) & kAllFields);
+    for (int k = 0; k < 21; ++k)
+        m |= (uint64_t)(w[2 + k] < a.thr1) << (3 * k) | (uint64_t)(w[2 + k] < a.thr0) << (3 * k + 1);
+    packed = m;
 }
 
+// All updates of iteration *t_base + t_off, both phases: entry
+// draws[phase base + q * U_p + s] = (I << 16 | column in the half strip,
+// packed masks) for update s of strip q; phase 0's entries first.
+__global__ void __launch_bounds__(128)
+ci_rw_draw_kernel(int L, int N, int NC, int nstrips, SweepArgs a, ulonglong2* __restrict__ draws)
+{
+    const int h0 = NC / 2, h1 = NC - NC / 2;
+    const uint64_t U0 = 10ull * N * h0, U1 = 10ull * N * h1;
+    const uint64_t n0 = U0 * nstrips, total = n0 + U1 * nstrips;
+    const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= total) return;
+    const int phase = k < n0 ? 0 : 1;
+    const uint64_t r = phase ? k - n0 : k;
+    const uint64_t U = phase ? U1 : U0;
+    const uint32_t q = (uint32_t)(r / U), step = (uint32_t)(r - (uint64_t)q * U);
+    const uint64_t t = *a.t_base + a.t_off;
+    const uint32_t x3 = 0x80000000u | ((uint32_t)(t >> 32) << 1) | (uint32_t)phase;
+    uint32_t I, jr;
+    uint64_t packed;
+    rw_draw(a, step, q, (uint32_t)t, x3, N, phase ? h1 : h0, I, jr, packed);
+    draws[k] = make_ulonglong2((uint64_t)(I << 16 | jr), packed);
+}
+
+// 16 bytes global -> shared, asynchronously.
+__device__ __forceinline__ void ring_copy(ulonglong2* smem_dst, const ulonglong2* gmem_src)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+template <bool PRE, bool WIN>
 __global__ void __launch_bounds__(kRwWindow)
-ci_rw_phase_kernel(uint64_t* S, int L, int N, int NC, int phase, SweepArgs a)
+ci_rw_phase_kernel(uint64_t* S, int L, int N, int NC, int phase, SweepArgs a, const ulonglong2* __restrict__ draws)
 {
     __shared__ uint32_t claim[kRwBuckets];
     __shared__ uint32_t sl_word[2][kRwWindow];          // I << 16 | column in the half strip
-    __shared__ uint64_t sl_c1[2][kRwWindow], sl_c0[2][kRwWindow];
+    __shared__ uint64_t sl_mask[2][kRwWindow];          // packed masks
     __shared__ uint32_t warp_keep[kRwWindow / 32];
+    __shared__ __align__(16) ulonglong2 ring[PRE ? kRwRing : 1];   // PRE: draws of steps next .. next + kRwRing - 1
+    extern __shared__ __align__(16) uint64_t win[];     // WIN: N rows x (h + 2) words
     const int tid = threadIdx.x;
     const uint32_t q = blockIdx.x;
     const int h = phase == 0 ? NC / 2 : NC - NC / 2;
@@ -265,26 +305,64 @@ ci_rw_phase_kernel(uint64_t* S, int L, int N, int NC, int phase, SweepArgs a)
     const uint64_t t = *a.t_base + a.t_off;
     const uint32_t tl = (uint32_t)t;
     const uint32_t x3 = 0x80000000u | ((uint32_t)(t >> 32) << 1) | (uint32_t)phase;
+    const ulonglong2* my_draws = PRE ? draws + (size_t)q * U : nullptr;   // this phase's block of draws
+    const uint64_t all1 = ((uint64_t)a.all1 << 32 | a.all1) & kAllFields;
+    const uint64_t all0 = ((uint64_t)a.all0 << 32 | a.all0) & kAllFields;
     constexpr uint32_t B = kRwBuckets - 1;
+    const int hw = h + 2;                                // window row: the column before, h, the column after
+    const uint64_t n_lat = (uint64_t)N * L, n_win = (uint64_t)N * hw;
     for (int i = tid; i < kRwBuckets; i += kRwWindow) claim[i] = 0xFFFFFFFFu;
+    if (WIN) {
+        for (int idx = tid; idx < N * hw; idx += kRwWindow) {
+            const int I = idx / hw, jl = idx - I * hw;
+            int J = col0 - 1 + jl;
+            J = J < 0 ? J + L : (J >= L ? J - L : J);
+            word_st(win, (uint64_t)idx, word_ld<false>(S, (uint64_t)I * L + J, n_lat, __LINE__), n_win, __LINE__);
+        }
+    }
+    if (PRE) {
+        // the ring starts with the draws of steps 0 .. kRwRing - 1
+        for (uint32_t j = tid; j < kRwRing && j < U; j += kRwWindow) ring_copy(&ring[j], &my_draws[j]);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
     uint32_t next = 0;
     int cnt = 0, buf = 0;
-    __syncthreads();
     for (;;) {
+        // the draws this round reads were copied at least three rounds ago
+        // (a round takes at most kRwWindow steps and the ring holds
+        // kRwRing = 4 kRwWindow), i.e. in groups older than the last two
+        if (PRE) asm volatile("cp.async.wait_group 2;" ::: "memory");
+        __syncthreads();
         // the free slots cnt .. take the next updates of the sequence
         const uint32_t fill = min((uint32_t)(kRwWindow - cnt), U - next);
         if (tid >= cnt && (uint32_t)(tid - cnt) < fill) {
+            const uint32_t step = next + (uint32_t)(tid - cnt);
             uint32_t I, jr;
-            uint64_t c1, c0;
-            rw_draw(a, next + (uint32_t)(tid - cnt), q, tl, x3, N, h, I, jr, c1, c0);
+            uint64_t packed;
+            if (PRE) {
+                const ulonglong2 d = ring[step & (kRwRing - 1)];
+                I = (uint32_t)d.x >> 16;
+                jr = (uint32_t)d.x & 0xFFFFu;
+                packed = d.y;
+            } else {
+                rw_draw(a, step, q, tl, x3, N, h, I, jr, packed);
+            }
             sl_word[buf][tid] = I << 16 | jr;
-            sl_c1[buf][tid] = c1;
-            sl_c0[buf][tid] = c0;
+            sl_mask[buf][tid] = packed;
         }
         next += fill;
         cnt += (int)fill;
         if (cnt == 0) break;
         __syncthreads();
+        if (PRE) {
+            // refill the ring positions just read with the draws kRwRing
+            // steps on, which arrive while the next rounds run
+            const uint32_t j = (uint32_t)tid;
+            const uint32_t step = next - fill + kRwRing + j;
+            if (j < fill && step < U) ring_copy(&ring[step & (kRwRing - 1)], &my_draws[step]);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
         // every pending update claims its word; the oldest claim wins
         const bool live = tid < cnt;
         uint32_t wI = 0, wj = 0, widx = 0;
@@ -309,22 +387,43 @@ ci_rw_phase_kernel(uint64_t* S, int L, int N, int NC, int phase, SweepArgs a)
         __syncthreads();
         if (live) claim[widx & B] = 0xFFFFFFFFu;
         if (ready) {
-            const uint64_t n = (uint64_t)N * L;
-            const int J = col0 + (int)wj;
-            const uint64_t row = (uint64_t)wI * L;
-            const uint64_t s = word_ld<false>(S, row + J, n, __LINE__);
-            const uint64_t xl = word_ld<false>(S, row + (J == 0 ? L - 1 : J - 1), n, __LINE__);
-            const uint64_t xr = word_ld<false>(S, row + (J == L - 1 ? 0 : J + 1), n, __LINE__);
-            const uint64_t xu = wI == 0 ? rotate_up(word_ld<false>(S, (uint64_t)(N - 1) * L + J, n, __LINE__))
-                                        : word_ld<false>(S, (uint64_t)(wI - 1) * L + J, n, __LINE__);
-            const uint64_t xd = wI == (uint32_t)N - 1 ? rotate_down(word_ld<false>(S, (uint64_t)J, n, __LINE__))
-                                                      : word_ld<false>(S, (uint64_t)(wI + 1) * L + J, n, __LINE__);
+            uint64_t s, xl, xr, xu, xd;
+            uint64_t* dst;
+            uint64_t didx, dn;
+            if (WIN) {
+                const uint64_t row = (uint64_t)wI * hw, jl = wj + 1;
+                s = word_ld<false>(win, row + jl, n_win, __LINE__);
+                xl = word_ld<false>(win, row + jl - 1, n_win, __LINE__);
+                xr = word_ld<false>(win, row + jl + 1, n_win, __LINE__);
+                xu = wI == 0 ? rotate_up(word_ld<false>(win, (uint64_t)(N - 1) * hw + jl, n_win, __LINE__))
+                             : word_ld<false>(win, row - hw + jl, n_win, __LINE__);
+                xd = wI == (uint32_t)N - 1 ? rotate_down(word_ld<false>(win, jl, n_win, __LINE__))
+                                           : word_ld<false>(win, row + hw + jl, n_win, __LINE__);
+                dst = win;
+                didx = row + jl;
+                dn = n_win;
+            } else {
+                const int J = col0 + (int)wj;
+                const uint64_t row = (uint64_t)wI * L;
+                s = word_ld<false>(S, row + J, n_lat, __LINE__);
+                xl = word_ld<false>(S, row + (J == 0 ? L - 1 : J - 1), n_lat, __LINE__);
+                xr = word_ld<false>(S, row + (J == L - 1 ? 0 : J + 1), n_lat, __LINE__);
+                xu = wI == 0 ? rotate_up(word_ld<false>(S, (uint64_t)(N - 1) * L + J, n_lat, __LINE__))
+                             : word_ld<false>(S, (uint64_t)(wI - 1) * L + J, n_lat, __LINE__);
+                xd = wI == (uint32_t)N - 1 ? rotate_down(word_ld<false>(S, (uint64_t)J, n_lat, __LINE__))
+                                           : word_ld<false>(S, (uint64_t)(wI + 1) * L + J, n_lat, __LINE__);
+                dst = S;
+                didx = row + J;
+                dn = n_lat;
+            }
             // Eq. 3: the 3-bit field sums hold a = 0..4 without carries
             const uint64_t A = (s ^ xu) + (s ^ xd) + (s ^ xl) + (s ^ xr);
             const uint64_t ge2 = ((A >> 1) | (A >> 2)) & kAllFields;
             const uint64_t any = (A | (A >> 1) | (A >> 2)) & kAllFields;
-            const uint64_t accept = ge2 | (any & sl_c1[buf][tid]) | (~any & sl_c0[buf][tid]);
-            word_st(S, row + J, s ^ (accept & kAllFields), n, __LINE__);
+            const uint64_t m = sl_mask[buf][tid];
+            const uint64_t c1 = (m & kAllFields) | all1, c0 = ((m >> 1) & kAllFields) | all0;
+            const uint64_t accept = ge2 | (any & c1) | (~any & c0);
+            word_st(dst, didx, s ^ (accept & kAllFields), dn, __LINE__);
         }
         __syncthreads();
         // the updates that did not run keep their order at the front
@@ -343,12 +442,18 @@ ci_rw_phase_kernel(uint64_t* S, int L, int N, int NC, int phase, SweepArgs a)
         if (keep) {
             const int pos = off + __popc(bal & ((1u << lane) - 1u));
             sl_word[buf ^ 1][pos] = sl_word[buf][tid];
-            sl_c1[buf ^ 1][pos] = sl_c1[buf][tid];
-            sl_c0[buf ^ 1][pos] = sl_c0[buf][tid];
+            sl_mask[buf ^ 1][pos] = sl_mask[buf][tid];
         }
         buf ^= 1;
         cnt = total;
-        __syncthreads();
+    }
+    if (WIN) {
+        // the half strip back to the lattice
+        for (int idx = tid; idx < N * h; idx += kRwWindow) {
+            const int I = idx / h, jr = idx - I * h;
+            word_st(S, (uint64_t)I * L + col0 + jr, word_ld<false>(win, (uint64_t)I * hw + jr + 1, n_win, __LINE__),
+                    n_lat, __LINE__);
+        }
     }
 }
 
@@ -358,9 +463,44 @@ bool ci_valid_side(int32_t L) { return L >= 84 && L <= 32760 && L % 84 == 0; }
 
 bool ci_valid_strips(int32_t L, int32_t nstrips) { return nstrips >= 1 && L % nstrips == 0 && L / nstrips >= 2; }
 
-cudaError_t ci_random_words_phase(uint64_t* S, int L, int nstrips, int phase, const SweepArgs& a, cudaStream_t s)
+size_t ci_rw_draw_bytes(int L, int nstrips)
 {
-    ci_rw_phase_kernel<<<nstrips, kRwWindow, 0, s>>>(S, L, L / 21, L / nstrips, phase, a);
+    (void)nstrips;   // every strip draws 10 N per column: 10 N L updates per iteration
+    return (size_t)10 * (L / 21) * L * sizeof(ulonglong2);
+}
+
+bool ci_rw_predraw(int L, int nstrips) { return ci_rw_draw_bytes(L, nstrips) <= kRwDrawBytesMax; }
+
+cudaError_t ci_random_words_iteration(uint64_t* S, int L, int nstrips, const SweepArgs& a, ulonglong2* draws,
+                                      cudaStream_t s)
+{
+    const int N = L / 21, NC = L / nstrips;
+    const size_t win_bytes = (size_t)N * (NC - NC / 2 + 2) * sizeof(uint64_t);
+    const bool win = win_bytes <= kRwWinBytesMax;
+    static bool attr_set = false;   // per process; the attribute is per function
+    if (win && !attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(ci_rw_phase_kernel<true, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRwWinBytesMax);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(ci_rw_phase_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kRwWinBytesMax);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const bool pre = draws != nullptr;
+    if (pre) {
+        const uint64_t total = 10ull * N * L;
+        ci_rw_draw_kernel<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(L, N, NC, nstrips, a, draws);
+    }
+    for (int phase = 0; phase < 2; ++phase) {
+        const int h = phase == 0 ? NC / 2 : NC - NC / 2;
+        const size_t smem = win ? (size_t)N * (h + 2) * sizeof(uint64_t) : 0;
+        const ulonglong2* d = pre ? draws + (phase ? (size_t)10 * N * (NC / 2) * nstrips : 0) : nullptr;
+        if (pre && win) ci_rw_phase_kernel<true, true><<<nstrips, kRwWindow, smem, s>>>(S, L, N, NC, phase, a, d);
+        else if (pre) ci_rw_phase_kernel<true, false><<<nstrips, kRwWindow, 0, s>>>(S, L, N, NC, phase, a, d);
+        else if (win) ci_rw_phase_kernel<false, true><<<nstrips, kRwWindow, smem, s>>>(S, L, N, NC, phase, a, d);
+        else ci_rw_phase_kernel<false, false><<<nstrips, kRwWindow, 0, s>>>(S, L, N, NC, phase, a, d);
+    }
     return cudaGetLastError();
 }
 

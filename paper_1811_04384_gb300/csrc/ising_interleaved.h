@@ -24,11 +24,17 @@ cudaError_t ci_mask_draw(int L, const SweepArgs& a, const uint64_t* t_base, uint
 cudaError_t ci_half_sweep_pre(int colour, bool record, uint64_t* S, int L, const SweepArgs& a,
                               const uint64_t* sweep_masks, cudaStream_t s);
 
-// The paper's random-word chain (Sec. 4-5, Appendix A): phase `phase` (0:
-// the left floor(NC/2) columns of each of the nstrips strips of NC = L /
-// nstrips columns, 1: the rest) of iteration *a.t_base + a.t_off, one block
-// per strip; thresholds and round keys from `a` (always 10 Philox rounds).
+// The paper's random-word chain (Sec. 4-5, Appendix A): iteration
+// *a.t_base + a.t_off, phase 0 (the left floor(NC/2) columns of each of the
+// nstrips strips of NC = L / nstrips columns) then phase 1 (the rest), one
+// block per strip; thresholds and round keys from `a` (always 10 Philox
+// rounds).  With `draws` (ci_rw_draw_bytes(L, nstrips) bytes of device
+// memory; used when ci_rw_predraw(L, nstrips)) the updates' draws are made
+// first on all SMs; with nullptr each block draws its own.
 bool ci_valid_strips(int32_t L, int32_t nstrips);   // nstrips divides L, L / nstrips >= 2
-cudaError_t ci_random_words_phase(uint64_t* S, int L, int nstrips, int phase, const SweepArgs& a, cudaStream_t s);
+size_t ci_rw_draw_bytes(int L, int nstrips);
+bool ci_rw_predraw(int L, int nstrips);
+cudaError_t ci_random_words_iteration(uint64_t* S, int L, int nstrips, const SweepArgs& a, ulonglong2* draws,
+                                      cudaStream_t s);
 
 }  // namespace ising

@@ -61,6 +61,7 @@ struct ising_lattice {
     int item_lanes = 0;                          // lanes per thread item on the launch path (0: auto)
     int chain = ISING_CHAIN_CHECKERBOARD;        // or the paper's random-word chain (interleaved layout)
     int nstrips = 1;                             // strips of the random-word chain
+    ulonglong2* rw_draws = nullptr;              // random-word chain: the draws of one iteration (lazily)
     cudaStream_t capture_stream = nullptr;       // graphs of sweep chunks are captured here
     cudaGraphExec_t graph_plain = nullptr;       // kGraphSweeps sweeps, no record
     cudaGraphExec_t graph_rec = nullptr;         // record intervals of graph_rec_every sweeps, each recorded
@@ -118,6 +119,7 @@ static int setup_handle(ising_lattice* h, int32_t L, uint64_t seed, char* base)
 static void free_handle(ising_lattice* h)
 {
     if (!h) return;
+    if (h->rw_draws) cudaFree(h->rw_draws);
     if (h->staging) cudaFree(h->staging);
     if (h->staging2) cudaFree(h->staging2);
     if (h->masks) cudaFree(h->masks);
@@ -611,13 +613,19 @@ template <typename RecOf>
 static int run_random_words(ising_lattice* h, int64_t n, RecOf rec_of)
 {
     SweepArgs a = base_args(h);
+    // the updates' draws are made first on all SMs unless the launch path was
+    // chosen or the buffer would be too large; then each block draws its own
+    const bool pre = h->path != ISING_PATH_LAUNCHES && ci_rw_predraw(h->g.L, h->nstrips);
+    if (pre && !h->rw_draws) {
+        cudaError_t e = cudaMalloc(&h->rw_draws, ci_rw_draw_bytes(h->g.L, h->nstrips));
+        if (e != cudaSuccess) { h->rw_draws = nullptr; cuda_fail(e, "cudaMalloc random-word draws"); return ISING_ENOMEM; }
+    }
     for (int64_t it = 1; it <= n; ++it) {
         a.t_off = (uint32_t)it;
         a.counts = nullptr;
-        for (int phase = 0; phase < 2; ++phase) {
-            cudaError_t e = ci_random_words_phase(h->words[0], h->g.L, h->nstrips, phase, a, h->stream);
-            if (e != cudaSuccess) return cuda_fail(e, "ci_rw_phase_kernel");
-        }
+        cudaError_t e = ci_random_words_iteration(h->words[0], h->g.L, h->nstrips, a, pre ? h->rw_draws : nullptr,
+                                                  h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "ci_rw_phase_kernel");
         const int rec = rec_of(it);
         if (rec >= 0) {
             a.counts = h->counts + (size_t)rec * kCountSlots * 2;

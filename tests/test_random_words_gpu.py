@@ -57,6 +57,27 @@ def test_random_words_match_oracle(ising, L, nstrips, beta, n, every):
     assert t == n
 
 
+@pytest.mark.parametrize("L,nstrips,path", [(1008, 1, None), (168, 6, "launches"), (1008, 1, "launches")])
+def test_random_words_every_form(ising, L, nstrips, path):
+    """The forms of the kernel: a half strip too wide for shared memory
+    (L = 1008 in one strip: 48 x 506 words) works in global memory; with the
+    launch path each strip draws its own updates instead of reading draws
+    made first on all SMs.  All equal the oracle."""
+    seed = 77 + L
+    with ising.Lattice(L, seed, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
+        if path == "launches":
+            lat.set_path(ising.ISING_PATH_LAUNCHES)
+        lat.init_hot()
+        lat.set_chain(ising.ISING_CHAIN_RANDOM_WORDS, nstrips)
+        lat.set_beta(BETA_TC)
+        E, M = lat.sweep_record(1, 1)
+        S = lat.get_spins()
+    Eo, Mo, so = oracle_rw(L, seed, BETA_TC, 1, nstrips)
+    np.testing.assert_array_equal(E, Eo)
+    np.testing.assert_array_equal(M, Mo)
+    np.testing.assert_array_equal(S, so)
+
+
 def test_random_words_cold_and_frozen(ising):
     """Cold start: at beta = 6 the ground state stays frozen; at T_c the chain
     leaves it exactly as the oracle does."""
