@@ -80,15 +80,17 @@ cudaError_t launch_resident_premasked(uint64_t* w0, uint64_t* w1, const Geom& g,
 // Launch `kernel` with programmatic stream serialization (the kernel calls
 // pdl_enter before its first read): the next launch's setup overlaps the end
 // of the previous one.  On a stream that is being captured into a graph the
-// launch is a plain one: measured on GB300, programmatic edges made replayed
-// graphs of short half-sweeps slower (L = 2016: 531 -> 298 spin-updates/ns),
-// while plain stream launches gained (L = 16384: +2.7%, L = 4096: +19%).
-// Errors are left for cudaGetLastError.
+// launch is a plain one unless in_graphs: measured on GB300, programmatic
+// edges made replayed graphs of the fused half-sweeps slower (L = 2016: 531
+// -> 298 spin-updates/ns), while plain stream launches gained (L = 16384:
+// +2.7%, L = 4096: +19%); the apply-only half-sweeps choose by size (see
+// launch_half_sweep_apply).  Errors are left for cudaGetLastError.
 template <typename... Params, typename... Args>
-inline void launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, cudaStream_t s, Args... args)
+inline void launch_pdl_opt(bool in_graphs, void (*kernel)(Params...), dim3 grid, dim3 block, cudaStream_t s,
+                           Args... args)
 {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    if (!in_graphs && cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
         cudaGetLastError();
         cs = cudaStreamCaptureStatusNone;
     }
@@ -103,6 +105,12 @@ inline void launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, cudaStr
     cfg.attrs = attr;
     cfg.numAttrs = cs == cudaStreamCaptureStatusNone ? 1 : 0;
     cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <typename... Params, typename... Args>
+inline void launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, cudaStream_t s, Args... args)
+{
+    launch_pdl_opt(false, kernel, grid, block, s, args...);
 }
 
 // Geometry checks shared by the entry points.

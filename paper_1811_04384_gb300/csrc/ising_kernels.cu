@@ -390,9 +390,21 @@ cudaError_t launch_half_sweep_apply(int colour, bool record, uint64_t* own, cons
 {
     const uint32_t threads = (uint32_t)(((g.L + 3) / 4) * g.W) * 4;
     const dim3 block(128), grid((threads + 127) / 128);
-    if (colour == 0) launch_pdl(half_sweep_apply_kernel<0, false>, grid, block, s, own, other, g, a, masks);
-    else if (record) launch_pdl(half_sweep_apply_kernel<1, true>, grid, block, s, own, other, g, a, masks);
-    else launch_pdl(half_sweep_apply_kernel<1, false>, grid, block, s, own, other, g, a, masks);
+    // Programmatic dependent launch also inside the captured graphs, where the
+    // fused half-sweeps use plain launches: measured on GB300 against plain
+    // launches in the same graphs (sweeps without records, spin-updates/ns),
+    // L = 300 / 512 / 700 / 1008: 35 / 97 / 171 / 314 against 31 / 87 / 156 /
+    // 294, and L = 4096: 1006 against 963, but L = 1500 / 2016 / 2600: 499 /
+    // 651 / 782 against 508 / 681 / 816 (L = 3000: equal).  So it is on up to
+    // 8192 items and from 80000 items.
+    const int items = ((g.L + 3) / 4) * g.W;
+    const bool in_graphs = items <= 8192 || items >= 80000;
+    if (colour == 0)
+        launch_pdl_opt(in_graphs, half_sweep_apply_kernel<0, false>, grid, block, s, own, other, g, a, masks);
+    else if (record)
+        launch_pdl_opt(in_graphs, half_sweep_apply_kernel<1, true>, grid, block, s, own, other, g, a, masks);
+    else
+        launch_pdl_opt(in_graphs, half_sweep_apply_kernel<1, false>, grid, block, s, own, other, g, a, masks);
     return cudaGetLastError();
 }
 
