@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "ising_interleaved.h"
+#include "ising_internal.h"
 
 namespace ising {
 namespace {
@@ -457,6 +458,55 @@ ci_rw_phase_kernel(uint64_t* S, int L, int N, int NC, int phase, SweepArgs a, co
     }
 }
 
+// The apply-only half-sweep of the graph replays with one word per thread:
+// thread k updates the colour-C word of word row I = k / (L / 2) in column
+// pair m = k % (L / 2) with its masks from ci_mask_draw_kernel (`masks`: this
+// sweep and colour's block, entry (q * L/2 + m) * 4 + e for I = 4q + e).  The
+// spin logic is ci_half_sweep_kernel's; four times its threads, each with a
+// quarter of the work, so a short half-sweep is not bound by the latency of
+// a few threads' chains.  RECORD counts the colour-1 word's anti-aligned
+// bonds and the up spins of both words of the column pair.
+template <int C, bool RECORD>
+__global__ void __launch_bounds__(128)
+ci_half_sweep_apply_kernel(uint64_t* __restrict__ S, int L, int N, SweepArgs a, const uint64_t* __restrict__ masks)
+{
+    pdl_enter();
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t half = (uint32_t)L / 2;
+    uint32_t anti = 0, up = 0;
+    if (k < (uint32_t)N * half) {
+        const uint64_t n = (uint64_t)N * L;
+        const int I = (int)(k / half), m = (int)(k - (uint32_t)I * half);
+        const int J = 2 * m + ((I + C) & 1);
+        const int Jl = J == 0 ? L - 1 : J - 1;
+        const int Jr = J == L - 1 ? 0 : J + 1;
+        const uint64_t row = (uint64_t)I * L;
+        const uint64_t s = word_ld<false>(S, row + J, n, __LINE__);
+        const uint64_t xl = word_ld<true>(S, row + Jl, n, __LINE__);
+        const uint64_t xr = word_ld<true>(S, row + Jr, n, __LINE__);
+        const uint64_t xu = I == 0 ? rotate_up(word_ld<true>(S, (uint64_t)(N - 1) * L + J, n, __LINE__))
+                                   : word_ld<true>(S, (uint64_t)(I - 1) * L + J, n, __LINE__);
+        const uint64_t xd = I == N - 1 ? rotate_down(word_ld<true>(S, (uint64_t)J, n, __LINE__))
+                                       : word_ld<true>(S, (uint64_t)(I + 1) * L + J, n, __LINE__);
+        const uint64_t packed = __ldg(masks + ((size_t)(I >> 2) * half + m) * 4 + (I & 3));
+        const uint64_t all0 = ((uint64_t)a.all0 << 32 | a.all0) & kAllFields;
+        const uint64_t all1 = ((uint64_t)a.all1 << 32 | a.all1) & kAllFields;
+        // Eq. 3: each XOR field is 0/1, so the 3-bit sums hold a = 0..4 without carries
+        const uint64_t A = (s ^ xu) + (s ^ xd) + (s ^ xl) + (s ^ xr);
+        const uint64_t ge2 = ((A >> 1) | (A >> 2)) & kAllFields;
+        const uint64_t any = (A | (A >> 1) | (A >> 2)) & kAllFields;
+        const uint64_t accept = ge2 | (any & (packed | all1)) | (~any & ((packed >> 1) | all0));
+        const uint64_t sn = s ^ (accept & kAllFields);
+        word_st(S, row + J, sn, n, __LINE__);
+        if (RECORD) {
+            const uint64_t other = (J & 1) ? xl : xr;    // the other word of the column pair
+            anti += __popcll(sn ^ xu) + __popcll(sn ^ xd) + __popcll(sn ^ xl) + __popcll(sn ^ xr);
+            up += __popcll(sn) + __popcll(other);
+        }
+    }
+    if (RECORD) block_add_counts(record_counts(a) + 2 * (blockIdx.x % kCountSlots), anti, up);
+}
+
 }  // namespace
 
 bool ci_valid_side(int32_t L) { return L >= 84 && L <= 32760 && L % 84 == 0; }
@@ -581,12 +631,16 @@ cudaError_t ci_half_sweep_pre(int colour, bool record, uint64_t* S, int L, const
                               const uint64_t* sweep_masks, cudaStream_t s)
 {
     const int N = L / 21;
-    dim3 block(32, 4);
-    dim3 grid((L / 2 + 31) / 32, (N / 4 + 3) / 4);
     const uint64_t* m = sweep_masks + (size_t)colour * (N / 4) * (L / 2) * 4;
-    if (colour == 0) ci_half_sweep_kernel<0, true, false, 10, true><<<grid, block, 0, s>>>(S, L, N, a, m);
-    else if (record) ci_half_sweep_kernel<1, true, true, 10, true><<<grid, block, 0, s>>>(S, L, N, a, m);
-    else ci_half_sweep_kernel<1, true, false, 10, true><<<grid, block, 0, s>>>(S, L, N, a, m);
+    const unsigned threads = (unsigned)N * (unsigned)(L / 2);
+    const dim3 grid((threads + 127) / 128), block(128);
+    // programmatic dependent launch inside the graphs as for the row-packed
+    // apply half-sweeps: up to 8192 and from 80000 thread items
+    const int items = (N / 4) * (L / 2);
+    const bool in_graphs = items <= 8192 || items >= 80000;
+    if (colour == 0) launch_pdl_opt(in_graphs, ci_half_sweep_apply_kernel<0, false>, grid, block, s, S, L, N, a, m);
+    else if (record) launch_pdl_opt(in_graphs, ci_half_sweep_apply_kernel<1, true>, grid, block, s, S, L, N, a, m);
+    else launch_pdl_opt(in_graphs, ci_half_sweep_apply_kernel<1, false>, grid, block, s, S, L, N, a, m);
     return cudaGetLastError();
 }
 
