@@ -253,13 +253,33 @@ int ising_set_item_lanes(ising_lattice *h, int32_t lanes);
  * L <= 292) the accept masks of the requested sweeps are first drawn by all
  * SMs into a device buffer the library allocates on first use (up to
  * 16 MB), and the on-chip block only applies them, one or two rows per
- * thread.  ISING_PATH_AUTO (default): resident up to 512 thread items; above
- * that the launch path, which is faster there.
+ * thread.
+ * ISING_PATH_CLUSTER: temporal blocking on one thread-block cluster (16
+ * blocks where the device runs such a cluster, else 8), for row-packed
+ * lattices with at least two rows per block whose window fits a block's
+ * shared memory (L from 32 up to 1638; otherwise EINVAL, and EINVAL on a
+ * device without clusters).  Block b keeps rows b L / C .. (b + 1) L / C - 1
+ * of both colours in shared memory for a piece of up to 256 sweeps.  After
+ * every k <= 12 half-sweeps the blocks pass a cluster barrier and copy k halo
+ * rows from their neighbours' shared memory (distributed shared memory),
+ * then run k half-sweeps on their rows plus halo.  The accept masks of each
+ * piece are drawn by the SMs the cluster leaves free, while the piece before
+ * is applied, into two device buffers the library allocates on first use (up
+ * to 32 MB together; 2 L pitch 8 bytes per sweep).  No spin-waits: only the
+ * hardware's block and cluster barriers.
+ * ISING_PATH_AUTO (default): resident up to 512 thread items (L <= 292), the
+ * cluster path above that up to L = 1100, the launch path above that.
  * Results are identical on every path. */
 #define ISING_PATH_AUTO 0
 #define ISING_PATH_LAUNCHES 1
 #define ISING_PATH_RESIDENT 2
+#define ISING_PATH_CLUSTER 3
 int ising_set_path(ising_lattice *h, int32_t path);
+
+/* The path the next ising_sweep / ising_sweep_record of the checkerboard
+ * chain takes (ISING_PATH_RESIDENT, ISING_PATH_CLUSTER or
+ * ISING_PATH_LAUNCHES; with the random-word chain, the path last set). */
+int ising_get_path(ising_lattice *h, int32_t *path);
 
 /* Which Markov chain ising_sweep and ising_sweep_record run.
  * ISING_CHAIN_CHECKERBOARD (default): the checkerboard sweeps of the

@@ -37,6 +37,7 @@ ISING_CHAIN_RANDOM_WORDS = 1
 ISING_PATH_AUTO = 0
 ISING_PATH_LAUNCHES = 1
 ISING_PATH_RESIDENT = 2
+ISING_PATH_CLUSTER = 3
 ISING_NOALLOC_MAX_RECORDS = 1024   # records one ising_sweep_record_noalloc call can hold
 
 _lib = None
@@ -197,8 +198,15 @@ class Lattice:
         _check(load().ising_set_chain(self._h, int(chain), int(nstrips)), "ising_set_chain")
 
     def set_path(self, path: int):
-        """ISING_PATH_AUTO, ISING_PATH_LAUNCHES or ISING_PATH_RESIDENT."""
+        """ISING_PATH_AUTO, ISING_PATH_LAUNCHES, ISING_PATH_RESIDENT or ISING_PATH_CLUSTER."""
         _check(load().ising_set_path(self._h, int(path)), "ising_set_path")
+
+    def get_path(self) -> int:
+        """The path the next sweeps take (ising_get_path): ISING_PATH_RESIDENT,
+        ISING_PATH_CLUSTER or ISING_PATH_LAUNCHES."""
+        p = ctypes.c_int32(0)
+        _check(load().ising_get_path(self._h, ctypes.byref(p)), "ising_get_path")
+        return p.value
 
     def layout(self) -> tuple[int, int, int]:
         """(W, pitch, live fields of the last word) of the row-packed layout (ising_layout)."""

@@ -1,0 +1,457 @@
+// Cluster-resident temporal blocking for mid-size lattices (above the
+// one-SM on-chip range, L of about 300 to 1100).
+//
+// There a half-sweep is short: a replayed graph node per half-sweep costs
+// more than its work.  Here one launch of a single thread-block cluster (16
+// blocks where the device allows it, else 8) runs a piece of up to 256
+// sweeps whose accept masks cl_mask_draw_kernel has drawn beforehand on all
+// SMs.  Block b of the cluster owns rows b L / C .. (b + 1) L / C - 1 of both
+// colours and keeps them in its shared memory for the whole launch, in a
+// window with k rows of halo above and below (k even, k <= kClHalo, k <= the
+// rows a block owns, so a halo lies in the two neighbouring blocks).  The
+// launch's half-sweeps run in phases of k:
+//   1. cluster barrier: every block's own rows are those after the previous
+//      phase;
+//   2. each block copies its halo rows from its neighbours' shared memory
+//      (distributed shared memory);
+//   3. cluster barrier: no block changes its own rows before its neighbours
+//      have copied them;
+//   4. k half-sweeps on the window: after half-sweep d (0-based) the window
+//      rows 1 + d .. R - 2 - d are exact, so after k of them the block's own
+//      rows still are (a trapezoid: the halo rows are recomputed by both
+//      neighbours).
+// The masks of each half-sweep stream into a ring of shared-memory slabs
+// with asynchronous 16-byte copies, up to kClMaxSlabs - 1 half-sweeps ahead.
+// Every thread updates the same 1, 2 or 4 window words in each half-sweep
+// (those inside its trapezoid), with their offsets worked out once per launch:
+// at these sizes a half-sweep is a few hundred instructions per SM, and the
+// index arithmetic of a general loop cost as much as the update itself.
+// The barriers are the hardware's (no flag polling, nothing to time out),
+// passed by every thread of every block the same number of times.  Each
+// update is the spin logic of row_apply with its row's pre-drawn masks, so
+// the results are those of the half-sweep kernels.  Records (colour 1 of a
+// recorded sweep) count each block's own rows only: every bond and spin once.
+#include <cuda_runtime.h>
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "ising_device.cuh"
+#include "ising_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace ising {
+namespace {
+
+constexpr int kClThreads = 1024;           // most threads of a block
+constexpr size_t kClSmemMax = 220 * 1024;   // dynamic shared memory of a block
+constexpr int kClHalo = 12;                 // most half-sweeps per phase
+constexpr int kClMaxSlabs = 8;              // mask slabs where they fit: staged up to 7 half-sweeps ahead
+
+struct ClusterArgs {
+    uint64_t* w[2];             // the lattice's colour arrays, L x P words each
+    Geom g;
+    int k;                      // half-sweeps per phase = halo rows
+    int q;                      // mask slabs in shared memory (2 or kClMaxSlabs): masks staged q - 1 half-sweeps ahead
+    int nsweeps;                // sweeps of this launch
+    int rmax;                   // window rows the shared memory holds (largest share of rows + 2 k)
+    const uint64_t* masks;      // masks[(h * L + i) * P + w]: half-sweep h = 2 j + c of the launch, row i, word w
+    int64_t s0;                 // the launch runs sweeps s0 + 1 .. s0 + nsweeps of the call
+    int64_t every;              // record after sweeps s with s % every == 0 (0: none)
+    unsigned long long* counts; // count slots (32 per record); record r of the call -> slot r
+    uint32_t all0, all1;        // "always" masks (threshold 2^32)
+};
+
+// 16 bytes global -> shared (a 32-bit shared-window address), asynchronously,
+// through L2.
+__device__ __forceinline__ void cl_copy16(uint32_t smem_dst, const void* gmem_src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_dst), "l"(gmem_src) : "memory");
+}
+
+__device__ __forceinline__ void cl_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cl_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ int wrap_index(int i, int L) { return i < 0 ? i + L : (i >= L ? i - L : i); }
+
+// A window word a thread updates in every half-sweep whose rows include its
+// row, with what the two colours need worked out once per launch.  The
+// neighbour to the side of a site of colour C in global row i is at m - 1
+// when (i + C) is even, else m + 1; its word is the next one to the left or
+// right, wrapped around the row, whose edge field comes in with a shift of
+// 60 bits, or 3 (rlast - 1) across the wrap.
+struct Slot {
+    int lr;          // window row, or -1 (no word)
+    uint32_t o;      // lr * P + w: the word in the own-colour, other-colour and mask arrays
+    uint32_t dl;     // side word - o for colour 0 (bits 0..15) and colour 1 (16..31), as int16
+    uint32_t bits;   // side shift for colour 0 (bits 0..6) and 1 (8..14); colour 0 takes the left
+                     // neighbour (16); last word of the row (17); an own row of the block (18)
+};
+
+// One update of colour C: the spin logic of row_apply with the packed masks
+// p (r < thr1 at bit 3k, r < thr0 at bit 3k + 1) staged in msk.  RECORD adds
+// the row's anti-aligned bonds and up spins.
+template <int C, bool RECORD>
+__device__ __forceinline__ void cl_update(uint64_t* own, const uint64_t* other, const uint64_t* msk, uint32_t P,
+                                          const Slot& sl, uint64_t live_last, uint64_t all0, uint64_t all1,
+                                          uint64_t n, uint32_t& anti, uint32_t& up)
+{
+    const uint32_t o = sl.o;
+    const bool left = ((sl.bits >> 16) & 1u) != (uint32_t)C;
+    const uint32_t so = o + (uint32_t)(int)(int16_t)(sl.dl >> (16 * C));
+    const uint32_t sh = (sl.bits >> (8 * C)) & 0x7fu;
+    const uint64_t live = (sl.bits & (1u << 17)) ? live_last : kSpinBits;
+    const uint64_t s = word_ld<false>(own, o, n, __LINE__);
+    const uint64_t u = word_ld<false>(other, o - P, n, __LINE__);
+    const uint64_t d = word_ld<false>(other, o + P, n, __LINE__);
+    const uint64_t h0 = word_ld<false>(other, o, n, __LINE__);
+    const uint64_t side = word_ld<false>(other, so, n, __LINE__);
+    const uint64_t p = word_ld<false>(msk, o, n, __LINE__);
+    const uint64_t h1 = left ? ((h0 << 3) | (side >> sh)) : ((h0 >> 3) | (side << sh));
+    const uint64_t x1 = s ^ u, x2 = s ^ d, x3 = s ^ h0, x4 = s ^ h1;
+    const uint64_t any = x1 | x2 | x3 | x4;
+    const uint64_t ge2 = (x1 & x2) | (x3 & x4) | ((x1 ^ x2) & (x3 ^ x4));
+    const uint64_t accept = ge2 | (any & (p | all1)) | (~any & ((p >> 1) | all0));
+    const uint64_t s_new = s ^ (accept & live);
+    word_st(own, o, s_new, n, __LINE__);
+    if (RECORD) {
+        anti += __popcll((s_new ^ u) & live) + __popcll((s_new ^ d) & live) + __popcll((s_new ^ h0) & live)
+              + __popcll((s_new ^ h1) & live);
+        up += __popcll(s_new & live) + __popcll(h0 & live);
+    }
+}
+
+// One half-sweep of colour C on window rows lo .. hi: each thread updates
+// those of its NS slots that lie there.  RECORD counts the block's own rows
+// into the count slots `counts`.
+template <int C, bool RECORD, int NS>
+__device__ __forceinline__ void cl_half_sweep(uint64_t* own, const uint64_t* other, const uint64_t* msk, uint32_t P,
+                                              const Slot (&slot)[NS], int lo, int hi, uint64_t live_last,
+                                              uint64_t all0, uint64_t all1, uint64_t n,
+                                              unsigned long long* counts)
+{
+    uint32_t anti = 0, up = 0;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+        if (slot[j].lr >= lo && slot[j].lr <= hi) {
+            if (RECORD && (slot[j].bits & (1u << 18)))
+                cl_update<C, true>(own, other, msk, P, slot[j], live_last, all0, all1, n, anti, up);
+            else
+                cl_update<C, false>(own, other, msk, P, slot[j], live_last, all0, all1, n, anti, up);
+        }
+    }
+    if (RECORD) block_add_counts(counts + 2 * (blockIdx.x % kCountSlots), anti, up);
+}
+
+// NS: window words per thread (the block has ceil(words / NS) threads,
+// rounded up to whole warps).  DEEP: kClMaxSlabs mask slabs, else 2.
+template <int NS, bool DEEP>
+__global__ void __launch_bounds__(kClThreads, 1)
+cluster_sweeps_kernel(ClusterArgs a)
+{
+    extern __shared__ __align__(16) uint64_t smem[];
+    // the next piece's mask draw (launched with programmatic stream
+    // serialization) may start now, on the SMs this cluster leaves free
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    constexpr int Q = DEEP ? kClMaxSlabs : 2;
+    cg::cluster_group cluster = cg::this_cluster();
+    const Geom& g = a.g;
+    const int T = blockDim.x;
+    const int C = (int)cluster.num_blocks(), b = (int)cluster.block_rank();
+    const int k = a.k;
+    auto row0 = [&](int rank) { return (int)((long long)rank * g.L / C); };
+    const int r0 = row0(b), r1 = row0(b + 1), S = r1 - r0, R = S + 2 * k;
+    const int bp = (b + C - 1) % C, bn = (b + 1) % C;
+    const int Sp = (bp == C - 1 ? g.L : row0(bp + 1)) - row0(bp);     // rows of the block above
+    const int top = r0 - k;                                            // global row of window row 0 (mod L)
+    const uint32_t P = (uint32_t)g.P, W = (uint32_t)g.W;
+    const uint64_t n = (uint64_t)a.rmax * P;
+    uint64_t* win[2] = {smem, smem + n};
+    uint64_t* msk = smem + 2 * n;                                       // Q slabs of n words
+    const int pairs = g.P / 2;
+    const uint32_t sh_wrap = 3u * (uint32_t)(g.rlast - 1);
+    // slots: window words e = t + j T of rows 1 .. R - 2, and the mask copies
+    // (16 bytes, word pairs) of the same rows
+    Slot slot[NS];
+    uint32_t cdst[NS], csrc[NS];
+    const uint32_t msk_sh = (uint32_t)__cvta_generic_to_shared(msk);
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+        const int e = threadIdx.x + j * T;
+        const int lr = 1 + e / g.W, w = e % g.W;
+        const bool first = w == 0, last = w == g.W - 1;
+        const bool left0 = ((top + lr) & 1) == 0;      // colour 0 at (i + 0) even
+        // left neighbour: word w - 1 (wrapped), right: w + 1 (wrapped)
+        const int dleft = first ? (int)W - 1 : -1, dright = last ? -((int)W - 1) : 1;
+        const uint32_t shl = first ? sh_wrap : 60u, shr = last ? sh_wrap : 60u;
+        slot[j].lr = lr <= R - 2 ? lr : -1;
+        slot[j].o = (uint32_t)lr * P + (uint32_t)w;
+        slot[j].dl = (uint32_t)(uint16_t)(int16_t)(left0 ? dleft : dright) |
+                     ((uint32_t)(uint16_t)(int16_t)(left0 ? dright : dleft) << 16);
+        slot[j].bits = (left0 ? shl : shr) | ((left0 ? shr : shl) << 8) | (left0 ? 1u << 16 : 0u) |
+                       (last ? 1u << 17 : 0u) | ((lr >= k && lr < R - k) ? 1u << 18 : 0u);
+        const int cr = 1 + e / pairs, cp = e % pairs;
+        cdst[j] = cr <= R - 2 ? msk_sh + 8u * ((uint32_t)cr * P + 2u * (uint32_t)cp) : ~0u;
+        csrc[j] = (uint32_t)wrap_index(top + cr, g.L) * P + 2u * (uint32_t)cp;
+    }
+    const uint64_t live_last = live_mask(g, g.W - 1);
+    const uint64_t all0 = (uint64_t)a.all0 << 32 | a.all0;
+    const uint64_t all1 = (uint64_t)a.all1 << 32 | a.all1;
+    const int total = 2 * a.nsweeps;
+    const uint32_t slab_bytes = (uint32_t)(n * sizeof(uint64_t));
+    const size_t plane = (size_t)g.L * P;                               // one half-sweep's masks
+    // masks of the next half-sweep to stage (number `next`) for window rows
+    // 1 .. R - 2 into slab `put` (one copy group per half-sweep, empty past
+    // the end)
+    const uint64_t* next_src = a.masks;
+    int next = 0, put = 0;
+    auto stage = [&]() {
+        if (next < total) {
+            const uint32_t off = (uint32_t)put * slab_bytes;
+#pragma unroll
+            for (int j = 0; j < NS; ++j)
+                if (cdst[j] != ~0u) cl_copy16(cdst[j] + off, next_src + csrc[j]);
+        }
+        cl_commit();
+        ++next;
+        next_src += plane;
+        put = put + 1 == Q ? 0 : put + 1;
+    };
+    // own rows of both colours, from the lattice, to window rows k .. k + S - 1
+    for (int c = 0; c < 2; ++c)
+        for (int e = threadIdx.x; e < S * pairs; e += T) {
+            const int r = e / pairs, cp = e - r * pairs;
+            cl_copy16((uint32_t)__cvta_generic_to_shared(win[c] + (size_t)(k + r) * P + 2 * cp),
+                      a.w[c] + (size_t)(r0 + r) * P + 2 * cp);
+        }
+    cl_commit();
+    cl_wait<0>();
+#pragma unroll
+    for (int h = 0; h < Q - 1; ++h) stage();
+    int use = 0;                                                        // slab of the current half-sweep
+    // before a half-sweep: its slab staged, the previous half-sweep done (its
+    // rows final, its slab free for the copies of half-sweep h + Q - 1)
+    auto step = [&]() {
+        cl_wait<Q - 2>();
+        __syncthreads();
+        stage();
+        const uint64_t* m = msk + (size_t)use * n;
+        use = use + 1 == Q ? 0 : use + 1;
+        return m;
+    };
+    int64_t s_call = a.s0;                                              // sweeps of the call done
+    int64_t next_rec = a.every > 0 ? (a.s0 / a.every + 1) * a.every : -1;
+    for (int hs0 = 0; hs0 < total; hs0 += k) {
+        const int kk = min(k, total - hs0);                             // even: phases start with colour 0
+        cluster.sync();      // every block's own rows are final for the previous phase
+        // halo rows from the neighbours' shared memory: the last k own rows of
+        // the block above (its window rows Sp .. Sp + k - 1) to rows 0 .. k - 1,
+        // the first k own rows of the block below (its rows k .. 2k - 1) to
+        // rows k + S .. 2k + S - 1
+        for (int c = 0; c < 2; ++c) {
+            const uint64_t* above = cluster.map_shared_rank(win[c], bp);
+            const uint64_t* below = cluster.map_shared_rank(win[c], bn);
+            for (int idx = threadIdx.x; idx < k * (int)P; idx += T) {
+                const int r = idx / (int)P, x = idx - r * (int)P;
+                win[c][(size_t)r * P + x] = above[(size_t)(Sp + r) * P + x];
+                win[c][(size_t)(k + S + r) * P + x] = below[(size_t)(k + r) * P + x];
+            }
+        }
+        cluster.sync();      // every block has its halo: own rows may change now
+        for (int d = 0; d < kk; d += 2) {
+            const uint64_t* m0 = step();
+            cl_half_sweep<0, false, NS>(win[0], win[1], m0, P, slot, 1 + d, R - 2 - d, live_last, all0, all1, n,
+                                        nullptr);
+            const uint64_t* m1 = step();
+            ++s_call;
+            if (s_call == next_rec) {
+                unsigned long long* cnt = a.counts + (size_t)(s_call / a.every - 1) * 2 * kCountSlots;
+                cl_half_sweep<1, true, NS>(win[1], win[0], m1, P, slot, 2 + d, R - 3 - d, live_last, all0, all1,
+                                           n, cnt);
+                next_rec += a.every;
+            } else {
+                cl_half_sweep<1, false, NS>(win[1], win[0], m1, P, slot, 2 + d, R - 3 - d, live_last, all0, all1,
+                                            n, nullptr);
+            }
+        }
+    }
+    // own rows back to the lattice
+    cl_wait<0>();
+    __syncthreads();
+    for (int c = 0; c < 2; ++c)
+        for (int idx = threadIdx.x; idx < S * (int)P; idx += T) {
+            const int r = idx / (int)P, x = idx - r * (int)P;
+            a.w[c][(size_t)(r0 + r) * P + x] = win[c][(size_t)(k + r) * P + x];
+        }
+    cluster.sync();          // no block leaves while another may still read its shared memory
+}
+
+// Masks of sweeps j = 0 .. nsweeps-1 after sweep (t_base ? *t_base : 0) + t0:
+// one thread per (sweep, colour, item) draws them with item_masks_thread (the
+// draws of sweep_rows) and writes them row-major, masks[((j * 2 + c) * L + i)
+// * P + w].
+template <int ROUNDS>
+__global__ void __launch_bounds__(128)
+cl_mask_draw_kernel(Geom g, SweepArgs a, const uint64_t* t_base, uint64_t t0, int nsweeps,
+                    uint64_t* __restrict__ masks)
+{
+    const int items = ((g.L + 3) / 4) * g.W;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 2LL * nsweeps * items) return;
+    const int jc = (int)(k / items);
+    const int item = (int)(k - (long long)jc * items);
+    const int grp = item / g.W;
+    const int w = item - grp * g.W;
+    const uint64_t t = (t_base ? *t_base : 0) + t0 + (uint64_t)(jc >> 1) + 1;
+    uint64_t p[4];
+    item_masks_thread<ROUNDS>(g, item, t, jc & 1, a.rk, a.thr0, a.thr1, a.one, p);
+    uint64_t* out = masks + (size_t)jc * g.L * g.P;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int i = 4 * grp + e;
+        if (i < g.L) out[(size_t)i * g.P + w] = p[e];
+    }
+}
+
+size_t cl_smem_bytes(const Geom& g, int blocks, int k, int q)
+{
+    const int smax = (g.L + blocks - 1) / blocks;
+    return (size_t)(2 + q) * (smax + 2 * k) * g.P * sizeof(uint64_t);
+}
+
+// The six forms of the kernel: 1, 2 or 4 words per thread, 2 or kClMaxSlabs mask slabs.
+using ClusterKernel = void (*)(ClusterArgs);
+constexpr ClusterKernel kClusterKernels[6] = {cluster_sweeps_kernel<1, false>, cluster_sweeps_kernel<2, false>,
+                                              cluster_sweeps_kernel<4, false>, cluster_sweeps_kernel<1, true>,
+                                              cluster_sweeps_kernel<2, true>,  cluster_sweeps_kernel<4, true>};
+
+ClusterKernel cluster_kernel(int ns, int q)
+{
+    return kClusterKernels[(q == kClMaxSlabs ? 3 : 0) + (ns == 1 ? 0 : (ns == 2 ? 1 : 2))];
+}
+
+int probe_max_cluster()
+{
+    for (ClusterKernel kern : kClusterKernels) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClSmemMax) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+    }
+    for (int c : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(c);
+        cfg.blockDim = dim3(kClThreads);
+        cfg.dynamicSmemBytes = kClSmemMax;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = c;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        bool ok = true;
+        for (ClusterKernel kern : kClusterKernels) {
+            int nc = 0;
+            ok = ok && cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) == cudaSuccess && nc >= 1;
+        }
+        if (ok) return c;
+        cudaGetLastError();
+    }
+    return 0;
+}
+
+}  // namespace
+
+// Cluster size, phase length, mask slabs and words per thread for side L:
+// 16 blocks if the device runs such a cluster, else 8; k = the most
+// half-sweeps per phase (even, <= kClHalo, <= the fewest rows a block owns)
+// whose window and kClMaxSlabs mask slabs fit in shared memory (else two
+// slabs), with at most 2 window words per thread where some k allows it,
+// else 4.  Measured on GB300 (sweeps without records, spin-updates/ns, by k
+// = 4 / 8 / 12): L = 296: 77 / 105 / 115, L = 512: 170 / 199 / 210,
+// L = 1008: 357 / 394 / 403; 4 words per thread (L = 1008, k = 16) 336.
+// Returns false if no such launch exists (a lattice too large or too small).
+bool cluster_plan(const Geom& g, ClusterPlan* plan)
+{
+    static const int max_cluster = probe_max_cluster();   // per process, set once
+    if (max_cluster == 0) return false;
+    const int c = max_cluster;
+    const int fewest = g.L / c;
+    for (int most : {2, 4}) {
+        for (int q : {kClMaxSlabs, 2}) {
+            for (int kk = std::min(kClHalo, fewest) & ~1; kk >= 2; kk -= 2) {
+                if (cl_smem_bytes(g, c, kk, q) > kClSmemMax) continue;
+                const long long words = (long long)((g.L + c - 1) / c + 2 * kk - 2) * g.W;
+                if (words > (long long)most * kClThreads) continue;
+                const int ns = words <= kClThreads ? 1 : (words <= 2 * kClThreads ? 2 : 4);
+                plan->blocks = c;
+                plan->k = kk;
+                plan->q = q;
+                plan->ns = ns;
+                plan->threads = (int)(((words + ns - 1) / ns + 31) / 32 * 32);
+                return true;
+            }
+        }
+    }
+    return false;
+}
+
+size_t cl_mask_bytes_per_sweep(const Geom& g) { return 2 * (size_t)g.L * g.P * sizeof(uint64_t); }
+
+cudaError_t launch_cl_mask_draw(const Geom& g, const SweepArgs& a, const uint64_t* t_base, uint64_t t0, int nsweeps,
+                                uint64_t* masks, bool overlap, cudaStream_t s)
+{
+    const long long threads = 2LL * nsweeps * (((g.L + 3) / 4) * g.W);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((threads + 127) / 128));
+    cfg.blockDim = dim3(128);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = overlap ? 1 : 0;
+    return a.rounds == 7 ? cudaLaunchKernelEx(&cfg, cl_mask_draw_kernel<7>, g, a, t_base, t0, nsweeps, masks)
+                         : cudaLaunchKernelEx(&cfg, cl_mask_draw_kernel<10>, g, a, t_base, t0, nsweeps, masks);
+}
+
+cudaError_t launch_cluster_sweeps(uint64_t* w0, uint64_t* w1, const Geom& g, const SweepArgs& a,
+                                  const ClusterPlan& plan, int nsweeps, const uint64_t* masks, int64_t s0,
+                                  int64_t every, cudaStream_t s)
+{
+    ClusterArgs ca;
+    ca.w[0] = w0;
+    ca.w[1] = w1;
+    ca.g = g;
+    ca.k = plan.k;
+    ca.q = plan.q;
+    ca.nsweeps = nsweeps;
+    ca.rmax = (g.L + plan.blocks - 1) / plan.blocks + 2 * plan.k;
+    ca.masks = masks;
+    ca.s0 = s0;
+    ca.every = every;
+    ca.counts = a.counts;
+    ca.all0 = a.all0;
+    ca.all1 = a.all1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(plan.blocks);
+    cfg.blockDim = dim3(plan.threads);
+    cfg.dynamicSmemBytes = cl_smem_bytes(g, plan.blocks, plan.k, plan.q);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = plan.blocks;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, cluster_kernel(plan.ns, plan.q), ca);
+}
+
+}  // namespace ising

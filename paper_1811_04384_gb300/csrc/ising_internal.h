@@ -77,6 +77,31 @@ cudaError_t launch_resident_premasked(uint64_t* w0, uint64_t* w1, const Geom& g,
                                       int n, int every, const ulonglong2* masks, long long* rec, size_t bytes,
                                       cudaStream_t s);
 
+// The cluster path (ising_cluster.cu): one thread-block cluster whose blocks
+// keep the lattice in their shared memory over many sweeps.  cluster_plan
+// picks the launch for side L (false if there is none); launch_cl_mask_draw
+// draws the masks of nsweeps sweeps after sweep (t_base ? *t_base : 0) + t0
+// (cl_mask_bytes_per_sweep bytes each); with `overlap` it is launched with
+// programmatic stream serialization, so that it runs beside the cluster
+// launch before it in the stream (which must not read `masks`).
+// launch_cluster_sweeps runs sweeps s0 + 1 .. s0 + nsweeps of a call from
+// them, recording after every `every`-th (0: none) into count slot
+// s / every - 1 past a.counts.
+struct ClusterPlan {
+    int blocks;     // cluster size
+    int k;          // half-sweeps per phase = halo rows
+    int q;          // mask slabs in shared memory
+    int ns;         // window words per thread: 1, 2 or 4
+    int threads;    // threads per block
+};
+bool cluster_plan(const Geom& g, ClusterPlan* plan);
+size_t cl_mask_bytes_per_sweep(const Geom& g);
+cudaError_t launch_cl_mask_draw(const Geom& g, const SweepArgs& a, const uint64_t* t_base, uint64_t t0, int nsweeps,
+                                uint64_t* masks, bool overlap, cudaStream_t s);
+cudaError_t launch_cluster_sweeps(uint64_t* w0, uint64_t* w1, const Geom& g, const SweepArgs& a,
+                                  const ClusterPlan& plan, int nsweeps, const uint64_t* masks, int64_t s0,
+                                  int64_t every, cudaStream_t s);
+
 // Launch `kernel` with programmatic stream serialization (the kernel calls
 // pdl_enter before its first read): the next launch's setup overlaps the end
 // of the previous one.  On a stream that is being captured into a graph the

@@ -529,7 +529,8 @@ static size_t resident_bytes(const Geom& g) { return 2 * (size_t)g.L * g.P * siz
 
 static bool use_resident(const ising_lattice* h)
 {
-    if (h->layout != ISING_LAYOUT_ROW_PACKED || h->path == ISING_PATH_LAUNCHES) return false;
+    if (h->layout != ISING_LAYOUT_ROW_PACKED || (h->path != ISING_PATH_AUTO && h->path != ISING_PATH_RESIDENT))
+        return false;
     if (resident_bytes(h->g) > kResidentMaxBytes) return false;
     return h->path == ISING_PATH_RESIDENT || ((h->g.L + 3) / 4) * h->g.W <= kResidentAutoMaxItems;
 }
@@ -586,6 +587,79 @@ static int run_resident(ising_lattice* h, int n, int every)
     return ISING_OK;
 }
 
+// ---- Cluster path (mid-size lattices)
+// Above the on-chip range and up to kClusterMaxL, one thread-block cluster
+// keeps the lattice in its blocks' shared memory over a whole piece of sweeps
+// (cluster_sweeps_kernel).  The masks of each piece are drawn on all SMs
+// into one of two buffers: the draw of piece j + 1 follows the cluster launch
+// of piece j in the stream with programmatic stream serialization, so it
+// runs on the SMs the cluster leaves free while piece j is applied, and
+// writes the buffer piece j - 1 read (complete before piece j started).
+// Replayed graphs of short half-sweeps stay for the launch path
+// (ISING_PATH_LAUNCHES) and for larger lattices.  Measured on GB300, sweeps
+// without records, spin-updates/ns, cluster against graphs: L = 296: 115 /
+// 34; L = 512: 210 / 97; L = 700: 265 / 169; L = 1008: 403 / 314; L = 1100:
+// 365 / 347; but L = 1200: 297 / 358, where the window needs 4 words per
+// thread.
+constexpr int kClusterMaxL = 1100;
+constexpr size_t kClusterMaskBytes = 32u << 20;    // both buffers
+constexpr int kClusterMaxPiece = 256;
+
+static bool use_cluster(const ising_lattice* h, ClusterPlan* plan)
+{
+    if (h->layout != ISING_LAYOUT_ROW_PACKED || h->chain != ISING_CHAIN_CHECKERBOARD) return false;
+    if (h->path == ISING_PATH_CLUSTER) return cluster_plan(h->g, plan);
+    if (h->path != ISING_PATH_AUTO || use_resident(h) || h->g.L > kClusterMaxL) return false;
+    return cluster_plan(h->g, plan);
+}
+
+// n sweeps on the cluster path; every > 0: after every `every`-th sweep s of
+// the n, a record into count slot s / every - 1 past `counts`.
+static int run_cluster(ising_lattice* h, int64_t n, int64_t every, unsigned long long* counts, const ClusterPlan& plan)
+{
+    const Geom& g = h->g;
+    const size_t per_sweep = cl_mask_bytes_per_sweep(g);
+    const int max_piece =
+        (int)std::max<size_t>(1, std::min<size_t>(kClusterMaxPiece, kClusterMaskBytes / (2 * per_sweep)));
+    const size_t buf = (size_t)std::min<int64_t>(n, max_piece) * per_sweep;
+    if (h->mask_bytes < 2 * buf) {
+        if (h->masks) cudaFree(h->masks);
+        h->masks = nullptr;
+        h->mask_bytes = 0;
+        cudaError_t e = cudaMalloc(&h->masks, 2 * buf);
+        if (e != cudaSuccess) { h->masks = nullptr; cuda_fail(e, "cudaMalloc masks"); return ISING_ENOMEM; }
+        h->mask_bytes = 2 * buf;
+    }
+    SweepArgs a = base_args(h);
+    a.counts = counts;
+    uint64_t* masks[2] = {reinterpret_cast<uint64_t*>(h->masks),
+                          reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(h->masks) + buf)};
+    // piece j: sweeps j * max_piece + 1 .. of the n, masks in buffer j & 1
+    auto part_of = [&](int64_t j) { return (int)std::min<int64_t>(n - j * max_piece, max_piece); };
+    const int64_t np = (n + max_piece - 1) / max_piece;
+    if (np > 0) {
+        cudaError_t e = launch_cl_mask_draw(g, a, nullptr, h->t, part_of(0), masks[0], false, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cl_mask_draw_kernel");
+    }
+    for (int64_t j = 0; j < np; ++j) {
+        const int64_t done = j * max_piece;
+        cudaError_t e = launch_cluster_sweeps(h->words[0], h->words[1], g, a, plan, part_of(j), masks[j & 1], done,
+                                              every, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cluster_sweeps_kernel");
+        if (j + 1 < np) {
+            e = launch_cl_mask_draw(g, a, nullptr, h->t + (uint64_t)(done + max_piece), part_of(j + 1),
+                                    masks[(j + 1) & 1], true, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cl_mask_draw_kernel");
+        }
+    }
+    if (n > 0) {
+        cudaError_t e = launch_advance_sweep(h->t_dev, (uint64_t)n, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "advance_sweep_kernel");
+        h->t += (uint64_t)n;
+    }
+    return ISING_OK;
+}
+
 extern "C" int ising_set_rng(ising_lattice* h, int32_t scheme)
 {
     if (!h) return ISING_EINVAL;
@@ -599,10 +673,26 @@ extern "C" int ising_set_rng(ising_lattice* h, int32_t scheme)
 extern "C" int ising_set_path(ising_lattice* h, int32_t path)
 {
     if (!h) return ISING_EINVAL;
-    if (path != ISING_PATH_AUTO && path != ISING_PATH_LAUNCHES && path != ISING_PATH_RESIDENT) return ISING_EINVAL;
+    if (path != ISING_PATH_AUTO && path != ISING_PATH_LAUNCHES && path != ISING_PATH_RESIDENT &&
+        path != ISING_PATH_CLUSTER)
+        return ISING_EINVAL;
     if (path == ISING_PATH_RESIDENT && (h->layout != ISING_LAYOUT_ROW_PACKED || resident_bytes(h->g) > kResidentMaxBytes))
         return ISING_EINVAL;
+    ClusterPlan cp;
+    if (path == ISING_PATH_CLUSTER && (h->layout != ISING_LAYOUT_ROW_PACKED || !cluster_plan(h->g, &cp)))
+        return ISING_EINVAL;
     h->path = path;
+    return ISING_OK;
+}
+
+extern "C" int ising_get_path(ising_lattice* h, int32_t* path)
+{
+    if (!h || !path) return ISING_EINVAL;
+    ClusterPlan cp;
+    if (h->chain == ISING_CHAIN_RANDOM_WORDS) *path = h->path;
+    else if (use_resident(h)) *path = ISING_PATH_RESIDENT;
+    else if (use_cluster(h, &cp)) *path = ISING_PATH_CLUSTER;
+    else *path = ISING_PATH_LAUNCHES;
     return ISING_OK;
 }
 
@@ -679,6 +769,16 @@ extern "C" int ising_sweep(ising_lattice* h, int64_t n)
         }
         return ISING_OK;
     }
+    ClusterPlan cp;
+    if (use_cluster(h, &cp)) {
+        while (n > 0) {
+            const int64_t c = n > (1 << 30) ? (1 << 30) : n;
+            int rc = run_cluster(h, c, 0, h->counts, cp);
+            if (rc != ISING_OK) return rc;
+            n -= c;
+        }
+        return ISING_OK;
+    }
     if (use_graphs(h)) {
         int rc = replay_plain(h, &n);
         if (rc != ISING_OK) return rc;
@@ -732,6 +832,7 @@ extern "C" int ising_sweep_record(ising_lattice* h, int64_t n, int64_t every, in
         if (rest > 0) return ising_sweep(h, rest);
         return ISING_OK;
     }
+    ClusterPlan cp;
     while (done_rec < nrec) {
         const int64_t chunk = (nrec - done_rec) < kRecordsPerChunk ? (nrec - done_rec) : kRecordsPerChunk;
         const size_t bytes = (size_t)chunk * kCountSlots * 2 * sizeof(unsigned long long);
@@ -742,6 +843,8 @@ extern "C" int ising_sweep_record(ising_lattice* h, int64_t n, int64_t every, in
             rc = run_random_words(h, chunk * every, [every](int64_t s) {
                 return (s % every == 0) ? (int)(s / every - 1) : -1;
             });
+        else if (use_cluster(h, &cp))
+            rc = run_cluster(h, chunk * every, every, h->counts, cp);
         else if (use_graphs(h) && every <= kGraphMaxEvery)
             rc = replay_records(h, chunk, (int)every);
         else
@@ -938,9 +1041,13 @@ extern "C" int ising_run_states(ising_lattice* h, const int8_t* const* states, i
             if (e == cudaSuccess) e = cudaEventRecord(h->ev_packed[b], h->stream);
             if (e != cudaSuccess) break;
             const int64_t base = (k - k0) * R;
-            rc = run_sweeps(h, sweeps, [every, base](int64_t s) {
-                return (s % every == 0) ? (int)(base + s / every - 1) : -1;
-            });
+            ClusterPlan cp;
+            if (use_cluster(h, &cp))
+                rc = run_cluster(h, sweeps, every, h->counts + (size_t)base * rec_words, cp);
+            else
+                rc = run_sweeps(h, sweeps, [every, base](int64_t s) {
+                    return (s % every == 0) ? (int)(base + s / every - 1) : -1;
+                });
             if (rc != ISING_OK) return rc;
         }
         if (e != cudaSuccess) return cuda_fail(e, "run_states");

@@ -1,0 +1,146 @@
+"""The cluster path (one thread-block cluster keeping the lattice in its
+blocks' shared memory, halos exchanged through distributed shared memory)
+against the oracle, bit-exact: int64 E/M series and final spins.
+
+Cases span two rows per block (L = 32, two half-sweeps per phase), the
+automatic range (L = 296 just above the on-chip path, up to L = 1100 with two
+mask pieces), L % 4 == 2, records out of step with the phases and pieces,
+odd numbers of half-sweeps per call, forced runs up to the largest side
+(L = 1638), cold starts, beta = 0 (every flip accepted) and a frozen
+lattice, runs continued across calls and paths, and ising_run_states.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+BETA_TC = 1.0 / 2.269
+
+
+@pytest.fixture(scope="module")
+def ising():
+    import paper_1811_04384_gb300 as p
+    p.load()
+    return p
+
+
+# (L, sweeps, every, beta, forced): forced sets ISING_PATH_CLUSTER, else the
+# automatic choice must be the cluster path
+CASES = [
+    (32, 9, 1, 0.44, True),        # two rows per block: phases of two half-sweeps
+    (64, 13, 2, 0.3, True),        # four rows per block, phases of 4
+    (296, 37, 1, BETA_TC, False),  # 74 half-sweeps: phases of 8 and a short last one
+    (514, 20, 3, 0.3, False),      # L % 4 == 2; 6 records, out of step with the phases
+    (1008, 24, 4, 0.44, False),    # the paper's L = 1008
+    (1100, 60, 5, BETA_TC, False), # largest automatic side: two mask pieces (34 + 26 sweeps)
+    (1500, 6, 1, 0.44, True),      # phases of 10 half-sweeps, 4 words per thread
+    (1638, 3, 1, BETA_TC, True),   # largest side with a plan: phases of 3
+]
+
+
+def test_cluster_path_matches_oracle(ising):
+    got = []
+    for L, n, every, beta, forced in CASES:
+        with ising.Lattice(L, L + 7) as lat:
+            if forced:
+                lat.set_path(ising.ISING_PATH_CLUSTER)
+            assert lat.get_path() == ising.ISING_PATH_CLUSTER, L
+            lat.init_hot()
+            lat.set_beta(beta)
+            E, M = lat.sweep_record(n, every)
+            assert lat.t == n
+            got.append((E, M, lat.get_spins()))
+    ora = oracle.run_jobs([(L, L + 7, beta, True, n, every) for L, n, every, beta, _ in CASES])
+    for (E, M, S), (Eo, Mo, So), case in zip(got, ora, CASES):
+        np.testing.assert_array_equal(E, Eo, err_msg=str(case))
+        np.testing.assert_array_equal(M, Mo, err_msg=str(case))
+        np.testing.assert_array_equal(S, So, err_msg=str(case))
+
+
+def test_cluster_continued_across_calls_and_paths(ising):
+    """Plain sweeps, recorded sweeps, a switch to the graph replays and back:
+    the sweep counter carries the draws across the calls and paths."""
+    L, seed, beta = 400, 31, 0.42
+    with ising.Lattice(L, seed) as lat:
+        lat.init_hot()
+        lat.set_beta(beta)
+        assert lat.get_path() == ising.ISING_PATH_CLUSTER
+        lat.sweep(5)
+        E1, M1 = lat.sweep_record(7, 1)
+        lat.set_path(ising.ISING_PATH_LAUNCHES)
+        assert lat.get_path() == ising.ISING_PATH_LAUNCHES
+        E2, M2 = lat.sweep_record(3, 1)
+        lat.set_path(ising.ISING_PATH_AUTO)
+        E3, M3 = lat.sweep_record(11, 2)
+        S = lat.get_spins()
+        assert lat.t == 26
+    s = oracle.init_hot(L, seed)
+    oracle.run(s, seed, beta, 0, 5, 5)
+    for (E, M), (t0, n, every) in zip([(E1, M1), (E2, M2), (E3, M3)], [(5, 7, 1), (12, 3, 1), (15, 11, 2)]):
+        Eo, Mo = oracle.run(s, seed, beta, t0, n, every)
+        np.testing.assert_array_equal(E, Eo)
+        np.testing.assert_array_equal(M, Mo)
+    np.testing.assert_array_equal(S, s)
+
+
+@pytest.mark.parametrize("beta,cold", [(0.0, False), (5.0, True), (0.6, True)])
+def test_cluster_extremes(ising, beta, cold):
+    """beta = 0 (every flip accepted: the always-accept masks), a frozen
+    lattice (beta = 5 from all +1: nothing flips) and a cold start."""
+    L, seed, n = 600, 5, 4
+    with ising.Lattice(L, seed) as lat:
+        if cold:
+            lat.init_cold(1)
+        else:
+            lat.init_hot()
+        lat.set_beta(beta)
+        E, M = lat.sweep_record(n, 1)
+        S = lat.get_spins()
+    s = oracle.init_cold(L, 1) if cold else oracle.init_hot(L, seed)
+    Eo, Mo = oracle.run(s, seed, beta, 0, n, 1)
+    np.testing.assert_array_equal(E, Eo)
+    np.testing.assert_array_equal(M, Mo)
+    np.testing.assert_array_equal(S, s)
+    if beta == 5.0:
+        assert (S == 1).all() and (M == L * L).all()
+
+
+def test_cluster_run_states(ising):
+    """ising_run_states on the cluster path: each state continues the sweep
+    counter, its records land in its own count slots."""
+    L, seed, beta, sweeps, every = 340, 9, 0.41, 6, 2
+    rng = np.random.default_rng(4)
+    states = [np.where(rng.random((L, L)) < 0.2 + 0.2 * k, 1, -1).astype(np.int8) for k in range(3)]
+    with ising.Lattice(L, seed) as lat:
+        lat.set_beta(beta)
+        assert lat.get_path() == ising.ISING_PATH_CLUSTER
+        E, M = lat.run_states(states, sweeps, every)
+        S = lat.get_spins()
+    for k, st in enumerate(states):
+        s = st.copy()
+        Eo, Mo = oracle.run(s, seed, beta, k * sweeps, sweeps, every)
+        np.testing.assert_array_equal(E[k], Eo)
+        np.testing.assert_array_equal(M[k], Mo)
+    np.testing.assert_array_equal(S, s)
+
+
+def test_cluster_path_choice(ising):
+    """Automatic choice by size; the forced path where no plan exists is
+    rejected (too few rows per block, or a share of rows too large for a
+    block's shared memory) and leaves the path unchanged."""
+    expect = {292: ising.ISING_PATH_RESIDENT, 296: ising.ISING_PATH_CLUSTER, 1100: ising.ISING_PATH_CLUSTER,
+              1102: ising.ISING_PATH_LAUNCHES}
+    for L, path in expect.items():
+        with ising.Lattice(L, 1) as lat:
+            assert lat.get_path() == path, L
+    for L in (4, 1640, 2600):
+        with ising.Lattice(L, 1) as lat:
+            with pytest.raises(ising.IsingError):
+                lat.set_path(ising.ISING_PATH_CLUSTER)
+            assert lat.get_path() != ising.ISING_PATH_CLUSTER
+    with ising.Lattice(1008, 1, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
+        with pytest.raises(ising.IsingError):
+            lat.set_path(ising.ISING_PATH_CLUSTER)
+        assert lat.get_path() == ising.ISING_PATH_LAUNCHES

@@ -418,6 +418,7 @@ def test_graphs_with_short_pieces_match_oracle(ising):
 def test_graph_replays_match_oracle(ising):
     L, seed, beta = 1026, 6, 0.44
     with ising.Lattice(L, seed) as lat:
+        lat.set_path(ising.ISING_PATH_LAUNCHES)
         lat.init_hot()
         lat.set_beta(beta)
         E, M = lat.sweep_record(40, 4)
