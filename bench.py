@@ -66,10 +66,11 @@ def parse():
     ap.add_argument("--tiling", default=None, help="rows,block_words,block_groups")
     ap.add_argument("--L", type=int, default=L_LARGE, help="lattice side (profiling of a smaller case)")
     ap.add_argument("--workload", default="large",
-                    choices=["large", "plain", "scan", "batched", "serving", "paper"],
+                    choices=["large", "plain", "scan", "batched", "serving", "paper", "midsize"],
                     help="large (default): L=16384 roofline config; plain: L=64 x 1000 sweeps; "
                          "scan: L=1024 x 26 temperatures; batched: 512 uneven replicas vs per-instance launches; "
-                         "paper: the paper's three test cases (Table 2) in both word layouts")
+                         "paper: the paper's three test cases (Table 2) in both word layouts; "
+                         "midsize: L = 296 .. 1008 on the cluster path and on the graph replays")
     ap.add_argument("--sweeps", type=int, default=None, help="override the workload's sweep count")
     ap.add_argument("--rng", type=int, default=10, choices=[10, 7],
                     help="Philox rounds of the sweep draws: 10 (default scheme) or the opt-in 7")
@@ -495,6 +496,82 @@ def run_plain(args, ising, local):
           "gpu_launches": 3})      # the timed on-chip call: mask draw, on-chip sweeps, sweep counter
 
 
+# Mid-size lattices, between the on-chip range (L <= 292) and L = 1080:
+# there the automatic path is the cluster path (one thread-block
+# cluster keeps the lattice on chip over pieces of up to 256 sweeps).
+MIDSIZE_L = [296, 400, 512, 700, 1008]
+
+
+def cluster_launches(L: int, sweeps: int, every: int) -> int:
+    """Kernel launches of ising_sweep_record(sweeps, every) on the cluster
+    path: per chunk of 1024 records, a mask draw and a cluster launch per
+    piece of sweeps (two mask buffers of at most 16 MB, 256 sweeps at most)
+    and one sweep-counter advance."""
+    W = -(-(L // 2) // 21)
+    P = W + (W & 1)
+    piece = max(1, min(256, (32 << 20) // (2 * 2 * L * P * 8)))
+    launches, records, rest = 0, sweeps // every, sweeps % every
+    while records > 0:
+        chunk = min(records, 1024)
+        launches += 2 * -(-(chunk * every) // piece) + 1
+        records -= chunk
+    if rest > 0:                       # the sweeps after the last record: one ising_sweep
+        launches += 2 * -(-rest // piece) + 1
+    return launches
+
+
+def run_midsize(args, ising, local):
+    """Each mid-size L on the automatic path (the cluster path) and on the
+    graph replays (ISING_PATH_LAUNCHES), T = 2.269 from a hot start, E/M every
+    10 sweeps, about 2e9 spin updates per L and path; CUDA events on the
+    lattice's stream.  The two paths' E/M series must be identical."""
+    import numpy as np
+    import torch
+    stream = torch.cuda.Stream()
+    cases = []
+    total_updates, total_s, launches = 0.0, 0.0, 0
+    with ClockSampler(local) as clocks:
+        for L in MIDSIZE_L:
+            sweeps = args.sweeps or max(10, int(2e9 // (L * L)))
+            sweeps -= sweeps % 10
+            entry = {"L": L, "sweeps": sweeps}
+            series = {}
+            for name, path in (("cluster", ising.ISING_PATH_AUTO), ("graphs", ising.ISING_PATH_LAUNCHES)):
+                with ising.Lattice(L, SEED_LARGE, stream=stream) as lat:
+                    lat.set_path(path)
+                    lat.init_hot()
+                    lat.set_beta(BETA)
+                    lat.sweep_record(40, 10)                     # warm-up (module load, graph capture)
+                    lat.init_hot()
+                    lat.t = 0
+                    if name == "cluster":
+                        assert lat.get_path() == ising.ISING_PATH_CLUSTER, L
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    E, M = lat.sweep_record(sweeps, 10)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    dt = e0.elapsed_time(e1) / 1e3
+                series[name] = (E, M)
+                entry[name] = L * L * sweeps / (dt * 1e9)
+                if name == "cluster":
+                    total_updates += L * L * sweeps
+                    total_s += dt
+                    launches += cluster_launches(L, sweeps, 10)
+            entry["cluster_over_graphs"] = entry["cluster"] / entry["graphs"]
+            entry["bit_exact_across_paths"] = bool(np.array_equal(series["cluster"][0], series["graphs"][0]) and
+                                                   np.array_equal(series["cluster"][1], series["graphs"][1]))
+            cases.append(entry)
+    emit({"metric": METRIC, "value": total_updates / (total_s * 1e9), "unit": METRIC, "n_gpus": 1, "steps": 1,
+          "warmup": 1, "ms_per_step": total_s * 1e3, "higher_is_better": True, "scaling": "weak",
+          "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+          "config": {"workload": "midsize: L = " + ", ".join(map(str, MIDSIZE_L)) + ", T=2.269, hot start seed 3, "
+                                 "about 2e9 spin updates per L, E/M every 10 sweeps; value = the automatic (cluster) "
+                                 "path over all sizes (CUDA events); each size also on the graph replays"},
+          "cases": cases, "clocks": clocks.summary(), "gpu_launches": launches})
+
+
 # The paper's test cases (Table 2): lattice side and iterations; an iteration
 # is 10 update attempts per spin, i.e. 10 sweeps of the checkerboard chain.
 PAPER_CASES = [("case 1", 2016, 5000), ("case 2", 2016, 4500), ("case 3", 1008, 4500)]
@@ -631,7 +708,7 @@ def main():
         import paper_1811_04384_gb300 as ising
         if rank == 0:
             {"batched": run_batched, "scan": run_scan, "plain": run_plain,
-             "serving": run_serving, "paper": run_paper}[args.workload](args, ising, local)
+             "serving": run_serving, "paper": run_paper, "midsize": run_midsize}[args.workload](args, ising, local)
         return
 
     import numpy as np

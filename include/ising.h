@@ -257,7 +257,7 @@ int ising_set_item_lanes(ising_lattice *h, int32_t lanes);
  * ISING_PATH_CLUSTER: temporal blocking on one thread-block cluster (16
  * blocks where the device runs such a cluster, else 8), for row-packed
  * lattices with at least two rows per block whose window fits a block's
- * shared memory (L from 32 up to 1638; otherwise EINVAL, and EINVAL on a
+ * shared memory (L from 32 up to 1600; otherwise EINVAL, and EINVAL on a
  * device without clusters).  Block b keeps rows b L / C .. (b + 1) L / C - 1
  * of both colours in shared memory for a piece of up to 256 sweeps.  After
  * every k <= 12 half-sweeps the blocks pass a cluster barrier and copy k halo
@@ -268,7 +268,7 @@ int ising_set_item_lanes(ising_lattice *h, int32_t lanes);
  * to 32 MB together; 2 L pitch 8 bytes per sweep).  No spin-waits: only the
  * hardware's block and cluster barriers.
  * ISING_PATH_AUTO (default): resident up to 512 thread items (L <= 292), the
- * cluster path above that up to L = 1100, the launch path above that.
+ * cluster path above that up to L = 1080, the launch path above that.
  * Results are identical on every path. */
 #define ISING_PATH_AUTO 0
 #define ISING_PATH_LAUNCHES 1

@@ -1,5 +1,5 @@
 // Cluster-resident temporal blocking for mid-size lattices (above the
-// one-SM on-chip range, L of about 300 to 1100).
+// one-SM on-chip range, L of about 300 to 1080).
 //
 // There a half-sweep is short: a replayed graph node per half-sweep costs
 // more than its work.  Here one launch of a single thread-block cluster (16
@@ -92,12 +92,13 @@ struct Slot {
 };
 
 // One update of colour C: the spin logic of row_apply with the packed masks
-// p (r < thr1 at bit 3k, r < thr0 at bit 3k + 1) staged in msk.  RECORD adds
-// the row's anti-aligned bonds and up spins.
+// p (r < thr1 at bit 3k, r < thr0 at bit 3k + 1, each already set where its
+// threshold is 2^32) staged in msk.  RECORD adds the row's anti-aligned
+// bonds and up spins.
 template <int C, bool RECORD>
 __device__ __forceinline__ void cl_update(uint64_t* own, const uint64_t* other, const uint64_t* msk, uint32_t P,
-                                          const Slot& sl, uint64_t live_last, uint64_t all0, uint64_t all1,
-                                          uint64_t n, uint32_t& anti, uint32_t& up)
+                                          const Slot& sl, uint64_t live_last, uint64_t n, uint32_t& anti,
+                                          uint32_t& up)
 {
     const uint32_t o = sl.o;
     const bool left = ((sl.bits >> 16) & 1u) != (uint32_t)C;
@@ -114,7 +115,7 @@ __device__ __forceinline__ void cl_update(uint64_t* own, const uint64_t* other, 
     const uint64_t x1 = s ^ u, x2 = s ^ d, x3 = s ^ h0, x4 = s ^ h1;
     const uint64_t any = x1 | x2 | x3 | x4;
     const uint64_t ge2 = (x1 & x2) | (x3 & x4) | ((x1 ^ x2) & (x3 ^ x4));
-    const uint64_t accept = ge2 | (any & (p | all1)) | (~any & ((p >> 1) | all0));
+    const uint64_t accept = ge2 | (any & p) | (~any & (p >> 1));
     const uint64_t s_new = s ^ (accept & live);
     word_st(own, o, s_new, n, __LINE__);
     if (RECORD) {
@@ -130,17 +131,16 @@ __device__ __forceinline__ void cl_update(uint64_t* own, const uint64_t* other, 
 template <int C, bool RECORD, int NS>
 __device__ __forceinline__ void cl_half_sweep(uint64_t* own, const uint64_t* other, const uint64_t* msk, uint32_t P,
                                               const Slot (&slot)[NS], int lo, int hi, uint64_t live_last,
-                                              uint64_t all0, uint64_t all1, uint64_t n,
-                                              unsigned long long* counts)
+                                              uint64_t n, unsigned long long* counts)
 {
     uint32_t anti = 0, up = 0;
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
         if (slot[j].lr >= lo && slot[j].lr <= hi) {
             if (RECORD && (slot[j].bits & (1u << 18)))
-                cl_update<C, true>(own, other, msk, P, slot[j], live_last, all0, all1, n, anti, up);
+                cl_update<C, true>(own, other, msk, P, slot[j], live_last, n, anti, up);
             else
-                cl_update<C, false>(own, other, msk, P, slot[j], live_last, all0, all1, n, anti, up);
+                cl_update<C, false>(own, other, msk, P, slot[j], live_last, n, anti, up);
         }
     }
     if (RECORD) block_add_counts(counts + 2 * (blockIdx.x % kCountSlots), anti, up);
@@ -173,21 +173,23 @@ cluster_sweeps_kernel(ClusterArgs a)
     uint64_t* msk = smem + 2 * n;                                       // Q slabs of n words
     const int pairs = g.P / 2;
     const uint32_t sh_wrap = 3u * (uint32_t)(g.rlast - 1);
-    // slots: window words e = t + j T of rows 1 .. R - 2, and the mask copies
-    // (16 bytes, word pairs) of the same rows
+    // slots: window words e = t + j T of rows 1 .. R - 2 in steps of the
+    // pitch P (a padding word W .. P - 1 has no update: a warp's loads stay
+    // on consecutive words, without bank conflicts), and the mask copies (16
+    // bytes, word pairs) of the same rows
     Slot slot[NS];
     uint32_t cdst[NS], csrc[NS];
     const uint32_t msk_sh = (uint32_t)__cvta_generic_to_shared(msk);
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
         const int e = threadIdx.x + j * T;
-        const int lr = 1 + e / g.W, w = e % g.W;
+        const int lr = 1 + e / g.P, w = e % g.P;
         const bool first = w == 0, last = w == g.W - 1;
         const bool left0 = ((top + lr) & 1) == 0;      // colour 0 at (i + 0) even
         // left neighbour: word w - 1 (wrapped), right: w + 1 (wrapped)
         const int dleft = first ? (int)W - 1 : -1, dright = last ? -((int)W - 1) : 1;
         const uint32_t shl = first ? sh_wrap : 60u, shr = last ? sh_wrap : 60u;
-        slot[j].lr = lr <= R - 2 ? lr : -1;
+        slot[j].lr = lr <= R - 2 && w < g.W ? lr : -1;
         slot[j].o = (uint32_t)lr * P + (uint32_t)w;
         slot[j].dl = (uint32_t)(uint16_t)(int16_t)(left0 ? dleft : dright) |
                      ((uint32_t)(uint16_t)(int16_t)(left0 ? dright : dleft) << 16);
@@ -198,8 +200,6 @@ cluster_sweeps_kernel(ClusterArgs a)
         csrc[j] = (uint32_t)wrap_index(top + cr, g.L) * P + 2u * (uint32_t)cp;
     }
     const uint64_t live_last = live_mask(g, g.W - 1);
-    const uint64_t all0 = (uint64_t)a.all0 << 32 | a.all0;
-    const uint64_t all1 = (uint64_t)a.all1 << 32 | a.all1;
     const int total = 2 * a.nsweeps;
     const uint32_t slab_bytes = (uint32_t)(n * sizeof(uint64_t));
     const size_t plane = (size_t)g.L * P;                               // one half-sweep's masks
@@ -220,6 +220,36 @@ cluster_sweeps_kernel(ClusterArgs a)
         next_src += plane;
         put = put + 1 == Q ? 0 : put + 1;
     };
+    // halo rows: receive slots rb(par, c, 0) for the k rows above the block's
+    // own (the last own rows of the block above), rb(par, c, 1) for the k rows
+    // below; two sets (par), used by alternate phases
+    const int kP = k * (int)P;
+    auto rb = [&](uint64_t* base, int par, int c, int dir) { return base + (size_t)((par * 2 + c) * 2 + dir) * kP; };
+    uint64_t* recv = msk + (size_t)Q * n;
+    // a block's first k own rows go to the slots below of the block above, its
+    // last k own rows to the slots above of the block below
+    auto push = [&](int par) {
+        uint64_t* up_recv = cluster.map_shared_rank(recv, bp);
+        uint64_t* dn_recv = cluster.map_shared_rank(recv, bn);
+        for (int c = 0; c < 2; ++c) {
+            uint64_t* to_up = rb(up_recv, par, c, 1);
+            uint64_t* to_dn = rb(dn_recv, par, c, 0);
+            for (int idx = threadIdx.x; idx < kP; idx += T) {
+                to_up[idx] = win[c][(size_t)k * P + idx];
+                to_dn[idx] = win[c][(size_t)S * P + idx];
+            }
+        }
+    };
+    auto receive = [&](int par) {
+        for (int c = 0; c < 2; ++c) {
+            const uint64_t* from_up = rb(recv, par, c, 0);
+            const uint64_t* from_dn = rb(recv, par, c, 1);
+            for (int idx = threadIdx.x; idx < kP; idx += T) {
+                win[c][idx] = from_up[idx];
+                win[c][(size_t)(k + S) * P + idx] = from_dn[idx];
+            }
+        }
+    };
     // own rows of both colours, from the lattice, to window rows k .. k + S - 1
     for (int c = 0; c < 2; ++c)
         for (int e = threadIdx.x; e < S * pairs; e += T) {
@@ -229,70 +259,66 @@ cluster_sweeps_kernel(ClusterArgs a)
         }
     cl_commit();
     cl_wait<0>();
+    __syncthreads();
+    push(0);
 #pragma unroll
     for (int h = 0; h < Q - 1; ++h) stage();
-    int use = 0;                                                        // slab of the current half-sweep
+    cluster.sync();          // the first phase's halos have arrived
+    int use = 0;             // slab of the current half-sweep
     // before a half-sweep: its slab staged, the previous half-sweep done (its
-    // rows final, its slab free for the copies of half-sweep h + Q - 1)
-    auto step = [&]() {
+    // rows final, its slab free for the copies of half-sweep h + Q - 1, which
+    // follow the update)
+    auto begin = [&]() {
         cl_wait<Q - 2>();
         __syncthreads();
-        stage();
         const uint64_t* m = msk + (size_t)use * n;
         use = use + 1 == Q ? 0 : use + 1;
         return m;
     };
     int64_t s_call = a.s0;                                              // sweeps of the call done
     int64_t next_rec = a.every > 0 ? (a.s0 / a.every + 1) * a.every : -1;
+    int par = 0;
     for (int hs0 = 0; hs0 < total; hs0 += k) {
         const int kk = min(k, total - hs0);                             // even: phases start with colour 0
-        cluster.sync();      // every block's own rows are final for the previous phase
-        // halo rows from the neighbours' shared memory: the last k own rows of
-        // the block above (its window rows Sp .. Sp + k - 1) to rows 0 .. k - 1,
-        // the first k own rows of the block below (its rows k .. 2k - 1) to
-        // rows k + S .. 2k + S - 1
-        for (int c = 0; c < 2; ++c) {
-            const uint64_t* above = cluster.map_shared_rank(win[c], bp);
-            const uint64_t* below = cluster.map_shared_rank(win[c], bn);
-            for (int idx = threadIdx.x; idx < k * (int)P; idx += T) {
-                const int r = idx / (int)P, x = idx - r * (int)P;
-                win[c][(size_t)r * P + x] = above[(size_t)(Sp + r) * P + x];
-                win[c][(size_t)(k + S + r) * P + x] = below[(size_t)(k + r) * P + x];
-            }
-        }
-        cluster.sync();      // every block has its halo: own rows may change now
+        receive(par);        // into the halo rows (ordered before the updates by begin's barrier)
         for (int d = 0; d < kk; d += 2) {
-            const uint64_t* m0 = step();
-            cl_half_sweep<0, false, NS>(win[0], win[1], m0, P, slot, 1 + d, R - 2 - d, live_last, all0, all1, n,
-                                        nullptr);
-            const uint64_t* m1 = step();
+            const uint64_t* m0 = begin();
+            cl_half_sweep<0, false, NS>(win[0], win[1], m0, P, slot, 1 + d, R - 2 - d, live_last, n, nullptr);
+            stage();
+            const uint64_t* m1 = begin();
             ++s_call;
             if (s_call == next_rec) {
                 unsigned long long* cnt = a.counts + (size_t)(s_call / a.every - 1) * 2 * kCountSlots;
-                cl_half_sweep<1, true, NS>(win[1], win[0], m1, P, slot, 2 + d, R - 3 - d, live_last, all0, all1,
-                                           n, cnt);
+                cl_half_sweep<1, true, NS>(win[1], win[0], m1, P, slot, 2 + d, R - 3 - d, live_last, n, cnt);
                 next_rec += a.every;
             } else {
-                cl_half_sweep<1, false, NS>(win[1], win[0], m1, P, slot, 2 + d, R - 3 - d, live_last, all0, all1,
-                                            n, nullptr);
+                cl_half_sweep<1, false, NS>(win[1], win[0], m1, P, slot, 2 + d, R - 3 - d, live_last, n, nullptr);
             }
+            stage();
         }
+        par ^= 1;
+        if (hs0 + k < total) {
+            __syncthreads();     // own rows final for this phase
+            push(par);
+        }
+        // the next phase's halos have arrived; the slots the next pushes write
+        // were read at the start of this phase; after the last phase: no block
+        // leaves while another may still write its shared memory
+        cluster.sync();
     }
     // own rows back to the lattice
     cl_wait<0>();
-    __syncthreads();
     for (int c = 0; c < 2; ++c)
         for (int idx = threadIdx.x; idx < S * (int)P; idx += T) {
             const int r = idx / (int)P, x = idx - r * (int)P;
             a.w[c][(size_t)(r0 + r) * P + x] = win[c][(size_t)(k + r) * P + x];
         }
-    cluster.sync();          // no block leaves while another may still read its shared memory
 }
 
 // Masks of sweeps j = 0 .. nsweeps-1 after sweep (t_base ? *t_base : 0) + t0:
 // one thread per (sweep, colour, item) draws them with item_masks_thread (the
 // draws of sweep_rows) and writes them row-major, masks[((j * 2 + c) * L + i)
-// * P + w].
+// * P + w], with the bits of a threshold of 2^32 set.
 template <int ROUNDS>
 __global__ void __launch_bounds__(128)
 cl_mask_draw_kernel(Geom g, SweepArgs a, const uint64_t* t_base, uint64_t t0, int nsweeps,
@@ -308,18 +334,23 @@ cl_mask_draw_kernel(Geom g, SweepArgs a, const uint64_t* t_base, uint64_t t0, in
     const uint64_t t = (t_base ? *t_base : 0) + t0 + (uint64_t)(jc >> 1) + 1;
     uint64_t p[4];
     item_masks_thread<ROUNDS>(g, item, t, jc & 1, a.rk, a.thr0, a.thr1, a.one, p);
+    // a threshold of 2^32 accepts always: its bits set here, not in the update
+    const uint64_t always = (((uint64_t)a.all1 << 32 | a.all1) & kSpinBits) |
+                            ((((uint64_t)a.all0 << 32 | a.all0) & kSpinBits) << 1);
     uint64_t* out = masks + (size_t)jc * g.L * g.P;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const int i = 4 * grp + e;
-        if (i < g.L) out[(size_t)i * g.P + w] = p[e];
+        if (i < g.L) out[(size_t)i * g.P + w] = p[e] | always;
     }
 }
 
+// Both colour windows and q mask slabs (largest share of rows + 2 k rows
+// each), and 8 halo receive slots of k rows.
 size_t cl_smem_bytes(const Geom& g, int blocks, int k, int q)
 {
     const int smax = (g.L + blocks - 1) / blocks;
-    return (size_t)(2 + q) * (smax + 2 * k) * g.P * sizeof(uint64_t);
+    return ((size_t)(2 + q) * (smax + 2 * k) + 8 * (size_t)k) * g.P * sizeof(uint64_t);
 }
 
 // The six forms of the kernel: 1, 2 or 4 words per thread, 2 or kClMaxSlabs mask slabs.
@@ -375,7 +406,9 @@ int probe_max_cluster()
 // slabs), with at most 2 window words per thread where some k allows it,
 // else 4.  Measured on GB300 (sweeps without records, spin-updates/ns, by k
 // = 4 / 8 / 12): L = 296: 77 / 105 / 115, L = 512: 170 / 199 / 210,
-// L = 1008: 357 / 394 / 403; 4 words per thread (L = 1008, k = 16) 336.
+// L = 1008: 357 / 394 / 403; 4 words per thread (L = 1008, k = 16) 336
+// (threads over the W live words of a row then; over the pitch since, which
+// gave L = 512: 215, L = 1008: 416 at k = 12).
 // Returns false if no such launch exists (a lattice too large or too small).
 bool cluster_plan(const Geom& g, ClusterPlan* plan)
 {
@@ -387,7 +420,7 @@ bool cluster_plan(const Geom& g, ClusterPlan* plan)
         for (int q : {kClMaxSlabs, 2}) {
             for (int kk = std::min(kClHalo, fewest) & ~1; kk >= 2; kk -= 2) {
                 if (cl_smem_bytes(g, c, kk, q) > kClSmemMax) continue;
-                const long long words = (long long)((g.L + c - 1) / c + 2 * kk - 2) * g.W;
+                const long long words = (long long)((g.L + c - 1) / c + 2 * kk - 2) * g.P;
                 if (words > (long long)most * kClThreads) continue;
                 const int ns = words <= kClThreads ? 1 : (words <= 2 * kClThreads ? 2 : 4);
                 plan->blocks = c;

@@ -598,10 +598,10 @@ static int run_resident(ising_lattice* h, int n, int every)
 // Replayed graphs of short half-sweeps stay for the launch path
 // (ISING_PATH_LAUNCHES) and for larger lattices.  Measured on GB300, sweeps
 // without records, spin-updates/ns, cluster against graphs: L = 296: 115 /
-// 34; L = 512: 210 / 97; L = 700: 265 / 169; L = 1008: 403 / 314; L = 1100:
-// 365 / 347; but L = 1200: 297 / 358, where the window needs 4 words per
-// thread.
-constexpr int kClusterMaxL = 1100;
+// 34; L = 512: 215 / 96; L = 700: 284 / 171; L = 1008: 416 / 314; but
+// L = 1100: 329 / 348, where the window allows phases of 2 half-sweeps only.
+// Up to L = 1086 the phases have 6 or more.
+constexpr int kClusterMaxL = 1080;
 constexpr size_t kClusterMaskBytes = 32u << 20;    // both buffers
 constexpr int kClusterMaxPiece = 256;
 

@@ -3,10 +3,10 @@ blocks' shared memory, halos exchanged through distributed shared memory)
 against the oracle, bit-exact: int64 E/M series and final spins.
 
 Cases span two rows per block (L = 32, two half-sweeps per phase), the
-automatic range (L = 296 just above the on-chip path, up to L = 1100 with two
+automatic range (L = 296 just above the on-chip path, up to L = 1080 with two
 mask pieces), L % 4 == 2, records out of step with the phases and pieces,
 odd numbers of half-sweeps per call, forced runs up to the largest side
-(L = 1638), cold starts, beta = 0 (every flip accepted) and a frozen
+(L = 1600), cold starts, beta = 0 (every flip accepted) and a frozen
 lattice, runs continued across calls and paths, and ising_run_states.
 """
 import numpy as np
@@ -34,9 +34,9 @@ CASES = [
     (296, 37, 1, BETA_TC, False),  # 74 half-sweeps: phases of 8 and a short last one
     (514, 20, 3, 0.3, False),      # L % 4 == 2; 6 records, out of step with the phases
     (1008, 24, 4, 0.44, False),    # the paper's L = 1008
-    (1100, 60, 5, BETA_TC, False), # largest automatic side: two mask pieces (34 + 26 sweeps)
+    (1080, 60, 5, BETA_TC, False), # largest automatic side: two mask pieces (37 + 23 sweeps)
     (1500, 6, 1, 0.44, True),      # phases of 10 half-sweeps, 4 words per thread
-    (1638, 3, 1, BETA_TC, True),   # largest side with a plan: phases of 3
+    (1600, 3, 1, BETA_TC, True),   # largest side with a plan: 4 words per thread
 ]
 
 
@@ -130,8 +130,8 @@ def test_cluster_path_choice(ising):
     """Automatic choice by size; the forced path where no plan exists is
     rejected (too few rows per block, or a share of rows too large for a
     block's shared memory) and leaves the path unchanged."""
-    expect = {292: ising.ISING_PATH_RESIDENT, 296: ising.ISING_PATH_CLUSTER, 1100: ising.ISING_PATH_CLUSTER,
-              1102: ising.ISING_PATH_LAUNCHES}
+    expect = {292: ising.ISING_PATH_RESIDENT, 296: ising.ISING_PATH_CLUSTER, 1080: ising.ISING_PATH_CLUSTER,
+              1082: ising.ISING_PATH_LAUNCHES}
     for L, path in expect.items():
         with ising.Lattice(L, 1) as lat:
             assert lat.get_path() == path, L
