@@ -70,6 +70,27 @@ __device__ __forceinline__ void cl_copy16(uint32_t smem_dst, const void* gmem_sr
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_dst), "l"(gmem_src) : "memory");
 }
 
+// cl_copy16 to shared address `dst` from `src`.  In a checked build the
+// copy is skipped and recorded (see word_ld) unless both words of the pair
+// lie in the `dst_words` words from shared address `dst_base` and in the
+// `src_words` words from `src_base`.
+__device__ __forceinline__ void cl_copy_pair(uint32_t dst, uint32_t dst_base, uint64_t dst_words, const uint64_t* src,
+                                             const uint64_t* src_base, uint64_t src_words, uint32_t line)
+{
+#ifdef ISING_CHECKED
+    if (!check_index((uint64_t)(dst - dst_base) / 8 + 1, dst_words, line) ||
+        !check_index((uint64_t)(src - src_base) + 1, src_words, line))
+        return;
+#else
+    (void)dst_base;
+    (void)dst_words;
+    (void)src_base;
+    (void)src_words;
+    (void)line;
+#endif
+    cl_copy16(dst, src);
+}
+
 __device__ __forceinline__ void cl_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
 template <int N>
@@ -179,6 +200,7 @@ cluster_sweeps_kernel(ClusterArgs a)
     // bytes, word pairs) of the same rows
     Slot slot[NS];
     uint32_t cdst[NS], csrc[NS];
+    const uint32_t smem_sh = (uint32_t)__cvta_generic_to_shared(smem);
     const uint32_t msk_sh = (uint32_t)__cvta_generic_to_shared(msk);
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
@@ -196,24 +218,28 @@ cluster_sweeps_kernel(ClusterArgs a)
         slot[j].bits = (left0 ? shl : shr) | ((left0 ? shr : shl) << 8) | (left0 ? 1u << 16 : 0u) |
                        (last ? 1u << 17 : 0u) | ((lr >= k && lr < R - k) ? 1u << 18 : 0u);
         const int cr = 1 + e / pairs, cp = e % pairs;
-        cdst[j] = cr <= R - 2 ? msk_sh + 8u * ((uint32_t)cr * P + 2u * (uint32_t)cp) : ~0u;
+        cdst[j] = cr <= R - 2 ? msk_sh + 8u * ((uint32_t)cr * P + 2u * (uint32_t)cp) : ~0u;   // in slab 0
         csrc[j] = (uint32_t)wrap_index(top + cr, g.L) * P + 2u * (uint32_t)cp;
     }
     const uint64_t live_last = live_mask(g, g.W - 1);
     const int total = 2 * a.nsweeps;
-    const uint32_t slab_bytes = (uint32_t)(n * sizeof(uint64_t));
     const size_t plane = (size_t)g.L * P;                               // one half-sweep's masks
+    const uint64_t mask_words = (uint64_t)total * plane;                // the launch's mask array
     // masks of the next half-sweep to stage (number `next`) for window rows
     // 1 .. R - 2 into slab `put` (one copy group per half-sweep, empty past
     // the end)
-    const uint64_t* next_src = a.masks;
     int next = 0, put = 0;
+    const uint64_t smem_words = (uint64_t)(2 + Q) * n + 8 * (uint64_t)k * P;
+    const uint32_t slab_bytes = (uint32_t)(n * sizeof(uint64_t));
+    const uint64_t* next_src = a.masks;
     auto stage = [&]() {
         if (next < total) {
             const uint32_t off = (uint32_t)put * slab_bytes;
 #pragma unroll
             for (int j = 0; j < NS; ++j)
-                if (cdst[j] != ~0u) cl_copy16(cdst[j] + off, next_src + csrc[j]);
+                if (cdst[j] != ~0u)
+                    cl_copy_pair(cdst[j] + off, smem_sh, smem_words, next_src + csrc[j], a.masks, mask_words,
+                                 __LINE__);
         }
         cl_commit();
         ++next;
@@ -235,8 +261,8 @@ cluster_sweeps_kernel(ClusterArgs a)
             uint64_t* to_up = rb(up_recv, par, c, 1);
             uint64_t* to_dn = rb(dn_recv, par, c, 0);
             for (int idx = threadIdx.x; idx < kP; idx += T) {
-                to_up[idx] = win[c][(size_t)k * P + idx];
-                to_dn[idx] = win[c][(size_t)S * P + idx];
+                word_st(to_up, idx, word_ld<false>(win[c], (uint64_t)k * P + idx, n, __LINE__), kP, __LINE__);
+                word_st(to_dn, idx, word_ld<false>(win[c], (uint64_t)S * P + idx, n, __LINE__), kP, __LINE__);
             }
         }
     };
@@ -245,8 +271,9 @@ cluster_sweeps_kernel(ClusterArgs a)
             const uint64_t* from_up = rb(recv, par, c, 0);
             const uint64_t* from_dn = rb(recv, par, c, 1);
             for (int idx = threadIdx.x; idx < kP; idx += T) {
-                win[c][idx] = from_up[idx];
-                win[c][(size_t)(k + S) * P + idx] = from_dn[idx];
+                word_st(win[c], idx, word_ld<false>(from_up, idx, kP, __LINE__), n, __LINE__);
+                word_st(win[c], (uint64_t)(k + S) * P + idx, word_ld<false>(from_dn, idx, kP, __LINE__), n,
+                        __LINE__);
             }
         }
     };
@@ -254,8 +281,8 @@ cluster_sweeps_kernel(ClusterArgs a)
     for (int c = 0; c < 2; ++c)
         for (int e = threadIdx.x; e < S * pairs; e += T) {
             const int r = e / pairs, cp = e - r * pairs;
-            cl_copy16((uint32_t)__cvta_generic_to_shared(win[c] + (size_t)(k + r) * P + 2 * cp),
-                      a.w[c] + (size_t)(r0 + r) * P + 2 * cp);
+            cl_copy_pair(smem_sh + 8u * (uint32_t)(c * n + (size_t)(k + r) * P + 2 * cp), smem_sh, smem_words,
+                         a.w[c] + (size_t)(r0 + r) * P + 2 * cp, a.w[c], lattice_words(g), __LINE__);
         }
     cl_commit();
     cl_wait<0>();
@@ -309,10 +336,9 @@ cluster_sweeps_kernel(ClusterArgs a)
     // own rows back to the lattice
     cl_wait<0>();
     for (int c = 0; c < 2; ++c)
-        for (int idx = threadIdx.x; idx < S * (int)P; idx += T) {
-            const int r = idx / (int)P, x = idx - r * (int)P;
-            a.w[c][(size_t)(r0 + r) * P + x] = win[c][(size_t)(k + r) * P + x];
-        }
+        for (int idx = threadIdx.x; idx < S * (int)P; idx += T)
+            word_st(a.w[c], (uint64_t)r0 * P + idx, word_ld<false>(win[c], (uint64_t)k * P + idx, n, __LINE__),
+                    lattice_words(g), __LINE__);
 }
 
 // Masks of sweeps j = 0 .. nsweeps-1 after sweep (t_base ? *t_base : 0) + t0:

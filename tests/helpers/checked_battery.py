@@ -56,6 +56,14 @@ def main():
         lattice_case(64, 5, path=p.ISING_PATH_LAUNCHES, lanes=F)
     lattice_case(130, 5, path=p.ISING_PATH_LAUNCHES, lanes=1, tiling=(4, 16, 8))
     cases += 7
+    # the cluster path: automatic at L = 300 (one word per thread, 8 mask
+    # slabs), forced at L = 64 (phases of 4), L = 700 (two words per thread)
+    # and L = 1500 (four words per thread, two slabs)
+    lattice_case(300, 14)
+    lattice_case(64, 9, path=p.ISING_PATH_CLUSTER, every=3)
+    lattice_case(700, 6, every=2)
+    lattice_case(1500, 3, path=p.ISING_PATH_CLUSTER)
+    cases += 4
     # batch of uneven replicas
     Ls = [6, 44, 130, 64, 12]
     seeds = [3, 4, 5, 6, 7]
