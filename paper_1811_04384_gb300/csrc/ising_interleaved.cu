@@ -109,16 +109,19 @@ ci_mask_draw_kernel(int L, int N, SweepArgs a, const uint64_t* t_base, uint64_t 
                     uint64_t* __restrict__ masks)
 {
     const long long Q = N / 4, M = L / 2;
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (long long)nsweeps * 2 * Q * M) return;
-    const int m = (int)(k % M);
-    const int q = (int)((k / M) % Q);
-    const int colour = (int)((k / (M * Q)) & 1);
-    const int j = (int)(k / (2 * M * Q));
-    uint64_t packed[4];
-    ci_masks<ROUNDS>(N, q, m, (t_base ? *t_base : 0) + t0 + (uint64_t)j + 1, colour, a, packed);
+    const long long total = (long long)nsweeps * 2 * Q * M;
+    const uint64_t tb = (t_base ? *t_base : 0) + t0 + 1;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)(k % M);
+        const int q = (int)((k / M) % Q);
+        const int colour = (int)((k / (M * Q)) & 1);
+        const int j = (int)(k / (2 * M * Q));
+        uint64_t packed[4];
+        ci_masks<ROUNDS>(N, q, m, tb + (uint64_t)j, colour, a, packed);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) masks[(size_t)k * 4 + e] = packed[e];
+        for (int e = 0; e < 4; ++e) masks[(size_t)k * 4 + e] = packed[e];
+    }
 }
 
 // One half-sweep of colour C.  Thread (m, q) owns word rows 4q .. 4q+3 and the
@@ -617,11 +620,12 @@ cudaError_t ci_half_sweep(int colour, bool update, bool record, uint64_t* S, int
 size_t ci_mask_bytes_per_sweep(int L) { return (size_t)8 * (L / 21) * L; }
 
 cudaError_t ci_mask_draw(int L, const SweepArgs& a, const uint64_t* t_base, uint64_t t0, int nsweeps,
-                         uint64_t* masks, cudaStream_t s)
+                         uint64_t* masks, int blocks_per_sm, cudaStream_t s)
 {
     const int N = L / 21;
     const long long threads = (long long)nsweeps * 2 * (N / 4) * (L / 2);
-    const unsigned blocks = (unsigned)((threads + 127) / 128);
+    unsigned blocks = (unsigned)((threads + 127) / 128);
+    if (blocks_per_sm > 0) blocks = std::min(blocks, (unsigned)(device_sm_count() * blocks_per_sm));
     if (a.rounds == 7) ci_mask_draw_kernel<7><<<blocks, 128, 0, s>>>(L, N, a, t_base, t0, nsweeps, masks);
     else ci_mask_draw_kernel<10><<<blocks, 128, 0, s>>>(L, N, a, t_base, t0, nsweeps, masks);
     return cudaGetLastError();

@@ -16,11 +16,12 @@ cudaError_t ci_half_sweep(int colour, bool update, bool record, uint64_t* S, int
                           cudaStream_t s);
 // Masks drawn ahead: ci_mask_draw fills `masks` with the accept masks of the
 // nsweeps sweeps after sweep (t_base ? *t_base : 0) + t0 (both colours,
-// ci_mask_bytes_per_sweep(L) bytes per sweep); ci_half_sweep_pre applies
-// the block of one sweep (`sweep_masks`) to colour `colour`.
+// ci_mask_bytes_per_sweep(L) bytes per sweep), with at most blocks_per_sm
+// 128-thread blocks per SM (0: one thread per unit); ci_half_sweep_pre
+// applies the block of one sweep (`sweep_masks`) to colour `colour`.
 size_t ci_mask_bytes_per_sweep(int L);
 cudaError_t ci_mask_draw(int L, const SweepArgs& a, const uint64_t* t_base, uint64_t t0, int nsweeps,
-                         uint64_t* masks, cudaStream_t s);
+                         uint64_t* masks, int blocks_per_sm, cudaStream_t s);
 cudaError_t ci_half_sweep_pre(int colour, bool record, uint64_t* S, int L, const SweepArgs& a,
                               const uint64_t* sweep_masks, cudaStream_t s);
 

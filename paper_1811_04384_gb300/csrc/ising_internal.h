@@ -67,8 +67,12 @@ inline int premasked_rows_per_thread(int items) { return items <= 256 ? 1 : 2; }
 // 32 / 64 / 100 against 0.57 / 0.44 / 0.45 / 0.87 with one, but 0.99
 // against 0.92 at L = 128 (128 items, 32 warps).
 inline int premasked_threads_per_row(int items) { return items <= 100 ? 2 : 1; }
+// blocks_per_sm > 0: at most that many 128-thread blocks per SM, each
+// looping over its share (0: one thread per sweep and item).
 cudaError_t launch_mask_draw(const Geom& g, const SweepArgs& a, const uint64_t* t_base, uint64_t t0, int nsweeps,
-                             ulonglong2* masks, cudaStream_t s);
+                             ulonglong2* masks, int blocks_per_sm, cudaStream_t s);
+// SMs of the current device (1 if the query fails).
+int device_sm_count();
 // One half-sweep that applies masks drawn by launch_mask_draw (`masks`: the
 // entries of its sweep), one thread per row.
 cudaError_t launch_half_sweep_apply(int colour, bool record, uint64_t* own, const uint64_t* other, const Geom& g,

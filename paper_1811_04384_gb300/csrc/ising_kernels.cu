@@ -224,17 +224,20 @@ __global__ void __launch_bounds__(128)
 mask_draw_kernel(Geom g, SweepArgs a, const uint64_t* t_base, uint64_t t0, int nsweeps, ulonglong2* __restrict__ masks)
 {
     const int items = ((g.L + 3) / 4) * g.W;
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (long long)nsweeps * items) return;
-    const int j = (int)(k / items);
-    const int item = (int)(k - (long long)j * items);
-    uint64_t p0[4], p1[4];
-    const uint64_t t = (t_base ? *t_base : 0) + t0 + (uint64_t)j + 1;
-    item_masks_thread<ROUNDS>(g, item, t, 0, a.rk, a.thr0, a.thr1, a.one, p0);
-    item_masks_thread<ROUNDS>(g, item, t, 1, a.rk, a.thr0, a.thr1, a.one, p1);
-    ulonglong2* out = masks + (size_t)k * 4;
+    const long long total = (long long)nsweeps * items;
+    const uint64_t tb = (t_base ? *t_base : 0) + t0 + 1;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(k / items);
+        const int item = (int)(k - (long long)j * items);
+        uint64_t p0[4], p1[4];
+        const uint64_t t = tb + (uint64_t)j;
+        item_masks_thread<ROUNDS>(g, item, t, 0, a.rk, a.thr0, a.thr1, a.one, p0);
+        item_masks_thread<ROUNDS>(g, item, t, 1, a.rk, a.thr0, a.thr1, a.one, p1);
+        ulonglong2* out = masks + (size_t)k * 4;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) out[e] = make_ulonglong2(p0[e], p1[e]);
+        for (int e = 0; e < 4; ++e) out[e] = make_ulonglong2(p0[e], p1[e]);
+    }
 }
 
 // The on-chip path with the masks drawn beforehand (mask_draw_kernel): one
@@ -649,13 +652,27 @@ cudaError_t launch_resident(uint64_t* w0, uint64_t* w1, const Geom& g, const Swe
     return cudaGetLastError();
 }
 
+int device_sm_count()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    return sms;
+}
+
 // Masks of the nsweeps sweeps following sweep (t_base ? *t_base : 0) + t0
-// into `masks` (nsweeps * items * 4 entries).
+// into `masks` (nsweeps * items * 4 entries), with at most
+// blocks_per_sm * (the device's SMs) blocks of 128 threads (0: one thread
+// per sweep and item).
 cudaError_t launch_mask_draw(const Geom& g, const SweepArgs& a, const uint64_t* t_base, uint64_t t0, int nsweeps,
-                             ulonglong2* masks, cudaStream_t s)
+                             ulonglong2* masks, int blocks_per_sm, cudaStream_t s)
 {
     const long long threads = (long long)nsweeps * (((g.L + 3) / 4) * g.W);
-    const unsigned blocks = (unsigned)((threads + 127) / 128);
+    unsigned blocks = (unsigned)((threads + 127) / 128);
+    if (blocks_per_sm > 0) blocks = std::min(blocks, (unsigned)(device_sm_count() * blocks_per_sm));
     if (a.rounds == 7) mask_draw_kernel<7><<<blocks, 128, 0, s>>>(g, a, t_base, t0, nsweeps, masks);
     else mask_draw_kernel<10><<<blocks, 128, 0, s>>>(g, a, t_base, t0, nsweeps, masks);
     return cudaGetLastError();

@@ -346,6 +346,23 @@ static int draw_sweeps(const ising_lattice* h)
     return (int)std::max<size_t>(1, std::min<size_t>(kMaxDrawSweeps, kGraphMaskBytes / (2 * 64 * items)));
 }
 
+// Blocks per SM of a graph's mask draws (0: one thread per unit): a capped
+// grid whose blocks loop over the piece leaves room on every SM for the
+// half-sweeps of the piece before, which run beside it on the other branch.
+// Measured on GB300 (sweeps without records, spin-updates/ns, one thread per
+// unit / 2 / 3 blocks per SM), row-packed: L = 1500: 508 / 539 / 532;
+// L = 2016: 680 / 744 / 703; L = 3000: 887 / 941 / 915; L = 4096: 1006 / 923
+// / 1035.  Column-interleaved: L = 1008: 305 / 283 / 291; L = 1512: 388 /
+// 445 / 427; L = 2016: 511 / 575 / 552; L = 3024: 611 / 669 / 645;
+// L = 4032: 683 / 295 / 360 (its half-sweeps use programmatic launches in the
+// graphs from 80,000 items).
+static int draw_blocks_per_sm(const ising_lattice* h)
+{
+    const int items = ((h->g.L + 3) / 4) * h->g.W;      // both layouts: the same thread count
+    if (h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED) return items >= 10000 && items < 80000 ? 2 : 0;
+    return items < 80000 ? 2 : 3;
+}
+
 static bool use_graphs(const ising_lattice* h)
 {
     return ((h->g.L + 3) / 4) * h->g.W <= kGraphMaxItems;      // both layouts: the same thread count
@@ -420,9 +437,9 @@ static int capture_sweeps(ising_lattice* h, int n, int every, cudaGraphExec_t* o
         const int count = std::min(D, n - first);
         char* buf = buffers + (size_t)(k & 1) * D * sweep_bytes;
         cudaError_t r = ci ? ci_mask_draw(h->g.L, a, h->t_dev, (uint64_t)first, count,
-                                          reinterpret_cast<uint64_t*>(buf), B)
+                                          reinterpret_cast<uint64_t*>(buf), draw_blocks_per_sm(h), B)
                            : launch_mask_draw(h->g, a, h->t_dev, (uint64_t)first, count,
-                                              reinterpret_cast<ulonglong2*>(buf), B);
+                                              reinterpret_cast<ulonglong2*>(buf), draw_blocks_per_sm(h), B);
         if (r == cudaSuccess) r = cudaEventRecord(h->draw_ev[k], B);
         return r;
     };
@@ -569,7 +586,7 @@ static int run_resident(ising_lattice* h, int n, int every)
         }
         for (int done = 0; done < n;) {
             const int part = std::min(n - done, max_sweeps);
-            cudaError_t e = launch_mask_draw(g, a, nullptr, h->t + (uint64_t)done, part, h->masks, h->stream);
+            cudaError_t e = launch_mask_draw(g, a, nullptr, h->t + (uint64_t)done, part, h->masks, 0, h->stream);
             if (e != cudaSuccess) return cuda_fail(e, "mask_draw_kernel");
             e = launch_resident_premasked(h->words[0], h->words[1], g, a, done, part, every, h->masks, rec,
                                           resident_bytes(g), h->stream);
