@@ -265,7 +265,7 @@ int ising_set_item_lanes(ising_lattice *h, int32_t lanes);
  * then run k half-sweeps on their rows plus halo.  The accept masks of each
  * piece are drawn by the SMs the cluster leaves free, while the piece before
  * is applied, into two device buffers the library allocates on first use (up
- * to 32 MB together; 2 L pitch 8 bytes per sweep).  No spin-waits: only the
+ * to 128 MB together; 2 L pitch 8 bytes per sweep).  No spin-waits: only the
  * hardware's block and cluster barriers.
  * ISING_PATH_AUTO (default): resident up to 512 thread items (L <= 292), the
  * cluster path above that up to L = 1080, the launch path above that.

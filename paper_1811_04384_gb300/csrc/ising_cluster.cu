@@ -105,8 +105,8 @@ __device__ __forceinline__ int wrap_index(int i, int L) { return i < 0 ? i + L :
 // right, wrapped around the row, whose edge field comes in with a shift of
 // 60 bits, or 3 (rlast - 1) across the wrap.
 struct Slot {
-    int lr;          // window row, or -1 (no word)
-    uint32_t o;      // lr * P + w: the word in the own-colour, other-colour and mask arrays
+    uint32_t o;      // lr * P + w (window row lr, word w): the word in the own-colour, other-colour and
+                     // mask arrays; ~0u: no word
     uint32_t dl;     // side word - o for colour 0 (bits 0..15) and colour 1 (16..31), as int16
     uint32_t bits;   // side shift for colour 0 (bits 0..6) and 1 (8..14); colour 0 takes the left
                      // neighbour (16); last word of the row (17); an own row of the block (18)
@@ -147,17 +147,18 @@ __device__ __forceinline__ void cl_update(uint64_t* own, const uint64_t* other, 
 }
 
 // One half-sweep of colour C on window rows lo .. hi: each thread updates
-// those of its NS slots that lie there.  RECORD counts the block's own rows
-// into the count slots `counts`.
+// those of its NS slots that lie there (words lo P .. (hi + 1) P - 1).
+// RECORD counts the block's own rows into the count slots `counts`.
 template <int C, bool RECORD, int NS>
 __device__ __forceinline__ void cl_half_sweep(uint64_t* own, const uint64_t* other, const uint64_t* msk, uint32_t P,
                                               const Slot (&slot)[NS], int lo, int hi, uint64_t live_last,
                                               uint64_t n, unsigned long long* counts)
 {
     uint32_t anti = 0, up = 0;
+    const uint32_t first = (uint32_t)lo * P, span = (uint32_t)(hi - lo + 1) * P;
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
-        if (slot[j].lr >= lo && slot[j].lr <= hi) {
+        if (slot[j].o - first < span) {
             if (RECORD && (slot[j].bits & (1u << 18)))
                 cl_update<C, true>(own, other, msk, P, slot[j], live_last, n, anti, up);
             else
@@ -211,8 +212,7 @@ cluster_sweeps_kernel(ClusterArgs a)
         // left neighbour: word w - 1 (wrapped), right: w + 1 (wrapped)
         const int dleft = first ? (int)W - 1 : -1, dright = last ? -((int)W - 1) : 1;
         const uint32_t shl = first ? sh_wrap : 60u, shr = last ? sh_wrap : 60u;
-        slot[j].lr = lr <= R - 2 && w < g.W ? lr : -1;
-        slot[j].o = (uint32_t)lr * P + (uint32_t)w;
+        slot[j].o = lr <= R - 2 && w < g.W ? (uint32_t)lr * P + (uint32_t)w : ~0u;
         slot[j].dl = (uint32_t)(uint16_t)(int16_t)(left0 ? dleft : dright) |
                      ((uint32_t)(uint16_t)(int16_t)(left0 ? dright : dleft) << 16);
         slot[j].bits = (left0 ? shl : shr) | ((left0 ? shr : shl) << 8) | (left0 ? 1u << 16 : 0u) |

@@ -614,12 +614,14 @@ static int run_resident(ising_lattice* h, int n, int every)
 // writes the buffer piece j - 1 read (complete before piece j started).
 // Replayed graphs of short half-sweeps stay for the launch path
 // (ISING_PATH_LAUNCHES) and for larger lattices.  Measured on GB300, sweeps
-// without records, spin-updates/ns, cluster against graphs: L = 296: 115 /
-// 34; L = 512: 215 / 96; L = 700: 284 / 171; L = 1008: 416 / 314; but
-// L = 1100: 329 / 348, where the window allows phases of 2 half-sweeps only.
-// Up to L = 1086 the phases have 6 or more.
+// without records, spin-updates/ns, cluster against graphs: L = 296: 133 /
+// 34; L = 512: 244 / 95; L = 700: 317 / 170; L = 1008: 458 / 311; L = 1080:
+// 458 / 341; but L = 1100: 329 / 348, where the window allows phases of 2
+// half-sweeps only.  Up to L = 1086 the phases have 6 or more.  Two 16 MB
+// mask buffers (43-sweep pieces at L = 1008) gave 444 there: each launch
+// loads and writes back the lattice and refills the mask ring.
 constexpr int kClusterMaxL = 1080;
-constexpr size_t kClusterMaskBytes = 32u << 20;    // both buffers
+constexpr size_t kClusterMaskBytes = 128u << 20;   // both buffers
 constexpr int kClusterMaxPiece = 256;
 
 static bool use_cluster(const ising_lattice* h, ClusterPlan* plan)

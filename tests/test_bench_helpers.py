@@ -42,9 +42,11 @@ def test_cluster_launch_count():
     # L = 296: pitch 8 words, 256-sweep pieces; 2280 records of 10 sweeps in
     # chunks of 1024, 1024 and 232 records: 40, 40 and 10 pieces
     assert bench.cluster_launches(296, 22800, 10) == (2 * 40 + 1) * 2 + 2 * 10 + 1
-    # L = 512: pitch 14 words, 146-sweep pieces; one chunk of 20 records
-    assert bench.cluster_launches(512, 200, 10) == 2 * 2 + 1
-    assert bench.cluster_launches(512, 205, 10) == 2 * 2 + 1 + 2 * 1 + 1     # 5 sweeps after the last record
+    # L = 512: pitch 14 words, 256-sweep pieces; one chunk of 20 records
+    assert bench.cluster_launches(512, 200, 10) == 2 * 1 + 1
+    assert bench.cluster_launches(512, 205, 10) == 2 * 1 + 1 + 2 * 1 + 1     # 5 sweeps after the last record
+    # L = 1008: pitch 24 words, 173-sweep pieces (two 64 MB buffers)
+    assert bench.cluster_launches(1008, 1960, 10) == 2 * 12 + 1
 
 
 def test_two_pipe_roofline_arithmetic():
