@@ -179,6 +179,7 @@ cluster_sweeps_kernel(ClusterArgs a)
     // serialization) may start now, on the SMs this cluster leaves free
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     constexpr int Q = DEEP ? kClMaxSlabs : 2;
+    static_assert((Q & (Q - 1)) == 0, "the mask ring's indices wrap by masking");
     cg::cluster_group cluster = cg::this_cluster();
     const Geom& g = a.g;
     const int T = blockDim.x;
@@ -244,7 +245,7 @@ cluster_sweeps_kernel(ClusterArgs a)
         cl_commit();
         ++next;
         next_src += plane;
-        put = put + 1 == Q ? 0 : put + 1;
+        put = (put + 1) & (Q - 1);
     };
     // halo rows: receive slots rb(par, c, 0) for the k rows above the block's
     // own (the last own rows of the block above), rb(par, c, 1) for the k rows
@@ -299,11 +300,20 @@ cluster_sweeps_kernel(ClusterArgs a)
         cl_wait<Q - 2>();
         __syncthreads();
         const uint64_t* m = msk + (size_t)use * n;
-        use = use + 1 == Q ? 0 : use + 1;
+        use = (use + 1) & (Q - 1);
         return m;
     };
-    int64_t s_call = a.s0;                                              // sweeps of the call done
-    int64_t next_rec = a.every > 0 ? (a.s0 / a.every + 1) * a.every : -1;
+    // records: sweep j of the launch (1-based) is sweep s0 + j of the call;
+    // the next recorded one, rec_j (past nsweeps: none), and its count slot
+    int j = 0, rec_j = a.nsweeps + 1;
+    unsigned long long* rec_counts = nullptr;
+    if (a.every > 0) {
+        const int64_t first = (a.s0 / a.every + 1) * a.every;          // first recorded sweep of the call > s0
+        if (first - a.s0 <= a.nsweeps) {
+            rec_j = (int)(first - a.s0);
+            rec_counts = a.counts + (size_t)(first / a.every - 1) * 2 * kCountSlots;
+        }
+    }
     int par = 0;
     for (int hs0 = 0; hs0 < total; hs0 += k) {
         const int kk = min(k, total - hs0);                             // even: phases start with colour 0
@@ -313,11 +323,11 @@ cluster_sweeps_kernel(ClusterArgs a)
             cl_half_sweep<0, false, NS>(win[0], win[1], m0, P, slot, 1 + d, R - 2 - d, live_last, n, nullptr);
             stage();
             const uint64_t* m1 = begin();
-            ++s_call;
-            if (s_call == next_rec) {
-                unsigned long long* cnt = a.counts + (size_t)(s_call / a.every - 1) * 2 * kCountSlots;
-                cl_half_sweep<1, true, NS>(win[1], win[0], m1, P, slot, 2 + d, R - 3 - d, live_last, n, cnt);
-                next_rec += a.every;
+            if (++j == rec_j) {
+                cl_half_sweep<1, true, NS>(win[1], win[0], m1, P, slot, 2 + d, R - 3 - d, live_last, n,
+                                           rec_counts);
+                rec_counts += 2 * kCountSlots;
+                rec_j = a.every <= a.nsweeps - j ? j + (int)a.every : a.nsweeps + 1;
             } else {
                 cl_half_sweep<1, false, NS>(win[1], win[0], m1, P, slot, 2 + d, R - 3 - d, live_last, n, nullptr);
             }

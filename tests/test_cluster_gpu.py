@@ -3,8 +3,8 @@ blocks' shared memory, halos exchanged through distributed shared memory)
 against the oracle, bit-exact: int64 E/M series and final spins.
 
 Cases span two rows per block (L = 32, two half-sweeps per phase), the
-automatic range (L = 296 just above the on-chip path, up to L = 1080 with two
-mask pieces), L % 4 == 2, records out of step with the phases and pieces,
+automatic range (L = 296 just above the on-chip path, with two mask pieces,
+up to L = 1080), L % 4 == 2, records out of step with the phases and pieces,
 odd numbers of half-sweeps per call, forced runs up to the largest side
 (L = 1600), cold starts, beta = 0 (every flip accepted) and a frozen
 lattice, runs continued across calls and paths, and ising_run_states.
@@ -31,10 +31,11 @@ def ising():
 CASES = [
     (32, 9, 1, 0.44, True),        # two rows per block: phases of two half-sweeps
     (64, 13, 2, 0.3, True),        # four rows per block, phases of 4
-    (296, 37, 1, BETA_TC, False),  # 74 half-sweeps: phases of 8 and a short last one
+    (296, 37, 1, BETA_TC, False),  # 74 half-sweeps: phases of 12 and a short last one
+    (296, 300, 7, 0.41, False),    # two mask pieces (256 + 44 sweeps), records across them
     (514, 20, 3, 0.3, False),      # L % 4 == 2; 6 records, out of step with the phases
     (1008, 24, 4, 0.44, False),    # the paper's L = 1008
-    (1080, 60, 5, BETA_TC, False), # largest automatic side: two mask pieces (37 + 23 sweeps)
+    (1080, 60, 5, BETA_TC, False), # largest automatic side
     (1500, 6, 1, 0.44, True),      # phases of 10 half-sweeps, 4 words per thread
     (1600, 3, 1, BETA_TC, True),   # largest side with a plan: 4 words per thread
 ]
