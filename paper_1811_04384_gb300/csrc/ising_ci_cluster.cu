@@ -1,0 +1,461 @@
+// Cluster-resident temporal blocking in the paper's column-interleaved
+// layout (Sec. 3): the form of ising_cluster.cu for N x L words, mid-size
+// lattices (L a multiple of 84 up to about 1100).
+//
+// Word S(I, J) holds s(I + kN, J) in field k and has colour (I + J) & 1.  A
+// half-sweep's neighbours of a word are the words left and right in its row
+// and above and below in its column, rotated by one field across the top
+// and bottom word rows (the paper's boundary rule).  So the lattice splits
+// by columns: block b of one thread-block cluster owns word columns
+// c0(b) .. c0(b + 1) - 1 (multiples of 4) of all N word rows and keeps them
+// in shared memory for a piece of up to 256 sweeps, in a window with k halo
+// columns on each side (k a multiple of 4).  Phases of k half-sweeps shrink
+// the valid columns by one per half-sweep (a trapezoid); at the end of a
+// phase each block pushes its first and last k own columns into the receive
+// slots of its left and right neighbours (distributed shared memory, two
+// sets by phase parity) and all pass one hardware cluster barrier.
+//
+// The window is kept split by column parity: E holds the even window
+// columns, O the odd ones, pair p = columns 2p, 2p + 1.  In row I the word
+// of colour C of pair p is in E when (I + C) is even, else in O; its
+// up / down neighbours are in the same array, its left / right neighbours in
+// the other at pairs p - 1, p or p, p + 1.  So every load of a warp over
+// consecutive pairs falls on consecutive words.  The accept masks, drawn
+// beforehand on the SMs the cluster leaves free (ci_masks, the draws of the
+// other interleaved kernels), stream into a ring of shared-memory slabs
+// indexed like the pairs.  The update is Eq. 3 in its arithmetic form, as in
+// ci_half_sweep_apply_kernel, so the results equal every other path's.
+#include <cuda_runtime.h>
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "ising_cluster.cuh"
+#include "ising_interleaved.cuh"
+#include "ising_interleaved.h"
+#include "ising_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace ising {
+namespace {
+
+constexpr int kCiThreads = 1024;           // most threads of a block
+constexpr size_t kCiSmemMax = 220 * 1024;   // dynamic shared memory of a block
+constexpr int kCiHalo = 12;                 // most half-sweeps per phase (a multiple of 4)
+constexpr int kCiMaxSlabs = 8;              // mask slabs where they fit
+
+struct CiClusterArgs {
+    uint64_t* S;                // the lattice, N x L words
+    int L, N;
+    int k;                      // half-sweeps per phase = halo columns
+    int nsweeps;                // sweeps of this launch
+    int wpm;                    // pairs per window row (the widest block's columns + 2 k, halved)
+    const uint64_t* masks;      // masks[(h * N + I) * L/2 + m]: half-sweep h, word row I, column pair m
+    int64_t s0;                 // the launch runs sweeps s0 + 1 .. s0 + nsweeps of the call
+    int64_t every;              // record after sweeps s with s % every == 0 (0: none)
+    unsigned long long* counts; // count slots (32 per record); record r of the call -> slot r
+};
+
+// First word column of block b of a cluster of C: a multiple of 4.
+__host__ __device__ __forceinline__ int ci_col0(int b, int C, int L)
+{
+    return 4 * (int)((long long)b * (L / 4) / C);
+}
+
+// A window pair a thread updates (the word of the half-sweep's colour in it)
+// in every half-sweep whose columns include that word.
+struct CiSlot {
+    uint32_t o;      // I * wpm + p: the pair in E, O and the mask slabs; ~0u: none
+    uint32_t bits;   // window column of the colour-0 word (bits 0..15); colour 0's word in O (16);
+                     // top word row (17); bottom word row (18); an own column pair of the block (19)
+};
+
+// One update of colour C (Eq. 3, arithmetic form): s, its four neighbours and
+// the packed masks p (r < thr1 at bit 3k, r < thr0 at 3k + 1, set where the
+// threshold is 2^32).  RECORD adds the word's anti-aligned bonds and the up
+// spins of its column pair.
+template <int C, bool RECORD>
+__device__ __forceinline__ void ci_cl_update(uint64_t* E, const uint64_t* msk, uint32_t wpm, uint32_t wrap,
+                                             uint64_t nw, const CiSlot& sl, uint32_t& anti, uint32_t& up)
+{
+    const uint32_t o = sl.o;
+    const uint32_t par = ((sl.bits >> 16) & 1u) ^ (uint32_t)C;       // 0: the word is in E, 1: in O
+    uint64_t* own = E + (size_t)par * nw;
+    const uint64_t* oth = E + (size_t)(par ^ 1u) * nw;
+    const uint64_t s = word_ld<false>(own, o, nw, __LINE__);
+    const bool top = (sl.bits >> 17) & 1u, bottom = (sl.bits >> 18) & 1u;
+    const uint64_t wu = word_ld<false>(own, top ? o + wrap : o - wpm, nw, __LINE__);
+    const uint64_t wd = word_ld<false>(own, bottom ? o - wrap : o + wpm, nw, __LINE__);
+    const uint64_t xu = top ? rotate_up(wu) : wu;
+    const uint64_t xd = bottom ? rotate_down(wd) : wd;
+    const uint64_t xl = word_ld<false>(oth, o - 1u + par, nw, __LINE__);
+    const uint64_t xr = word_ld<false>(oth, o + par, nw, __LINE__);
+    const uint64_t p = word_ld<false>(msk, o, nw, __LINE__);
+    // the 3-bit field sums of the four XORs hold a = 0..4 without carries
+    const uint64_t A = (s ^ xu) + (s ^ xd) + (s ^ xl) + (s ^ xr);
+    const uint64_t ge2 = ((A >> 1) | (A >> 2)) & kAllFields;
+    const uint64_t any = (A | (A >> 1) | (A >> 2)) & kAllFields;
+    const uint64_t accept = ge2 | (any & p) | (~any & (p >> 1));
+    const uint64_t sn = s ^ (accept & kAllFields);
+    word_st(own, o, sn, nw, __LINE__);
+    if (RECORD) {
+        const uint64_t pair_other = par ? xl : xr;       // the pair's other word
+        anti += __popcll(sn ^ xu) + __popcll(sn ^ xd) + __popcll(sn ^ xl) + __popcll(sn ^ xr);
+        up += __popcll(sn) + __popcll(pair_other);
+    }
+}
+
+// One half-sweep of colour C on window columns lo .. hi.
+template <int C, bool RECORD, int NS>
+__device__ __forceinline__ void ci_cl_half_sweep(uint64_t* E, const uint64_t* msk, uint32_t wpm, uint32_t wrap,
+                                                 uint64_t nw, const CiSlot (&slot)[NS], int lo, int hi,
+                                                 unsigned long long* counts)
+{
+    uint32_t anti = 0, up = 0;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+        const int w = (int)(slot[j].bits & 0xffffu) ^ C;              // the colour-C word's window column
+        if (slot[j].o != ~0u && w >= lo && w <= hi) {
+            if (RECORD && (slot[j].bits & (1u << 19)))
+                ci_cl_update<C, true>(E, msk, wpm, wrap, nw, slot[j], anti, up);
+            else
+                ci_cl_update<C, false>(E, msk, wpm, wrap, nw, slot[j], anti, up);
+        }
+    }
+    if (RECORD) block_add_counts(counts + 2 * (blockIdx.x % kCountSlots), anti, up);
+}
+
+// NS: window pairs per thread; DEEP: kCiMaxSlabs mask slabs, else 2.
+template <int NS, bool DEEP>
+__global__ void __launch_bounds__(kCiThreads, 1)
+ci_cluster_sweeps_kernel(CiClusterArgs a)
+{
+    extern __shared__ __align__(16) uint64_t smem[];
+    // the next piece's mask draw (launched with programmatic stream
+    // serialization) may start now, on the SMs this cluster leaves free
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    constexpr int Q = DEEP ? kCiMaxSlabs : 2;
+    static_assert((Q & (Q - 1)) == 0, "the mask ring's indices wrap by masking");
+    cg::cluster_group cluster = cg::this_cluster();
+    const int T = blockDim.x;
+    const int C = (int)cluster.num_blocks(), b = (int)cluster.block_rank();
+    const int L = a.L, N = a.N, k = a.k, kh = k / 2, PL = L / 2;
+    const int c0 = ci_col0(b, C, L), S = ci_col0(b + 1, C, L) - c0;    // own columns
+    const int bp = (b + C - 1) % C, bn = (b + 1) % C;                  // left and right blocks
+    const int Wn = S + 2 * k, Wp = Wn / 2;                               // window columns and pairs
+    const uint32_t wpm = (uint32_t)a.wpm;
+    const uint64_t nw = (uint64_t)N * wpm;                              // words of E, O, a slab
+    uint64_t* E = smem;                                                  // O = E + nw
+    uint64_t* msk = smem + 2 * nw;                                       // Q slabs
+    uint64_t* recv = msk + (size_t)Q * nw;                               // receive slots
+    const int slotw = N * kh;                                            // words of one receive slot
+    const uint64_t smem_words = (2 + Q) * nw + 8 * (uint64_t)slotw;
+    const uint32_t smem_sh = (uint32_t)__cvta_generic_to_shared(smem);
+    const uint32_t msk_sh = (uint32_t)__cvta_generic_to_shared(msk);
+    const int gp0 = c0 / 2 - kh;                                         // global pair of window pair 0 (mod PL)
+    const uint32_t wrap = (uint32_t)(N - 1) * wpm;                       // top <-> bottom word row
+    // slots: pairs e = t + j T over the rows (I = e / wpm, p = e % wpm), and
+    // the mask copies (16 bytes: two pairs) of the same rows
+    CiSlot slot[NS];
+    uint32_t cdst[NS], csrc[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+        const int e = threadIdx.x + j * T;
+        const int I = e / (int)wpm, p = e % (int)wpm;
+        const bool valid = I < N && p < Wp;
+        const int par0 = I & 1;                                          // colour 0's word: column 2p + par0
+        slot[j].o = valid ? (uint32_t)e : ~0u;
+        slot[j].bits = (uint32_t)(2 * p + par0) | ((uint32_t)par0 << 16) | (I == 0 ? 1u << 17 : 0u) |
+                       (I == N - 1 ? 1u << 18 : 0u) | ((p >= kh && p < kh + S / 2) ? 1u << 19 : 0u);
+        const int half = (int)wpm / 2;                                   // copies per window row
+        const int cI = e / half, cq = e % half;
+        cdst[j] = cI < N && cq < Wp / 2 ? msk_sh + 8u * ((uint32_t)cI * wpm + 2u * (uint32_t)cq) : ~0u;
+        csrc[j] = (uint32_t)cI * (uint32_t)PL + (uint32_t)wrap_index(gp0 + 2 * cq, PL);
+    }
+    const int total = 2 * a.nsweeps;
+    const size_t plane = (size_t)N * PL;                                 // one half-sweep's masks
+    const uint64_t mask_words = (uint64_t)total * plane;
+    const uint32_t slab_bytes = (uint32_t)(nw * sizeof(uint64_t));
+    const uint64_t* next_src = a.masks;
+    int next = 0, put = 0;
+    auto stage = [&]() {
+        if (next < total) {
+            const uint32_t off = (uint32_t)put * slab_bytes;
+#pragma unroll
+            for (int j = 0; j < NS; ++j)
+                if (cdst[j] != ~0u)
+                    cl_copy_pair(cdst[j] + off, smem_sh, smem_words, next_src + csrc[j], a.masks, mask_words,
+                                 __LINE__);
+        }
+        cl_commit();
+        ++next;
+        next_src += plane;
+        put = (put + 1) & (Q - 1);
+    };
+    // receive slots: rs(par, dir, arr) holds k/2 pairs of array arr (0: E,
+    // 1: O) of all word rows, dir 0 for the block's left halo (the left
+    // block's last k own columns), 1 for its right halo; two sets by phase
+    auto rs = [&](uint64_t* base, int par, int dir, int arr) {
+        return base + (size_t)((par * 2 + dir) * 2 + arr) * slotw;
+    };
+    // a block's first k own columns (pairs kh .. k - 1) go to the right-halo
+    // slots of the left block, its last k (pairs S/2 .. S/2 + kh - 1) to the
+    // left-halo slots of the right block
+    auto push = [&](int par) {
+        uint64_t* to_left = cluster.map_shared_rank(recv, bp);
+        uint64_t* to_right = cluster.map_shared_rank(recv, bn);
+        for (int arr = 0; arr < 2; ++arr) {
+            const uint64_t* A = E + (size_t)arr * nw;
+            uint64_t* dl = rs(to_left, par, 1, arr);
+            uint64_t* dr = rs(to_right, par, 0, arr);
+            for (int idx = threadIdx.x; idx < slotw; idx += T) {
+                const int I = idx / kh, x = idx - I * kh;
+                word_st(dl, idx, word_ld<false>(A, (uint64_t)I * wpm + kh + x, nw, __LINE__), slotw, __LINE__);
+                word_st(dr, idx, word_ld<false>(A, (uint64_t)I * wpm + S / 2 + x, nw, __LINE__), slotw, __LINE__);
+            }
+        }
+    };
+    auto receive = [&](int par) {
+        for (int arr = 0; arr < 2; ++arr) {
+            uint64_t* A = E + (size_t)arr * nw;
+            const uint64_t* fl = rs(recv, par, 0, arr);
+            const uint64_t* fr = rs(recv, par, 1, arr);
+            for (int idx = threadIdx.x; idx < slotw; idx += T) {
+                const int I = idx / kh, x = idx - I * kh;
+                word_st(A, (uint64_t)I * wpm + x, word_ld<false>(fl, idx, slotw, __LINE__), nw, __LINE__);
+                word_st(A, (uint64_t)I * wpm + (S + k) / 2 + x, word_ld<false>(fr, idx, slotw, __LINE__), nw,
+                        __LINE__);
+            }
+        }
+    };
+    // own columns from the lattice: word (I, c0 + x) -> window column k + x
+    const uint64_t lattice_n = (uint64_t)N * L;
+    for (int e = threadIdx.x; e < N * S; e += T) {
+        const int I = e / S, x = e - I * S;
+        const int w = k + x;
+        word_st(E + (size_t)(w & 1) * nw, (uint64_t)I * wpm + (w >> 1),
+                word_ld<false>(a.S, (uint64_t)I * L + c0 + x, lattice_n, __LINE__), nw, __LINE__);
+    }
+    __syncthreads();
+    push(0);
+#pragma unroll
+    for (int h = 0; h < Q - 1; ++h) stage();
+    cluster.sync();          // the first phase's halos have arrived
+    int use = 0;             // slab of the current half-sweep
+    auto begin = [&]() {
+        cl_wait<Q - 2>();
+        __syncthreads();
+        const uint64_t* m = msk + (size_t)use * nw;
+        use = (use + 1) & (Q - 1);
+        return m;
+    };
+    // records: sweep j of the launch is sweep s0 + j of the call
+    int j = 0, rec_j = a.nsweeps + 1;
+    unsigned long long* rec_counts = nullptr;
+    if (a.every > 0) {
+        const int64_t first = (a.s0 / a.every + 1) * a.every;
+        if (first - a.s0 <= a.nsweeps) {
+            rec_j = (int)(first - a.s0);
+            rec_counts = a.counts + (size_t)(first / a.every - 1) * 2 * kCountSlots;
+        }
+    }
+    int par = 0;
+    for (int hs0 = 0; hs0 < total; hs0 += k) {
+        const int kk = min(k, total - hs0);                             // even: phases start with colour 0
+        receive(par);
+        for (int d = 0; d < kk; d += 2) {
+            const uint64_t* m0 = begin();
+            ci_cl_half_sweep<0, false, NS>(E, m0, wpm, wrap, nw, slot, 1 + d, Wn - 2 - d, nullptr);
+            stage();
+            const uint64_t* m1 = begin();
+            if (++j == rec_j) {
+                ci_cl_half_sweep<1, true, NS>(E, m1, wpm, wrap, nw, slot, 2 + d, Wn - 3 - d, rec_counts);
+                rec_counts += 2 * kCountSlots;
+                rec_j = a.every <= a.nsweeps - j ? j + (int)a.every : a.nsweeps + 1;
+            } else {
+                ci_cl_half_sweep<1, false, NS>(E, m1, wpm, wrap, nw, slot, 2 + d, Wn - 3 - d, nullptr);
+            }
+            stage();
+        }
+        par ^= 1;
+        if (hs0 + k < total) {
+            __syncthreads();     // own columns final for this phase
+            push(par);
+        }
+        // the next phase's halos have arrived; the slots the next pushes write
+        // were read at the start of this phase; after the last phase: no block
+        // leaves while another may still write its shared memory
+        cluster.sync();
+    }
+    // own columns back to the lattice
+    cl_wait<0>();
+    for (int e = threadIdx.x; e < N * S; e += T) {
+        const int I = e / S, x = e - I * S;
+        const int w = k + x;
+        word_st(a.S, (uint64_t)I * L + c0 + x,
+                word_ld<false>(E + (size_t)(w & 1) * nw, (uint64_t)I * wpm + (w >> 1), nw, __LINE__), lattice_n,
+                __LINE__);
+    }
+}
+
+// Masks of sweeps j = 0 .. nsweeps-1 after sweep t0, one thread per (sweep,
+// colour, row group q, column pair m) with ci_masks, written as planes:
+// masks[((j * 2 + c) * N + 4 q + e) * L/2 + m], with the bits of a
+// threshold of 2^32 set.
+template <int ROUNDS>
+__global__ void __launch_bounds__(128)
+ci_cl_mask_draw_kernel(int L, int N, SweepArgs a, uint64_t t0, int nsweeps, uint64_t* __restrict__ masks)
+{
+    const long long Q4 = N / 4, M = L / 2;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)nsweeps * 2 * Q4 * M) return;
+    const int m = (int)(k % M);
+    const int q = (int)((k / M) % Q4);
+    const int jc = (int)(k / (M * Q4));                 // sweep * 2 + colour
+    uint64_t packed[4];
+    ci_masks<ROUNDS>(N, q, m, t0 + (uint64_t)(jc >> 1) + 1, jc & 1, a, packed);
+    const uint64_t always = (((uint64_t)a.all1 << 32 | a.all1) & kAllFields) |
+                            ((((uint64_t)a.all0 << 32 | a.all0) & kAllFields) << 1);
+    uint64_t* plane = masks + (size_t)jc * N * M;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) plane[(size_t)(4 * q + e) * M + m] = packed[e] | always;
+}
+
+// The widest block's columns: c0(b + 1) - c0(b) <= 4 ceil((L / 4) / C).
+int ci_widest(int L, int C) { return 4 * ((L / 4 + C - 1) / C); }
+
+// E, O and q mask slabs of N x wpm words, and 8 receive slots of N x k / 2.
+size_t ci_cl_smem_bytes(int L, int N, int C, int k, int q)
+{
+    const size_t wpm = (size_t)(ci_widest(L, C) + 2 * k) / 2;
+    return ((size_t)(2 + q) * N * wpm + 4 * (size_t)N * k) * sizeof(uint64_t);
+}
+
+using CiClusterKernel = void (*)(CiClusterArgs);
+constexpr CiClusterKernel kCiClusterKernels[6] = {
+    ci_cluster_sweeps_kernel<1, false>, ci_cluster_sweeps_kernel<2, false>, ci_cluster_sweeps_kernel<4, false>,
+    ci_cluster_sweeps_kernel<1, true>,  ci_cluster_sweeps_kernel<2, true>,  ci_cluster_sweeps_kernel<4, true>};
+
+CiClusterKernel ci_cluster_kernel(int ns, int q)
+{
+    return kCiClusterKernels[(q == kCiMaxSlabs ? 3 : 0) + (ns == 1 ? 0 : (ns == 2 ? 1 : 2))];
+}
+
+int ci_probe_max_cluster()
+{
+    for (CiClusterKernel kern : kCiClusterKernels) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCiSmemMax) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+    }
+    for (int c : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(c);
+        cfg.blockDim = dim3(kCiThreads);
+        cfg.dynamicSmemBytes = kCiSmemMax;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = c;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        bool ok = true;
+        for (CiClusterKernel kern : kCiClusterKernels) {
+            int nc = 0;
+            ok = ok && cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) == cudaSuccess && nc >= 1;
+        }
+        if (ok) return c;
+        cudaGetLastError();
+    }
+    return 0;
+}
+
+}  // namespace
+
+// Cluster size, phase length (a multiple of 4, <= kCiHalo, <= the fewest
+// columns a block owns), mask slabs and pairs per thread for side L, as
+// cluster_plan: the largest k whose window, kCiMaxSlabs slabs (else 2) and
+// receive slots fit in shared memory with at most 2 pairs per thread where
+// some k allows it, else 4.  False if L is not a side of the layout or no
+// such launch exists.
+bool ci_cluster_plan(int L, ClusterPlan* plan)
+{
+    if (!ci_valid_side(L)) return false;
+    static const int max_cluster = ci_probe_max_cluster();   // per process, set once
+    if (max_cluster == 0) return false;
+    const int c = max_cluster, N = L / 21;
+    const int fewest = 4 * ((L / 4) / c), widest = ci_widest(L, c);
+    for (int most : {2, 4}) {
+        for (int q : {kCiMaxSlabs, 2}) {
+            for (int kk = std::min(kCiHalo, fewest) & ~3; kk >= 4; kk -= 4) {
+                if (ci_cl_smem_bytes(L, N, c, kk, q) > kCiSmemMax) continue;
+                const long long words = (long long)N * ((widest + 2 * kk) / 2);
+                if (words > (long long)most * kCiThreads) continue;
+                const int ns = words <= kCiThreads ? 1 : (words <= 2 * kCiThreads ? 2 : 4);
+                plan->blocks = c;
+                plan->k = kk;
+                plan->q = q;
+                plan->ns = ns;
+                plan->threads = (int)(((words + ns - 1) / ns + 31) / 32 * 32);
+                return true;
+            }
+        }
+    }
+    return false;
+}
+
+size_t ci_cl_mask_bytes_per_sweep(int L) { return 2 * (size_t)(L / 21) * (L / 2) * sizeof(uint64_t); }
+
+cudaError_t ci_cl_mask_draw(int L, const SweepArgs& a, uint64_t t0, int nsweeps, uint64_t* masks, bool overlap,
+                            cudaStream_t s)
+{
+    const int N = L / 21;
+    const long long threads = (long long)nsweeps * 2 * (N / 4) * (L / 2);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((threads + 127) / 128));
+    cfg.blockDim = dim3(128);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = overlap ? 1 : 0;
+    return a.rounds == 7 ? cudaLaunchKernelEx(&cfg, ci_cl_mask_draw_kernel<7>, L, N, a, t0, nsweeps, masks)
+                         : cudaLaunchKernelEx(&cfg, ci_cl_mask_draw_kernel<10>, L, N, a, t0, nsweeps, masks);
+}
+
+cudaError_t ci_cluster_sweeps(uint64_t* S, int L, const SweepArgs& a, const ClusterPlan& plan, int nsweeps,
+                              const uint64_t* masks, int64_t s0, int64_t every, cudaStream_t s)
+{
+    CiClusterArgs ca;
+    ca.S = S;
+    ca.L = L;
+    ca.N = L / 21;
+    ca.k = plan.k;
+    ca.nsweeps = nsweeps;
+    ca.wpm = (ci_widest(L, plan.blocks) + 2 * plan.k) / 2;
+    ca.masks = masks;
+    ca.s0 = s0;
+    ca.every = every;
+    ca.counts = a.counts;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(plan.blocks);
+    cfg.blockDim = dim3(plan.threads);
+    cfg.dynamicSmemBytes = ci_cl_smem_bytes(L, ca.N, plan.blocks, plan.k, plan.q);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = plan.blocks;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, ci_cluster_kernel(plan.ns, plan.q), ca);
+}
+
+}  // namespace ising

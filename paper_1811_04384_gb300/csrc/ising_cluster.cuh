@@ -1,0 +1,48 @@
+// Helpers of the cluster kernels (ising_cluster.cu, ising_ci_cluster.cu):
+// asynchronous 16-byte copies into shared memory, with a range-checked form
+// for the checked build.
+#pragma once
+#include <cstdint>
+
+#include "ising_device.cuh"
+
+namespace ising {
+namespace {
+
+// 16 bytes global -> shared (a 32-bit shared-window address), asynchronously,
+// through L2.
+__device__ __forceinline__ void cl_copy16(uint32_t smem_dst, const void* gmem_src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_dst), "l"(gmem_src) : "memory");
+}
+
+// cl_copy16 to shared address `dst` from `src`.  In a checked build the
+// copy is skipped and recorded (see word_ld) unless both words of the pair
+// lie in the `dst_words` words from shared address `dst_base` and in the
+// `src_words` words from `src_base`.
+__device__ __forceinline__ void cl_copy_pair(uint32_t dst, uint32_t dst_base, uint64_t dst_words, const uint64_t* src,
+                                             const uint64_t* src_base, uint64_t src_words, uint32_t line)
+{
+#ifdef ISING_CHECKED
+    if (!check_index((uint64_t)(dst - dst_base) / 8 + 1, dst_words, line) ||
+        !check_index((uint64_t)(src - src_base) + 1, src_words, line))
+        return;
+#else
+    (void)dst_base;
+    (void)dst_words;
+    (void)src_base;
+    (void)src_words;
+    (void)line;
+#endif
+    cl_copy16(dst, src);
+}
+
+__device__ __forceinline__ void cl_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cl_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ int wrap_index(int i, int L) { return i < 0 ? i + L : (i >= L ? i - L : i); }
+
+}  // namespace
+}  // namespace ising

@@ -16,22 +16,11 @@
 #include <cuda_runtime.h>
 
 #include "ising_interleaved.h"
+#include "ising_interleaved.cuh"
 #include "ising_internal.h"
 
 namespace ising {
 namespace {
-
-constexpr uint64_t kAllFields = 0x1249249249249249ull;   // bit 3k, k = 0..20
-
-__device__ __forceinline__ uint64_t rotate_up(uint64_t s)    // field k <- field k - 1 (periodic)
-{
-    return ((s << 3) | (s >> 60)) & kAllFields;
-}
-
-__device__ __forceinline__ uint64_t rotate_down(uint64_t s)  // field k <- field k + 1 (periodic)
-{
-    return ((s >> 3) | (s << 60)) & kAllFields;
-}
 
 // Hot start: field k of S(I, J) is +1 iff the Philox draw at t = 0 of site
 // (I + kN, J) is below 2^31.  One thread per word.
@@ -75,28 +64,6 @@ __global__ void ci_unpack_kernel(const uint64_t* __restrict__ S, int L, int N, i
     const uint64_t word = S[(size_t)I * L + J];
     for (int k = 0; k < 21; ++k)
         s[(size_t)(I + k * N) * L + J] = ((word >> (3 * k)) & 1ull) ? (int8_t)1 : (int8_t)-1;
-}
-
-// Accept masks of the words of thread (m, q) of ci_half_sweep_kernel for
-// sweep t, colour C: Philox call k (counter (q + kN/4, m, t, C)) gives the
-// draws of field k of the four words.  packed[e] holds r < thr1 of field k
-// at bit 3k and r < thr0 at bit 3k + 1.
-template <int ROUNDS>
-__device__ __forceinline__ void ci_masks(int N, int q, int m, uint64_t t, int C, const SweepArgs& a,
-                                         uint64_t packed[4])
-{
-    const uint32_t tl = (uint32_t)t;
-    const uint32_t th = ((uint32_t)(t >> 32) << 1) | (uint32_t)C;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) packed[e] = 0;
-    for (int k = 0; k < 21; ++k) {
-        const PhiloxRowKey pk = philox_row_key((uint32_t)(q + k * (N / 4)), tl, th, a.rk);
-        uint32_t r[4];
-        philox_row<ROUNDS>(pk, a.rk, (uint32_t)m, r);
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-            packed[e] |= (uint64_t)(r[e] < a.thr1) << (3 * k) | (uint64_t)(r[e] < a.thr0) << (3 * k + 1);
-    }
 }
 
 // The masks of ci_half_sweep_kernel for the sweeps j = 0 .. nsweeps-1 after

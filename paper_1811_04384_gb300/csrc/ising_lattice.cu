@@ -621,15 +621,22 @@ static int run_resident(ising_lattice* h, int n, int every)
 // mask buffers (43-sweep pieces at L = 1008) gave 444 there: each launch
 // loads and writes back the lattice and refills the mask ring.
 constexpr int kClusterMaxL = 1080;
+constexpr int kCiClusterMaxL = 1008;               // the column-interleaved layout (L % 84 == 0)
 constexpr size_t kClusterMaskBytes = 128u << 20;   // both buffers
 constexpr int kClusterMaxPiece = 256;
 
+static bool plan_cluster(const ising_lattice* h, ClusterPlan* plan)
+{
+    return h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED ? ci_cluster_plan(h->g.L, plan) : cluster_plan(h->g, plan);
+}
+
 static bool use_cluster(const ising_lattice* h, ClusterPlan* plan)
 {
-    if (h->layout != ISING_LAYOUT_ROW_PACKED || h->chain != ISING_CHAIN_CHECKERBOARD) return false;
-    if (h->path == ISING_PATH_CLUSTER) return cluster_plan(h->g, plan);
-    if (h->path != ISING_PATH_AUTO || use_resident(h) || h->g.L > kClusterMaxL) return false;
-    return cluster_plan(h->g, plan);
+    if (h->chain != ISING_CHAIN_CHECKERBOARD) return false;
+    if (h->path == ISING_PATH_CLUSTER) return plan_cluster(h, plan);
+    if (h->path != ISING_PATH_AUTO || use_resident(h)) return false;
+    if (h->g.L > (h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED ? kCiClusterMaxL : kClusterMaxL)) return false;
+    return plan_cluster(h, plan);
 }
 
 // n sweeps on the cluster path; every > 0: after every `every`-th sweep s of
@@ -637,7 +644,8 @@ static bool use_cluster(const ising_lattice* h, ClusterPlan* plan)
 static int run_cluster(ising_lattice* h, int64_t n, int64_t every, unsigned long long* counts, const ClusterPlan& plan)
 {
     const Geom& g = h->g;
-    const size_t per_sweep = cl_mask_bytes_per_sweep(g);
+    const bool ci = h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED;
+    const size_t per_sweep = ci ? ci_cl_mask_bytes_per_sweep(g.L) : cl_mask_bytes_per_sweep(g);
     const int max_piece =
         (int)std::max<size_t>(1, std::min<size_t>(kClusterMaxPiece, kClusterMaskBytes / (2 * per_sweep)));
     const size_t buf = (size_t)std::min<int64_t>(n, max_piece) * per_sweep;
@@ -656,19 +664,25 @@ static int run_cluster(ising_lattice* h, int64_t n, int64_t every, unsigned long
     // piece j: sweeps j * max_piece + 1 .. of the n, masks in buffer j & 1
     auto part_of = [&](int64_t j) { return (int)std::min<int64_t>(n - j * max_piece, max_piece); };
     const int64_t np = (n + max_piece - 1) / max_piece;
+    auto draw = [&](int64_t j, bool overlap) {
+        const uint64_t t0 = h->t + (uint64_t)(j * max_piece);
+        return ci ? ci_cl_mask_draw(g.L, a, t0, part_of(j), masks[j & 1], overlap, h->stream)
+                  : launch_cl_mask_draw(g, a, nullptr, t0, part_of(j), masks[j & 1], overlap, h->stream);
+    };
     if (np > 0) {
-        cudaError_t e = launch_cl_mask_draw(g, a, nullptr, h->t, part_of(0), masks[0], false, h->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cl_mask_draw_kernel");
+        cudaError_t e = draw(0, false);
+        if (e != cudaSuccess) return cuda_fail(e, "cluster mask draw");
     }
     for (int64_t j = 0; j < np; ++j) {
         const int64_t done = j * max_piece;
-        cudaError_t e = launch_cluster_sweeps(h->words[0], h->words[1], g, a, plan, part_of(j), masks[j & 1], done,
-                                              every, h->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cluster_sweeps_kernel");
+        cudaError_t e = ci ? ci_cluster_sweeps(h->words[0], g.L, a, plan, part_of(j), masks[j & 1], done, every,
+                                               h->stream)
+                           : launch_cluster_sweeps(h->words[0], h->words[1], g, a, plan, part_of(j), masks[j & 1],
+                                                   done, every, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cluster sweeps kernel");
         if (j + 1 < np) {
-            e = launch_cl_mask_draw(g, a, nullptr, h->t + (uint64_t)(done + max_piece), part_of(j + 1),
-                                    masks[(j + 1) & 1], true, h->stream);
-            if (e != cudaSuccess) return cuda_fail(e, "cl_mask_draw_kernel");
+            e = draw(j + 1, true);
+            if (e != cudaSuccess) return cuda_fail(e, "cluster mask draw");
         }
     }
     if (n > 0) {
@@ -698,8 +712,7 @@ extern "C" int ising_set_path(ising_lattice* h, int32_t path)
     if (path == ISING_PATH_RESIDENT && (h->layout != ISING_LAYOUT_ROW_PACKED || resident_bytes(h->g) > kResidentMaxBytes))
         return ISING_EINVAL;
     ClusterPlan cp;
-    if (path == ISING_PATH_CLUSTER && (h->layout != ISING_LAYOUT_ROW_PACKED || !cluster_plan(h->g, &cp)))
-        return ISING_EINVAL;
+    if (path == ISING_PATH_CLUSTER && !plan_cluster(h, &cp)) return ISING_EINVAL;
     h->path = path;
     return ISING_OK;
 }

@@ -1,5 +1,6 @@
 """The cluster path (one thread-block cluster keeping the lattice in its
-blocks' shared memory, halos exchanged through distributed shared memory)
+blocks' shared memory, halos exchanged through distributed shared memory),
+in the row-packed layout and in the paper's column-interleaved layout,
 against the oracle, bit-exact: int64 E/M series and final spins.
 
 Cases span two rows per block (L = 32, two half-sweeps per phase), the
@@ -58,6 +59,70 @@ def test_cluster_path_matches_oracle(ising):
         np.testing.assert_array_equal(E, Eo, err_msg=str(case))
         np.testing.assert_array_equal(M, Mo, err_msg=str(case))
         np.testing.assert_array_equal(S, So, err_msg=str(case))
+
+
+# the paper's column-interleaved layout (L % 84 == 0): (L, sweeps, every,
+# beta, forced)
+CI_CASES = [
+    (84, 9, 1, 0.44, False),       # N = 4 word rows, 16 blocks of 4 or 8 columns, phases of 4
+    (252, 26, 3, BETA_TC, False),  # phases of 12, records out of step with them
+    (504, 300, 7, 0.41, False),    # two mask pieces (256 + 44 sweeps)
+    (840, 20, 4, 0.44, False),     # two pairs per thread
+    (1008, 24, 5, BETA_TC, False), # the paper's L = 1008 (N = 48), phases of 8
+    (1092, 6, 1, 0.44, True),      # four pairs per thread
+    (1512, 3, 1, BETA_TC, True),   # two mask slabs, four pairs per thread
+]
+
+
+def test_interleaved_cluster_path_matches_oracle(ising):
+    got = []
+    for L, n, every, beta, forced in CI_CASES:
+        with ising.Lattice(L, L + 3, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
+            if forced:
+                lat.set_path(ising.ISING_PATH_CLUSTER)
+            assert lat.get_path() == ising.ISING_PATH_CLUSTER, L
+            lat.init_hot()
+            lat.set_beta(beta)
+            E, M = lat.sweep_record(n, every)
+            assert lat.t == n
+            got.append((E, M, lat.get_spins()))
+    ora = oracle.run_jobs([(L, L + 3, beta, True, n, every) for L, n, every, beta, _ in CI_CASES])
+    for (E, M, S), (Eo, Mo, So), case in zip(got, ora, CI_CASES):
+        np.testing.assert_array_equal(E, Eo, err_msg=str(case))
+        np.testing.assert_array_equal(M, Mo, err_msg=str(case))
+        np.testing.assert_array_equal(S, So, err_msg=str(case))
+
+
+def test_interleaved_cluster_extremes_and_continuation(ising):
+    """beta = 0 and a frozen cold lattice in the interleaved layout, then a
+    run continued across the cluster path and the graph replays."""
+    L = 336
+    for beta, cold in ((0.0, False), (5.0, True)):
+        with ising.Lattice(L, 8, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
+            lat.init_cold(1) if cold else lat.init_hot()
+            lat.set_beta(beta)
+            E, M = lat.sweep_record(4, 1)
+            S = lat.get_spins()
+        s = oracle.init_cold(L, 1) if cold else oracle.init_hot(L, 8)
+        Eo, Mo = oracle.run(s, 8, beta, 0, 4, 1)
+        np.testing.assert_array_equal(E, Eo)
+        np.testing.assert_array_equal(M, Mo)
+        np.testing.assert_array_equal(S, s)
+    with ising.Lattice(L, 9, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
+        lat.init_hot()
+        lat.set_beta(0.43)
+        lat.sweep(5)
+        lat.set_path(ising.ISING_PATH_LAUNCHES)
+        E1, M1 = lat.sweep_record(6, 2)
+        lat.set_path(ising.ISING_PATH_AUTO)
+        E2, M2 = lat.sweep_record(9, 3)
+        S = lat.get_spins()
+    s = oracle.init_hot(L, 9)
+    oracle.run(s, 9, 0.43, 0, 5, 5)
+    Eo1, Mo1 = oracle.run(s, 9, 0.43, 5, 6, 2)
+    Eo2, Mo2 = oracle.run(s, 9, 0.43, 11, 9, 3)
+    for got, want in ((E1, Eo1), (M1, Mo1), (E2, Eo2), (M2, Mo2), (S, s)):
+        np.testing.assert_array_equal(got, want)
 
 
 def test_cluster_continued_across_calls_and_paths(ising):
@@ -141,7 +206,11 @@ def test_cluster_path_choice(ising):
             with pytest.raises(ising.IsingError):
                 lat.set_path(ising.ISING_PATH_CLUSTER)
             assert lat.get_path() != ising.ISING_PATH_CLUSTER
-    with ising.Lattice(1008, 1, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
+    with ising.Lattice(1596, 1, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
         with pytest.raises(ising.IsingError):
             lat.set_path(ising.ISING_PATH_CLUSTER)
+        assert lat.get_path() == ising.ISING_PATH_LAUNCHES
+    with ising.Lattice(1008, 1, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
+        assert lat.get_path() == ising.ISING_PATH_CLUSTER
+        lat.set_path(ising.ISING_PATH_LAUNCHES)
         assert lat.get_path() == ising.ISING_PATH_LAUNCHES

@@ -21,10 +21,14 @@ def interleaved(ising, L, seed):
     return ising.Lattice(L, seed, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED)
 
 
+@pytest.mark.parametrize("path", ["auto", "launches"])
 @pytest.mark.parametrize("L", [84, 168, 252])
-def test_interleaved_matches_oracle(ising, L):
+def test_interleaved_matches_oracle(ising, L, path):
+    """Automatic path (the cluster path at these sizes) and the graph replays."""
     beta = 0.41
     with interleaved(ising, L, 5 + L) as lat:
+        if path == "launches":
+            lat.set_path(ising.ISING_PATH_LAUNCHES)
         lat.init_hot()
         np.testing.assert_array_equal(lat.get_spins(), oracle.init_hot(L, 5 + L))
         lat.set_beta(beta)
@@ -39,10 +43,15 @@ def test_interleaved_matches_oracle(ising, L):
     assert e_now == oracle.energy(s) and m_now == oracle.magnetization(s)
 
 
+@pytest.mark.parametrize("path", ["auto", "launches"])
 @pytest.mark.parametrize("L", [1008, 2016])
-def test_paper_sizes_equal_row_packed(ising, L):
-    """The paper's lattice sizes (N = 48 and 96 word rows)."""
+def test_paper_sizes_equal_row_packed(ising, L, path):
+    """The paper's lattice sizes (N = 48 and 96 word rows), the interleaved
+    lattice on the automatic path (the cluster path at L = 1008) and on the
+    graph replays, the row-packed one on its automatic path."""
     with interleaved(ising, L, 11) as a, ising.Lattice(L, 11) as b:
+        if path == "launches":
+            a.set_path(ising.ISING_PATH_LAUNCHES)
         for lat in (a, b):
             lat.init_hot()
             lat.set_beta(1.0 / 2.269)
