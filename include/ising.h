@@ -255,20 +255,26 @@ int ising_set_item_lanes(ising_lattice *h, int32_t lanes);
  * 16 MB), and the on-chip block only applies them, one or two rows per
  * thread.
  * ISING_PATH_CLUSTER: temporal blocking on one thread-block cluster (16
- * blocks where the device runs such a cluster, else 8), for row-packed
+ * blocks where the device runs such a cluster, else 8).  Row-packed
  * lattices with at least two rows per block whose window fits a block's
- * shared memory (L from 32 up to 1600; otherwise EINVAL, and EINVAL on a
- * device without clusters).  Block b keeps rows b L / C .. (b + 1) L / C - 1
- * of both colours in shared memory for a piece of up to 256 sweeps.  After
- * every k <= 12 half-sweeps the blocks pass a cluster barrier and copy k halo
- * rows from their neighbours' shared memory (distributed shared memory),
- * then run k half-sweeps on their rows plus halo.  The accept masks of each
+ * shared memory (L from 32 up to 1600): block b keeps rows b L / C ..
+ * (b + 1) L / C - 1 of both colours in shared memory for a piece of up to
+ * 256 sweeps.  Column-interleaved lattices (L from 84 up to 1512): block b
+ * keeps a band of word columns (multiples of 4) of all N word rows.
+ * Otherwise EINVAL, and EINVAL on a device without clusters.  After every
+ * k <= 12 half-sweeps each block writes its first and last k own rows (or
+ * columns) into its neighbours' shared memory (distributed shared memory)
+ * and the blocks pass a cluster barrier; then they run k half-sweeps on
+ * their own rows plus halo.  The accept masks of each
  * piece are drawn by the SMs the cluster leaves free, while the piece before
  * is applied, into two device buffers the library allocates on first use (up
  * to 128 MB together; 2 L pitch 8 bytes per sweep).  No spin-waits: only the
  * hardware's block and cluster barriers.
- * ISING_PATH_AUTO (default): resident up to 512 thread items (L <= 292), the
- * cluster path above that up to L = 1080, the launch path above that.
+ * ISING_PATH_AUTO (default), row-packed: resident up to 128 thread items
+ * (L <= 128), the cluster path above that up to L = 1080, the launch path
+ * above that (on a device without clusters: resident up to 512 items, L <=
+ * 292, then the launch path); column-interleaved: the cluster path up to
+ * L = 1008, the launch path above.
  * Results are identical on every path. */
 #define ISING_PATH_AUTO 0
 #define ISING_PATH_LAUNCHES 1

@@ -25,7 +25,13 @@ constexpr int kRecordsPerChunk = 1024;           // count slots resident on the 
 constexpr size_t kCountBytes = (size_t)kRecordsPerChunk * kCountSlots * 2 * sizeof(unsigned long long);
 constexpr size_t kAlign = 256;
 constexpr size_t kResidentMaxBytes = 220 * 1024;   // shared memory for the on-chip path
-constexpr int kResidentAutoMaxItems = kPremaskedMaxItems;   // auto: on-chip up to 512 items (L <= 292); launches above
+// auto: on-chip up to 128 thread items (L <= 128), the cluster path above;
+// on a device without thread-block clusters on-chip up to 512 items (L <= 292).
+// Measured on GB300 (sweeps without records / a record after every sweep,
+// spin-updates/ns, on-chip against cluster): L = 100: 16.8 / 12.8 against
+// 16.5 / 9.9; L = 128: 25.8 / 17.7 against 30.6 / 17.2; L = 168: 34.4 / 23.8
+// against 55.8 / 31.0; L = 256: 27.8 / 22.8 against 102 / 59.
+constexpr int kResidentAutoMaxItems = 128;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -549,7 +555,12 @@ static bool use_resident(const ising_lattice* h)
     if (h->layout != ISING_LAYOUT_ROW_PACKED || (h->path != ISING_PATH_AUTO && h->path != ISING_PATH_RESIDENT))
         return false;
     if (resident_bytes(h->g) > kResidentMaxBytes) return false;
-    return h->path == ISING_PATH_RESIDENT || ((h->g.L + 3) / 4) * h->g.W <= kResidentAutoMaxItems;
+    if (h->path == ISING_PATH_RESIDENT) return true;
+    const int items = ((h->g.L + 3) / 4) * h->g.W;
+    if (items <= kResidentAutoMaxItems) return true;
+    if (items > kPremaskedMaxItems) return false;
+    ClusterPlan cp;
+    return !cluster_plan(h->g, &cp);
 }
 
 // Pre-drawn masks of the on-chip path: 64 B per item and sweep, drawn for

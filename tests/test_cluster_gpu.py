@@ -196,8 +196,8 @@ def test_cluster_path_choice(ising):
     """Automatic choice by size; the forced path where no plan exists is
     rejected (too few rows per block, or a share of rows too large for a
     block's shared memory) and leaves the path unchanged."""
-    expect = {292: ising.ISING_PATH_RESIDENT, 296: ising.ISING_PATH_CLUSTER, 1080: ising.ISING_PATH_CLUSTER,
-              1082: ising.ISING_PATH_LAUNCHES}
+    expect = {128: ising.ISING_PATH_RESIDENT, 130: ising.ISING_PATH_CLUSTER, 292: ising.ISING_PATH_CLUSTER,
+              296: ising.ISING_PATH_CLUSTER, 1080: ising.ISING_PATH_CLUSTER, 1082: ising.ISING_PATH_LAUNCHES}
     for L, path in expect.items():
         with ising.Lattice(L, 1) as lat:
             assert lat.get_path() == path, L
