@@ -73,16 +73,20 @@ def main():
         Eo, Mo = oracle.run(s, seeds[k], BETA, 0, [7, 5, 6, 7, 4][k], 1)
         check(f"batch replica L={L}", (E[k], M[k]), (Eo, Mo))
     cases += 1
-    # the paper's column-interleaved layout: checkerboard and random-word chains
+    # the paper's column-interleaved layout: checkerboard chain on its
+    # cluster path (automatic here) and on the graph replays, random-word chain
     for L in (84, 168):
-        with p.Lattice(L, 9, layout=p.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
-            lat.init_hot()
-            lat.set_beta(BETA)
-            E, M = lat.sweep_record(34, 2)
-            S = lat.get_spins()
-        s = oracle.init_hot(L, 9)
-        Eo, Mo = oracle.run(s, 9, BETA, 0, 34, 2)
-        check(f"interleaved L={L}", (E, M, S), (Eo, Mo, s))
+        for path in (p.ISING_PATH_AUTO, p.ISING_PATH_LAUNCHES):
+            with p.Lattice(L, 9, layout=p.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
+                lat.set_path(path)
+                lat.init_hot()
+                lat.set_beta(BETA)
+                E, M = lat.sweep_record(34, 2)
+                S = lat.get_spins()
+            s = oracle.init_hot(L, 9)
+            Eo, Mo = oracle.run(s, 9, BETA, 0, 34, 2)
+            check(f"interleaved L={L} path={path}", (E, M, S), (Eo, Mo, s))
+            cases += 1
         for nstrips in (1, 6, L // 2):
             with p.Lattice(L, 5, layout=p.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
                 lat.init_hot()
