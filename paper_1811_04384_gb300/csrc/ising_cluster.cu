@@ -73,15 +73,18 @@ struct ClusterArgs {
 struct Slot {
     uint32_t o;      // lr * P + w (window row lr, word w): the word in the own-colour, other-colour and
                      // mask arrays; ~0u: no word
-    uint32_t dl;     // side word - o for colour 0 (bits 0..15) and colour 1 (16..31), as int16
+    uint32_t so;     // the side word's offset for colour 0 (bits 0..15) and colour 1 (16..31)
     uint32_t bits;   // side shift for colour 0 (bits 0..6) and 1 (8..14); colour 0 takes the left
                      // neighbour (16); last word of the row (17); an own row of the block (18)
 };
 
 // One update of colour C: the spin logic of row_apply with the packed masks
 // p (r < thr1 at bit 3k, r < thr0 at bit 3k + 1, each already set where its
-// threshold is 2^32) staged in msk.  RECORD adds the row's anti-aligned
-// bonds and up spins.
+// threshold is 2^32, and zero on the dead fields of a row's last word)
+// staged in msk.  Off the spin bits and on dead fields `accept` is then
+// zero or masked by kSpinBits: of the four neighbours only h1 can be nonzero
+// on a dead field, so there a < 2 and the zero masks decide.  RECORD adds
+// the row's anti-aligned bonds and up spins over the live fields.
 template <int C, bool RECORD>
 __device__ __forceinline__ void cl_update(uint64_t* own, const uint64_t* other, const uint64_t* msk, uint32_t P,
                                           const Slot& sl, uint64_t live_last, uint64_t n, uint32_t& anti,
@@ -89,9 +92,8 @@ __device__ __forceinline__ void cl_update(uint64_t* own, const uint64_t* other, 
 {
     const uint32_t o = sl.o;
     const bool left = ((sl.bits >> 16) & 1u) != (uint32_t)C;
-    const uint32_t so = o + (uint32_t)(int)(int16_t)(sl.dl >> (16 * C));
+    const uint32_t so = C == 0 ? (sl.so & 0xffffu) : (sl.so >> 16);
     const uint32_t sh = (sl.bits >> (8 * C)) & 0x7fu;
-    const uint64_t live = (sl.bits & (1u << 17)) ? live_last : kSpinBits;
     const uint64_t s = word_ld<false>(own, o, n, __LINE__);
     const uint64_t u = word_ld<false>(other, o - P, n, __LINE__);
     const uint64_t d = word_ld<false>(other, o + P, n, __LINE__);
@@ -103,9 +105,10 @@ __device__ __forceinline__ void cl_update(uint64_t* own, const uint64_t* other, 
     const uint64_t any = x1 | x2 | x3 | x4;
     const uint64_t ge2 = (x1 & x2) | (x3 & x4) | ((x1 ^ x2) & (x3 ^ x4));
     const uint64_t accept = ge2 | (any & p) | (~any & (p >> 1));
-    const uint64_t s_new = s ^ (accept & live);
+    const uint64_t s_new = s ^ (accept & kSpinBits);
     word_st(own, o, s_new, n, __LINE__);
     if (RECORD) {
+        const uint64_t live = (sl.bits & (1u << 17)) ? live_last : kSpinBits;
         anti += __popcll((s_new ^ u) & live) + __popcll((s_new ^ d) & live) + __popcll((s_new ^ h0) & live)
               + __popcll((s_new ^ h1) & live);
         up += __popcll(s_new & live) + __popcll(h0 & live);
@@ -156,7 +159,7 @@ cluster_sweeps_kernel(ClusterArgs a)
     const int bp = (b + C - 1) % C, bn = (b + 1) % C;
     const int Sp = (bp == C - 1 ? g.L : row0(bp + 1)) - row0(bp);     // rows of the block above
     const int top = r0 - k;                                            // global row of window row 0 (mod L)
-    const uint32_t P = (uint32_t)g.P, W = (uint32_t)g.W;
+    const uint32_t P = (uint32_t)g.P;
     const uint64_t n = (uint64_t)a.rmax * P;
     uint64_t* win[2] = {smem, smem + n};
     uint64_t* msk = smem + 2 * n;                                       // Q slabs of n words
@@ -176,12 +179,13 @@ cluster_sweeps_kernel(ClusterArgs a)
         const int lr = 1 + e / g.P, w = e % g.P;
         const bool first = w == 0, last = w == g.W - 1;
         const bool left0 = ((top + lr) & 1) == 0;      // colour 0 at (i + 0) even
-        // left neighbour: word w - 1 (wrapped), right: w + 1 (wrapped)
-        const int dleft = first ? (int)W - 1 : -1, dright = last ? -((int)W - 1) : 1;
+        // left neighbour: word w - 1 (wrapped), right: w + 1 (wrapped); the
+        // window's words fit 16 bits (fewer than 220 KB / 8)
+        const uint32_t row = (uint32_t)lr * P;
+        const uint32_t sl = row + (uint32_t)(first ? g.W - 1 : w - 1), sr = row + (uint32_t)(last ? 0 : w + 1);
         const uint32_t shl = first ? sh_wrap : 60u, shr = last ? sh_wrap : 60u;
-        slot[j].o = lr <= R - 2 && w < g.W ? (uint32_t)lr * P + (uint32_t)w : ~0u;
-        slot[j].dl = (uint32_t)(uint16_t)(int16_t)(left0 ? dleft : dright) |
-                     ((uint32_t)(uint16_t)(int16_t)(left0 ? dright : dleft) << 16);
+        slot[j].o = lr <= R - 2 && w < g.W ? row + (uint32_t)w : ~0u;
+        slot[j].so = ((left0 ? sl : sr) & 0xffffu) | ((left0 ? sr : sl) << 16);
         slot[j].bits = (left0 ? shl : shr) | ((left0 ? shr : shl) << 8) | (left0 ? 1u << 16 : 0u) |
                        (last ? 1u << 17 : 0u) | ((lr >= k && lr < R - k) ? 1u << 18 : 0u);
         const int cr = 1 + e / pairs, cp = e % pairs;
@@ -320,7 +324,8 @@ cluster_sweeps_kernel(ClusterArgs a)
 // Masks of sweeps j = 0 .. nsweeps-1 after sweep (t_base ? *t_base : 0) + t0:
 // one thread per (sweep, colour, item) draws them with item_masks_thread (the
 // draws of sweep_rows) and writes them row-major, masks[((j * 2 + c) * L + i)
-// * P + w], with the bits of a threshold of 2^32 set.
+// * P + w], with the bits of a threshold of 2^32 set and those of the dead
+// fields of a row's last word cleared.
 template <int ROUNDS>
 __global__ void __launch_bounds__(128)
 cl_mask_draw_kernel(Geom g, SweepArgs a, const uint64_t* t_base, uint64_t t0, int nsweeps,
@@ -339,11 +344,14 @@ cl_mask_draw_kernel(Geom g, SweepArgs a, const uint64_t* t_base, uint64_t t0, in
     // a threshold of 2^32 accepts always: its bits set here, not in the update
     const uint64_t always = (((uint64_t)a.all1 << 32 | a.all1) & kSpinBits) |
                             ((((uint64_t)a.all0 << 32 | a.all0) & kSpinBits) << 1);
+    // the dead fields of a row's last word: both masks zero
+    const uint64_t live = live_mask(g, w);
+    const uint64_t keep = live | (live << 1);
     uint64_t* out = masks + (size_t)jc * g.L * g.P;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const int i = 4 * grp + e;
-        if (i < g.L) out[(size_t)i * g.P + w] = p[e] | always;
+        if (i < g.L) out[(size_t)i * g.P + w] = (p[e] | always) & keep;
     }
 }
 
