@@ -271,10 +271,10 @@ int ising_set_item_lanes(ising_lattice *h, int32_t lanes);
  * to 128 MB together; 2 L pitch 8 bytes per sweep).  No spin-waits: only the
  * hardware's block and cluster barriers.
  * ISING_PATH_AUTO (default), row-packed: resident up to 128 thread items
- * (L <= 128), the cluster path above that up to L = 1080, the launch path
+ * (L <= 128), the cluster path above that up to L = 1176, the launch path
  * above that (on a device without clusters: resident up to 512 items, L <=
  * 292, then the launch path); column-interleaved: the cluster path up to
- * L = 1008, the launch path above.
+ * L = 1092, the launch path above.
  * Results are identical on every path. */
 #define ISING_PATH_AUTO 0
 #define ISING_PATH_LAUNCHES 1

@@ -128,7 +128,7 @@ __device__ __forceinline__ void ci_cl_half_sweep(uint64_t* E, const uint64_t* ms
 
 // NS: window pairs per thread; DEEP: kCiMaxSlabs mask slabs, else 2.
 template <int NS, bool DEEP>
-__global__ void __launch_bounds__(kCiThreads, 1)
+__global__ void __launch_bounds__(NS == 3 ? 768 : kCiThreads, 1)
 ci_cluster_sweeps_kernel(CiClusterArgs a)
 {
     extern __shared__ __align__(16) uint64_t smem[];
@@ -333,14 +333,18 @@ size_t ci_cl_smem_bytes(int L, int N, int C, int k, int q)
 }
 
 using CiClusterKernel = void (*)(CiClusterArgs);
-constexpr CiClusterKernel kCiClusterKernels[6] = {
-    ci_cluster_sweeps_kernel<1, false>, ci_cluster_sweeps_kernel<2, false>, ci_cluster_sweeps_kernel<4, false>,
-    ci_cluster_sweeps_kernel<1, true>,  ci_cluster_sweeps_kernel<2, true>,  ci_cluster_sweeps_kernel<4, true>};
+constexpr CiClusterKernel kCiClusterKernels[8] = {
+    ci_cluster_sweeps_kernel<1, false>, ci_cluster_sweeps_kernel<2, false>, ci_cluster_sweeps_kernel<3, false>, ci_cluster_sweeps_kernel<4, false>,
+    ci_cluster_sweeps_kernel<1, true>,  ci_cluster_sweeps_kernel<2, true>,  ci_cluster_sweeps_kernel<3, true>,  ci_cluster_sweeps_kernel<4, true>};
 
 CiClusterKernel ci_cluster_kernel(int ns, int q)
 {
-    return kCiClusterKernels[(q == kCiMaxSlabs ? 3 : 0) + (ns == 1 ? 0 : (ns == 2 ? 1 : 2))];
+    return kCiClusterKernels[(q == kCiMaxSlabs ? 4 : 0) + (ns - 1)];
 }
+
+// Window words a block takes with at most `ns` words per thread: 1024
+// threads for 1, 2 or 4 (64 registers each), 768 for 3 (80 registers).
+long long max_words(int ns) { return ns == 3 ? 3 * 768 : (long long)ns * kCiThreads; }
 
 int ci_probe_max_cluster()
 {
@@ -355,7 +359,6 @@ int ci_probe_max_cluster()
     for (int c : {16, 8}) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(c);
-        cfg.blockDim = dim3(kCiThreads);
         cfg.dynamicSmemBytes = kCiSmemMax;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -365,9 +368,10 @@ int ci_probe_max_cluster()
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         bool ok = true;
-        for (CiClusterKernel kern : kCiClusterKernels) {
+        for (int i = 0; i < 8; ++i) {                 // form i: (i % 4) + 1 words per thread
+            cfg.blockDim = dim3(i % 4 == 2 ? 768 : kCiThreads);
             int nc = 0;
-            ok = ok && cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) == cudaSuccess && nc >= 1;
+            ok = ok && cudaOccupancyMaxActiveClusters(&nc, kCiClusterKernels[i], &cfg) == cudaSuccess && nc >= 1;
         }
         if (ok) return c;
         cudaGetLastError();
@@ -380,9 +384,11 @@ int ci_probe_max_cluster()
 // Cluster size, phase length (a multiple of 4, <= kCiHalo, <= the fewest
 // columns a block owns), mask slabs and pairs per thread for side L, as
 // cluster_plan: the largest k whose window, kCiMaxSlabs slabs (else 2) and
-// receive slots fit in shared memory with at most 2 pairs per thread where
-// some k allows it, else 4.  False if L is not a side of the layout or no
-// such launch exists.
+// receive slots fit in shared memory with at most 3 pairs per thread where
+// some k allows it, else 4 (L = 1008: k = 12 with 3 pairs per thread, 373
+// spin-updates/ns, against k = 8 with 2, 367; L = 1092: 3 pairs, 403,
+// against 4, 232).  False if L is not a side of the layout or no such launch
+// exists.
 bool ci_cluster_plan(int L, ClusterPlan* plan)
 {
     if (!ci_valid_side(L)) return false;
@@ -390,13 +396,13 @@ bool ci_cluster_plan(int L, ClusterPlan* plan)
     if (max_cluster == 0) return false;
     const int c = max_cluster, N = L / 21;
     const int fewest = 4 * ((L / 4) / c), widest = ci_widest(L, c);
-    for (int most : {2, 4}) {
+    for (int most : {3, 4}) {
         for (int q : {kCiMaxSlabs, 2}) {
             for (int kk = std::min(kCiHalo, fewest) & ~3; kk >= 4; kk -= 4) {
                 if (ci_cl_smem_bytes(L, N, c, kk, q) > kCiSmemMax) continue;
                 const long long words = (long long)N * ((widest + 2 * kk) / 2);
-                if (words > (long long)most * kCiThreads) continue;
-                const int ns = words <= kCiThreads ? 1 : (words <= 2 * kCiThreads ? 2 : 4);
+                if (words > max_words(most)) continue;
+                const int ns = words <= kCiThreads ? 1 : (words <= 2 * kCiThreads ? 2 : (words <= max_words(3) ? 3 : 4));
                 plan->blocks = c;
                 plan->k = kk;
                 plan->q = q;

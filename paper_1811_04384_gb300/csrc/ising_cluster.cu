@@ -140,7 +140,7 @@ __device__ __forceinline__ void cl_half_sweep(uint64_t* own, const uint64_t* oth
 // NS: window words per thread (the block has ceil(words / NS) threads,
 // rounded up to whole warps).  DEEP: kClMaxSlabs mask slabs, else 2.
 template <int NS, bool DEEP>
-__global__ void __launch_bounds__(kClThreads, 1)
+__global__ void __launch_bounds__(NS == 3 ? 768 : kClThreads, 1)
 cluster_sweeps_kernel(ClusterArgs a)
 {
     extern __shared__ __align__(16) uint64_t smem[];
@@ -365,14 +365,18 @@ size_t cl_smem_bytes(const Geom& g, int blocks, int k, int q)
 
 // The six forms of the kernel: 1, 2 or 4 words per thread, 2 or kClMaxSlabs mask slabs.
 using ClusterKernel = void (*)(ClusterArgs);
-constexpr ClusterKernel kClusterKernels[6] = {cluster_sweeps_kernel<1, false>, cluster_sweeps_kernel<2, false>,
-                                              cluster_sweeps_kernel<4, false>, cluster_sweeps_kernel<1, true>,
-                                              cluster_sweeps_kernel<2, true>,  cluster_sweeps_kernel<4, true>};
+constexpr ClusterKernel kClusterKernels[8] = {
+    cluster_sweeps_kernel<1, false>, cluster_sweeps_kernel<2, false>, cluster_sweeps_kernel<3, false>, cluster_sweeps_kernel<4, false>,
+    cluster_sweeps_kernel<1, true>,  cluster_sweeps_kernel<2, true>,  cluster_sweeps_kernel<3, true>,  cluster_sweeps_kernel<4, true>};
 
 ClusterKernel cluster_kernel(int ns, int q)
 {
-    return kClusterKernels[(q == kClMaxSlabs ? 3 : 0) + (ns == 1 ? 0 : (ns == 2 ? 1 : 2))];
+    return kClusterKernels[(q == kClMaxSlabs ? 4 : 0) + (ns - 1)];
 }
+
+// Window words a block takes with at most `ns` words per thread: 1024
+// threads for 1, 2 or 4 (64 registers each), 768 for 3 (80 registers).
+long long max_words(int ns) { return ns == 3 ? 3 * 768 : (long long)ns * kClThreads; }
 
 int probe_max_cluster()
 {
@@ -387,7 +391,6 @@ int probe_max_cluster()
     for (int c : {16, 8}) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(c);
-        cfg.blockDim = dim3(kClThreads);
         cfg.dynamicSmemBytes = kClSmemMax;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -397,9 +400,10 @@ int probe_max_cluster()
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         bool ok = true;
-        for (ClusterKernel kern : kClusterKernels) {
+        for (int i = 0; i < 8; ++i) {                 // form i: (i % 4) + 1 words per thread
+            cfg.blockDim = dim3(i % 4 == 2 ? 768 : kClThreads);
             int nc = 0;
-            ok = ok && cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) == cudaSuccess && nc >= 1;
+            ok = ok && cudaOccupancyMaxActiveClusters(&nc, kClusterKernels[i], &cfg) == cudaSuccess && nc >= 1;
         }
         if (ok) return c;
         cudaGetLastError();
@@ -413,26 +417,29 @@ int probe_max_cluster()
 // 16 blocks if the device runs such a cluster, else 8; k = the most
 // half-sweeps per phase (even, <= kClHalo, <= the fewest rows a block owns)
 // whose window and kClMaxSlabs mask slabs fit in shared memory (else two
-// slabs), with at most 2 window words per thread where some k allows it,
-// else 4.  Measured on GB300 (sweeps without records, spin-updates/ns, by k
-// = 4 / 8 / 12): L = 296: 77 / 105 / 115, L = 512: 170 / 199 / 210,
-// L = 1008: 357 / 394 / 403; 4 words per thread (L = 1008, k = 16) 336
-// (threads over the W live words of a row then; over the pitch since, which
-// gave L = 512: 215, L = 1008: 416 at k = 12).
-// Returns false if no such launch exists (a lattice too large or too small).
+// slabs), with at most 3 window words per thread (1024 threads for 1 or 2,
+// 768 for 3) where some k allows it, else 4.  Measured on GB300 (sweeps
+// without records, spin-updates/ns, by k = 4 / 8 / 12): L = 296: 77 / 105 /
+// 115, L = 512: 170 / 199 / 210, L = 1008: 357 / 394 / 403 (threads over
+// the W live words of a row then; over the pitch since, which gave L = 512:
+// 215, L = 1008: 416 at k = 12).  3 words per thread against the plan with
+// at most 2: L = 1080: 478 (k = 10) against 463 (k = 6); L = 1100: 465
+// (k = 6) against 367 (k = 2); 4 words per thread spill registers (L = 1200:
+// 297).  Returns false if no such launch exists (a lattice too large or too
+// small).
 bool cluster_plan(const Geom& g, ClusterPlan* plan)
 {
     static const int max_cluster = probe_max_cluster();   // per process, set once
     if (max_cluster == 0) return false;
     const int c = max_cluster;
     const int fewest = g.L / c;
-    for (int most : {2, 4}) {
+    for (int most : {3, 4}) {
         for (int q : {kClMaxSlabs, 2}) {
             for (int kk = std::min(kClHalo, fewest) & ~1; kk >= 2; kk -= 2) {
                 if (cl_smem_bytes(g, c, kk, q) > kClSmemMax) continue;
                 const long long words = (long long)((g.L + c - 1) / c + 2 * kk - 2) * g.P;
-                if (words > (long long)most * kClThreads) continue;
-                const int ns = words <= kClThreads ? 1 : (words <= 2 * kClThreads ? 2 : 4);
+                if (words > max_words(most)) continue;
+                const int ns = words <= kClThreads ? 1 : (words <= 2 * kClThreads ? 2 : (words <= max_words(3) ? 3 : 4));
                 plan->blocks = c;
                 plan->k = kk;
                 plan->q = q;

@@ -625,14 +625,16 @@ static int run_resident(ising_lattice* h, int n, int every)
 // writes the buffer piece j - 1 read (complete before piece j started).
 // Replayed graphs of short half-sweeps stay for the launch path
 // (ISING_PATH_LAUNCHES) and for larger lattices.  Measured on GB300, sweeps
-// without records, spin-updates/ns, cluster against graphs: L = 296: 133 /
-// 34; L = 512: 244 / 95; L = 700: 317 / 170; L = 1008: 458 / 311; L = 1080:
-// 458 / 341; but L = 1100: 329 / 348, where the window allows phases of 2
-// half-sweeps only.  Up to L = 1086 the phases have 6 or more.  Two 16 MB
-// mask buffers (43-sweep pieces at L = 1008) gave 444 there: each launch
-// loads and writes back the lattice and refills the mask ring.
-constexpr int kClusterMaxL = 1080;
-constexpr int kCiClusterMaxL = 1008;               // the column-interleaved layout (L % 84 == 0)
+// without records, spin-updates/ns, cluster against graphs: L = 296: 138 /
+// 34; L = 512: 255 / 96; L = 700: 328 / 170; L = 1008: 472 / 313; L = 1080:
+// 478 / 342; L = 1150: 499 / 362; but L = 1200: 297 / 368, where the window
+// needs 4 words per thread, which spill registers (up to L = 1176 3 words
+// per thread allow phases of 4 half-sweeps or more).  Two 16 MB mask buffers
+// (43-sweep pieces at L = 1008) gave 444 there: each launch loads and writes
+// back the lattice and refills the mask ring.  In the column-interleaved
+// layout: L = 1008: 373 / 304; L = 1092: 403 / 338.
+constexpr int kClusterMaxL = 1176;
+constexpr int kCiClusterMaxL = 1092;               // the column-interleaved layout (L % 84 == 0)
 constexpr size_t kClusterMaskBytes = 128u << 20;   // both buffers
 constexpr int kClusterMaxPiece = 256;
 

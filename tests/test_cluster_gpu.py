@@ -5,7 +5,7 @@ against the oracle, bit-exact: int64 E/M series and final spins.
 
 Cases span two rows per block (L = 32, two half-sweeps per phase), the
 automatic range (L = 296 just above the on-chip path, with two mask pieces,
-up to L = 1080), L % 4 == 2, records out of step with the phases and pieces,
+up to L = 1176), L % 4 == 2, records out of step with the phases and pieces,
 odd numbers of half-sweeps per call, forced runs up to the largest side
 (L = 1600), cold starts, beta = 0 (every flip accepted) and a frozen
 lattice, runs continued across calls and paths, and ising_run_states.
@@ -36,7 +36,8 @@ CASES = [
     (296, 300, 7, 0.41, False),    # two mask pieces (256 + 44 sweeps), records across them
     (514, 20, 3, 0.3, False),      # L % 4 == 2; 6 records, out of step with the phases
     (1008, 24, 4, 0.44, False),    # the paper's L = 1008
-    (1080, 60, 5, BETA_TC, False), # largest automatic side
+    (1080, 60, 5, BETA_TC, False), # three words per thread, phases of 10
+    (1176, 8, 2, 0.44, False),     # largest automatic side: phases of 4
     (1500, 6, 1, 0.44, True),      # phases of 10 half-sweeps, 4 words per thread
     (1600, 3, 1, BETA_TC, True),   # largest side with a plan: 4 words per thread
 ]
@@ -68,8 +69,9 @@ CI_CASES = [
     (252, 26, 3, BETA_TC, False),  # phases of 12, records out of step with them
     (504, 300, 7, 0.41, False),    # two mask pieces (256 + 44 sweeps)
     (840, 20, 4, 0.44, False),     # two pairs per thread
-    (1008, 24, 5, BETA_TC, False), # the paper's L = 1008 (N = 48), phases of 8
-    (1092, 6, 1, 0.44, True),      # four pairs per thread
+    (1008, 24, 5, BETA_TC, False), # the paper's L = 1008 (N = 48), phases of 12, three pairs per thread
+    (1092, 6, 1, 0.44, False),     # three pairs per thread, largest automatic side
+    (1260, 4, 1, 0.41, True),      # four pairs per thread
     (1512, 3, 1, BETA_TC, True),   # two mask slabs, four pairs per thread
 ]
 
@@ -197,7 +199,7 @@ def test_cluster_path_choice(ising):
     rejected (too few rows per block, or a share of rows too large for a
     block's shared memory) and leaves the path unchanged."""
     expect = {128: ising.ISING_PATH_RESIDENT, 130: ising.ISING_PATH_CLUSTER, 292: ising.ISING_PATH_CLUSTER,
-              296: ising.ISING_PATH_CLUSTER, 1080: ising.ISING_PATH_CLUSTER, 1082: ising.ISING_PATH_LAUNCHES}
+              296: ising.ISING_PATH_CLUSTER, 1176: ising.ISING_PATH_CLUSTER, 1178: ising.ISING_PATH_LAUNCHES}
     for L, path in expect.items():
         with ising.Lattice(L, 1) as lat:
             assert lat.get_path() == path, L
