@@ -23,8 +23,9 @@
 // consecutive pairs falls on consecutive words.  The accept masks, drawn
 // beforehand on the SMs the cluster leaves free (ci_masks, the draws of the
 // other interleaved kernels), stream into a ring of shared-memory slabs
-// indexed like the pairs.  The update is Eq. 3 in its arithmetic form, as in
-// ci_half_sweep_apply_kernel, so the results equal every other path's.
+// indexed like the pairs.  The update is Eq. 3 summed bitwise, as in the
+// row-packed kernels: the decisions of ci_half_sweep_apply_kernel's 3-bit
+// field sums, so the results equal every other path's.
 #include <cuda_runtime.h>
 #include <cooperative_groups.h>
 
@@ -71,7 +72,7 @@ struct CiSlot {
                      // top word row (17); bottom word row (18); an own column pair of the block (19)
 };
 
-// One update of colour C (Eq. 3, arithmetic form): s, its four neighbours and
+// One update of colour C (Eq. 3): s, its four neighbours and
 // the packed masks p (r < thr1 at bit 3k, r < thr0 at 3k + 1, set where the
 // threshold is 2^32).  RECORD adds the word's anti-aligned bonds and the up
 // spins of its column pair.
@@ -92,10 +93,14 @@ __device__ __forceinline__ void ci_cl_update(uint64_t* E, const uint64_t* msk, u
     const uint64_t xl = word_ld<false>(oth, o - 1u + par, nw, __LINE__);
     const uint64_t xr = word_ld<false>(oth, o + par, nw, __LINE__);
     const uint64_t p = word_ld<false>(msk, o, nw, __LINE__);
-    // the 3-bit field sums of the four XORs hold a = 0..4 without carries
-    const uint64_t A = (s ^ xu) + (s ^ xd) + (s ^ xl) + (s ^ xr);
-    const uint64_t ge2 = ((A >> 1) | (A >> 2)) & kAllFields;
-    const uint64_t any = (A | (A >> 1) | (A >> 2)) & kAllFields;
+    // Eq. 3 summed bitwise (as the row-packed kernels do): with x_n = s ^ n
+    // the field's spin bit of x_n is set iff neighbour n is anti-aligned;
+    // a >= 1 is their OR, a >= 2 that two of them are set.  The same
+    // decisions as the carry-free 3-bit field sum of the other interleaved
+    // kernels, in fewer instructions.
+    const uint64_t x1 = s ^ xu, x2 = s ^ xd, x3 = s ^ xl, x4 = s ^ xr;
+    const uint64_t any = x1 | x2 | x3 | x4;
+    const uint64_t ge2 = (x1 & x2) | (x3 & x4) | ((x1 ^ x2) & (x3 ^ x4));
     const uint64_t accept = ge2 | (any & p) | (~any & (p >> 1));
     const uint64_t sn = s ^ (accept & kAllFields);
     word_st(own, o, sn, nw, __LINE__);
