@@ -287,6 +287,21 @@ int ising_set_path(ising_lattice *h, int32_t path);
  * ISING_PATH_LAUNCHES; with the random-word chain, the path last set). */
 int ising_get_path(ising_lattice *h, int32_t *path);
 
+/* Clusters of one cluster-path launch (row-packed lattices): 0 = automatic
+ * (the default), 1 .. 16 = that many thread-block clusters whose blocks own
+ * consecutive row bands.  Inside a cluster the halo rows travel through
+ * distributed shared memory; between clusters the two boundary blocks pass
+ * them through a small device buffer the library allocates on first use
+ * (clusters x 8 k pitch 8 bytes, k <= 12) with release/acquire flags.  A
+ * flag wait gives up after one second of the GPU's clock (for example when
+ * other work keeps a cluster from being resident): the call then returns
+ * ISING_ETIMEOUT, the sweeps it ran are void, and the sweep counter has
+ * advanced (restore a checkpoint with ising_set_words / ising_set_sweep to
+ * retry).  A number of clusters the device cannot hold at once, or for which
+ * the lattice has no window plan, gives EINVAL; so does a count other than 0
+ * or 1 on a column-interleaved lattice.  Results do not depend on it. */
+int ising_set_clusters(ising_lattice *h, int32_t clusters);
+
 /* Which Markov chain ising_sweep and ising_sweep_record run.
  * ISING_CHAIN_CHECKERBOARD (default): the checkerboard sweeps of the
  * conventions above (nstrips ignored).  ISING_CHAIN_RANDOM_WORDS: the paper's

@@ -201,6 +201,10 @@ class Lattice:
         """ISING_PATH_AUTO, ISING_PATH_LAUNCHES, ISING_PATH_RESIDENT or ISING_PATH_CLUSTER."""
         _check(load().ising_set_path(self._h, int(path)), "ising_set_path")
 
+    def set_clusters(self, clusters: int = 0):
+        """Clusters of one cluster-path launch (ising_set_clusters): 0 = automatic."""
+        _check(load().ising_set_clusters(self._h, int(clusters)), "ising_set_clusters")
+
     def get_path(self) -> int:
         """The path the next sweeps take (ising_get_path): ISING_PATH_RESIDENT,
         ISING_PATH_CLUSTER or ISING_PATH_LAUNCHES."""

@@ -413,6 +413,7 @@ bool ci_cluster_plan(int L, ClusterPlan* plan)
                 plan->q = q;
                 plan->ns = ns;
                 plan->threads = (int)(((words + ns - 1) / ns + 31) / 32 * 32);
+                plan->clusters = 1;
                 return true;
             }
         }

@@ -62,6 +62,11 @@ struct ClusterArgs {
     int64_t every;              // record after sweeps s with s % every == 0 (0: none)
     unsigned long long* counts; // count slots (32 per record); record r of the call -> slot r
     uint32_t all0, all1;        // "always" masks (threshold 2^32)
+    int G;                      // clusters of the launch: blocks g C .. g C + C - 1 form cluster g
+    uint64_t* xbuf;             // G > 1: halo rows between clusters, [boundary][dir][parity][colour], k x P words
+    unsigned long long* xflag;  // G > 1: [boundary][dir] sequence flags
+    unsigned long long xseq;    // push m of this launch sets its flags to xseq + m + 1
+    unsigned int* xerr;         // set to 1 when a wait for a flag gives up
 };
 
 // A window word a thread updates in every half-sweep whose rows include its
@@ -139,7 +144,9 @@ __device__ __forceinline__ void cl_half_sweep(uint64_t* own, const uint64_t* oth
 
 // NS: window words per thread (the block has ceil(words / NS) threads,
 // rounded up to whole warps).  DEEP: kClMaxSlabs mask slabs, else 2.
-template <int NS, bool DEEP>
+// MULTI: several clusters (G > 1), with the halo exchange between them;
+// without it the form has no code for that exchange.
+template <int NS, bool DEEP, bool MULTI>
 __global__ void __launch_bounds__(NS == 3 ? 768 : kClThreads, 1)
 cluster_sweeps_kernel(ClusterArgs a)
 {
@@ -154,10 +161,16 @@ cluster_sweeps_kernel(ClusterArgs a)
     const int T = blockDim.x;
     const int C = (int)cluster.num_blocks(), b = (int)cluster.block_rank();
     const int k = a.k;
-    auto row0 = [&](int rank) { return (int)((long long)rank * g.L / C); };
-    const int r0 = row0(b), r1 = row0(b + 1), S = r1 - r0, R = S + 2 * k;
-    const int bp = (b + C - 1) % C, bn = (b + 1) % C;
-    const int Sp = (bp == C - 1 ? g.L : row0(bp + 1)) - row0(bp);     // rows of the block above
+    // the launch's G C blocks own consecutive row bands: block B = gc C + b
+    const int G = a.G, gc = (int)blockIdx.x / C, NB = G * C, B = gc * C + b;
+    auto row0 = [&](int blk) { return (int)((long long)blk * g.L / NB); };
+    const int r0 = row0(B), r1 = row0(B + 1), S = r1 - r0, R = S + 2 * k;
+    const int bp = (b + C - 1) % C, bn = (b + 1) % C;                   // the blocks above and below in the cluster
+    // with G > 1 a cluster's first block takes its upper halo from the last
+    // block of the cluster above (boundary bd_up, through global memory), its
+    // last block the lower halo from the first block of the cluster below
+    const bool up_remote = MULTI && b == 0, dn_remote = MULTI && b == C - 1;
+    const int bd_up = (gc + G - 1) % G, bd_dn = gc;
     const int top = r0 - k;                                            // global row of window row 0 (mod L)
     const uint32_t P = (uint32_t)g.P;
     const uint64_t n = (uint64_t)a.rmax * P;
@@ -223,28 +236,52 @@ cluster_sweeps_kernel(ClusterArgs a)
     const int kP = k * (int)P;
     auto rb = [&](uint64_t* base, int par, int c, int dir) { return base + (size_t)((par * 2 + c) * 2 + dir) * kP; };
     uint64_t* recv = msk + (size_t)Q * n;
-    // a block's first k own rows go to the slots below of the block above, its
+    // the global slots between clusters: dir 0 carries the last k own rows of
+    // cluster bd's last block down to the first block of cluster bd + 1, dir 1
+    // the first k own rows of that block up
+    auto xs = [&](int bd, int dir, int par, int c) {
+        return a.xbuf + (size_t)(((bd * 2 + dir) * 2 + par) * 2 + c) * kP;
+    };
+    // push m (m = 0 before the first phase, m = p + 1 after phase p): a
+    // block's first k own rows go to the slots below of the block above, its
     // last k own rows to the slots above of the block below
-    auto push = [&](int par) {
-        uint64_t* up_recv = cluster.map_shared_rank(recv, bp);
-        uint64_t* dn_recv = cluster.map_shared_rank(recv, bn);
+    auto push = [&](int par, int m) {
+        uint64_t* up_recv = up_remote ? nullptr : cluster.map_shared_rank(recv, bp);
+        uint64_t* dn_recv = dn_remote ? nullptr : cluster.map_shared_rank(recv, bn);
         for (int c = 0; c < 2; ++c) {
-            uint64_t* to_up = rb(up_recv, par, c, 1);
-            uint64_t* to_dn = rb(dn_recv, par, c, 0);
+            uint64_t* to_up = up_remote ? xs(bd_up, 1, par, c) : rb(up_recv, par, c, 1);
+            uint64_t* to_dn = dn_remote ? xs(bd_dn, 0, par, c) : rb(dn_recv, par, c, 0);
             for (int idx = threadIdx.x; idx < kP; idx += T) {
                 word_st(to_up, idx, word_ld<false>(win[c], (uint64_t)k * P + idx, n, __LINE__), kP, __LINE__);
                 word_st(to_dn, idx, word_ld<false>(win[c], (uint64_t)S * P + idx, n, __LINE__), kP, __LINE__);
             }
         }
+        if (up_remote || dn_remote) {
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (up_remote) cl_flag_release(a.xflag + bd_up * 2 + 1, a.xseq + m + 1);
+                if (dn_remote) cl_flag_release(a.xflag + bd_dn * 2 + 0, a.xseq + m + 1);
+            }
+        }
     };
-    auto receive = [&](int par) {
+    // the halos of phase p (push p of the neighbours)
+    auto receive = [&](int par, int p) {
+        if (up_remote || dn_remote) {
+            if (threadIdx.x == 0) {
+                if (up_remote) cl_wait_flag(a.xflag + bd_up * 2 + 0, a.xseq + p + 1, a.xerr);
+                if (dn_remote) cl_wait_flag(a.xflag + bd_dn * 2 + 1, a.xseq + p + 1, a.xerr);
+            }
+            __syncthreads();
+        }
         for (int c = 0; c < 2; ++c) {
-            const uint64_t* from_up = rb(recv, par, c, 0);
-            const uint64_t* from_dn = rb(recv, par, c, 1);
+            const uint64_t* from_up = up_remote ? xs(bd_up, 0, par, c) : rb(recv, par, c, 0);
+            const uint64_t* from_dn = dn_remote ? xs(bd_dn, 1, par, c) : rb(recv, par, c, 1);
             for (int idx = threadIdx.x; idx < kP; idx += T) {
-                word_st(win[c], idx, word_ld<false>(from_up, idx, kP, __LINE__), n, __LINE__);
-                word_st(win[c], (uint64_t)(k + S) * P + idx, word_ld<false>(from_dn, idx, kP, __LINE__), n,
-                        __LINE__);
+                const uint64_t vu = up_remote ? __ldcg(from_up + idx) : word_ld<false>(from_up, idx, kP, __LINE__);
+                const uint64_t vd = dn_remote ? __ldcg(from_dn + idx) : word_ld<false>(from_dn, idx, kP, __LINE__);
+                word_st(win[c], idx, vu, n, __LINE__);
+                word_st(win[c], (uint64_t)(k + S) * P + idx, vd, n, __LINE__);
             }
         }
     };
@@ -258,7 +295,7 @@ cluster_sweeps_kernel(ClusterArgs a)
     cl_commit();
     cl_wait<0>();
     __syncthreads();
-    push(0);
+    push(0, 0);
 #pragma unroll
     for (int h = 0; h < Q - 1; ++h) stage();
     cluster.sync();          // the first phase's halos have arrived
@@ -284,10 +321,10 @@ cluster_sweeps_kernel(ClusterArgs a)
             rec_counts = a.counts + (size_t)(first / a.every - 1) * 2 * kCountSlots;
         }
     }
-    int par = 0;
-    for (int hs0 = 0; hs0 < total; hs0 += k) {
+    int par = 0, phase = 0;
+    for (int hs0 = 0; hs0 < total; hs0 += k, ++phase) {
         const int kk = min(k, total - hs0);                             // even: phases start with colour 0
-        receive(par);        // into the halo rows (ordered before the updates by begin's barrier)
+        receive(par, phase);  // into the halo rows (ordered before the updates by begin's barrier)
         for (int d = 0; d < kk; d += 2) {
             const uint64_t* m0 = begin();
             cl_half_sweep<0, false, NS>(win[0], win[1], m0, P, slot, 1 + d, R - 2 - d, live_last, n, nullptr);
@@ -306,7 +343,7 @@ cluster_sweeps_kernel(ClusterArgs a)
         par ^= 1;
         if (hs0 + k < total) {
             __syncthreads();     // own rows final for this phase
-            push(par);
+            push(par, phase + 1);
         }
         // the next phase's halos have arrived; the slots the next pushes write
         // were read at the start of this phase; after the last phase: no block
@@ -363,20 +400,31 @@ size_t cl_smem_bytes(const Geom& g, int blocks, int k, int q)
     return ((size_t)(2 + q) * (smax + 2 * k) + 8 * (size_t)k) * g.P * sizeof(uint64_t);
 }
 
-// The six forms of the kernel: 1, 2 or 4 words per thread, 2 or kClMaxSlabs mask slabs.
+// The forms of the kernel: 1 .. 4 words per thread, 2 or kClMaxSlabs mask
+// slabs, one cluster or several.
 using ClusterKernel = void (*)(ClusterArgs);
-constexpr ClusterKernel kClusterKernels[8] = {
-    cluster_sweeps_kernel<1, false>, cluster_sweeps_kernel<2, false>, cluster_sweeps_kernel<3, false>, cluster_sweeps_kernel<4, false>,
-    cluster_sweeps_kernel<1, true>,  cluster_sweeps_kernel<2, true>,  cluster_sweeps_kernel<3, true>,  cluster_sweeps_kernel<4, true>};
+constexpr ClusterKernel kClusterKernels[16] = {
+    cluster_sweeps_kernel<1, false, false>, cluster_sweeps_kernel<2, false, false>,
+    cluster_sweeps_kernel<3, false, false>, cluster_sweeps_kernel<4, false, false>,
+    cluster_sweeps_kernel<1, true, false>,  cluster_sweeps_kernel<2, true, false>,
+    cluster_sweeps_kernel<3, true, false>,  cluster_sweeps_kernel<4, true, false>,
+    cluster_sweeps_kernel<1, false, true>,  cluster_sweeps_kernel<2, false, true>,
+    cluster_sweeps_kernel<3, false, true>,  cluster_sweeps_kernel<4, false, true>,
+    cluster_sweeps_kernel<1, true, true>,   cluster_sweeps_kernel<2, true, true>,
+    cluster_sweeps_kernel<3, true, true>,   cluster_sweeps_kernel<4, true, true>};
 
-ClusterKernel cluster_kernel(int ns, int q)
+ClusterKernel cluster_kernel(int ns, int q, bool multi)
 {
-    return kClusterKernels[(q == kClMaxSlabs ? 4 : 0) + (ns - 1)];
+    return kClusterKernels[(multi ? 8 : 0) + (q == kClMaxSlabs ? 4 : 0) + (ns - 1)];
 }
 
 // Window words a block takes with at most `ns` words per thread: 1024
 // threads for 1, 2 or 4 (64 registers each), 768 for 3 (80 registers).
 long long max_words(int ns) { return ns == 3 ? 3 * 768 : (long long)ns * kClThreads; }
+
+// Clusters of the largest size that can be resident at once (set by
+// probe_max_cluster).
+int g_max_active = 0;
 
 int probe_max_cluster()
 {
@@ -400,12 +448,17 @@ int probe_max_cluster()
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         bool ok = true;
-        for (int i = 0; i < 8; ++i) {                 // form i: (i % 4) + 1 words per thread
+        int active = 1 << 30;
+        for (int i = 0; i < 16; ++i) {                // form i: (i % 4) + 1 words per thread
             cfg.blockDim = dim3(i % 4 == 2 ? 768 : kClThreads);
             int nc = 0;
             ok = ok && cudaOccupancyMaxActiveClusters(&nc, kClusterKernels[i], &cfg) == cudaSuccess && nc >= 1;
+            active = std::min(active, nc);
         }
-        if (ok) return c;
+        if (ok) {
+            g_max_active = active;
+            return c;
+        }
         cudaGetLastError();
     }
     return 0;
@@ -427,17 +480,23 @@ int probe_max_cluster()
 // (k = 6) against 367 (k = 2); 4 words per thread spill registers (L = 1200:
 // 297).  Returns false if no such launch exists (a lattice too large or too
 // small).
-bool cluster_plan(const Geom& g, ClusterPlan* plan)
+int cluster_max_active()
 {
     static const int max_cluster = probe_max_cluster();   // per process, set once
-    if (max_cluster == 0) return false;
-    const int c = max_cluster;
-    const int fewest = g.L / c;
+    return max_cluster == 0 ? 0 : g_max_active;
+}
+
+bool cluster_plan(const Geom& g, int clusters, ClusterPlan* plan)
+{
+    static const int max_cluster = probe_max_cluster();   // per process, set once
+    if (max_cluster == 0 || clusters < 1 || clusters > g_max_active) return false;
+    const int c = max_cluster, nb = clusters * c;         // cluster size, blocks of the launch
+    const int fewest = g.L / nb;
     for (int most : {3, 4}) {
         for (int q : {kClMaxSlabs, 2}) {
             for (int kk = std::min(kClHalo, fewest) & ~1; kk >= 2; kk -= 2) {
-                if (cl_smem_bytes(g, c, kk, q) > kClSmemMax) continue;
-                const long long words = (long long)((g.L + c - 1) / c + 2 * kk - 2) * g.P;
+                if (cl_smem_bytes(g, nb, kk, q) > kClSmemMax) continue;
+                const long long words = (long long)((g.L + nb - 1) / nb + 2 * kk - 2) * g.P;
                 if (words > max_words(most)) continue;
                 const int ns = words <= kClThreads ? 1 : (words <= 2 * kClThreads ? 2 : (words <= max_words(3) ? 3 : 4));
                 plan->blocks = c;
@@ -445,11 +504,22 @@ bool cluster_plan(const Geom& g, ClusterPlan* plan)
                 plan->q = q;
                 plan->ns = ns;
                 plan->threads = (int)(((words + ns - 1) / ns + 31) / 32 * 32);
+                plan->clusters = clusters;
                 return true;
             }
         }
     }
     return false;
+}
+
+size_t cl_exchange_words(const Geom& g, const ClusterPlan& plan)
+{
+    return (size_t)plan.clusters * 2 * 2 * 2 * plan.k * g.P;     // [boundary][dir][parity][colour] k x P
+}
+
+unsigned long long cl_exchange_seqs(const ClusterPlan& plan, int nsweeps)
+{
+    return (unsigned long long)((2 * nsweeps + plan.k - 1) / plan.k) + 1;   // pushes of a launch, + 1
 }
 
 size_t cl_mask_bytes_per_sweep(const Geom& g) { return 2 * (size_t)g.L * g.P * sizeof(uint64_t); }
@@ -473,8 +543,9 @@ cudaError_t launch_cl_mask_draw(const Geom& g, const SweepArgs& a, const uint64_
 
 cudaError_t launch_cluster_sweeps(uint64_t* w0, uint64_t* w1, const Geom& g, const SweepArgs& a,
                                   const ClusterPlan& plan, int nsweeps, const uint64_t* masks, int64_t s0,
-                                  int64_t every, cudaStream_t s)
+                                  int64_t every, const ClusterExchange& x, cudaStream_t s)
 {
+    const int nb = plan.clusters * plan.blocks;
     ClusterArgs ca;
     ca.w[0] = w0;
     ca.w[1] = w1;
@@ -482,17 +553,23 @@ cudaError_t launch_cluster_sweeps(uint64_t* w0, uint64_t* w1, const Geom& g, con
     ca.k = plan.k;
     ca.q = plan.q;
     ca.nsweeps = nsweeps;
-    ca.rmax = (g.L + plan.blocks - 1) / plan.blocks + 2 * plan.k;
+    ca.rmax = (g.L + nb - 1) / nb + 2 * plan.k;
     ca.masks = masks;
     ca.s0 = s0;
     ca.every = every;
     ca.counts = a.counts;
     ca.all0 = a.all0;
     ca.all1 = a.all1;
+    ca.G = plan.clusters;
+    ca.xbuf = x.buf;
+    ca.xflag = x.flags;
+    ca.xseq = x.seq;
+    ca.xerr = x.err;
+    if (plan.clusters > 1 && (!x.buf || !x.flags || !x.err)) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(plan.blocks);
+    cfg.gridDim = dim3(nb);
     cfg.blockDim = dim3(plan.threads);
-    cfg.dynamicSmemBytes = cl_smem_bytes(g, plan.blocks, plan.k, plan.q);
+    cfg.dynamicSmemBytes = cl_smem_bytes(g, nb, plan.k, plan.q);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -501,7 +578,7 @@ cudaError_t launch_cluster_sweeps(uint64_t* w0, uint64_t* w1, const Geom& g, con
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, cluster_kernel(plan.ns, plan.q), ca);
+    return cudaLaunchKernelEx(&cfg, cluster_kernel(plan.ns, plan.q, plan.clusters > 1), ca);
 }
 
 }  // namespace ising

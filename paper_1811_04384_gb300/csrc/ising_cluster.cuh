@@ -1,6 +1,6 @@
 // Helpers of the cluster kernels (ising_cluster.cu, ising_ci_cluster.cu):
 // asynchronous 16-byte copies into shared memory, with a range-checked form
-// for the checked build.
+// for the checked build, and the flags of the exchanges between clusters.
 #pragma once
 #include <cstdint>
 
@@ -43,6 +43,50 @@ template <int N>
 __device__ __forceinline__ void cl_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ int wrap_index(int i, int L) { return i < 0 ? i + L : (i >= L ? i - L : i); }
+
+// Sequence flags of the exchanges between clusters (global memory).  The
+// writer stores the rows, fences, passes a block barrier, and one thread
+// stores the flag with release semantics; the reader's one thread waits for
+// it with acquire loads, the block passes a barrier, and its threads read the
+// rows past L1 (__ldcg).
+__device__ __forceinline__ void cl_flag_release(unsigned long long* f, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(f), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long cl_flag_acquire(const unsigned long long* f)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(f) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long cl_globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr unsigned long long kClWaitNs = 1000000000ull;   // a wait gives up after one second
+
+// Waits until *f >= want; gives up after kClWaitNs of the GPU's global
+// timer, records the failure in *err and returns false (the caller carries
+// on with stale rows: the launch ends, its result is void, and the host
+// reports the error).
+__device__ __forceinline__ bool cl_wait_flag(const unsigned long long* f, unsigned long long want,
+                                             unsigned int* err)
+{
+    const unsigned long long t0 = cl_globaltimer();
+    while (cl_flag_acquire(f) < want) {
+        if (cl_globaltimer() - t0 > kClWaitNs) {
+            atomicExch(err, 1u);
+            return false;
+        }
+        __nanosleep(100);
+    }
+    return true;
+}
 
 }  // namespace
 }  // namespace ising

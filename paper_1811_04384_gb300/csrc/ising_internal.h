@@ -95,16 +95,31 @@ struct ClusterPlan {
     int blocks;     // cluster size
     int k;          // half-sweeps per phase = halo rows
     int q;          // mask slabs in shared memory
-    int ns;         // window words per thread: 1, 2 or 4
+    int ns;         // window words per thread: 1 .. 4
     int threads;    // threads per block
+    int clusters;   // clusters of a launch (1: the halos never leave the cluster)
 };
-bool cluster_plan(const Geom& g, ClusterPlan* plan);
+// The rows crossing between the clusters of a launch (clusters > 1): `buf`
+// holds cl_exchange_words(g, plan) words, `flags` 2 per cluster (zero when
+// allocated, then only ever raised), `seq` the flag base of the launch (the
+// caller adds cl_exchange_seqs(plan, nsweeps) after each launch), `err` a
+// word set to 1 when a wait gave up.
+struct ClusterExchange {
+    uint64_t* buf;
+    unsigned long long* flags;
+    unsigned long long seq;
+    unsigned int* err;
+};
+bool cluster_plan(const Geom& g, int clusters, ClusterPlan* plan);
+int cluster_max_active();   // clusters of one launch that can be resident at once (0: none)
+size_t cl_exchange_words(const Geom& g, const ClusterPlan& plan);
+unsigned long long cl_exchange_seqs(const ClusterPlan& plan, int nsweeps);
 size_t cl_mask_bytes_per_sweep(const Geom& g);
 cudaError_t launch_cl_mask_draw(const Geom& g, const SweepArgs& a, const uint64_t* t_base, uint64_t t0, int nsweeps,
                                 uint64_t* masks, bool overlap, cudaStream_t s);
 cudaError_t launch_cluster_sweeps(uint64_t* w0, uint64_t* w1, const Geom& g, const SweepArgs& a,
                                   const ClusterPlan& plan, int nsweeps, const uint64_t* masks, int64_t s0,
-                                  int64_t every, cudaStream_t s);
+                                  int64_t every, const ClusterExchange& x, cudaStream_t s);
 
 // Launch `kernel` with programmatic stream serialization (the kernel calls
 // pdl_enter before its first read): the next launch's setup overlaps the end

@@ -78,6 +78,12 @@ struct ising_lattice {
     ulonglong2* graph_masks = nullptr;           // two buffers of draw_sweeps() sweeps' masks, drawn inside the graphs
     cudaStream_t draw_stream = nullptr;          // the graphs' mask draws are captured here, beside the half-sweeps
     cudaEvent_t fork_ev = nullptr, draw_ev[64] = {}, apply_ev[64] = {};   // kMaxPieces each
+    int clusters = 0;                            // clusters of the cluster path's launches (0: automatic)
+    uint64_t* xbuf = nullptr;                    // rows between clusters (lazily, several clusters only)
+    size_t xbuf_bytes = 0;
+    unsigned long long* xflag = nullptr;         // their flags (2 per cluster, at most 16 clusters) and the error word
+    unsigned long long xseq = 0;                 // flag base of the next launch
+    unsigned int* host_xerr = nullptr;           // pinned copy of the error word
 };
 
 static void drop_graphs(ising_lattice* h);
@@ -130,6 +136,9 @@ static void free_handle(ising_lattice* h)
     if (h->staging2) cudaFree(h->staging2);
     if (h->masks) cudaFree(h->masks);
     if (h->graph_masks) cudaFree(h->graph_masks);
+    if (h->xbuf) cudaFree(h->xbuf);
+    if (h->xflag) cudaFree(h->xflag);
+    if (h->host_xerr) cudaFreeHost(h->host_xerr);
     for (int b = 0; b < 2; ++b) {
         if (h->ev_copied[b]) cudaEventDestroy(h->ev_copied[b]);
         if (h->ev_packed[b]) cudaEventDestroy(h->ev_packed[b]);
@@ -560,7 +569,7 @@ static bool use_resident(const ising_lattice* h)
     if (items <= kResidentAutoMaxItems) return true;
     if (items > kPremaskedMaxItems) return false;
     ClusterPlan cp;
-    return !cluster_plan(h->g, &cp);
+    return !cluster_plan(h->g, 1, &cp);
 }
 
 // Pre-drawn masks of the on-chip path: 64 B per item and sweep, drawn for
@@ -616,40 +625,67 @@ static int run_resident(ising_lattice* h, int n, int every)
 }
 
 // ---- Cluster path (mid-size lattices)
-// Above the on-chip range and up to kClusterMaxL, one thread-block cluster
-// keeps the lattice in its blocks' shared memory over a whole piece of sweeps
-// (cluster_sweeps_kernel).  The masks of each piece are drawn on all SMs
-// into one of two buffers: the draw of piece j + 1 follows the cluster launch
-// of piece j in the stream with programmatic stream serialization, so it
-// runs on the SMs the cluster leaves free while piece j is applied, and
-// writes the buffer piece j - 1 read (complete before piece j started).
-// Replayed graphs of short half-sweeps stay for the launch path
-// (ISING_PATH_LAUNCHES) and for larger lattices.  Measured on GB300, sweeps
-// without records, spin-updates/ns, cluster against graphs: L = 296: 138 /
-// 34; L = 512: 255 / 96; L = 700: 328 / 170; L = 1008: 472 / 313; L = 1080:
-// 478 / 342; L = 1150: 499 / 362; but L = 1200: 297 / 368, where the window
-// needs 4 words per thread, which spill registers (up to L = 1176 3 words
-// per thread allow phases of 4 half-sweeps or more).  Two 16 MB mask buffers
-// (43-sweep pieces at L = 1008) gave 444 there: each launch loads and writes
-// back the lattice and refills the mask ring.  In the column-interleaved
-// layout: L = 1008: 373 / 304; L = 1092: 403 / 338.
-constexpr int kClusterMaxL = 1176;
+// Above the on-chip range and up to kClusterMaxL, thread-block clusters keep
+// the lattice in their blocks' shared memory over a whole piece of sweeps
+// (cluster_sweeps_kernel): one cluster, or several (auto_clusters) whose
+// boundary blocks pass their halo rows through a small global buffer.  The
+// masks of each piece are drawn on all SMs into one of two buffers: the draw
+// of piece j + 1 follows the cluster launch of piece j in the stream with
+// programmatic stream serialization, so it runs on the SMs the clusters leave
+// free while piece j is applied, and writes the buffer piece j - 1 read
+// (complete before piece j started).  Replayed graphs of short half-sweeps
+// stay for the launch path (ISING_PATH_LAUNCHES) and, above kClusterMaxL,
+// the fused half-sweeps.  With one cluster (before several), sweeps without
+// records, spin-updates/ns, cluster against graphs: L = 296: 138 / 34;
+// L = 512: 255 / 96; L = 1008: 472 / 313; L = 1150: 499 / 362; but L = 1200:
+// 297 / 368, where the window needs 4 words per thread, which spill
+// registers.  Two 16 MB mask buffers (43-sweep pieces at L = 1008) gave 444
+// there: each launch loads and writes back the lattice and refills the mask
+// ring.  In the column-interleaved layout (one cluster): L = 1008: 373 /
+// 304; L = 1092: 403 / 338.
+constexpr int kClusterMaxL = 3000;
 constexpr int kCiClusterMaxL = 1092;               // the column-interleaved layout (L % 84 == 0)
 constexpr size_t kClusterMaskBytes = 128u << 20;   // both buffers
 constexpr int kClusterMaxPiece = 256;
 
-static bool plan_cluster(const ising_lattice* h, ClusterPlan* plan)
+// Clusters of a launch on the automatic path for side L (0: not the cluster
+// path).  Measured on GB300, sweeps without records, spin-updates/ns by
+// clusters 1 .. 7 (graph replays): L = 296: 124 / 86 / 73 / 55 / 29 / 28 / 27
+// (34); L = 700: 302 / 352 / 383 / 381 / 347 / 300 / 300 (173); L = 1008:
+// 439 / 506 / 552 / 667 / 638 / 626 / 598 (311); L = 1300: 240 / 651 / 717 /
+// 739 / 767 / 773 / 723 (399); L = 1500: 409 / 771 / 922 / 904 / 943 / 904 /
+// 880 (539); L = 2016: - / 657 / 993 / 1009 / 982 / 946 / 918 (742);
+// L = 3000: four clusters 980 (939); L = 4096: seven 954 against the fused
+// launches' 1031.  More clusters leave fewer SMs for the mask draws.
+static int auto_clusters(int L)
 {
-    return h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED ? ci_cluster_plan(h->g.L, plan) : cluster_plan(h->g, plan);
+    constexpr struct { int max_L, clusters; } kRule[] = {
+        {558, 1}, {898, 3}, {1098, 4}, {1448, 6}, {1698, 5}, {kClusterMaxL, 4}};
+    for (const auto& r : kRule)
+        if (L <= r.max_L) return r.clusters;
+    return 0;
+}
+
+// The cluster-path launch for h: the clusters set by ising_set_clusters, else
+// the automatic count; `forced` (ISING_PATH_CLUSTER) first tries one
+// cluster at any size.
+static bool plan_cluster(const ising_lattice* h, ClusterPlan* plan, bool forced)
+{
+    if (h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED) return h->clusters <= 1 && ci_cluster_plan(h->g.L, plan);
+    if (h->clusters > 0) return cluster_plan(h->g, h->clusters, plan);
+    const int G = auto_clusters(h->g.L);
+    if (G > 0 && cluster_plan(h->g, G, plan)) return true;
+    return forced && cluster_plan(h->g, 1, plan);
 }
 
 static bool use_cluster(const ising_lattice* h, ClusterPlan* plan)
 {
     if (h->chain != ISING_CHAIN_CHECKERBOARD) return false;
-    if (h->path == ISING_PATH_CLUSTER) return plan_cluster(h, plan);
+    if (h->path == ISING_PATH_CLUSTER) return plan_cluster(h, plan, true);
     if (h->path != ISING_PATH_AUTO || use_resident(h)) return false;
-    if (h->g.L > (h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED ? kCiClusterMaxL : kClusterMaxL)) return false;
-    return plan_cluster(h, plan);
+    if (h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED && h->g.L > kCiClusterMaxL) return false;
+    if (h->layout == ISING_LAYOUT_ROW_PACKED && h->clusters == 0 && auto_clusters(h->g.L) == 0) return false;
+    return plan_cluster(h, plan, false);
 }
 
 // n sweeps on the cluster path; every > 0: after every `every`-th sweep s of
@@ -686,13 +722,38 @@ static int run_cluster(ising_lattice* h, int64_t n, int64_t every, unsigned long
         cudaError_t e = draw(0, false);
         if (e != cudaSuccess) return cuda_fail(e, "cluster mask draw");
     }
+    ClusterExchange x = {nullptr, nullptr, 0, nullptr};
+    if (plan.clusters > 1) {
+        const size_t xb = cl_exchange_words(g, plan) * sizeof(uint64_t);
+        cudaError_t e = cudaSuccess;
+        if (h->xbuf_bytes < xb) {
+            if (h->xbuf) cudaFree(h->xbuf);
+            h->xbuf = nullptr;
+            h->xbuf_bytes = 0;
+            e = cudaMalloc(&h->xbuf, xb);
+            if (e != cudaSuccess) { h->xbuf = nullptr; cuda_fail(e, "cudaMalloc exchange"); return ISING_ENOMEM; }
+            h->xbuf_bytes = xb;
+        }
+        if (!h->xflag) {
+            e = cudaMalloc(&h->xflag, (2 * 16 + 1) * sizeof(unsigned long long));
+            if (e == cudaSuccess) e = cudaMemsetAsync(h->xflag, 0, (2 * 16 + 1) * sizeof(unsigned long long), h->stream);
+            if (e == cudaSuccess && !h->host_xerr) e = cudaMallocHost(&h->host_xerr, sizeof(unsigned int));
+            if (e != cudaSuccess) { cuda_fail(e, "exchange flags"); return ISING_ENOMEM; }
+            h->xseq = 0;
+        }
+        x = {h->xbuf, h->xflag, h->xseq, reinterpret_cast<unsigned int*>(h->xflag + 2 * 16)};
+    }
     for (int64_t j = 0; j < np; ++j) {
         const int64_t done = j * max_piece;
         cudaError_t e = ci ? ci_cluster_sweeps(h->words[0], g.L, a, plan, part_of(j), masks[j & 1], done, every,
                                                h->stream)
                            : launch_cluster_sweeps(h->words[0], h->words[1], g, a, plan, part_of(j), masks[j & 1],
-                                                   done, every, h->stream);
+                                                   done, every, x, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "cluster sweeps kernel");
+        if (plan.clusters > 1) {
+            x.seq += cl_exchange_seqs(plan, part_of(j));
+            h->xseq = x.seq;
+        }
         if (j + 1 < np) {
             e = draw(j + 1, true);
             if (e != cudaSuccess) return cuda_fail(e, "cluster mask draw");
@@ -703,6 +764,28 @@ static int run_cluster(ising_lattice* h, int64_t n, int64_t every, unsigned long
         if (e != cudaSuccess) return cuda_fail(e, "advance_sweep_kernel");
         h->t += (uint64_t)n;
     }
+    if (plan.clusters > 1) {
+        // a wait between clusters that gave up voids the sweeps (the counter
+        // has advanced; the caller restores a checkpoint to retry)
+        cudaError_t e = cudaMemcpyAsync(h->host_xerr, x.err, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cluster exchange status");
+        if (*h->host_xerr != 0) {
+            cudaMemsetAsync(x.err, 0, sizeof(unsigned int), h->stream);
+            *h->host_xerr = 0;
+            return ISING_ETIMEOUT;
+        }
+    }
+    return ISING_OK;
+}
+
+extern "C" int ising_set_clusters(ising_lattice* h, int32_t clusters)
+{
+    if (!h || clusters < 0 || clusters > 16) return ISING_EINVAL;
+    ClusterPlan cp;
+    if (clusters > 0 && (h->layout != ISING_LAYOUT_ROW_PACKED ? clusters != 1 : !cluster_plan(h->g, clusters, &cp)))
+        return ISING_EINVAL;
+    h->clusters = clusters;
     return ISING_OK;
 }
 
@@ -725,7 +808,7 @@ extern "C" int ising_set_path(ising_lattice* h, int32_t path)
     if (path == ISING_PATH_RESIDENT && (h->layout != ISING_LAYOUT_ROW_PACKED || resident_bytes(h->g) > kResidentMaxBytes))
         return ISING_EINVAL;
     ClusterPlan cp;
-    if (path == ISING_PATH_CLUSTER && !plan_cluster(h, &cp)) return ISING_EINVAL;
+    if (path == ISING_PATH_CLUSTER && !plan_cluster(h, &cp, true)) return ISING_EINVAL;
     h->path = path;
     return ISING_OK;
 }

@@ -4,10 +4,11 @@ in the row-packed layout and in the paper's column-interleaved layout,
 against the oracle, bit-exact: int64 E/M series and final spins.
 
 Cases span two rows per block (L = 32, two half-sweeps per phase), the
-automatic range (L = 296 just above the on-chip path, with two mask pieces,
-up to L = 1176), L % 4 == 2, records out of step with the phases and pieces,
-odd numbers of half-sweeps per call, forced runs up to the largest side
-(L = 1600), cold starts, beta = 0 (every flip accepted) and a frozen
+automatic range with one cluster (L = 296 just above the on-chip path, with
+two mask pieces) and with several (their halos between clusters through
+global memory), L % 4 == 2, records out of step with the phases and pieces,
+odd numbers of half-sweeps per call, cold starts, beta = 0 (every flip
+accepted) and a frozen
 lattice, runs continued across calls and paths, and ising_run_states.
 """
 import numpy as np
@@ -36,10 +37,10 @@ CASES = [
     (296, 300, 7, 0.41, False),    # two mask pieces (256 + 44 sweeps), records across them
     (514, 20, 3, 0.3, False),      # L % 4 == 2; 6 records, out of step with the phases
     (1008, 24, 4, 0.44, False),    # the paper's L = 1008
-    (1080, 60, 5, BETA_TC, False), # three words per thread, phases of 10
-    (1176, 8, 2, 0.44, False),     # largest automatic side: phases of 4
-    (1500, 6, 1, 0.44, True),      # phases of 10 half-sweeps, 4 words per thread
-    (1600, 3, 1, BETA_TC, True),   # largest side with a plan: 4 words per thread
+    (1080, 60, 5, BETA_TC, False), # four clusters
+    (1176, 8, 2, 0.44, False),     # six clusters
+    (1500, 6, 1, 0.44, True),      # five clusters
+    (1600, 3, 1, BETA_TC, True),   # five clusters
 ]
 
 
@@ -127,6 +128,64 @@ def test_interleaved_cluster_extremes_and_continuation(ising):
         np.testing.assert_array_equal(got, want)
 
 
+# several clusters per launch, halos between clusters through global memory:
+# (L, clusters, sweeps, every)
+MULTI_CASES = [
+    (600, 2, 26, 3),     # 32 blocks of 18-19 rows
+    (1000, 3, 14, 2),    # 48 blocks
+    (1600, 2, 8, 4),     # 50 rows per block
+    (2016, 3, 6, 1),     # the paper's L = 2016
+    (3000, 5, 3, 1),     # 80 blocks
+]
+
+
+def test_multi_cluster_matches_oracle(ising):
+    got = []
+    for L, G, n, every in MULTI_CASES:
+        with ising.Lattice(L, L + 11) as lat:
+            lat.set_clusters(G)
+            assert lat.get_path() == ising.ISING_PATH_CLUSTER, (L, G)
+            lat.init_hot()
+            lat.set_beta(0.42)
+            E, M = lat.sweep_record(n, every)
+            got.append((E, M, lat.get_spins()))
+    ora = oracle.run_jobs([(L, L + 11, 0.42, True, n, every) for L, G, n, every in MULTI_CASES])
+    for (E, M, S), (Eo, Mo, So), case in zip(got, ora, MULTI_CASES):
+        np.testing.assert_array_equal(E, Eo, err_msg=str(case))
+        np.testing.assert_array_equal(M, Mo, err_msg=str(case))
+        np.testing.assert_array_equal(S, So, err_msg=str(case))
+
+
+def test_multi_cluster_continued_and_rejected(ising):
+    """Calls continued with 2, then 3 clusters, then 1 (the exchange flags
+    only ever rise across launches), and the counts a lattice rejects."""
+    L, seed, beta = 900, 17, 0.44
+    with ising.Lattice(L, seed) as lat:
+        lat.init_hot()
+        lat.set_beta(beta)
+        lat.set_clusters(2)
+        lat.sweep(5)
+        E1, M1 = lat.sweep_record(7, 1)
+        lat.set_clusters(3)
+        E2, M2 = lat.sweep_record(8, 2)
+        lat.set_clusters(1)
+        E3, M3 = lat.sweep_record(3, 3)
+        S = lat.get_spins()
+        for bad in (-1, 17, 16):
+            with pytest.raises(ising.IsingError):
+                lat.set_clusters(bad)
+    s = oracle.init_hot(L, seed)
+    oracle.run(s, seed, beta, 0, 5, 5)
+    for (E, M), (t0, n, every) in zip([(E1, M1), (E2, M2), (E3, M3)], [(5, 7, 1), (12, 8, 2), (20, 3, 3)]):
+        Eo, Mo = oracle.run(s, seed, beta, t0, n, every)
+        np.testing.assert_array_equal(E, Eo)
+        np.testing.assert_array_equal(M, Mo)
+    np.testing.assert_array_equal(S, s)
+    with ising.Lattice(1008, 1, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
+        with pytest.raises(ising.IsingError):
+            lat.set_clusters(2)
+
+
 def test_cluster_continued_across_calls_and_paths(ising):
     """Plain sweeps, recorded sweeps, a switch to the graph replays and back:
     the sweep counter carries the draws across the calls and paths."""
@@ -196,14 +255,16 @@ def test_cluster_run_states(ising):
 
 def test_cluster_path_choice(ising):
     """Automatic choice by size; the forced path where no plan exists is
-    rejected (too few rows per block, or a share of rows too large for a
-    block's shared memory) and leaves the path unchanged."""
+    rejected (too few rows per block; above the automatic range a share of
+    rows too large for one cluster's shared memory) and leaves the path
+    unchanged."""
     expect = {128: ising.ISING_PATH_RESIDENT, 130: ising.ISING_PATH_CLUSTER, 292: ising.ISING_PATH_CLUSTER,
-              296: ising.ISING_PATH_CLUSTER, 1176: ising.ISING_PATH_CLUSTER, 1178: ising.ISING_PATH_LAUNCHES}
+              1176: ising.ISING_PATH_CLUSTER, 2016: ising.ISING_PATH_CLUSTER, 3000: ising.ISING_PATH_CLUSTER,
+              3002: ising.ISING_PATH_LAUNCHES}
     for L, path in expect.items():
         with ising.Lattice(L, 1) as lat:
             assert lat.get_path() == path, L
-    for L in (4, 1640, 2600):
+    for L in (4, 8192):
         with ising.Lattice(L, 1) as lat:
             with pytest.raises(ising.IsingError):
                 lat.set_path(ising.ISING_PATH_CLUSTER)
