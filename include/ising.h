@@ -302,6 +302,12 @@ int ising_get_path(ising_lattice *h, int32_t *path);
  * or 1 on a column-interleaved lattice.  Results do not depend on it. */
 int ising_set_clusters(ising_lattice *h, int32_t clusters);
 
+/* Test hook of that wait: the next `launches` cluster-path launches with
+ * several clusters wait for flag values no push reaches, so every wait
+ * between clusters gives up after its second and the call returns
+ * ISING_ETIMEOUT (the GPU keeps running; nothing traps).  0 clears it. */
+int ising_cluster_inject_stall(ising_lattice *h, int32_t launches);
+
 /* Which Markov chain ising_sweep and ising_sweep_record run.
  * ISING_CHAIN_CHECKERBOARD (default): the checkerboard sweeps of the
  * conventions above (nstrips ignored).  ISING_CHAIN_RANDOM_WORDS: the paper's

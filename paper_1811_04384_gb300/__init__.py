@@ -205,6 +205,10 @@ class Lattice:
         """Clusters of one cluster-path launch (ising_set_clusters): 0 = automatic."""
         _check(load().ising_set_clusters(self._h, int(clusters)), "ising_set_clusters")
 
+    def inject_stall(self, launches: int = 1):
+        """Test hook (ising_cluster_inject_stall): the next launches' waits between clusters give up."""
+        _check(load().ising_cluster_inject_stall(self._h, int(launches)), "ising_cluster_inject_stall")
+
     def get_path(self) -> int:
         """The path the next sweeps take (ising_get_path): ISING_PATH_RESIDENT,
         ISING_PATH_CLUSTER or ISING_PATH_LAUNCHES."""

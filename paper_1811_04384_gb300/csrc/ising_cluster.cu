@@ -66,6 +66,7 @@ struct ClusterArgs {
     uint64_t* xbuf;             // G > 1: halo rows between clusters, [boundary][dir][parity][colour], k x P words
     unsigned long long* xflag;  // G > 1: [boundary][dir] sequence flags
     unsigned long long xseq;    // push m of this launch sets its flags to xseq + m + 1
+    unsigned long long xwait;   // added to the values the receives wait for (0; a test stalls with more)
     unsigned int* xerr;         // set to 1 when a wait for a flag gives up
 };
 
@@ -269,8 +270,8 @@ cluster_sweeps_kernel(ClusterArgs a)
     auto receive = [&](int par, int p) {
         if (up_remote || dn_remote) {
             if (threadIdx.x == 0) {
-                if (up_remote) cl_wait_flag(a.xflag + bd_up * 2 + 0, a.xseq + p + 1, a.xerr);
-                if (dn_remote) cl_wait_flag(a.xflag + bd_dn * 2 + 1, a.xseq + p + 1, a.xerr);
+                if (up_remote) cl_wait_flag(a.xflag + bd_up * 2 + 0, a.xseq + a.xwait + p + 1, a.xerr);
+                if (dn_remote) cl_wait_flag(a.xflag + bd_dn * 2 + 1, a.xseq + a.xwait + p + 1, a.xerr);
             }
             __syncthreads();
         }
@@ -564,6 +565,7 @@ cudaError_t launch_cluster_sweeps(uint64_t* w0, uint64_t* w1, const Geom& g, con
     ca.xbuf = x.buf;
     ca.xflag = x.flags;
     ca.xseq = x.seq;
+    ca.xwait = x.wait_add;
     ca.xerr = x.err;
     if (plan.clusters > 1 && (!x.buf || !x.flags || !x.err)) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};

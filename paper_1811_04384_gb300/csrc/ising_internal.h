@@ -103,12 +103,14 @@ struct ClusterPlan {
 // holds cl_exchange_words(g, plan) words, `flags` 2 per cluster (zero when
 // allocated, then only ever raised), `seq` the flag base of the launch (the
 // caller adds cl_exchange_seqs(plan, nsweeps) after each launch), `err` a
-// word set to 1 when a wait gave up.
+// word set to 1 when a wait gave up, `wait_add` 0 (a test sets it to a value
+// no push reaches, so that every wait of the launch gives up).
 struct ClusterExchange {
     uint64_t* buf;
     unsigned long long* flags;
     unsigned long long seq;
     unsigned int* err;
+    unsigned long long wait_add;   // added to the flag values a launch waits for (a test hook: nonzero stalls it)
 };
 bool cluster_plan(const Geom& g, int clusters, ClusterPlan* plan);
 int cluster_max_active();   // clusters of one launch that can be resident at once (0: none)

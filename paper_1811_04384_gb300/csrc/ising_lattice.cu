@@ -84,6 +84,7 @@ struct ising_lattice {
     unsigned long long* xflag = nullptr;         // their flags (2 per cluster, at most 16 clusters) and the error word
     unsigned long long xseq = 0;                 // flag base of the next launch
     unsigned int* host_xerr = nullptr;           // pinned copy of the error word
+    int stall_launches = 0;                      // test hook: launches whose waits between clusters give up
 };
 
 static void drop_graphs(ising_lattice* h);
@@ -722,7 +723,7 @@ static int run_cluster(ising_lattice* h, int64_t n, int64_t every, unsigned long
         cudaError_t e = draw(0, false);
         if (e != cudaSuccess) return cuda_fail(e, "cluster mask draw");
     }
-    ClusterExchange x = {nullptr, nullptr, 0, nullptr};
+    ClusterExchange x = {nullptr, nullptr, 0, nullptr, 0};
     if (plan.clusters > 1) {
         const size_t xb = cl_exchange_words(g, plan) * sizeof(uint64_t);
         cudaError_t e = cudaSuccess;
@@ -741,10 +742,15 @@ static int run_cluster(ising_lattice* h, int64_t n, int64_t every, unsigned long
             if (e != cudaSuccess) { cuda_fail(e, "exchange flags"); return ISING_ENOMEM; }
             h->xseq = 0;
         }
-        x = {h->xbuf, h->xflag, h->xseq, reinterpret_cast<unsigned int*>(h->xflag + 2 * 16)};
+        x = {h->xbuf, h->xflag, h->xseq, reinterpret_cast<unsigned int*>(h->xflag + 2 * 16), 0};
     }
     for (int64_t j = 0; j < np; ++j) {
         const int64_t done = j * max_piece;
+        x.wait_add = 0;
+        if (plan.clusters > 1 && h->stall_launches > 0) {
+            --h->stall_launches;
+            x.wait_add = 1ull << 62;                 // no push reaches it: every wait gives up
+        }
         cudaError_t e = ci ? ci_cluster_sweeps(h->words[0], g.L, a, plan, part_of(j), masks[j & 1], done, every,
                                                h->stream)
                            : launch_cluster_sweeps(h->words[0], h->words[1], g, a, plan, part_of(j), masks[j & 1],
@@ -786,6 +792,13 @@ extern "C" int ising_set_clusters(ising_lattice* h, int32_t clusters)
     if (clusters > 0 && (h->layout != ISING_LAYOUT_ROW_PACKED ? clusters != 1 : !cluster_plan(h->g, clusters, &cp)))
         return ISING_EINVAL;
     h->clusters = clusters;
+    return ISING_OK;
+}
+
+extern "C" int ising_cluster_inject_stall(ising_lattice* h, int32_t launches)
+{
+    if (!h || launches < 0) return ISING_EINVAL;
+    h->stall_launches = launches;
     return ISING_OK;
 }
 

@@ -186,6 +186,34 @@ def test_multi_cluster_continued_and_rejected(ising):
             lat.set_clusters(2)
 
 
+def test_multi_cluster_wait_gives_up_and_recovers(ising):
+    """A launch whose waits between clusters can never be satisfied (the test
+    hook): each wait gives up after a second of the GPU's clock, the call
+    returns ISING_ETIMEOUT, the context stays usable, and after restoring a
+    checkpoint the run continues bit-exactly."""
+    L, seed, beta = 600, 23, 0.43
+    with ising.Lattice(L, seed) as lat:
+        lat.set_clusters(2)
+        lat.init_hot()
+        lat.set_beta(beta)
+        lat.sweep(3)
+        words, t = lat.get_words(), lat.t
+        lat.inject_stall(1)
+        with pytest.raises(ising.IsingError) as err:
+            lat.sweep(2)
+        assert err.value.code == ising.ISING_ETIMEOUT
+        lat.set_words(words)
+        lat.t = t
+        E, M = lat.sweep_record(6, 2)
+        S = lat.get_spins()
+    s = oracle.init_hot(L, seed)
+    oracle.run(s, seed, beta, 0, 3, 3)
+    Eo, Mo = oracle.run(s, seed, beta, 3, 6, 2)
+    np.testing.assert_array_equal(E, Eo)
+    np.testing.assert_array_equal(M, Mo)
+    np.testing.assert_array_equal(S, s)
+
+
 def test_cluster_continued_across_calls_and_paths(ising):
     """Plain sweeps, recorded sweeps, a switch to the graph replays and back:
     the sweep counter carries the draws across the calls and paths."""
