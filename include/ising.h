@@ -270,11 +270,15 @@ int ising_set_item_lanes(ising_lattice *h, int32_t lanes);
  * is applied, into two device buffers the library allocates on first use (up
  * to 128 MB together; 2 L pitch 8 bytes per sweep).  No spin-waits: only the
  * hardware's block and cluster barriers.
+ * Row-packed lattices may run several clusters per launch (see
+ * ising_set_clusters), which takes the path to L = 3000 and past the sizes
+ * one cluster's shared memory holds.
  * ISING_PATH_AUTO (default), row-packed: resident up to 128 thread items
- * (L <= 128), the cluster path above that up to L = 1176, the launch path
- * above that (on a device without clusters: resident up to 512 items, L <=
- * 292, then the launch path); column-interleaved: the cluster path up to
- * L = 1092, the launch path above.
+ * (L <= 128), the cluster path above that up to L = 3000 (one cluster up to
+ * L = 558, then 3 to 6 by size), the launch path above that (on a device
+ * without clusters: resident up to 512 items, L <= 292, then the launch
+ * path); column-interleaved: the cluster path (one cluster) up to L = 1092,
+ * the launch path above.
  * Results are identical on every path. */
 #define ISING_PATH_AUTO 0
 #define ISING_PATH_LAUNCHES 1
