@@ -270,15 +270,15 @@ int ising_set_item_lanes(ising_lattice *h, int32_t lanes);
  * is applied, into two device buffers the library allocates on first use (up
  * to 128 MB together; 2 L pitch 8 bytes per sweep).  No spin-waits: only the
  * hardware's block and cluster barriers.
- * Row-packed lattices may run several clusters per launch (see
- * ising_set_clusters), which takes the path to L = 3000 and past the sizes
- * one cluster's shared memory holds.
+ * Both layouts may run several clusters per launch (see
+ * ising_set_clusters), which takes the path past the sizes one cluster's
+ * shared memory holds.
  * ISING_PATH_AUTO (default), row-packed: resident up to 128 thread items
  * (L <= 128), the cluster path above that up to L = 3000 (one cluster up to
  * L = 558, then 3 to 6 by size), the launch path above that (on a device
  * without clusters: resident up to 512 items, L <= 292, then the launch
- * path); column-interleaved: the cluster path (one cluster) up to L = 1092,
- * the launch path above.
+ * path); column-interleaved: the cluster path up to L = 2604 (one cluster up
+ * to L = 840, then 3 to 5), the launch path above.
  * Results are identical on every path. */
 #define ISING_PATH_AUTO 0
 #define ISING_PATH_LAUNCHES 1
@@ -291,7 +291,7 @@ int ising_set_path(ising_lattice *h, int32_t path);
  * ISING_PATH_LAUNCHES; with the random-word chain, the path last set). */
 int ising_get_path(ising_lattice *h, int32_t *path);
 
-/* Clusters of one cluster-path launch (row-packed lattices): 0 = automatic
+/* Clusters of one cluster-path launch: 0 = automatic
  * (the default), 1 .. 16 = that many thread-block clusters whose blocks own
  * consecutive row bands.  Inside a cluster the halo rows travel through
  * distributed shared memory; between clusters the two boundary blocks pass
@@ -302,8 +302,9 @@ int ising_get_path(ising_lattice *h, int32_t *path);
  * ISING_ETIMEOUT, the sweeps it ran are void, and the sweep counter has
  * advanced (restore a checkpoint with ising_set_words / ising_set_sweep to
  * retry).  A number of clusters the device cannot hold at once, or for which
- * the lattice has no window plan, gives EINVAL; so does a count other than 0
- * or 1 on a column-interleaved lattice.  Results do not depend on it. */
+ * the lattice has no window plan, gives EINVAL.  Column-interleaved lattices
+ * split their word columns the same way (k halo columns of all word rows
+ * between clusters).  Results do not depend on it. */
 int ising_set_clusters(ising_lattice *h, int32_t clusters);
 
 /* Test hook of that wait: the next `launches` cluster-path launches with

@@ -56,6 +56,12 @@ struct CiClusterArgs {
     int64_t s0;                 // the launch runs sweeps s0 + 1 .. s0 + nsweeps of the call
     int64_t every;              // record after sweeps s with s % every == 0 (0: none)
     unsigned long long* counts; // count slots (32 per record); record r of the call -> slot r
+    int G;                      // clusters of the launch: blocks g C .. g C + C - 1 form cluster g
+    uint64_t* xbuf;             // G > 1: halo columns between clusters, [boundary][dir][parity][array], N x k/2 words
+    unsigned long long* xflag;  // G > 1: [boundary][dir] sequence flags
+    unsigned long long xseq;    // push m of this launch sets its flags to xseq + m + 1
+    unsigned long long xwait;   // added to the values the receives wait for (0; a test stalls with more)
+    unsigned int* xerr;         // set to 1 when a wait for a flag gives up
 };
 
 // First word column of block b of a cluster of C: a multiple of 4.
@@ -131,8 +137,10 @@ __device__ __forceinline__ void ci_cl_half_sweep(uint64_t* E, const uint64_t* ms
     if (RECORD) block_add_counts(counts + 2 * (blockIdx.x % kCountSlots), anti, up);
 }
 
-// NS: window pairs per thread; DEEP: kCiMaxSlabs mask slabs, else 2.
-template <int NS, bool DEEP>
+// NS: window pairs per thread; DEEP: kCiMaxSlabs mask slabs, else 2;
+// MULTI: several clusters, whose boundary blocks pass their halo columns
+// through global memory (as in cluster_sweeps_kernel).
+template <int NS, bool DEEP, bool MULTI>
 __global__ void __launch_bounds__(NS == 3 ? 768 : kCiThreads, 1)
 ci_cluster_sweeps_kernel(CiClusterArgs a)
 {
@@ -146,8 +154,15 @@ ci_cluster_sweeps_kernel(CiClusterArgs a)
     const int T = blockDim.x;
     const int C = (int)cluster.num_blocks(), b = (int)cluster.block_rank();
     const int L = a.L, N = a.N, k = a.k, kh = k / 2, PL = L / 2;
-    const int c0 = ci_col0(b, C, L), S = ci_col0(b + 1, C, L) - c0;    // own columns
-    const int bp = (b + C - 1) % C, bn = (b + 1) % C;                  // left and right blocks
+    // the launch's G C blocks own consecutive column bands: block B = gc C + b
+    const int G = a.G, gc = (int)blockIdx.x / C, NB = G * C, B = gc * C + b;
+    const int c0 = ci_col0(B, NB, L), S = ci_col0(B + 1, NB, L) - c0;  // own columns
+    const int bp = (b + C - 1) % C, bn = (b + 1) % C;                  // left and right blocks in the cluster
+    // with G > 1 a cluster's first block takes its left halo from the last
+    // block of the cluster to its left (boundary bd_l, global memory), its
+    // last block the right halo from the first block of the next cluster
+    const bool l_remote = MULTI && b == 0, r_remote = MULTI && b == C - 1;
+    const int bd_l = (gc + G - 1) % G, bd_r = gc;
     const int Wn = S + 2 * k, Wp = Wn / 2;                               // window columns and pairs
     const uint32_t wpm = (uint32_t)a.wpm;
     const uint64_t nw = (uint64_t)N * wpm;                              // words of E, O, a slab
@@ -207,30 +222,54 @@ ci_cluster_sweeps_kernel(CiClusterArgs a)
     // a block's first k own columns (pairs kh .. k - 1) go to the right-halo
     // slots of the left block, its last k (pairs S/2 .. S/2 + kh - 1) to the
     // left-halo slots of the right block
-    auto push = [&](int par) {
-        uint64_t* to_left = cluster.map_shared_rank(recv, bp);
-        uint64_t* to_right = cluster.map_shared_rank(recv, bn);
+    // the global slots between clusters: dir 0 carries the last k own columns
+    // of cluster bd's last block right to the first block of cluster bd + 1,
+    // dir 1 the first k own columns of that block left
+    auto xs = [&](int bd, int dir, int par, int arr) {
+        return a.xbuf + (size_t)(((bd * 2 + dir) * 2 + par) * 2 + arr) * slotw;
+    };
+    // push m (m = 0 before the first phase, m = p + 1 after phase p)
+    auto push = [&](int par, int m) {
+        uint64_t* to_left = l_remote ? nullptr : cluster.map_shared_rank(recv, bp);
+        uint64_t* to_right = r_remote ? nullptr : cluster.map_shared_rank(recv, bn);
         for (int arr = 0; arr < 2; ++arr) {
             const uint64_t* A = E + (size_t)arr * nw;
-            uint64_t* dl = rs(to_left, par, 1, arr);
-            uint64_t* dr = rs(to_right, par, 0, arr);
+            uint64_t* dl = l_remote ? xs(bd_l, 1, par, arr) : rs(to_left, par, 1, arr);
+            uint64_t* dr = r_remote ? xs(bd_r, 0, par, arr) : rs(to_right, par, 0, arr);
             for (int idx = threadIdx.x; idx < slotw; idx += T) {
                 const int I = idx / kh, x = idx - I * kh;
                 word_st(dl, idx, word_ld<false>(A, (uint64_t)I * wpm + kh + x, nw, __LINE__), slotw, __LINE__);
                 word_st(dr, idx, word_ld<false>(A, (uint64_t)I * wpm + S / 2 + x, nw, __LINE__), slotw, __LINE__);
             }
         }
+        if (l_remote || r_remote) {
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (l_remote) cl_flag_release(a.xflag + bd_l * 2 + 1, a.xseq + m + 1);
+                if (r_remote) cl_flag_release(a.xflag + bd_r * 2 + 0, a.xseq + m + 1);
+            }
+        }
     };
-    auto receive = [&](int par) {
+    // the halos of phase p (push p of the neighbours)
+    auto receive = [&](int par, int p) {
+        if (l_remote || r_remote) {
+            if (threadIdx.x == 0) {
+                if (l_remote) cl_wait_flag(a.xflag + bd_l * 2 + 0, a.xseq + a.xwait + p + 1, a.xerr);
+                if (r_remote) cl_wait_flag(a.xflag + bd_r * 2 + 1, a.xseq + a.xwait + p + 1, a.xerr);
+            }
+            __syncthreads();
+        }
         for (int arr = 0; arr < 2; ++arr) {
             uint64_t* A = E + (size_t)arr * nw;
-            const uint64_t* fl = rs(recv, par, 0, arr);
-            const uint64_t* fr = rs(recv, par, 1, arr);
+            const uint64_t* fl = l_remote ? xs(bd_l, 0, par, arr) : rs(recv, par, 0, arr);
+            const uint64_t* fr = r_remote ? xs(bd_r, 1, par, arr) : rs(recv, par, 1, arr);
             for (int idx = threadIdx.x; idx < slotw; idx += T) {
                 const int I = idx / kh, x = idx - I * kh;
-                word_st(A, (uint64_t)I * wpm + x, word_ld<false>(fl, idx, slotw, __LINE__), nw, __LINE__);
-                word_st(A, (uint64_t)I * wpm + (S + k) / 2 + x, word_ld<false>(fr, idx, slotw, __LINE__), nw,
-                        __LINE__);
+                const uint64_t vl = l_remote ? __ldcg(fl + idx) : word_ld<false>(fl, idx, slotw, __LINE__);
+                const uint64_t vr = r_remote ? __ldcg(fr + idx) : word_ld<false>(fr, idx, slotw, __LINE__);
+                word_st(A, (uint64_t)I * wpm + x, vl, nw, __LINE__);
+                word_st(A, (uint64_t)I * wpm + (S + k) / 2 + x, vr, nw, __LINE__);
             }
         }
     };
@@ -243,7 +282,7 @@ ci_cluster_sweeps_kernel(CiClusterArgs a)
                 word_ld<false>(a.S, (uint64_t)I * L + c0 + x, lattice_n, __LINE__), nw, __LINE__);
     }
     __syncthreads();
-    push(0);
+    push(0, 0);
 #pragma unroll
     for (int h = 0; h < Q - 1; ++h) stage();
     cluster.sync();          // the first phase's halos have arrived
@@ -265,10 +304,10 @@ ci_cluster_sweeps_kernel(CiClusterArgs a)
             rec_counts = a.counts + (size_t)(first / a.every - 1) * 2 * kCountSlots;
         }
     }
-    int par = 0;
-    for (int hs0 = 0; hs0 < total; hs0 += k) {
+    int par = 0, phase = 0;
+    for (int hs0 = 0; hs0 < total; hs0 += k, ++phase) {
         const int kk = min(k, total - hs0);                             // even: phases start with colour 0
-        receive(par);
+        receive(par, phase);
         for (int d = 0; d < kk; d += 2) {
             const uint64_t* m0 = begin();
             ci_cl_half_sweep<0, false, NS>(E, m0, wpm, wrap, nw, slot, 1 + d, Wn - 2 - d, nullptr);
@@ -286,7 +325,7 @@ ci_cluster_sweeps_kernel(CiClusterArgs a)
         par ^= 1;
         if (hs0 + k < total) {
             __syncthreads();     // own columns final for this phase
-            push(par);
+            push(par, phase + 1);
         }
         // the next phase's halos have arrived; the slots the next pushes write
         // were read at the start of this phase; after the last phase: no block
@@ -338,18 +377,26 @@ size_t ci_cl_smem_bytes(int L, int N, int C, int k, int q)
 }
 
 using CiClusterKernel = void (*)(CiClusterArgs);
-constexpr CiClusterKernel kCiClusterKernels[8] = {
-    ci_cluster_sweeps_kernel<1, false>, ci_cluster_sweeps_kernel<2, false>, ci_cluster_sweeps_kernel<3, false>, ci_cluster_sweeps_kernel<4, false>,
-    ci_cluster_sweeps_kernel<1, true>,  ci_cluster_sweeps_kernel<2, true>,  ci_cluster_sweeps_kernel<3, true>,  ci_cluster_sweeps_kernel<4, true>};
+constexpr CiClusterKernel kCiClusterKernels[16] = {
+    ci_cluster_sweeps_kernel<1, false, false>, ci_cluster_sweeps_kernel<2, false, false>,
+    ci_cluster_sweeps_kernel<3, false, false>, ci_cluster_sweeps_kernel<4, false, false>,
+    ci_cluster_sweeps_kernel<1, true, false>,  ci_cluster_sweeps_kernel<2, true, false>,
+    ci_cluster_sweeps_kernel<3, true, false>,  ci_cluster_sweeps_kernel<4, true, false>,
+    ci_cluster_sweeps_kernel<1, false, true>,  ci_cluster_sweeps_kernel<2, false, true>,
+    ci_cluster_sweeps_kernel<3, false, true>,  ci_cluster_sweeps_kernel<4, false, true>,
+    ci_cluster_sweeps_kernel<1, true, true>,   ci_cluster_sweeps_kernel<2, true, true>,
+    ci_cluster_sweeps_kernel<3, true, true>,   ci_cluster_sweeps_kernel<4, true, true>};
 
-CiClusterKernel ci_cluster_kernel(int ns, int q)
+CiClusterKernel ci_cluster_kernel(int ns, int q, bool multi)
 {
-    return kCiClusterKernels[(q == kCiMaxSlabs ? 4 : 0) + (ns - 1)];
+    return kCiClusterKernels[(multi ? 8 : 0) + (q == kCiMaxSlabs ? 4 : 0) + (ns - 1)];
 }
 
 // Window words a block takes with at most `ns` words per thread: 1024
 // threads for 1, 2 or 4 (64 registers each), 768 for 3 (80 registers).
 long long max_words(int ns) { return ns == 3 ? 3 * 768 : (long long)ns * kCiThreads; }
+
+int g_ci_max_active = 0;   // clusters of the largest size resident at once (set by the probe)
 
 int ci_probe_max_cluster()
 {
@@ -373,12 +420,17 @@ int ci_probe_max_cluster()
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         bool ok = true;
-        for (int i = 0; i < 8; ++i) {                 // form i: (i % 4) + 1 words per thread
+        int active = 1 << 30;
+        for (int i = 0; i < 16; ++i) {                // form i: (i % 4) + 1 pairs per thread
             cfg.blockDim = dim3(i % 4 == 2 ? 768 : kCiThreads);
             int nc = 0;
             ok = ok && cudaOccupancyMaxActiveClusters(&nc, kCiClusterKernels[i], &cfg) == cudaSuccess && nc >= 1;
+            active = std::min(active, nc);
         }
-        if (ok) return c;
+        if (ok) {
+            g_ci_max_active = active;
+            return c;
+        }
         cudaGetLastError();
     }
     return 0;
@@ -394,17 +446,17 @@ int ci_probe_max_cluster()
 // spin-updates/ns, against k = 8 with 2, 367; L = 1092: 3 pairs, 403,
 // against 4, 232).  False if L is not a side of the layout or no such launch
 // exists.
-bool ci_cluster_plan(int L, ClusterPlan* plan)
+bool ci_cluster_plan(int L, int clusters, ClusterPlan* plan)
 {
     if (!ci_valid_side(L)) return false;
     static const int max_cluster = ci_probe_max_cluster();   // per process, set once
-    if (max_cluster == 0) return false;
-    const int c = max_cluster, N = L / 21;
-    const int fewest = 4 * ((L / 4) / c), widest = ci_widest(L, c);
+    if (max_cluster == 0 || clusters < 1 || clusters > g_ci_max_active) return false;
+    const int c = max_cluster, nb = clusters * c, N = L / 21;         // cluster size, blocks of the launch
+    const int fewest = 4 * ((L / 4) / nb), widest = ci_widest(L, nb);
     for (int most : {3, 4}) {
         for (int q : {kCiMaxSlabs, 2}) {
             for (int kk = std::min(kCiHalo, fewest) & ~3; kk >= 4; kk -= 4) {
-                if (ci_cl_smem_bytes(L, N, c, kk, q) > kCiSmemMax) continue;
+                if (ci_cl_smem_bytes(L, N, nb, kk, q) > kCiSmemMax) continue;
                 const long long words = (long long)N * ((widest + 2 * kk) / 2);
                 if (words > max_words(most)) continue;
                 const int ns = words <= kCiThreads ? 1 : (words <= 2 * kCiThreads ? 2 : (words <= max_words(3) ? 3 : 4));
@@ -413,12 +465,17 @@ bool ci_cluster_plan(int L, ClusterPlan* plan)
                 plan->q = q;
                 plan->ns = ns;
                 plan->threads = (int)(((words + ns - 1) / ns + 31) / 32 * 32);
-                plan->clusters = 1;
+                plan->clusters = clusters;
                 return true;
             }
         }
     }
     return false;
+}
+
+size_t ci_cl_exchange_words(int L, const ClusterPlan& plan)
+{
+    return (size_t)plan.clusters * 2 * 2 * 2 * (L / 21) * (plan.k / 2);   // [boundary][dir][parity][array] N x k/2
 }
 
 size_t ci_cl_mask_bytes_per_sweep(int L) { return 2 * (size_t)(L / 21) * (L / 2) * sizeof(uint64_t); }
@@ -442,23 +499,32 @@ cudaError_t ci_cl_mask_draw(int L, const SweepArgs& a, uint64_t t0, int nsweeps,
 }
 
 cudaError_t ci_cluster_sweeps(uint64_t* S, int L, const SweepArgs& a, const ClusterPlan& plan, int nsweeps,
-                              const uint64_t* masks, int64_t s0, int64_t every, cudaStream_t s)
+                              const uint64_t* masks, int64_t s0, int64_t every, const ClusterExchange& x,
+                              cudaStream_t s)
 {
+    const int nb = plan.clusters * plan.blocks;
     CiClusterArgs ca;
     ca.S = S;
     ca.L = L;
     ca.N = L / 21;
     ca.k = plan.k;
     ca.nsweeps = nsweeps;
-    ca.wpm = (ci_widest(L, plan.blocks) + 2 * plan.k) / 2;
+    ca.wpm = (ci_widest(L, nb) + 2 * plan.k) / 2;
     ca.masks = masks;
     ca.s0 = s0;
     ca.every = every;
     ca.counts = a.counts;
+    ca.G = plan.clusters;
+    ca.xbuf = x.buf;
+    ca.xflag = x.flags;
+    ca.xseq = x.seq;
+    ca.xwait = x.wait_add;
+    ca.xerr = x.err;
+    if (plan.clusters > 1 && (!x.buf || !x.flags || !x.err)) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(plan.blocks);
+    cfg.gridDim = dim3(nb);
     cfg.blockDim = dim3(plan.threads);
-    cfg.dynamicSmemBytes = ci_cl_smem_bytes(L, ca.N, plan.blocks, plan.k, plan.q);
+    cfg.dynamicSmemBytes = ci_cl_smem_bytes(L, ca.N, nb, plan.k, plan.q);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -467,7 +533,7 @@ cudaError_t ci_cluster_sweeps(uint64_t* S, int L, const SweepArgs& a, const Clus
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, ci_cluster_kernel(plan.ns, plan.q), ca);
+    return cudaLaunchKernelEx(&cfg, ci_cluster_kernel(plan.ns, plan.q, plan.clusters > 1), ca);
 }
 
 }  // namespace ising

@@ -7,7 +7,8 @@
 
 namespace ising {
 
-struct ClusterPlan;   // ising_internal.h
+struct ClusterPlan;       // ising_internal.h
+struct ClusterExchange;
 
 bool ci_valid_side(int32_t L);   // L % 84 == 0 (N = L / 21 divisible by 4), 84 <= L <= 32760
 cudaError_t ci_init_hot(uint64_t* S, int L, uint64_t seed, cudaStream_t s);
@@ -37,15 +38,18 @@ cudaError_t ci_half_sweep_pre(int colour, bool record, uint64_t* S, int L, const
 bool ci_valid_strips(int32_t L, int32_t nstrips);   // nstrips divides L, L / nstrips >= 2
 size_t ci_rw_draw_bytes(int L, int nstrips);
 // The cluster path in this layout (ising_ci_cluster.cu), as cluster_plan,
-// cl_mask_bytes_per_sweep, launch_cl_mask_draw and launch_cluster_sweeps of
-// the row-packed one (ising_internal.h): the masks of nsweeps sweeps after
-// sweep t0 (host value), then sweeps s0 + 1 .. s0 + nsweeps of a call.
-bool ci_cluster_plan(int L, ClusterPlan* plan);
+// cl_exchange_words, cl_mask_bytes_per_sweep, launch_cl_mask_draw and
+// launch_cluster_sweeps of the row-packed one (ising_internal.h): the masks
+// of nsweeps sweeps after sweep t0 (host value), then sweeps s0 + 1 ..
+// s0 + nsweeps of a call.
+bool ci_cluster_plan(int L, int clusters, ClusterPlan* plan);
+size_t ci_cl_exchange_words(int L, const ClusterPlan& plan);
 size_t ci_cl_mask_bytes_per_sweep(int L);
 cudaError_t ci_cl_mask_draw(int L, const SweepArgs& a, uint64_t t0, int nsweeps, uint64_t* masks, bool overlap,
                             cudaStream_t s);
 cudaError_t ci_cluster_sweeps(uint64_t* S, int L, const SweepArgs& a, const ClusterPlan& plan, int nsweeps,
-                              const uint64_t* masks, int64_t s0, int64_t every, cudaStream_t s);
+                              const uint64_t* masks, int64_t s0, int64_t every, const ClusterExchange& x,
+                              cudaStream_t s);
 bool ci_rw_predraw(int L, int nstrips);
 cudaError_t ci_random_words_iteration(uint64_t* S, int L, int nstrips, const SweepArgs& a, ulonglong2* draws,
                                       cudaStream_t s);

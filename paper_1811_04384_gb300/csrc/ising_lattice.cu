@@ -509,7 +509,6 @@ template <typename RecOf>
 static int run_sweeps(ising_lattice* h, int64_t n, RecOf rec_of)
 {
     SweepArgs a = base_args(h);
-    const Geom& g = h->g;
     for (int64_t s = 1; s <= n; ++s) {
         a.t_off = (uint32_t)s;
         cudaError_t e = launch_hs(h, 0, true, false, a);
@@ -643,9 +642,9 @@ static int run_resident(ising_lattice* h, int n, int every)
 // registers.  Two 16 MB mask buffers (43-sweep pieces at L = 1008) gave 444
 // there: each launch loads and writes back the lattice and refills the mask
 // ring.  In the column-interleaved layout (one cluster): L = 1008: 373 /
-// 304; L = 1092: 403 / 338.
+// 304; L = 1092: 403 / 338; several clusters below (ci_auto_clusters).
 constexpr int kClusterMaxL = 3000;
-constexpr int kCiClusterMaxL = 1092;               // the column-interleaved layout (L % 84 == 0)
+constexpr int kCiClusterMaxL = 2604;               // the column-interleaved layout (L % 84 == 0)
 constexpr size_t kClusterMaskBytes = 128u << 20;   // both buffers
 constexpr int kClusterMaxPiece = 256;
 
@@ -670,13 +669,40 @@ static int auto_clusters(int L)
 // The cluster-path launch for h: the clusters set by ising_set_clusters, else
 // the automatic count; `forced` (ISING_PATH_CLUSTER) first tries one
 // cluster at any size.
+// The same for the column-interleaved layout, whose per-word draws cost more
+// (19 Philox products per call against 16), so the draws on the SMs the
+// clusters leave free bound it sooner.  Measured on GB300, sweeps without
+// records, spin-updates/ns by clusters 1 .. 7 (graph replays): L = 1008:
+// 378 / 397 / 427 / 466 / 441 / 449 / 444 (305); L = 1512: 354 / 567 / 589 /
+// 583 / 578 / 583 / 563 (444); L = 2016: - / 548 / 538 / 651 / 629 / 611 /
+// 598 (574); L = 2520: three to seven 613 / 600 / 655 / 648 / 595 (633);
+// L = 3024: four to seven 620 / 623 / 598 / 588 (666).
+static int ci_auto_clusters(int L)
+{
+    constexpr struct { int max_L, clusters; } kRule[] = {
+        {840, 1}, {1092, 4}, {1764, 3}, {2184, 4}, {kCiClusterMaxL, 5}};
+    for (const auto& r : kRule)
+        if (L <= r.max_L) return r.clusters;
+    return 0;
+}
+
+static bool plan_cluster_g(const ising_lattice* h, int clusters, ClusterPlan* plan)
+{
+    return h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED ? ci_cluster_plan(h->g.L, clusters, plan)
+                                                        : cluster_plan(h->g, clusters, plan);
+}
+
+static int auto_clusters_of(const ising_lattice* h)
+{
+    return h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED ? ci_auto_clusters(h->g.L) : auto_clusters(h->g.L);
+}
+
 static bool plan_cluster(const ising_lattice* h, ClusterPlan* plan, bool forced)
 {
-    if (h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED) return h->clusters <= 1 && ci_cluster_plan(h->g.L, plan);
-    if (h->clusters > 0) return cluster_plan(h->g, h->clusters, plan);
-    const int G = auto_clusters(h->g.L);
-    if (G > 0 && cluster_plan(h->g, G, plan)) return true;
-    return forced && cluster_plan(h->g, 1, plan);
+    if (h->clusters > 0) return plan_cluster_g(h, h->clusters, plan);
+    const int G = auto_clusters_of(h);
+    if (G > 0 && plan_cluster_g(h, G, plan)) return true;
+    return forced && plan_cluster_g(h, 1, plan);
 }
 
 static bool use_cluster(const ising_lattice* h, ClusterPlan* plan)
@@ -684,8 +710,7 @@ static bool use_cluster(const ising_lattice* h, ClusterPlan* plan)
     if (h->chain != ISING_CHAIN_CHECKERBOARD) return false;
     if (h->path == ISING_PATH_CLUSTER) return plan_cluster(h, plan, true);
     if (h->path != ISING_PATH_AUTO || use_resident(h)) return false;
-    if (h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED && h->g.L > kCiClusterMaxL) return false;
-    if (h->layout == ISING_LAYOUT_ROW_PACKED && h->clusters == 0 && auto_clusters(h->g.L) == 0) return false;
+    if (h->clusters == 0 && auto_clusters_of(h) == 0) return false;
     return plan_cluster(h, plan, false);
 }
 
@@ -725,7 +750,7 @@ static int run_cluster(ising_lattice* h, int64_t n, int64_t every, unsigned long
     }
     ClusterExchange x = {nullptr, nullptr, 0, nullptr, 0};
     if (plan.clusters > 1) {
-        const size_t xb = cl_exchange_words(g, plan) * sizeof(uint64_t);
+        const size_t xb = (ci ? ci_cl_exchange_words(g.L, plan) : cl_exchange_words(g, plan)) * sizeof(uint64_t);
         cudaError_t e = cudaSuccess;
         if (h->xbuf_bytes < xb) {
             if (h->xbuf) cudaFree(h->xbuf);
@@ -751,7 +776,7 @@ static int run_cluster(ising_lattice* h, int64_t n, int64_t every, unsigned long
             --h->stall_launches;
             x.wait_add = 1ull << 62;                 // no push reaches it: every wait gives up
         }
-        cudaError_t e = ci ? ci_cluster_sweeps(h->words[0], g.L, a, plan, part_of(j), masks[j & 1], done, every,
+        cudaError_t e = ci ? ci_cluster_sweeps(h->words[0], g.L, a, plan, part_of(j), masks[j & 1], done, every, x,
                                                h->stream)
                            : launch_cluster_sweeps(h->words[0], h->words[1], g, a, plan, part_of(j), masks[j & 1],
                                                    done, every, x, h->stream);
@@ -789,8 +814,7 @@ extern "C" int ising_set_clusters(ising_lattice* h, int32_t clusters)
 {
     if (!h || clusters < 0 || clusters > 16) return ISING_EINVAL;
     ClusterPlan cp;
-    if (clusters > 0 && (h->layout != ISING_LAYOUT_ROW_PACKED ? clusters != 1 : !cluster_plan(h->g, clusters, &cp)))
-        return ISING_EINVAL;
+    if (clusters > 0 && !plan_cluster_g(h, clusters, &cp)) return ISING_EINVAL;
     h->clusters = clusters;
     return ISING_OK;
 }

@@ -70,8 +70,8 @@ CI_CASES = [
     (252, 26, 3, BETA_TC, False),  # phases of 12, records out of step with them
     (504, 300, 7, 0.41, False),    # two mask pieces (256 + 44 sweeps)
     (840, 20, 4, 0.44, False),     # two pairs per thread
-    (1008, 24, 5, BETA_TC, False), # the paper's L = 1008 (N = 48), phases of 12, three pairs per thread
-    (1092, 6, 1, 0.44, False),     # three pairs per thread, largest automatic side
+    (1008, 24, 5, BETA_TC, False), # the paper's L = 1008 (N = 48), four clusters
+    (1092, 6, 1, 0.44, False),     # four clusters
     (1260, 4, 1, 0.41, True),      # four pairs per thread
     (1512, 3, 1, BETA_TC, True),   # two mask slabs, four pairs per thread
 ]
@@ -156,6 +156,32 @@ def test_multi_cluster_matches_oracle(ising):
         np.testing.assert_array_equal(S, So, err_msg=str(case))
 
 
+# the column-interleaved layout on several clusters: (L, clusters, sweeps, every)
+CI_MULTI_CASES = [
+    (504, 2, 20, 3),
+    (1008, 3, 12, 2),
+    (2016, 4, 4, 1),     # the paper's cases 1-2 size
+    (3024, 5, 2, 1),
+]
+
+
+def test_interleaved_multi_cluster_matches_oracle(ising):
+    got = []
+    for L, G, n, every in CI_MULTI_CASES:
+        with ising.Lattice(L, L + 13, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
+            lat.set_clusters(G)
+            assert lat.get_path() == ising.ISING_PATH_CLUSTER, (L, G)
+            lat.init_hot()
+            lat.set_beta(0.44)
+            E, M = lat.sweep_record(n, every)
+            got.append((E, M, lat.get_spins()))
+    ora = oracle.run_jobs([(L, L + 13, 0.44, True, n, every) for L, G, n, every in CI_MULTI_CASES])
+    for (E, M, S), (Eo, Mo, So), case in zip(got, ora, CI_MULTI_CASES):
+        np.testing.assert_array_equal(E, Eo, err_msg=str(case))
+        np.testing.assert_array_equal(M, Mo, err_msg=str(case))
+        np.testing.assert_array_equal(S, So, err_msg=str(case))
+
+
 def test_multi_cluster_continued_and_rejected(ising):
     """Calls continued with 2, then 3 clusters, then 1 (the exchange flags
     only ever rise across launches), and the counts a lattice rejects."""
@@ -181,9 +207,9 @@ def test_multi_cluster_continued_and_rejected(ising):
         np.testing.assert_array_equal(E, Eo)
         np.testing.assert_array_equal(M, Mo)
     np.testing.assert_array_equal(S, s)
-    with ising.Lattice(1008, 1, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
+    with ising.Lattice(84, 1, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
         with pytest.raises(ising.IsingError):
-            lat.set_clusters(2)
+            lat.set_clusters(2)      # 21 column groups of 4 for 32 blocks
 
 
 def test_multi_cluster_wait_gives_up_and_recovers(ising):
@@ -297,11 +323,14 @@ def test_cluster_path_choice(ising):
             with pytest.raises(ising.IsingError):
                 lat.set_path(ising.ISING_PATH_CLUSTER)
             assert lat.get_path() != ising.ISING_PATH_CLUSTER
-    with ising.Lattice(1596, 1, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
+    with ising.Lattice(8400, 1, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
         with pytest.raises(ising.IsingError):
             lat.set_path(ising.ISING_PATH_CLUSTER)
         assert lat.get_path() == ising.ISING_PATH_LAUNCHES
+    for L, path in ((1008, ising.ISING_PATH_CLUSTER), (2604, ising.ISING_PATH_CLUSTER),
+                    (2688, ising.ISING_PATH_LAUNCHES)):
+        with ising.Lattice(L, 1, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
+            assert lat.get_path() == path, L
     with ising.Lattice(1008, 1, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
-        assert lat.get_path() == ising.ISING_PATH_CLUSTER
         lat.set_path(ising.ISING_PATH_LAUNCHES)
         assert lat.get_path() == ising.ISING_PATH_LAUNCHES
