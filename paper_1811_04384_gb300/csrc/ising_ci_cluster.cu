@@ -1,19 +1,21 @@
 // Cluster-resident temporal blocking in the paper's column-interleaved
 // layout (Sec. 3): the form of ising_cluster.cu for N x L words, mid-size
-// lattices (L a multiple of 84 up to about 1100).
+// lattices (L a multiple of 84 up to about 2600).
 //
 // Word S(I, J) holds s(I + kN, J) in field k and has colour (I + J) & 1.  A
 // half-sweep's neighbours of a word are the words left and right in its row
 // and above and below in its column, rotated by one field across the top
 // and bottom word rows (the paper's boundary rule).  So the lattice splits
-// by columns: block b of one thread-block cluster owns word columns
-// c0(b) .. c0(b + 1) - 1 (multiples of 4) of all N word rows and keeps them
-// in shared memory for a piece of up to 256 sweeps, in a window with k halo
-// columns on each side (k a multiple of 4).  Phases of k half-sweeps shrink
-// the valid columns by one per half-sweep (a trapezoid); at the end of a
-// phase each block pushes its first and last k own columns into the receive
-// slots of its left and right neighbours (distributed shared memory, two
-// sets by phase parity) and all pass one hardware cluster barrier.
+// by columns: block B of the launch's G thread-block clusters owns word
+// columns c0(B) .. c0(B + 1) - 1 (multiples of 4) of all N word rows and
+// keeps them in shared memory for a piece of up to 256 sweeps, in a window
+// with k halo columns on each side (k a multiple of 4).  Phases of k
+// half-sweeps shrink the valid columns by one per half-sweep (a trapezoid);
+// at the end of a phase each block pushes its first and last k own columns
+// into the receive slots of its left and right neighbours (distributed shared
+// memory inside a cluster, the global buffer and flags of ising_cluster.cu
+// between clusters, two sets by phase parity) and the blocks of a cluster
+// pass one hardware cluster barrier.
 //
 // The window is kept split by column parity: E holds the even window
 // columns, O the odd ones, pair p = columns 2p, 2p + 1.  In row I the word

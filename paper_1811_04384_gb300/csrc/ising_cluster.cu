@@ -1,36 +1,41 @@
 // Cluster-resident temporal blocking for mid-size lattices (above the
-// one-SM on-chip range, L of about 300 to 1080).
+// one-SM on-chip range, L of about 130 to 3000).
 //
 // There a half-sweep is short: a replayed graph node per half-sweep costs
-// more than its work.  Here one launch of a single thread-block cluster (16
+// more than its work.  Here one launch of G thread-block clusters (of 16
 // blocks where the device allows it, else 8) runs a piece of up to 256
-// sweeps whose accept masks cl_mask_draw_kernel has drawn beforehand on all
-// SMs.  Block b of the cluster owns rows b L / C .. (b + 1) L / C - 1 of both
-// colours and keeps them in its shared memory for the whole launch, in a
-// window with k rows of halo above and below (k even, k <= kClHalo, k <= the
-// rows a block owns, so a halo lies in the two neighbouring blocks).  The
-// launch's half-sweeps run in phases of k:
-//   1. cluster barrier: every block's own rows are those after the previous
-//      phase;
-//   2. each block copies its halo rows from its neighbours' shared memory
-//      (distributed shared memory);
-//   3. cluster barrier: no block changes its own rows before its neighbours
-//      have copied them;
-//   4. k half-sweeps on the window: after half-sweep d (0-based) the window
+// sweeps whose accept masks cl_mask_draw_kernel draws on the SMs the
+// clusters leave free.  The launch's G C blocks own consecutive row bands of
+// both colours, block B rows B L / (G C) .. (B + 1) L / (G C) - 1, and keep
+// them in shared memory for the whole launch, in a window with k rows of
+// halo above and below (k even, k <= kClHalo, k <= the rows a block owns,
+// so a halo lies in the two neighbouring blocks).  The launch's half-sweeps
+// run in phases of k:
+//   1. each block takes the halo rows its neighbours pushed at the end of the
+//      phase before (two sets of slots, by phase parity);
+//   2. k half-sweeps on the window: after half-sweep d (0-based) the window
 //      rows 1 + d .. R - 2 - d are exact, so after k of them the block's own
 //      rows still are (a trapezoid: the halo rows are recomputed by both
-//      neighbours).
+//      neighbours);
+//   3. each block pushes its first and last k own rows to the blocks above
+//      and below: into their shared memory inside a cluster (distributed
+//      shared memory), through a small global buffer with release/acquire
+//      sequence flags between clusters;
+//   4. a cluster barrier.
 // The masks of each half-sweep stream into a ring of shared-memory slabs
 // with asynchronous 16-byte copies, up to kClMaxSlabs - 1 half-sweeps ahead.
-// Every thread updates the same 1, 2 or 4 window words in each half-sweep
+// Every thread updates the same 1 to 4 window words in each half-sweep
 // (those inside its trapezoid), with their offsets worked out once per launch:
 // at these sizes a half-sweep is a few hundred instructions per SM, and the
 // index arithmetic of a general loop cost as much as the update itself.
-// The barriers are the hardware's (no flag polling, nothing to time out),
-// passed by every thread of every block the same number of times.  Each
-// update is the spin logic of row_apply with its row's pre-drawn masks, so
-// the results are those of the half-sweep kernels.  Records (colour 1 of a
-// recorded sweep) count each block's own rows only: every bond and spin once.
+// Inside a cluster only the hardware's barriers synchronise.  Between
+// clusters a boundary block waits for its neighbour's flag for at most one
+// second of the GPU's global timer, then records the failure and carries on,
+// so every launch ends and every thread passes the same barriers; the host
+// reports the failure.  Each update is the spin logic of row_apply with its
+// row's pre-drawn masks, so the results are those of the half-sweep kernels.
+// Records (colour 1 of a recorded sweep) count each block's own rows only:
+// every bond and spin once.
 #include <cuda_runtime.h>
 #include <cooperative_groups.h>
 
