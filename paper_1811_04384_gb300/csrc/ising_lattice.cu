@@ -700,8 +700,9 @@ static int auto_clusters_of(const ising_lattice* h)
 static bool plan_cluster(const ising_lattice* h, ClusterPlan* plan, bool forced)
 {
     if (h->clusters > 0) return plan_cluster_g(h, h->clusters, plan);
-    const int G = auto_clusters_of(h);
-    if (G > 0 && plan_cluster_g(h, G, plan)) return true;
+    // the rule's count, or fewer where the device holds fewer clusters at once
+    for (int G = auto_clusters_of(h); G >= 1; --G)
+        if (plan_cluster_g(h, G, plan)) return true;
     return forced && plan_cluster_g(h, 1, plan);
 }
 
