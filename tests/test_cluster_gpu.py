@@ -132,6 +132,7 @@ def test_interleaved_cluster_extremes_and_continuation(ising):
 # (L, clusters, sweeps, every)
 MULTI_CASES = [
     (600, 2, 26, 3),     # 32 blocks of 18-19 rows
+    (600, 2, 300, 10),   # two pieces (256 + 44 sweeps): the flags carry on across launches
     (1000, 3, 14, 2),    # 48 blocks
     (1600, 2, 8, 4),     # 50 rows per block
     (2016, 3, 6, 1),     # the paper's L = 2016
