@@ -54,7 +54,8 @@ enum {
                              NULL pointer, buffer too small, bad count */
     ISING_ENOMEM = -2,    /* device or host allocation failed */
     ISING_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
-    ISING_ETIMEOUT = -4,  /* a bounded wait gave up (ising_server_wait); no kernel spin-waits */
+    ISING_ETIMEOUT = -4,  /* a bounded wait gave up: ising_server_wait, or a wait between
+                             clusters of a cluster-path launch (each gives up after 1 s) */
     ISING_EBUSY = -5,     /* no free slot / budget (server admission) */
     ISING_ENOTFOUND = -6, /* unknown request id */
     ISING_EINTERNAL = -7  /* a host exception inside the server's worker thread
@@ -129,7 +130,10 @@ int ising_get_thresholds(ising_lattice *h, uint64_t host_thr[2]);
  * Carlo iteration (Sec. 2: every spin proposed once), in checkerboard order:
  * all colour-0 sites, then all colour-1 sites.  Asynchronous on the stream
  * (the first call on the on-chip path or with graph replays allocates its
- * mask buffer).  Errors: EINVAL (NULL, n < 0), ENOMEM (that buffer), ECUDA. */
+ * mask buffer), except on the cluster path with several clusters, where the
+ * call synchronises the stream to read the status of the waits between
+ * clusters.  Errors: EINVAL (NULL, n < 0), ENOMEM (that buffer), ETIMEOUT
+ * (a wait between clusters gave up; see ising_set_clusters), ECUDA. */
 int ising_sweep(ising_lattice *h, int64_t n);
 
 /* Run n sweeps and record E and M after sweeps t+every, t+2*every, ...:
@@ -137,7 +141,8 @@ int ising_sweep(ising_lattice *h, int64_t n);
  * each; either may be NULL.  n >= 0, 1 <= every <= 2^22.  Synchronises the stream.
  * The counts come from the reduction fused into the colour-1 half-sweep.
  * Errors: EINVAL (NULL, n < 0, every out of range), ENOMEM (the mask
- * buffer of the on-chip path or of the graph replays), ECUDA. */
+ * buffer of the on-chip path or of the graph replays), ETIMEOUT (as for
+ * ising_sweep), ECUDA. */
 int ising_sweep_record(ising_lattice *h, int64_t n, int64_t every,
                        int64_t *host_E, int64_t *host_M);
 
@@ -185,7 +190,7 @@ int ising_set_spins(ising_lattice *h, const int8_t *host_in, size_t n);
  * interleaved layout, or with more than 1024 records per state, the calls
  * run in turn.  No counterpart in the paper (input streaming).
  * Synchronises.  Errors: EINVAL (null state, sweeps > 2^30, every out of
- * 1..2^22), ENOMEM, ECUDA. */
+ * 1..2^22), ENOMEM, ETIMEOUT (as for ising_sweep), ECUDA. */
 int ising_run_states(ising_lattice *h, const int8_t *const *states, int32_t nstates, int64_t sweeps,
                      int64_t every, int64_t *E, int64_t *M);
 
@@ -300,9 +305,10 @@ int ising_get_path(ising_lattice *h, int32_t *path);
  * flag wait gives up after one second of the GPU's clock (for example when
  * other work keeps a cluster from being resident): the call then returns
  * ISING_ETIMEOUT, the sweeps it ran are void, and the sweep counter has
- * advanced (restore a checkpoint with ising_set_words / ising_set_sweep to
- * retry).  A number of clusters the device cannot hold at once, or for which
- * the lattice has no window plan, gives EINVAL.  Column-interleaved lattices
+ * advanced (restore a checkpoint with ising_set_words, or ising_set_spins
+ * in the column-interleaved layout, and ising_set_sweep to retry).  A
+ * number of clusters the device cannot hold at once, or for which the
+ * lattice has no window plan, gives EINVAL.  Column-interleaved lattices
  * split their word columns the same way (k halo columns of all word rows
  * between clusters).  Results do not depend on it. */
 int ising_set_clusters(ising_lattice *h, int32_t clusters);

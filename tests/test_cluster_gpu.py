@@ -241,6 +241,33 @@ def test_multi_cluster_wait_gives_up_and_recovers(ising):
     np.testing.assert_array_equal(S, s)
 
 
+def test_interleaved_multi_cluster_wait_gives_up_and_recovers(ising):
+    """The same give-up in the column-interleaved cluster kernel (its halo
+    columns between clusters wait on the same flags), with the checkpoint
+    taken as spins."""
+    L, seed, beta = 504, 29, 0.43
+    with ising.Lattice(L, seed, layout=ising.ISING_LAYOUT_COLUMN_INTERLEAVED) as lat:
+        lat.set_clusters(2)
+        lat.init_hot()
+        lat.set_beta(beta)
+        lat.sweep(3)
+        spins, t = lat.get_spins(), lat.t
+        lat.inject_stall(1)
+        with pytest.raises(ising.IsingError) as err:
+            lat.sweep(2)
+        assert err.value.code == ising.ISING_ETIMEOUT
+        lat.set_spins(spins)
+        lat.t = t
+        E, M = lat.sweep_record(6, 2)
+        S = lat.get_spins()
+    s = oracle.init_hot(L, seed)
+    oracle.run(s, seed, beta, 0, 3, 3)
+    Eo, Mo = oracle.run(s, seed, beta, 3, 6, 2)
+    np.testing.assert_array_equal(E, Eo)
+    np.testing.assert_array_equal(M, Mo)
+    np.testing.assert_array_equal(S, s)
+
+
 def test_cluster_continued_across_calls_and_paths(ising):
     """Plain sweeps, recorded sweeps, a switch to the graph replays and back:
     the sweep counter carries the draws across the calls and paths."""
