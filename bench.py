@@ -505,11 +505,11 @@ MIDSIZE_L = [296, 400, 512, 700, 1008]
 def cluster_launches(L: int, sweeps: int, every: int) -> int:
     """Kernel launches of ising_sweep_record(sweeps, every) on the cluster
     path: per chunk of 1024 records, a mask draw and a cluster launch per
-    piece of sweeps (two mask buffers of at most 64 MB, 256 sweeps at most)
+    piece of sweeps (two mask buffers of at most 128 MB, 256 sweeps at most)
     and one sweep-counter advance."""
     W = -(-(L // 2) // 21)
     P = W + (W & 1)
-    piece = max(1, min(256, (128 << 20) // (2 * 2 * L * P * 8)))
+    piece = max(1, min(256, (256 << 20) // (2 * 2 * L * P * 8)))
     launches, records, rest = 0, sweeps // every, sweeps % every
     while records > 0:
         chunk = min(records, 1024)

@@ -273,7 +273,7 @@ int ising_set_item_lanes(ising_lattice *h, int32_t lanes);
  * their own rows plus halo.  The accept masks of each
  * piece are drawn by the SMs the cluster leaves free, while the piece before
  * is applied, into two device buffers the library allocates on first use (up
- * to 128 MB together; 2 L pitch 8 bytes per sweep).  No spin-waits: only the
+ * to 256 MB together; 2 L pitch 8 bytes per sweep).  No spin-waits: only the
  * hardware's block and cluster barriers.
  * Both layouts may run several clusters per launch (see
  * ising_set_clusters), which takes the path past the sizes one cluster's
@@ -308,7 +308,14 @@ int ising_get_path(ising_lattice *h, int32_t *path);
  * advanced (restore a checkpoint with ising_set_words, or ising_set_spins
  * in the column-interleaved layout, and ising_set_sweep to retry).  A
  * number of clusters the device cannot hold at once, or for which the
- * lattice has no window plan, gives EINVAL.  Column-interleaved lattices
+ * lattice has no window plan, gives EINVAL.  A launch with several
+ * clusters writes its lattice rows back only if all its blocks were
+ * resident together, which all its blocks agree on at their end.  If they
+ * were not (other work on the device held SMs; its waits then give up), the
+ * launch writes nothing, the rest of the call runs on the launch path with
+ * the same results, and the automatic choice keeps to one cluster until the
+ * next ising_set_path or ising_set_clusters.  ISING_ETIMEOUT is left for a
+ * wait that gave up while all blocks were resident.  Column-interleaved lattices
  * split their word columns the same way (k halo columns of all word rows
  * between clusters).  Results do not depend on it. */
 int ising_set_clusters(ising_lattice *h, int32_t clusters);
@@ -318,6 +325,13 @@ int ising_set_clusters(ising_lattice *h, int32_t clusters);
  * between clusters gives up after its second and the call returns
  * ISING_ETIMEOUT (the GPU keeps running; nothing traps).  0 clears it. */
 int ising_cluster_inject_stall(ising_lattice *h, int32_t launches);
+
+/* Test hook of that agreement: the launch with several clusters that comes
+ * after `after` (>= 0) more such launches counts on one block more than it
+ * has, so its blocks agree after 0.1 s that not all were resident and write
+ * nothing; the call finishes on the launch path (results unchanged).  -1
+ * clears it; below -1: EINVAL. */
+int ising_cluster_inject_absent(ising_lattice *h, int32_t after);
 
 /* Which Markov chain ising_sweep and ising_sweep_record run.
  * ISING_CHAIN_CHECKERBOARD (default): the checkerboard sweeps of the

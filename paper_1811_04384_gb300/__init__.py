@@ -209,6 +209,12 @@ class Lattice:
         """Test hook (ising_cluster_inject_stall): the next launches' waits between clusters give up."""
         _check(load().ising_cluster_inject_stall(self._h, int(launches)), "ising_cluster_inject_stall")
 
+    def inject_absent(self, after: int = 0):
+        """Test hook (ising_cluster_inject_absent): the launch with several
+        clusters after `after` more of them counts on one block more than it
+        has, so it writes nothing and the call finishes on the launch path; -1 clears."""
+        _check(load().ising_cluster_inject_absent(self._h, int(after)), "ising_cluster_inject_absent")
+
     def get_path(self) -> int:
         """The path the next sweeps take (ising_get_path): ISING_PATH_RESIDENT,
         ISING_PATH_CLUSTER or ISING_PATH_LAUNCHES."""

@@ -67,6 +67,7 @@ SYMBOLS = {
     "ising_get_path": (_int, [_vp, _vp]),
     "ising_set_clusters": (_int, [_vp, _i32]),
     "ising_cluster_inject_stall": (_int, [_vp, _i32]),
+    "ising_cluster_inject_absent": (_int, [_vp, _i32]),
     "ising_set_rng": (_int, [_vp, _i32]),
     "ising_set_chain": (_int, [_vp, _i32, _i32]),
     "ising_philox_blocks": (_int, [_u64, _pu32, _pu32, _i64]),

@@ -64,6 +64,9 @@ struct CiClusterArgs {
     unsigned long long xseq;    // push m of this launch sets its flags to xseq + m + 1
     unsigned long long xwait;   // added to the values the receives wait for (0; a test stalls with more)
     unsigned int* xerr;         // set to 1 when a wait for a flag gives up
+    unsigned int* gate;         // G > 1: the words the blocks agree through (cl_count_in, cl_decide)
+    unsigned int gate_blocks;   // blocks that must have counted in (the launch's; one more in a test)
+    unsigned int piece;         // the launch's piece of the call
 };
 
 // First word column of block b of a cluster of C: a multiple of 4.
@@ -158,6 +161,12 @@ ci_cluster_sweeps_kernel(CiClusterArgs a)
     const int L = a.L, N = a.N, k = a.k, kh = k / 2, PL = L / 2;
     // the launch's G C blocks own consecutive column bands: block B = gc C + b
     const int G = a.G, gc = (int)blockIdx.x / C, NB = G * C, B = gc * C + b;
+    // several clusters: count in (a launch after a piece that gave up does nothing)
+    if (__builtin_expect(MULTI && !(NS == 1 ? cl_count_in(a.gate, a.piece) : cl_count_in_call(a.gate, a.piece)), 0))
+        return;
+    // every block of the cluster has started before any block writes into
+    // another's shared memory: arrive now, wait just before the first push
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
     const int c0 = ci_col0(B, NB, L), S = ci_col0(B + 1, NB, L) - c0;  // own columns
     const int bp = (b + C - 1) % C, bn = (b + 1) % C;                  // left and right blocks in the cluster
     // with G > 1 a cluster's first block takes its left halo from the last
@@ -284,6 +293,7 @@ ci_cluster_sweeps_kernel(CiClusterArgs a)
                 word_ld<false>(a.S, (uint64_t)I * L + c0 + x, lattice_n, __LINE__), nw, __LINE__);
     }
     __syncthreads();
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
     push(0, 0);
 #pragma unroll
     for (int h = 0; h < Q - 1; ++h) stage();
@@ -334,8 +344,12 @@ ci_cluster_sweeps_kernel(CiClusterArgs a)
         // leaves while another may still write its shared memory
         cluster.sync();
     }
-    // own columns back to the lattice
+    // own columns back to the lattice, with several clusters only if every
+    // block of the launch was resident (otherwise none writes)
     cl_wait<0>();
+    if (__builtin_expect(MULTI && !(NS == 1 ? cl_decide(a.gate, a.gate_blocks, a.piece)
+                                            : cl_decide_call(a.gate, a.gate_blocks, a.piece)), 0))
+        return;
     for (int e = threadIdx.x; e < N * S; e += T) {
         const int I = e / S, x = e - I * S;
         const int w = k + x;
@@ -522,7 +536,10 @@ cudaError_t ci_cluster_sweeps(uint64_t* S, int L, const SweepArgs& a, const Clus
     ca.xseq = x.seq;
     ca.xwait = x.wait_add;
     ca.xerr = x.err;
-    if (plan.clusters > 1 && (!x.buf || !x.flags || !x.err)) return cudaErrorInvalidValue;
+    ca.gate = x.gate;
+    ca.gate_blocks = (unsigned int)(nb) + x.absent;
+    ca.piece = x.piece;
+    if (plan.clusters > 1 && (!x.buf || !x.flags || !x.err || !x.gate)) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nb);
     cfg.blockDim = dim3(plan.threads);

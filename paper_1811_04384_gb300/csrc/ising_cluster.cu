@@ -73,6 +73,9 @@ struct ClusterArgs {
     unsigned long long xseq;    // push m of this launch sets its flags to xseq + m + 1
     unsigned long long xwait;   // added to the values the receives wait for (0; a test stalls with more)
     unsigned int* xerr;         // set to 1 when a wait for a flag gives up
+    unsigned int* gate;         // G > 1: the words the blocks agree through (cl_count_in, cl_decide)
+    unsigned int gate_blocks;   // blocks that must have counted in (the launch's; one more in a test)
+    unsigned int piece;         // the launch's piece of the call
 };
 
 // A window word a thread updates in every half-sweep whose rows include its
@@ -169,6 +172,12 @@ cluster_sweeps_kernel(ClusterArgs a)
     const int k = a.k;
     // the launch's G C blocks own consecutive row bands: block B = gc C + b
     const int G = a.G, gc = (int)blockIdx.x / C, NB = G * C, B = gc * C + b;
+    // several clusters: count in (a launch after a piece that gave up does nothing)
+    if (__builtin_expect(MULTI && !(NS == 1 ? cl_count_in(a.gate, a.piece) : cl_count_in_call(a.gate, a.piece)), 0))
+        return;
+    // every block of the cluster has started before any block writes into
+    // another's shared memory: arrive now, wait just before the first push
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
     auto row0 = [&](int blk) { return (int)((long long)blk * g.L / NB); };
     const int r0 = row0(B), r1 = row0(B + 1), S = r1 - r0, R = S + 2 * k;
     const int bp = (b + C - 1) % C, bn = (b + 1) % C;                   // the blocks above and below in the cluster
@@ -301,6 +310,7 @@ cluster_sweeps_kernel(ClusterArgs a)
     cl_commit();
     cl_wait<0>();
     __syncthreads();
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
     push(0, 0);
 #pragma unroll
     for (int h = 0; h < Q - 1; ++h) stage();
@@ -356,8 +366,12 @@ cluster_sweeps_kernel(ClusterArgs a)
         // leaves while another may still write its shared memory
         cluster.sync();
     }
-    // own rows back to the lattice
+    // own rows back to the lattice, with several clusters only if every block
+    // of the launch was resident (otherwise none writes)
     cl_wait<0>();
+    if (__builtin_expect(MULTI && !(NS == 1 ? cl_decide(a.gate, a.gate_blocks, a.piece)
+                                            : cl_decide_call(a.gate, a.gate_blocks, a.piece)), 0))
+        return;
     for (int c = 0; c < 2; ++c)
         for (int idx = threadIdx.x; idx < S * (int)P; idx += T)
             word_st(a.w[c], (uint64_t)r0 * P + idx, word_ld<false>(win[c], (uint64_t)k * P + idx, n, __LINE__),
@@ -572,7 +586,10 @@ cudaError_t launch_cluster_sweeps(uint64_t* w0, uint64_t* w1, const Geom& g, con
     ca.xseq = x.seq;
     ca.xwait = x.wait_add;
     ca.xerr = x.err;
-    if (plan.clusters > 1 && (!x.buf || !x.flags || !x.err)) return cudaErrorInvalidValue;
+    ca.gate = x.gate;
+    ca.gate_blocks = (unsigned int)(nb) + x.absent;
+    ca.piece = x.piece;
+    if (plan.clusters > 1 && (!x.buf || !x.flags || !x.err || !x.gate)) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nb);
     cfg.blockDim = dim3(plan.threads);

@@ -70,6 +70,94 @@ __device__ __forceinline__ unsigned long long cl_globaltimer()
 
 constexpr unsigned long long kClWaitNs = 1000000000ull;   // a wait gives up after one second
 
+__device__ __forceinline__ unsigned int cl_load_acquire(const unsigned int* p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// The agreement of a launch with several clusters.  Its boundary blocks
+// wait for rows from other clusters, which needs every cluster of the launch
+// resident at once; other work on the device (another stream or process) can
+// hold SMs so that some are not, and then those waits give up and the rows
+// are stale.  So a launch writes its lattice rows back only if all its blocks
+// were resident together, and all its blocks agree on that:
+//   gate[0..3]  two sets of {blocks counted in, verdict}, used by alternate
+//               pieces of a call (both zeroed before the call's first launch);
+//   gate[4]     the first piece of the call whose launch gave up (kClNoPiece
+//               before it; the launches after it in the call do nothing).
+// Every block counts in as it starts (cl_count_in, no wait) and decides at
+// its end, before the write-back (cl_decide): it proposes "go" (1) if it sees
+// all blocks counted in, else, after kClCheckInNs, "give up" (2).  The first
+// proposal written is the verdict every block reads, so the blocks all write
+// back or none does; "go" implies that every block had started while the
+// proposer ran, so all were resident together.  Normally each block finds
+// the count complete at once, and nobody waits.  On "go" block 0 zeroes the
+// other set for the next piece (the launch before, which used it, has ended).
+// The kernels with more than one word per thread call them through the
+// non-inlined forms below: inlined, they cost the 80-register form a spill
+// in its loop (3% at L = 2016 on GB300); the one-word form runs faster with
+// them inlined (3% at L = 1008).
+constexpr unsigned int kClCheckInNs = 100000000u;   // 0.1 s (on the low 32 bits of the global timer)
+constexpr unsigned int kClNoPiece = 0xffffffffu;
+
+__device__ __forceinline__ unsigned int cl_globaltimer_lo()
+{
+    unsigned int t;
+    asm volatile("mov.u32 %0, %%globaltimer_lo;" : "=r"(t));
+    return t;
+}
+
+// Every thread of the block: false if an earlier piece of the call gave up
+// (then the block returns at once); else thread 0 has counted the block in.
+__device__ __forceinline__ bool cl_count_in(unsigned int* gate, unsigned int piece)
+{
+    int live = 0;
+    if (threadIdx.x == 0 && cl_load_acquire(gate + 4) == kClNoPiece) {
+        atomicAdd(gate + 2 * (piece & 1u), 1u);
+        live = 1;
+    }
+    return __syncthreads_or(live) != 0;
+}
+
+// Every thread of the block, at its end: true if the launch writes back.
+__device__ __forceinline__ bool cl_decide(unsigned int* gate, unsigned int blocks, unsigned int piece)
+{
+    int go = 0;
+    if (threadIdx.x == 0) {
+        unsigned int* set = gate + 2 * (piece & 1u);
+        const unsigned int t0 = cl_globaltimer_lo();
+        unsigned int proposal = 1;
+        while (cl_load_acquire(set) < blocks) {
+            if (cl_load_acquire(set + 1) != 0 || cl_globaltimer_lo() - t0 > kClCheckInNs) {
+                proposal = 2;
+                break;
+            }
+            __nanosleep(64);
+        }
+        const unsigned int old = atomicCAS(set + 1, 0u, proposal);
+        go = (old == 0 ? proposal : old) == 1;
+        if (!go) atomicMin(gate + 4, piece);
+        if (go && blockIdx.x == 0) {
+            unsigned int* other = gate + 2 * ((piece + 1u) & 1u);
+            other[0] = 0;
+            other[1] = 0;
+        }
+    }
+    return __syncthreads_or(go) != 0;
+}
+
+__device__ __noinline__ bool cl_count_in_call(unsigned int* gate, unsigned int piece)
+{
+    return cl_count_in(gate, piece);
+}
+
+__device__ __noinline__ bool cl_decide_call(unsigned int* gate, unsigned int blocks, unsigned int piece)
+{
+    return cl_decide(gate, blocks, piece);
+}
+
 // Waits until *f >= want; gives up after kClWaitNs of the GPU's global
 // timer, records the failure in *err and returns false (the caller carries
 // on with stale rows: the launch ends, its result is void, and the host
@@ -79,6 +167,8 @@ __device__ __forceinline__ bool cl_wait_flag(const unsigned long long* f, unsign
 {
     const unsigned long long t0 = cl_globaltimer();
     while (cl_flag_acquire(f) < want) {
+        // another wait of the launch gave up: its rows are void anyway
+        if (*(volatile unsigned int*)err != 0) return false;
         if (cl_globaltimer() - t0 > kClWaitNs) {
             atomicExch(err, 1u);
             return false;

@@ -111,6 +111,9 @@ struct ClusterExchange {
     unsigned long long seq;
     unsigned int* err;
     unsigned long long wait_add;   // added to the flag values a launch waits for (a test hook: nonzero stalls it)
+    unsigned int* gate;            // the launch's agreement words (cl_count_in, cl_decide)
+    unsigned int piece;            // the launch's piece of the call
+    unsigned int absent;           // blocks counted on beyond the launch's (a test hook: 1 gives up)
 };
 bool cluster_plan(const Geom& g, int clusters, ClusterPlan* plan);
 int cluster_max_active();   // clusters of one launch that can be resident at once (0: none)

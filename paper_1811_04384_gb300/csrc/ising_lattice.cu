@@ -81,10 +81,13 @@ struct ising_lattice {
     int clusters = 0;                            // clusters of the cluster path's launches (0: automatic)
     uint64_t* xbuf = nullptr;                    // rows between clusters (lazily, several clusters only)
     size_t xbuf_bytes = 0;
-    unsigned long long* xflag = nullptr;         // their flags (2 per cluster, at most 16 clusters) and the error word
+    unsigned long long* xflag = nullptr;         // kXWords: their flags, the error word and the agreement words
     unsigned long long xseq = 0;                 // flag base of the next launch
-    unsigned int* host_xerr = nullptr;           // pinned copy of the error word
+    unsigned int* host_xerr = nullptr;           // pinned copy of the error and agreement words
     int stall_launches = 0;                      // test hook: launches whose waits between clusters give up
+    int absent_after = -1;                       // test hook: the launch after this many more counts on one
+                                                 // block more than it has (-1: none)
+    bool multi_gave_up = false;                  // a launch's blocks were not all resident: auto keeps to one cluster
 };
 
 static void drop_graphs(ising_lattice* h);
@@ -645,8 +648,16 @@ static int run_resident(ising_lattice* h, int n, int every)
 // 304; L = 1092: 403 / 338; several clusters below (ci_auto_clusters).
 constexpr int kClusterMaxL = 3000;
 constexpr int kCiClusterMaxL = 2604;               // the column-interleaved layout (L % 84 == 0)
-constexpr size_t kClusterMaskBytes = 128u << 20;   // both buffers
+constexpr size_t kClusterMaskBytes = 256u << 20;   // both buffers
 constexpr int kClusterMaxPiece = 256;
+// The words between clusters (xflag, u64 each): 2 flags for each of at most
+// 16 boundaries, the error word of the waits (u32), the agreement words
+// (cl_decide: two sets of {count, verdict} and the first piece given up,
+// u32 each); the host reads the status words [kXErr, kXWords) back.
+constexpr int kXErr = 2 * 16;
+constexpr int kXGate = kXErr + 1;
+constexpr int kXWords = kXGate + 3;
+constexpr int kXStatusWords = kXWords - kXErr;
 
 // Clusters of a launch on the automatic path for side L (0: not the cluster
 // path).  Measured on GB300, sweeps without records, spin-updates/ns by
@@ -666,9 +677,6 @@ static int auto_clusters(int L)
     return 0;
 }
 
-// The cluster-path launch for h: the clusters set by ising_set_clusters, else
-// the automatic count; `forced` (ISING_PATH_CLUSTER) first tries one
-// cluster at any size.
 // The same for the column-interleaved layout, whose per-word draws cost more
 // (19 Philox products per call against 16), so the draws on the SMs the
 // clusters leave free bound it sooner.  Measured on GB300, sweeps without
@@ -697,11 +705,17 @@ static int auto_clusters_of(const ising_lattice* h)
     return h->layout == ISING_LAYOUT_COLUMN_INTERLEAVED ? ci_auto_clusters(h->g.L) : auto_clusters(h->g.L);
 }
 
+// The cluster-path launch for h: the clusters set by ising_set_clusters, else
+// the automatic count, or fewer where the device holds fewer clusters at
+// once; one cluster on the automatic path once a launch found its blocks
+// not all resident together (other work held SMs); `forced`
+// (ISING_PATH_CLUSTER) also takes one cluster at any size it fits.
 static bool plan_cluster(const ising_lattice* h, ClusterPlan* plan, bool forced)
 {
     if (h->clusters > 0) return plan_cluster_g(h, h->clusters, plan);
-    // the rule's count, or fewer where the device holds fewer clusters at once
-    for (int G = auto_clusters_of(h); G >= 1; --G)
+    int G0 = auto_clusters_of(h);
+    if (h->multi_gave_up && h->path == ISING_PATH_AUTO) G0 = std::min(G0, 1);
+    for (int G = G0; G >= 1; --G)
         if (plan_cluster_g(h, G, plan)) return true;
     return forced && plan_cluster_g(h, 1, plan);
 }
@@ -749,7 +763,8 @@ static int run_cluster(ising_lattice* h, int64_t n, int64_t every, unsigned long
         cudaError_t e = draw(0, false);
         if (e != cudaSuccess) return cuda_fail(e, "cluster mask draw");
     }
-    ClusterExchange x = {nullptr, nullptr, 0, nullptr, 0};
+    ClusterExchange x = {nullptr, nullptr, 0, nullptr, 0, nullptr, 0, 0};
+    const uint64_t t_start = h->t;
     if (plan.clusters > 1) {
         const size_t xb = (ci ? ci_cl_exchange_words(g.L, plan) : cl_exchange_words(g, plan)) * sizeof(uint64_t);
         cudaError_t e = cudaSuccess;
@@ -762,21 +777,30 @@ static int run_cluster(ising_lattice* h, int64_t n, int64_t every, unsigned long
             h->xbuf_bytes = xb;
         }
         if (!h->xflag) {
-            e = cudaMalloc(&h->xflag, (2 * 16 + 1) * sizeof(unsigned long long));
-            if (e == cudaSuccess) e = cudaMemsetAsync(h->xflag, 0, (2 * 16 + 1) * sizeof(unsigned long long), h->stream);
-            if (e == cudaSuccess && !h->host_xerr) e = cudaMallocHost(&h->host_xerr, sizeof(unsigned int));
+            e = cudaMalloc(&h->xflag, kXWords * sizeof(unsigned long long));
+            if (e == cudaSuccess) e = cudaMemsetAsync(h->xflag, 0, kXWords * sizeof(unsigned long long), h->stream);
+            if (e == cudaSuccess && !h->host_xerr) e = cudaMallocHost(&h->host_xerr, kXStatusWords * sizeof(unsigned long long));
             if (e != cudaSuccess) { cuda_fail(e, "exchange flags"); return ISING_ENOMEM; }
             h->xseq = 0;
         }
-        x = {h->xbuf, h->xflag, h->xseq, reinterpret_cast<unsigned int*>(h->xflag + 2 * 16), 0};
+        unsigned int* gate = reinterpret_cast<unsigned int*>(h->xflag + kXGate);
+        // both agreement sets undecided, no piece given up
+        e = cudaMemsetAsync(gate, 0, 4 * sizeof(unsigned int), h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(gate + 4, 0xff, sizeof(unsigned int), h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cluster agreement words");
+        x = {h->xbuf, h->xflag, h->xseq, reinterpret_cast<unsigned int*>(h->xflag + kXErr), 0, gate, 0, 0};
     }
     for (int64_t j = 0; j < np; ++j) {
         const int64_t done = j * max_piece;
         x.wait_add = 0;
+        x.piece = (unsigned int)j;
+        x.absent = 0;
         if (plan.clusters > 1 && h->stall_launches > 0) {
             --h->stall_launches;
             x.wait_add = 1ull << 62;                 // no push reaches it: every wait gives up
         }
+        if (plan.clusters > 1 && h->absent_after >= 0 && h->absent_after-- == 0)
+            x.absent = 1;                            // one block more than the launch has: it gives up
         cudaError_t e = ci ? ci_cluster_sweeps(h->words[0], g.L, a, plan, part_of(j), masks[j & 1], done, every, x,
                                                h->stream)
                            : launch_cluster_sweeps(h->words[0], h->words[1], g, a, plan, part_of(j), masks[j & 1],
@@ -797,16 +821,42 @@ static int run_cluster(ising_lattice* h, int64_t n, int64_t every, unsigned long
         h->t += (uint64_t)n;
     }
     if (plan.clusters > 1) {
-        // a wait between clusters that gave up voids the sweeps (the counter
-        // has advanced; the caller restores a checkpoint to retry)
-        cudaError_t e = cudaMemcpyAsync(h->host_xerr, x.err, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream);
+        cudaError_t e = cudaMemcpyAsync(h->host_xerr, h->xflag + kXErr, kXStatusWords * sizeof(unsigned long long),
+                                        cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "cluster exchange status");
-        if (*h->host_xerr != 0) {
-            cudaMemsetAsync(x.err, 0, sizeof(unsigned int), h->stream);
-            *h->host_xerr = 0;
-            return ISING_ETIMEOUT;
+        const unsigned int err = h->host_xerr[0];
+        const unsigned int gave_up = h->host_xerr[2 * (kXGate - kXErr) + 4];
+        if (err != 0) {
+            e = cudaMemsetAsync(x.err, 0, sizeof(unsigned int), h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cluster exchange status");
+            h->host_xerr[0] = 0;
         }
+        if (gave_up != 0xffffffffu) {
+            // the launch of piece gave_up did not have all its blocks resident
+            // together: it wrote no lattice row, nor did the launches after
+            // it.  The pieces before it stand; its records are cleared and the
+            // rest of the call runs on the launch path (the same draws, so the
+            // same results); the automatic path keeps to one cluster from now on.
+            const int64_t done = (int64_t)gave_up * max_piece;
+            h->multi_gave_up = true;
+            int rc = reset_t(h, t_start + (uint64_t)done);
+            if (rc != ISING_OK) return rc;
+            const int64_t rec_base = (int64_t)(counts - h->counts) / (2 * kCountSlots);
+            if (every > 0 && n / every > done / every) {
+                const size_t slot_bytes = 2 * kCountSlots * sizeof(unsigned long long);
+                e = cudaMemsetAsync(counts + (size_t)(done / every) * 2 * kCountSlots, 0,
+                                    (size_t)(n / every - done / every) * slot_bytes, h->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "cluster records");
+            }
+            return run_sweeps(h, n - done, [every, done, rec_base](int64_t s) {
+                return (every > 0 && (done + s) % every == 0) ? (int)(rec_base + (done + s) / every - 1) : -1;
+            });
+        }
+        // a wait between clusters that gave up while all were resident voids
+        // the sweeps (the counter has advanced; the caller restores a
+        // checkpoint to retry)
+        if (err != 0) return ISING_ETIMEOUT;
     }
     return ISING_OK;
 }
@@ -817,6 +867,7 @@ extern "C" int ising_set_clusters(ising_lattice* h, int32_t clusters)
     ClusterPlan cp;
     if (clusters > 0 && !plan_cluster_g(h, clusters, &cp)) return ISING_EINVAL;
     h->clusters = clusters;
+    h->multi_gave_up = false;
     return ISING_OK;
 }
 
@@ -824,6 +875,13 @@ extern "C" int ising_cluster_inject_stall(ising_lattice* h, int32_t launches)
 {
     if (!h || launches < 0) return ISING_EINVAL;
     h->stall_launches = launches;
+    return ISING_OK;
+}
+
+extern "C" int ising_cluster_inject_absent(ising_lattice* h, int32_t after)
+{
+    if (!h || after < -1) return ISING_EINVAL;
+    h->absent_after = after;
     return ISING_OK;
 }
 
@@ -848,6 +906,7 @@ extern "C" int ising_set_path(ising_lattice* h, int32_t path)
     ClusterPlan cp;
     if (path == ISING_PATH_CLUSTER && !plan_cluster(h, &cp, true)) return ISING_EINVAL;
     h->path = path;
+    h->multi_gave_up = false;
     return ISING_OK;
 }
 

@@ -75,6 +75,7 @@ def test_invalid_arguments_are_rejected_before_any_device_call(lib):
     assert lib.ising_set_path(None, p.ISING_PATH_CLUSTER) == p.ISING_EINVAL
     assert lib.ising_set_clusters(None, 2) == p.ISING_EINVAL
     assert lib.ising_cluster_inject_stall(None, 1) == p.ISING_EINVAL
+    assert lib.ising_cluster_inject_absent(None, 0) == p.ISING_EINVAL
     path = ctypes.c_int32(-1)
     assert lib.ising_get_path(None, ctypes.byref(path)) == p.ISING_EINVAL and path.value == -1
     assert lib.ising_philox_blocks(1, None, None, 4) == p.ISING_EINVAL

@@ -45,8 +45,10 @@ def test_cluster_launch_count():
     # L = 512: pitch 14 words, 256-sweep pieces; one chunk of 20 records
     assert bench.cluster_launches(512, 200, 10) == 2 * 1 + 1
     assert bench.cluster_launches(512, 205, 10) == 2 * 1 + 1 + 2 * 1 + 1     # 5 sweeps after the last record
-    # L = 1008: pitch 24 words, 173-sweep pieces (two 64 MB buffers)
-    assert bench.cluster_launches(1008, 1960, 10) == 2 * 12 + 1
+    # L = 1008: pitch 24 words, 256-sweep pieces (346 fit two 128 MB buffers)
+    assert bench.cluster_launches(1008, 1960, 10) == 2 * 8 + 1
+    # L = 2016: pitch 48 words, 86-sweep pieces (two 128 MB buffers)
+    assert bench.cluster_launches(2016, 1960, 10) == 2 * 23 + 1
 
 
 def test_two_pipe_roofline_arithmetic():

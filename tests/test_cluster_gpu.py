@@ -268,6 +268,70 @@ def test_interleaved_multi_cluster_wait_gives_up_and_recovers(ising):
     np.testing.assert_array_equal(S, s)
 
 
+# (L, layout, after, sweeps, every): the launch with several clusters after
+# `after` more of them counts on one block more than it has
+ABSENT_CASES = [
+    (1008, "row", 1, 400, 7),      # piece 0 (256 sweeps) on four clusters, piece 1 (144) on the launch path
+    (1008, "ci", 1, 400, 5),       # the same in the column-interleaved layout
+    (2016, "row", 0, 20, 3),       # the first launch already: the whole call on the launch path
+]
+
+
+def test_launch_without_all_blocks_resident_writes_nothing(ising):
+    """A launch with several clusters whose blocks were not all resident at
+    once (the test hook) writes nothing: the pieces before it stand, the rest
+    of the call runs on the launch path, and every result equals the
+    oracle's.  The automatic choice then keeps to one cluster (none fits
+    L = 2016: the launch path) until ising_set_path."""
+    got, jobs = [], []
+    for L, layout, after, n, every in ABSENT_CASES:
+        lay = ising.ISING_LAYOUT_ROW_PACKED if layout == "row" else ising.ISING_LAYOUT_COLUMN_INTERLEAVED
+        with ising.Lattice(L, L + 3, layout=lay) as lat:
+            lat.init_hot()
+            lat.set_beta(0.43)
+            assert lat.get_path() == ising.ISING_PATH_CLUSTER
+            lat.inject_absent(after)
+            E, M = lat.sweep_record(n, every)
+            path_after = lat.get_path()
+            lat.set_path(ising.ISING_PATH_AUTO)
+            assert lat.get_path() == ising.ISING_PATH_CLUSTER
+            E2, M2 = lat.sweep_record(6, 2)
+            got.append((E, M, E2, M2, lat.get_spins(), path_after))
+        jobs.append((L, L + 3, 0.43, True, n, every))
+    ora = oracle.run_jobs(jobs)
+    for (E, M, E2, M2, S, path_after), (Eo, Mo, So), case in zip(got, ora, ABSENT_CASES):
+        L, layout, after, n, every = case
+        np.testing.assert_array_equal(E, Eo, err_msg=str(case))
+        np.testing.assert_array_equal(M, Mo, err_msg=str(case))
+        s = So.copy()
+        Eo2, Mo2 = oracle.run(s, L + 3, 0.43, n, 6, 2)
+        np.testing.assert_array_equal(E2, Eo2, err_msg=str(case))
+        np.testing.assert_array_equal(M2, Mo2, err_msg=str(case))
+        np.testing.assert_array_equal(S, s, err_msg=str(case))
+        assert path_after == (ising.ISING_PATH_LAUNCHES if L == 2016 else ising.ISING_PATH_CLUSTER), case
+
+
+def test_launch_without_all_blocks_resident_inside_run_states(ising):
+    """The same inside ising_run_states: the second state's first launch
+    gives up, and its sweeps and records on the launch path land in that
+    state's count slots."""
+    L, seed, beta, sweeps, every = 1008, 31, 0.42, 180, 9     # one piece per state
+    rng = np.random.default_rng(8)
+    states = [np.where(rng.random((L, L)) < 0.3 + 0.3 * k, 1, -1).astype(np.int8) for k in range(2)]
+    with ising.Lattice(L, seed) as lat:
+        lat.set_beta(beta)
+        assert lat.get_path() == ising.ISING_PATH_CLUSTER
+        lat.inject_absent(1)                                  # the second state's launch
+        E, M = lat.run_states(states, sweeps, every)
+        S = lat.get_spins()
+    for k, st in enumerate(states):
+        s = st.copy()
+        Eo, Mo = oracle.run(s, seed, beta, k * sweeps, sweeps, every)
+        np.testing.assert_array_equal(E[k], Eo)
+        np.testing.assert_array_equal(M[k], Mo)
+    np.testing.assert_array_equal(S, s)
+
+
 def test_cluster_continued_across_calls_and_paths(ising):
     """Plain sweeps, recorded sweeps, a switch to the graph replays and back:
     the sweep counter carries the draws across the calls and paths."""
