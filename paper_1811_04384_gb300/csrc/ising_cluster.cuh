@@ -111,10 +111,13 @@ __device__ __forceinline__ unsigned int cl_globaltimer_lo()
 
 // Every thread of the block: false if an earlier piece of the call gave up
 // (then the block returns at once); else thread 0 has counted the block in.
+// Only an earlier piece counts: this launch's own give-up can be written
+// while its late clusters start, and the blocks of a cluster must all go on
+// or all return (they write into one another's shared memory).
 __device__ __forceinline__ bool cl_count_in(unsigned int* gate, unsigned int piece)
 {
     int live = 0;
-    if (threadIdx.x == 0 && cl_load_acquire(gate + 4) == kClNoPiece) {
+    if (threadIdx.x == 0 && cl_load_acquire(gate + 4) >= piece) {
         atomicAdd(gate + 2 * (piece & 1u), 1u);
         live = 1;
     }
