@@ -652,7 +652,7 @@ def integer_peaks(ising, clocks_summary: dict) -> dict:
     rates of 32x32->64 multiply-adds, 32-bit multiply-adds and three-input
     XORs measured by ising_probe_int_pipes (the SM's cycle counter, so
     independent of the clock), times the maximum SM clock that nvidia-smi
-    reported during the timed region (clocks.max.sm), else the driver-written
+    reported during the timed region (clocks.max.sm), else the measured
     MEASURED_PEAKS.json's sm_max_mhz, else the nominal 2070 MHz."""
     probe = ising.probe_int_pipes()
     mhz, src = clocks_summary.get("sm_max_mhz"), "nvidia-smi clocks.max.sm during the timed region"
