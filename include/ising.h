@@ -302,22 +302,20 @@ int ising_get_path(ising_lattice *h, int32_t *path);
  * distributed shared memory; between clusters the two boundary blocks pass
  * them through a small device buffer the library allocates on first use
  * (clusters x 8 k pitch 8 bytes, k <= 12) with release/acquire flags.  A
- * flag wait gives up after one second of the GPU's clock (for example when
- * other work keeps a cluster from being resident): the call then returns
- * ISING_ETIMEOUT, the sweeps it ran are void, and the sweep counter has
- * advanced (restore a checkpoint with ising_set_words, or ising_set_spins
- * in the column-interleaved layout, and ising_set_sweep to retry).  A
- * number of clusters the device cannot hold at once, or for which the
- * lattice has no window plan, gives EINVAL.  A launch with several
- * clusters writes its lattice rows back only if all its blocks were
+ * flag wait gives up after one second of the GPU's clock.  A launch with
+ * several clusters writes its lattice rows back only if all its blocks were
  * resident together, which all its blocks agree on at their end.  If they
- * were not (other work on the device held SMs; its waits then give up), the
+ * were not (other work on the device held SMs, so waits gave up), the
  * launch writes nothing, the rest of the call runs on the launch path with
  * the same results, and the automatic choice keeps to one cluster until the
- * next ising_set_path or ising_set_clusters.  ISING_ETIMEOUT is left for a
- * wait that gave up while all blocks were resident.  Column-interleaved lattices
- * split their word columns the same way (k halo columns of all word rows
- * between clusters).  Results do not depend on it. */
+ * next ising_set_path or ising_set_clusters.  If a wait gave up while all
+ * blocks were resident, the call returns ISING_ETIMEOUT, the sweeps it ran
+ * are void, and the sweep counter has advanced (restore a checkpoint with
+ * ising_set_words, or ising_set_spins in the column-interleaved layout, and
+ * ising_set_sweep to retry).  A number of clusters the device cannot hold at
+ * once, or for which the lattice has no window plan, gives EINVAL.
+ * Column-interleaved lattices split their word columns the same way (k halo
+ * columns of all word rows between clusters).  Results do not depend on it. */
 int ising_set_clusters(ising_lattice *h, int32_t clusters);
 
 /* Test hook of that wait: the next `launches` cluster-path launches with
